@@ -1,0 +1,275 @@
+/*
+ * robast.h -- C ABI of the GB300 (sm_103a) non-sequential photon tracer.
+ *
+ * Method: Okumura, Noda, Rulten, "ROBAST: Development of a Non-Sequential
+ * Ray-Tracing Simulation Library and its Applications in the Cherenkov
+ * Telescope Array", ICRC 2015 (arXiv:1508.07803).
+ *   Sec. 1, 2.1  non-sequential tracing: at every step the photon goes to the
+ *                NEAREST intersection over all surfaces; the surface's role
+ *                decides the interaction (mirror: reflect; lens: refract;
+ *                focal surface: detect; obscuration: absorb); repeat until
+ *                the photon terminates.
+ *   Sec. 2.2     shapes: primitive shapes, the aspheric disk, the polygonal
+ *                Winston cone and the Bezier-profile polygonal cone.
+ *   Sec. 3       workloads: segmented dishes with masts and camera boxes,
+ *                Schwarzschild-Couder aspheric two-mirror optics, hexagonal
+ *                light concentrators; results are spot diagrams (PSF) and
+ *                collection efficiency.
+ *
+ * Conventions for every call:
+ *   - return 0 on success, a negative ROBAST_E* code on failure; the message
+ *     of the last failure on this host thread is robast_last_error().  The
+ *     library never aborts, traps or exits.  Problems of single photons
+ *     (Newton non-convergence, non-finite directions, traversal stack
+ *     overflow) are reported as ROBAST_ST_ERROR in that photon's status, not
+ *     as a return code.
+ *   - lengths in metres (any consistent unit works), wavelengths in nm,
+ *     angles in radians.
+ *   - "device pointer": memory the CUDA runtime can address from the GPU
+ *     (cudaMalloc / torch CUDA tensors); "host pointer": ordinary memory.
+ *   - vectors of n photons are SoA in ONE buffer of 3n elements: all x, then
+ *     all y, then all z.  Element type is float for precision 32 and double
+ *     for precision 64.
+ *   - all GPU work is asynchronous on the caller's stream unless stated.
+ */
+#ifndef ROBAST_H
+#define ROBAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define ROBAST_OK 0
+#define ROBAST_E_INVALID (-1)   /* bad descriptor or argument */
+#define ROBAST_E_NULL (-2)      /* required pointer is NULL */
+#define ROBAST_E_CUDA (-3)      /* CUDA runtime error */
+#define ROBAST_E_OOM (-4)       /* device or host allocation failed */
+#define ROBAST_E_UNSUPPORTED (-5)
+
+/* surface shapes (Sec. 2.2) */
+#define ROBAST_SHAPE_SAG 0      /* even asphere: conic + A1 r^2 .. A8 r^16 (plane, sphere, paraboloid included) */
+#define ROBAST_SHAPE_CYLINDER 1 /* open finite cylinder, local z axis, 0 <= z <= length */
+#define ROBAST_SHAPE_BOX 2      /* box centred at the local origin */
+#define ROBAST_SHAPE_HEXCONE 3  /* hexagonal cone, quadratic-Bezier wall profile (Winston / Okumura cone) */
+
+/* surface roles (Sec. 2.1: AMirror, ALens, AFocalSurface, AObscuration) */
+#define ROBAST_ROLE_MIRROR 0
+#define ROBAST_ROLE_REFRACT 1
+#define ROBAST_ROLE_FOCAL 2
+#define ROBAST_ROLE_OBSCURATION 3
+
+/* apertures of a SAG surface, on the local (x, y) of the hit; edges inclusive */
+#define ROBAST_AP_NONE 0    /* unbounded */
+#define ROBAST_AP_CIRCLE 1  /* ap[0] = r_max */
+#define ROBAST_AP_ANNULUS 2 /* ap[0] = r_min, ap[1] = r_max */
+#define ROBAST_AP_SECTOR 3  /* ap[0..1] = r_min, r_max; ap[2..3] = phi0 < phi1, phi1 - phi0 <= pi */
+#define ROBAST_AP_HEXAGON 4 /* ap[0] = apothem; flats face 0, 60, 120 deg of local x */
+#define ROBAST_AP_RECT 5    /* ap[0] = half width in x, ap[1] = half width in y */
+
+/* photon end states */
+#define ROBAST_ST_DETECTED 1    /* front side of a focal surface */
+#define ROBAST_ST_ABSORBED 2    /* lost to a mirror's reflectivity draw */
+#define ROBAST_ST_OBSCURED 3    /* obscuration, or the back of a mirror / focal surface */
+#define ROBAST_ST_ESCAPED 4     /* no further intersection */
+#define ROBAST_ST_MAX_BOUNCES 5 /* still alive after max_bounces interactions */
+#define ROBAST_ST_ERROR 6       /* Newton failure, non-finite state, stack overflow */
+
+/* counters accumulated by robast_trace* (device uint64 array, never cleared by the library) */
+#define ROBAST_CNT_BOUNCES 0  /* sum of bounce counts */
+#define ROBAST_CNT_PHOTONS 7  /* photons finished; [1..6] = photons per status */
+#define ROBAST_N_COUNTERS 8
+
+/* ------------------------------------------------------------- geometry */
+/*
+ * One surface in its own local frame.  A world point p has local coordinates
+ * R' (p - origin), where R' = Ry(tilt[1])^T Rx(tilt[0])^T R and R = rot
+ * (row-major, row k = local axis k in world coordinates, orthonormal).  The
+ * tilt is a rotation of the surface about its local x axis, then its local y
+ * axis, through the local origin (facet alignment errors, Sec. 3).
+ *
+ * SAG: z = c rho / (1 + sqrt(1 - (1+k) c^2 rho)) + sum_i asph[i-1] rho^i,
+ *      rho = x^2 + y^2, i = 1..8.  Front side = the side the local +z axis
+ *      points to.  With any asph != 0 the intersection is found by Newton from
+ *      the first on-branch root of the conic (only within 1.1x the aperture's
+ *      bounding radius).
+ * CYLINDER: prm[0] = radius, prm[1] = length.
+ * BOX: prm[0..2] = half extents.
+ * HEXCONE: prm[0..5] = (r, z) of the Bezier control points P0, P1, P2; wall j
+ *      (j = 0..5) faces direction (cos j pi/3, sin j pi/3); front side = the
+ *      side facing the cone axis.
+ */
+typedef struct robast_surface_desc {
+    int32_t shape, role, aperture;
+    int32_t material;                   /* MIRROR: index into materials */
+    int32_t medium_front, medium_back;  /* REFRACT: media on the front / back side */
+    int32_t reserved;
+    double origin[3];
+    double rot[9];
+    double tilt[2];
+    double curv, conic;
+    double asph[8];
+    double ap[4];
+    double prm[8];
+} robast_surface_desc;
+
+#define ROBAST_MAX_TABLE 16
+/* Mirror coating: reflectivity R(lambda) piecewise linear in (lam, refl),
+ * clamped outside; roughness = Gaussian tilt of the normal, sigma per tangent
+ * axis (rad). */
+typedef struct robast_material_desc {
+    int32_t n, reserved;
+    double lam[ROBAST_MAX_TABLE];
+    double refl[ROBAST_MAX_TABLE];
+    double sigma;
+} robast_material_desc;
+
+/* Refractive medium: n_const > 0 gives a constant index, otherwise the
+ * Sellmeier form n^2 = 1 + sum B_i l^2 / (l^2 - C_i), l in micrometres. */
+typedef struct robast_medium_desc {
+    double n_const;
+    double B[3], C[3];
+} robast_medium_desc;
+
+/*
+ * The optical system(s).  variant_offsets (n_variants + 1 entries, NULL for a
+ * single variant) splits the surface array into independent systems traced
+ * side by side (batching); a photon sees only its variant's surfaces.
+ * length_scale (L_sys, > 0) sets the default self-intersection epsilon.
+ */
+typedef struct robast_geom_desc {
+    int32_t n_surfaces, n_materials, n_media, n_variants;
+    const robast_surface_desc* surfaces;
+    const robast_material_desc* materials;
+    const robast_medium_desc* media;
+    const int32_t* variant_offsets;
+    double length_scale;
+} robast_geom_desc;
+
+typedef struct robast_geom robast_geom; /* opaque */
+
+/*
+ * Compile a host descriptor into device tables (per-surface frames and shape
+ * records in FP32 and FP64, a BVH over surface bounding boxes per variant)
+ * and upload them to the current CUDA device.  The descriptor and all arrays
+ * it points to are host memory owned by the caller and are deep-copied; the
+ * caller may free them on return.  *out receives a handle owned by the
+ * caller, released with robast_free_geometry.  Synchronous.
+ * Errors: ROBAST_E_NULL, ROBAST_E_INVALID (message names the surface and
+ * field), ROBAST_E_OOM, ROBAST_E_CUDA.
+ */
+int robast_build_geometry(const robast_geom_desc* desc, robast_geom** out);
+
+/* Free a geometry (NULL is ignored).  Synchronises the device first. */
+void robast_free_geometry(robast_geom* g);
+
+/* Geometry facts: number of surfaces, variants, BVH nodes. */
+int robast_geometry_info(const robast_geom* g, int32_t* n_surfaces, int32_t* n_variants, int32_t* n_bvh_nodes);
+
+/* ---------------------------------------------------------------- trace */
+/*
+ * Output arrays (device pointers, caller-owned, n photons).  Any pointer may
+ * be NULL, in which case that field is not written.
+ *   status [n] u8, bounces [n] u8 (interactions incl. the terminating one),
+ *   hit [3n] final position (the detecting / absorbing point, or the last
+ *        interaction point, or the origin if there was none),
+ *   dir [3n] final direction, last_surface [n] i32 (-1: none),
+ *   focal_xy [2n] local (x, y) on the focal surface (DETECTED only, else 0),
+ *   counters [ROBAST_N_COUNTERS] u64, atomically accumulated.
+ */
+typedef struct robast_trace_out {
+    uint8_t* status;
+    uint8_t* bounces;
+    void* hit;
+    void* dir;
+    int32_t* last_surface;
+    void* focal_xy;
+    unsigned long long* counters;
+} robast_trace_out;
+
+typedef struct robast_trace_opts {
+    int32_t precision;        /* 32 (default) or 64 */
+    int32_t max_bounces;      /* 1..255; 0 = 100 */
+    void* stream;             /* cudaStream_t; NULL = legacy default stream */
+    const int32_t* variant_of_photon; /* device [n] or NULL (all variant 0) */
+    int64_t first_photon_id;  /* photon i uses random stream id first_photon_id + i */
+    double eps;               /* self-intersection epsilon; 0 = 1e-6 L_sys (FP32) / 1e-9 L_sys (FP64) */
+    int32_t block_size;       /* 64, 128 or 256; 0 = library choice (128) */
+    int32_t blocks_per_sm;    /* 0 = as many as fit */
+    unsigned long long* work_units; /* device [ROBAST_N_UNITS] or NULL; non-NULL runs the
+                                       counting build of the kernel (block 128, slower) and
+                                       adds the work units below to it */
+} robast_trace_opts;
+
+/* Work units counted when opts.work_units is set: ray-box tests, quadric root
+ * solves, aspheric Newton iterations, aperture tests, cylinder tests, box
+ * tests, Bezier wall tests, reflections, Fresnel/Snell evaluations, roughness
+ * perturbations, Philox calls, frame transforms. */
+#define ROBAST_N_UNITS 12
+
+/* Fill opts with the defaults. */
+void robast_trace_opts_default(robast_trace_opts* opts);
+
+/*
+ * Trace n photons through g (Sec. 2.1 loop): origins [3n], dirs [3n] (unit
+ * length), wavelengths [n] nm, all device pointers of the precision's element
+ * type.  Random draws come from Philox4x32-10 with key (seed_lo, seed_hi) and
+ * counter (id_lo, id_hi, bounce index, 0), id = first_photon_id + i, so the
+ * result of every photon is independent of launch shape and scheduling.
+ * robast_trace uses the default options (FP32, 100 bounces, default stream).
+ * n = 0 is a no-op.  Errors: ROBAST_E_NULL (g, inputs, out), ROBAST_E_INVALID
+ * (precision, max_bounces, n < 0, a variant table without variants),
+ * ROBAST_E_CUDA (launch failure).
+ */
+int robast_trace(const robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
+                 uint64_t seed, const robast_trace_out* out);
+int robast_trace_ex(const robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
+                    int64_t n, uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts);
+
+/*
+ * The same trace with HOST inputs and outputs: the library copies the inputs
+ * to a device staging area owned by g (grown on demand), traces, copies the
+ * outputs back and synchronises the stream before returning.  Output
+ * pointers in `out` are host pointers here (counters too, added to).
+ */
+int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
+                      uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts);
+
+/* ----------------------------------------------------------- reductions */
+/*
+ * Spot diagram statistics of DETECTED photons (Fig. 1 g-i): centroid of
+ * focal_xy and R80 = the nearest-rank 80th percentile (sorted index
+ * ceil(0.8 N) - 1) of the radial distance to the centroid.  status [n] and
+ * focal_xy are device pointers (precision 32: float, 64: double); the local
+ * x of photon i is focal_xy[i] and its y is focal_xy[ld + i] (ld >= n; ld = 0
+ * means n), so a window of a larger trace output is reduced in place.
+ * result is a HOST array of 4 doubles {N_detected, cx, cy, R80} (NaN when
+ * nothing is detected).  Synchronises the stream.  Uses device scratch owned
+ * by g.
+ */
+int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t n, int64_t ld,
+               int32_t precision, void* stream, double* result);
+
+/* ----------------------------------------------------------- measurement */
+/*
+ * Measurement helper, not part of the method: FP32 (precision 32) or FP64
+ * (64) fused-multiply-add throughput of the current device in FLOP/s (one FMA
+ * = 2 FLOP), from independent FMA chains on every SM, timed with CUDA events
+ * on `stream` (best of 5 after a warm-up).  Synchronous.  This is the
+ * denominator of the ALU roofline the benchmark reports.
+ */
+int robast_measure_alu_peak(int32_t precision, void* stream, double* flops_per_s);
+
+/* Last error message of this host thread ("" if none). */
+const char* robast_last_error(void);
+
+/* Library version string. */
+const char* robast_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROBAST_H */

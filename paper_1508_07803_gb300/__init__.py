@@ -1,0 +1,339 @@
+"""Python binding of the GB300 non-sequential photon tracer (include/robast.h).
+
+Argument marshalling only: every step of the trace runs in the CUDA library
+(`_build/librobast.so`, built from csrc/ for sm_103a).  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library cannot
+be loaded, every call raises.
+
+Typical use:
+
+    import paper_1508_07803_gb300 as robast
+    geom = robast.build_geometry(scene)          # scene: surfaces/materials/media records
+    out = robast.trace(geom, origins, dirs, wavelengths, seed=0, precision=32)
+
+`origins` and `dirs` are CUDA tensors of shape [3, n] (x row, y row, z row),
+`wavelengths` [n] in nm; float32 for precision 32, float64 for precision 64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["build_geometry", "trace", "trace_host", "psf", "Geometry", "load", "STATUS", "RobastError"]
+
+STATUS = {1: "DETECTED", 2: "ABSORBED", 3: "OBSCURED", 4: "ESCAPED", 5: "MAX_BOUNCES", 6: "ERROR"}
+N_COUNTERS = 8
+
+_SHAPES = {"sag": 0, "cylinder": 1, "box": 2, "hexcone": 3}
+_ROLES = {"mirror": 0, "refract": 1, "focal": 2, "obscuration": 3}
+_APS = {"none": 0, "circle": 1, "annulus": 2, "sector": 3, "hexagon": 4, "rect": 5}
+
+
+class RobastError(RuntimeError):
+    pass
+
+
+class SurfaceDesc(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("role", ctypes.c_int32), ("aperture", ctypes.c_int32),
+                ("material", ctypes.c_int32), ("medium_front", ctypes.c_int32), ("medium_back", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("origin", ctypes.c_double * 3), ("rot", ctypes.c_double * 9),
+                ("tilt", ctypes.c_double * 2), ("curv", ctypes.c_double), ("conic", ctypes.c_double),
+                ("asph", ctypes.c_double * 8), ("ap", ctypes.c_double * 4), ("prm", ctypes.c_double * 8)]
+
+
+class MaterialDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("reserved", ctypes.c_int32), ("lam", ctypes.c_double * 16),
+                ("refl", ctypes.c_double * 16), ("sigma", ctypes.c_double)]
+
+
+class MediumDesc(ctypes.Structure):
+    _fields_ = [("n_const", ctypes.c_double), ("B", ctypes.c_double * 3), ("C", ctypes.c_double * 3)]
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("n_surfaces", ctypes.c_int32), ("n_materials", ctypes.c_int32), ("n_media", ctypes.c_int32),
+                ("n_variants", ctypes.c_int32), ("surfaces", ctypes.POINTER(SurfaceDesc)),
+                ("materials", ctypes.POINTER(MaterialDesc)), ("media", ctypes.POINTER(MediumDesc)),
+                ("variant_offsets", ctypes.POINTER(ctypes.c_int32)), ("length_scale", ctypes.c_double)]
+
+
+class TraceOut(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_void_p), ("bounces", ctypes.c_void_p), ("hit", ctypes.c_void_p),
+                ("dir", ctypes.c_void_p), ("last_surface", ctypes.c_void_p), ("focal_xy", ctypes.c_void_p),
+                ("counters", ctypes.c_void_p)]
+
+
+class TraceOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_bounces", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("variant_of_photon", ctypes.c_void_p), ("first_photon_id", ctypes.c_int64),
+                ("eps", ctypes.c_double), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("work_units", ctypes.c_void_p)]
+
+N_UNITS = 12
+UNIT_NAMES = ("aabb", "sag", "newton", "aperture", "cylinder", "box", "hexwall", "reflect", "refract", "rough",
+              "philox", "rebase")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = True):
+    """Load librobast.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RobastError(f"CUDA library not built: {path} is missing (run paper_1508_07803_gb300.build.build())")
+        lib = ctypes.CDLL(path)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.robast_build_geometry.argtypes = [ctypes.POINTER(GeomDesc), ctypes.POINTER(vp)]
+        lib.robast_build_geometry.restype = ctypes.c_int
+        lib.robast_free_geometry.argtypes = [vp]
+        lib.robast_free_geometry.restype = None
+        lib.robast_geometry_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.robast_trace.argtypes = [vp, vp, vp, vp, i64, ctypes.c_uint64, ctypes.POINTER(TraceOut)]
+        lib.robast_trace_ex.argtypes = [vp, vp, vp, vp, i64, ctypes.c_uint64, ctypes.POINTER(TraceOut),
+                                        ctypes.POINTER(TraceOpts)]
+        lib.robast_trace_host.argtypes = [vp, vp, vp, vp, i64, ctypes.c_uint64, ctypes.POINTER(TraceOut),
+                                          ctypes.POINTER(TraceOpts)]
+        lib.robast_trace_opts_default.argtypes = [ctypes.POINTER(TraceOpts)]
+        lib.robast_trace_opts_default.restype = None
+        lib.robast_psf.argtypes = [vp, vp, vp, i64, i64, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.robast_last_error.restype = ctypes.c_char_p
+        lib.robast_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = _lib.robast_last_error().decode()
+        raise RobastError(f"robast error {rc}: {msg}")
+
+
+def _fill(arr, vals, n):
+    vals = list(vals) + [0.0] * (n - len(vals))
+    for i in range(n):
+        arr[i] = float(vals[i])
+
+
+def _pack(scene):
+    surfs = (SurfaceDesc * len(scene.surfaces))()
+    for k, s in enumerate(scene.surfaces):
+        d = surfs[k]
+        d.shape, d.role, d.aperture = _SHAPES[s.shape], _ROLES[s.role], _APS[s.aperture]
+        d.material, d.medium_front, d.medium_back = int(s.material), int(s.medium_front), int(s.medium_back)
+        _fill(d.origin, s.origin, 3)
+        _fill(d.rot, s.rot, 9)
+        _fill(d.tilt, s.tilt, 2)
+        d.curv, d.conic = float(s.curv), float(s.conic)
+        _fill(d.asph, s.asph, 8)
+        _fill(d.ap, s.ap, 4)
+        _fill(d.prm, s.prm, 8)
+    mats = (MaterialDesc * max(1, len(scene.materials)))()
+    for k, m in enumerate(scene.materials):
+        mats[k].n = len(m.lam)
+        _fill(mats[k].lam, m.lam, 16)
+        _fill(mats[k].refl, m.refl, 16)
+        mats[k].sigma = float(m.sigma)
+    meds = (MediumDesc * max(1, len(scene.media)))()
+    for k, m in enumerate(scene.media):
+        meds[k].n_const = float(m.n_const)
+        _fill(meds[k].B, m.B, 3)
+        _fill(meds[k].C, m.C, 3)
+    desc = GeomDesc()
+    desc.n_surfaces = len(scene.surfaces)
+    desc.n_materials = len(scene.materials)
+    desc.n_media = len(scene.media)
+    desc.surfaces = surfs
+    desc.materials = mats
+    desc.media = meds
+    offs = None
+    if getattr(scene, "variant_offsets", None) is not None:
+        offs = (ctypes.c_int32 * len(scene.variant_offsets))(*scene.variant_offsets)
+        desc.n_variants = len(scene.variant_offsets) - 1
+        desc.variant_offsets = offs
+    else:
+        desc.n_variants = 1
+    desc.length_scale = float(scene.length_scale)
+    return desc, (surfs, mats, meds, offs)
+
+
+class Geometry:
+    """Device-resident optical system(s); frees its device tables on close/GC."""
+
+    def __init__(self, handle, scene):
+        self._h = ctypes.c_void_p(handle)
+        self.length_scale = float(scene.length_scale)
+        self.n_surfaces = len(scene.surfaces)
+        ns, nv, nn = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.robast_geometry_info(self._h, ctypes.byref(ns), ctypes.byref(nv), ctypes.byref(nn)))
+        self.n_variants, self.n_bvh_nodes = nv.value, nn.value
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RobastError("geometry already freed")
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value and _lib is not None:
+            _lib.robast_free_geometry(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_geometry(scene) -> Geometry:
+    """robast_build_geometry: compile `scene` (surface/material/medium records) onto the current CUDA device."""
+    lib = load()
+    desc, keep = _pack(scene)
+    h = ctypes.c_void_p()
+    _check(lib.robast_build_geometry(ctypes.byref(desc), ctypes.byref(h)))
+    del keep
+    return Geometry(h.value, scene)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_size, blocks_per_sm, units=None):
+    o = TraceOpts()
+    _lib.robast_trace_opts_default(ctypes.byref(o))
+    o.precision = int(precision)
+    o.max_bounces = int(max_bounces)
+    o.stream = stream
+    o.variant_of_photon = vop_ptr
+    o.first_photon_id = int(first_photon_id)
+    o.eps = float(eps or 0.0)
+    o.block_size = int(block_size)
+    o.blocks_per_sm = int(blocks_per_sm)
+    o.work_units = ctypes.c_void_p(units.data_ptr()) if units is not None else None
+    return o
+
+
+def alloc_outputs(n: int, precision: int = 32, device="cuda", fields=None):
+    """Output tensors for robast_trace (all fields unless `fields` restricts them)."""
+    import torch
+    dt = torch.float32 if precision == 32 else torch.float64
+    all_fields = {
+        "status": lambda: torch.empty(n, dtype=torch.uint8, device=device),
+        "bounces": lambda: torch.empty(n, dtype=torch.uint8, device=device),
+        "hit": lambda: torch.empty((3, n), dtype=dt, device=device),
+        "dir": lambda: torch.empty((3, n), dtype=dt, device=device),
+        "last_surface": lambda: torch.empty(n, dtype=torch.int32, device=device),
+        "focal_xy": lambda: torch.empty((2, n), dtype=dt, device=device),
+        "counters": lambda: torch.zeros(N_COUNTERS, dtype=torch.int64, device=device),
+    }
+    keys = fields if fields is not None else list(all_fields)
+    return {k: all_fields[k]() for k in keys}
+
+
+def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32, max_bounces: int = 100,
+          stream=None, variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None,
+          block_size: int = 0, blocks_per_sm: int = 0, out: Optional[dict] = None, work_units=None):
+    """robast_trace_ex on CUDA tensors; returns the dict of output tensors.
+
+    work_units: optional CUDA int64 tensor [N_UNITS]; when given, the counting
+    build of the kernel runs and adds its work units (UNIT_NAMES) to it.
+    """
+    import torch
+    lib = load()
+    dt = torch.float32 if precision == 32 else torch.float64
+    n = int(wavelengths.shape[0])
+    for name, t, shape in (("origins", origins, (3, n)), ("dirs", dirs, (3, n)), ("wavelengths", wavelengths, (n,))):
+        if t.dtype != dt or tuple(t.shape) != shape or not t.is_cuda or not t.is_contiguous():
+            raise RobastError(f"{name}: need a contiguous CUDA {dt} tensor of shape {shape}")
+    if out is None:
+        out = alloc_outputs(n, precision, origins.device)
+    tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
+                      for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
+    if stream is None:
+        stream = torch.cuda.current_stream(origins.device)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    vop = None
+    if variant_of_photon is not None:
+        if variant_of_photon.dtype != torch.int32 or not variant_of_photon.is_cuda:
+            raise RobastError("variant_of_photon: need a CUDA int32 tensor")
+        vop = ctypes.c_void_p(variant_of_photon.data_ptr())
+    o = _opts(precision, max_bounces, sp, vop, first_photon_id, eps, block_size, blocks_per_sm, work_units)
+    _check(lib.robast_trace_ex(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,
+                               ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(tout), ctypes.byref(o)))
+    return out
+
+
+def trace_host(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32,
+               max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
+               eps: Optional[float] = None, variant_of_photon=None):
+    """robast_trace_host: host (CPU, ideally pinned) tensors in and out; synchronous."""
+    import torch
+    lib = load()
+    dt = torch.float32 if precision == 32 else torch.float64
+    n = int(wavelengths.shape[0])
+    for name, t in (("origins", origins), ("dirs", dirs), ("wavelengths", wavelengths)):
+        if t.dtype != dt or t.is_cuda or not t.is_contiguous():
+            raise RobastError(f"{name}: need a contiguous host {dt} tensor")
+    if out is None:
+        out = alloc_outputs(n, precision, "cpu")
+    tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
+                      for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    vop = ctypes.c_void_p(variant_of_photon.data_ptr()) if variant_of_photon is not None else None
+    o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), vop, first_photon_id, eps, 0, 0)
+    _check(lib.robast_trace_host(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,
+                                 ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(tout), ctypes.byref(o)))
+    return out
+
+
+def psf(geom: Geometry, status, focal_xy, precision: int = 32, stream=None, start: int = 0, count=None):
+    """robast_psf: (N_detected, cx, cy, R80) of the DETECTED photons' focal-plane points.
+
+    status [N] and focal_xy [2, N] are trace outputs; photons start .. start+count-1 are reduced.
+    """
+    import torch
+    lib = load()
+    N = int(status.shape[0])
+    count = N - start if count is None else int(count)
+    if not (0 <= start and start + count <= N and focal_xy.shape == (2, N) and focal_xy.is_contiguous()):
+        raise RobastError("psf: need status [N], contiguous focal_xy [2, N] and a window inside N")
+    if stream is None:
+        stream = torch.cuda.current_stream(status.device)
+    res = (ctypes.c_double * 4)()
+    es = focal_xy.element_size()
+    _check(lib.robast_psf(geom.handle, ctypes.c_void_p(status.data_ptr() + start),
+                          ctypes.c_void_p(focal_xy.data_ptr() + start * es), count, N, int(precision),
+                          ctypes.c_void_p(stream.cuda_stream), res))
+    return tuple(res)
+
+
+def version() -> str:
+    return load().robast_version().decode()
+
+
+def measure_alu_peak(precision: int = 32, stream=None) -> float:
+    """robast_measure_alu_peak: FMA throughput of the current GPU in FLOP/s (roofline denominator)."""
+    import torch
+    lib = load()
+    lib.robast_measure_alu_peak.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    v = ctypes.c_double()
+    _check(lib.robast_measure_alu_peak(int(precision), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(v)))
+    return v.value

@@ -1,0 +1,1023 @@
+// Host side of the C ABI (include/robast.h): descriptor validation, the
+// geometry compiler (tilted local frames, FP32/FP64 surface records,
+// conservative bounding boxes, one BVH per variant), trace launches, the
+// spot-diagram reduction and error reporting.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/robast.h"
+#include "launch.h"
+
+using namespace robast;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    return fail(ROBAST_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+extern "C" const char* robast_last_error(void) { return g_err.c_str(); }
+extern "C" const char* robast_version(void) { return "robast-gb300 0.1 (sm_103a)"; }
+
+// --------------------------------------------------------------- geometry
+struct robast_geom {
+    int device = 0;
+    int n_surf = 0, n_var = 0, n_mat = 0, n_med = 0;
+    int n_nodes = 0, n_prims = 0, n_glob = 0;
+    double length_scale = 1.0;
+    void* dmem = nullptr;  // one allocation holding every table
+    Tables tab32{}, tab64{};
+    size_t smem32 = 0, smem64 = 0;  // bytes to stage each precision's tables
+    int num_sms = 0;
+    // per-launch work counters (a ring, so launches on several streams do not share one)
+    unsigned long long* work = nullptr;
+    std::atomic<unsigned> work_slot{0};
+    // staging for robast_trace_host and scratch for reductions
+    std::mutex mu;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+static const int kWorkSlots = 256;
+
+namespace {
+
+struct Box {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    void add(const double p[3]) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], p[k]);
+            hi[k] = std::max(hi[k], p[k]);
+        }
+    }
+    void add(const Box& b) {
+        add(b.lo);
+        add(b.hi);
+    }
+    double centre(int k) const { return 0.5 * (lo[k] + hi[k]); }
+};
+
+void mat3_mul(const double a[9], const double b[9], double c[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+
+// Rows of the tilted frame: Ry(b)^T Rx(a)^T R (rotation about local x by a,
+// then about the new local y by b).
+void tilted_rows(const robast_surface_desc& s, double out[9]) {
+    const double ca = std::cos(s.tilt[0]), sa = std::sin(s.tilt[0]);
+    const double cb = std::cos(s.tilt[1]), sb = std::sin(s.tilt[1]);
+    const double rxT[9] = {1, 0, 0, 0, ca, sa, 0, -sa, ca};
+    const double ryT[9] = {cb, 0, -sb, 0, 1, 0, sb, 0, cb};
+    double tmp[9];
+    mat3_mul(rxT, s.rot, tmp);
+    mat3_mul(ryT, tmp, out);
+}
+
+double aperture_bound(const robast_surface_desc& s) {
+    switch (s.aperture) {
+        case ROBAST_AP_CIRCLE: return s.ap[0];
+        case ROBAST_AP_ANNULUS:
+        case ROBAST_AP_SECTOR: return s.ap[1];
+        case ROBAST_AP_HEXAGON: return s.ap[0] * 2.0 / std::sqrt(3.0);
+        case ROBAST_AP_RECT: return std::sqrt(s.ap[0] * s.ap[0] + s.ap[1] * s.ap[1]);
+    }
+    return INFINITY;
+}
+
+bool any_asph(const robast_surface_desc& s) {
+    for (int i = 0; i < 8; ++i)
+        if (s.asph[i] != 0.0) return true;
+    return false;
+}
+
+double sag_eval(const robast_surface_desc& s, double rho, bool* ok) {
+    const double arg = 1.0 - (1.0 + s.conic) * s.curv * s.curv * rho;
+    if (arg < 0.0) {
+        *ok = false;
+        return 0.0;
+    }
+    double z = s.curv * rho / (1.0 + std::sqrt(arg)), rp = rho;
+    for (int i = 0; i < 8; ++i) {
+        z += s.asph[i] * rp;
+        rp *= rho;
+    }
+    *ok = true;
+    return z;
+}
+
+// local (x, y) bounding rectangle of a SAG aperture
+void aperture_rect(const robast_surface_desc& s, double* x0, double* x1, double* y0, double* y1) {
+    switch (s.aperture) {
+        case ROBAST_AP_CIRCLE:
+        case ROBAST_AP_ANNULUS: {
+            const double r = aperture_bound(s);
+            *x0 = *y0 = -r;
+            *x1 = *y1 = r;
+            return;
+        }
+        case ROBAST_AP_SECTOR: {
+            // corners plus the axis extremes the arc passes through
+            const double r0 = s.ap[0], r1 = s.ap[1], p0 = s.ap[2], p1 = s.ap[3];
+            double xs[8], ys[8];
+            int n = 0;
+            for (double r : {r0, r1})
+                for (double p : {p0, p1}) {
+                    xs[n] = r * std::cos(p);
+                    ys[n] = r * std::sin(p);
+                    ++n;
+                }
+            *x0 = *x1 = xs[0];
+            *y0 = *y1 = ys[0];
+            for (int k = 1; k < n; ++k) {
+                *x0 = std::min(*x0, xs[k]);
+                *x1 = std::max(*x1, xs[k]);
+                *y0 = std::min(*y0, ys[k]);
+                *y1 = std::max(*y1, ys[k]);
+            }
+            for (int q = -4; q <= 8; ++q) {
+                const double a = q * M_PI / 2.0;
+                if (a >= p0 && a <= p1) {
+                    *x0 = std::min(*x0, r1 * std::cos(a));
+                    *x1 = std::max(*x1, r1 * std::cos(a));
+                    *y0 = std::min(*y0, r1 * std::sin(a));
+                    *y1 = std::max(*y1, r1 * std::sin(a));
+                }
+            }
+            return;
+        }
+        case ROBAST_AP_HEXAGON:
+            *x0 = -s.ap[0];
+            *x1 = s.ap[0];
+            *y0 = -s.ap[0] * 2.0 / std::sqrt(3.0);
+            *y1 = -*y0;
+            return;
+        case ROBAST_AP_RECT:
+            *x0 = -s.ap[0];
+            *x1 = s.ap[0];
+            *y0 = -s.ap[1];
+            *y1 = s.ap[1];
+            return;
+    }
+    *x0 = *y0 = -INFINITY;
+    *x1 = *y1 = INFINITY;
+}
+
+// Local bounding box of a surface; false if unbounded (tested every bounce).
+bool local_box(const robast_surface_desc& s, double lo[3], double hi[3]) {
+    switch (s.shape) {
+        case ROBAST_SHAPE_SAG: {
+            if (s.aperture == ROBAST_AP_NONE) return false;
+            aperture_rect(s, &lo[0], &hi[0], &lo[1], &hi[1]);
+            // z range of the sag over the radii the aperture spans
+            double rmin = 0.0;
+            if (s.aperture == ROBAST_AP_ANNULUS || s.aperture == ROBAST_AP_SECTOR) rmin = s.ap[0];
+            const double rmax = aperture_bound(s);
+            double zlo = INFINITY, zhi = -INFINITY;
+            const int N = 512;
+            for (int k = 0; k <= N; ++k) {
+                const double r = rmin + (rmax - rmin) * k / N;
+                bool ok;
+                const double z = sag_eval(s, r * r, &ok);
+                if (!ok) continue;
+                zlo = std::min(zlo, z);
+                zhi = std::max(zhi, z);
+            }
+            if (!(zlo <= zhi)) zlo = zhi = 0.0;
+            // sampling margin: a fraction of the range plus the step's slope bound
+            const double m = 0.01 * (zhi - zlo) + 1e-9 * rmax;
+            lo[2] = zlo - m;
+            hi[2] = zhi + m;
+            return true;
+        }
+        case ROBAST_SHAPE_CYLINDER:
+            lo[0] = lo[1] = -s.prm[0];
+            hi[0] = hi[1] = s.prm[0];
+            lo[2] = 0.0;
+            hi[2] = s.prm[1];
+            return true;
+        case ROBAST_SHAPE_BOX:
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = -s.prm[k];
+                hi[k] = s.prm[k];
+            }
+            return true;
+        case ROBAST_SHAPE_HEXCONE: {
+            const double rm = std::max({s.prm[0], s.prm[2], s.prm[4]}) * 2.0 / std::sqrt(3.0);
+            lo[0] = lo[1] = -rm;
+            hi[0] = hi[1] = rm;
+            lo[2] = std::min({s.prm[1], s.prm[3], s.prm[5]});
+            hi[2] = std::max({s.prm[1], s.prm[3], s.prm[5]});
+            return true;
+        }
+    }
+    return false;
+}
+
+// World box of the local box through the tilted frame, padded and rounded
+// outwards to float.
+Box world_box(const double rows[9], const double o[3], const double lo[3], const double hi[3], double pad) {
+    Box b;
+    for (int c = 0; c < 8; ++c) {
+        const double l[3] = {(c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1], (c & 4) ? hi[2] : lo[2]};
+        double w[3];
+        for (int k = 0; k < 3; ++k) w[k] = o[k] + rows[k] * l[0] + rows[3 + k] * l[1] + rows[6 + k] * l[2];
+        b.add(w);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double p = pad + 1e-6 * std::max(std::fabs(b.lo[k]), std::fabs(b.hi[k]));
+        b.lo[k] = std::nextafter((double)(float)(b.lo[k] - p), -INFINITY);
+        b.hi[k] = std::nextafter((double)(float)(b.hi[k] + p), INFINITY);
+        b.lo[k] = (double)std::nextafterf((float)b.lo[k], -INFINITY);
+        b.hi[k] = (double)std::nextafterf((float)b.hi[k], INFINITY);
+    }
+    return b;
+}
+
+struct BvhBuilder {
+    const std::vector<Box>& boxes;
+    std::vector<Node>& nodes;
+    std::vector<int>& prims;
+    static const int kLeaf = 2;
+
+    void set_box(int ni, const Box& b) {
+        for (int k = 0; k < 3; ++k) {
+            nodes[ni].lo[k] = (float)b.lo[k];
+            nodes[ni].hi[k] = (float)b.hi[k];
+        }
+    }
+    // node ni covers ids[b, e)
+    void build(int ni, std::vector<int>& ids, int b, int e) {
+        Box bb, cb;
+        for (int k = b; k < e; ++k) {
+            bb.add(boxes[ids[k]]);
+            const double c[3] = {boxes[ids[k]].centre(0), boxes[ids[k]].centre(1), boxes[ids[k]].centre(2)};
+            cb.add(c);
+        }
+        set_box(ni, bb);
+        if (e - b <= kLeaf) {
+            nodes[ni].a = (int)prims.size();
+            nodes[ni].b = e - b;
+            for (int k = b; k < e; ++k) prims.push_back(ids[k]);
+            return;
+        }
+        int ax = 0;
+        for (int k = 1; k < 3; ++k)
+            if (cb.hi[k] - cb.lo[k] > cb.hi[ax] - cb.lo[ax]) ax = k;
+        const int mid = (b + e) / 2;
+        std::nth_element(ids.begin() + b, ids.begin() + mid, ids.begin() + e, [&](int x, int y) {
+            const double cx = boxes[x].centre(ax), cy = boxes[y].centre(ax);
+            return cx < cy || (cx == cy && x < y);
+        });
+        const int left = (int)nodes.size();
+        nodes.push_back(Node{});
+        nodes.push_back(Node{});
+        nodes[ni].a = left;
+        nodes[ni].b = 0;
+        build(left, ids, b, mid);
+        build(left + 1, ids, mid, e);
+    }
+};
+
+int validate(const robast_geom_desc* d) {
+    if (!d) return fail(ROBAST_E_NULL, "robast_build_geometry: desc is NULL");
+    if (d->n_surfaces <= 0 || !d->surfaces)
+        return fail(ROBAST_E_INVALID, "robast_build_geometry: need n_surfaces > 0 and a surface array");
+    if (d->n_materials < 0 || d->n_media < 0 || (d->n_materials > 0 && !d->materials) ||
+        (d->n_media > 0 && !d->media))
+        return fail(ROBAST_E_INVALID, "robast_build_geometry: material/medium counts and arrays disagree");
+    if (!(d->length_scale > 0.0) || !std::isfinite(d->length_scale))
+        return fail(ROBAST_E_INVALID, "robast_build_geometry: length_scale must be finite and > 0");
+    const int nv = d->variant_offsets ? d->n_variants : 1;
+    if (d->variant_offsets) {
+        if (d->n_variants <= 0) return fail(ROBAST_E_INVALID, "robast_build_geometry: n_variants must be > 0");
+        if (d->variant_offsets[0] != 0 || d->variant_offsets[nv] != d->n_surfaces)
+            return fail(ROBAST_E_INVALID, "robast_build_geometry: variant_offsets must run from 0 to n_surfaces");
+        for (int v = 0; v < nv; ++v)
+            if (d->variant_offsets[v + 1] < d->variant_offsets[v])
+                return fail(ROBAST_E_INVALID, "robast_build_geometry: variant_offsets must be non-decreasing");
+    }
+    for (int i = 0; i < d->n_materials; ++i) {
+        const robast_material_desc& m = d->materials[i];
+        if (m.n < 1 || m.n > ROBAST_MAX_TABLE)
+            return fail(ROBAST_E_INVALID, "material %d: table size %d outside 1..%d", i, m.n, ROBAST_MAX_TABLE);
+        for (int k = 0; k + 1 < m.n; ++k)
+            if (!(m.lam[k + 1] > m.lam[k]))
+                return fail(ROBAST_E_INVALID, "material %d: wavelengths must increase", i);
+        if (!(m.sigma >= 0.0)) return fail(ROBAST_E_INVALID, "material %d: sigma must be >= 0", i);
+    }
+    for (int i = 0; i < d->n_surfaces; ++i) {
+        const robast_surface_desc& s = d->surfaces[i];
+        if (s.shape < 0 || s.shape > 3) return fail(ROBAST_E_INVALID, "surface %d: unknown shape %d", i, s.shape);
+        if (s.role < 0 || s.role > 3) return fail(ROBAST_E_INVALID, "surface %d: unknown role %d", i, s.role);
+        if (s.aperture < 0 || s.aperture > 5)
+            return fail(ROBAST_E_INVALID, "surface %d: unknown aperture %d", i, s.aperture);
+        if (s.role == ROBAST_ROLE_MIRROR && (s.material < 0 || s.material >= d->n_materials))
+            return fail(ROBAST_E_INVALID, "surface %d: material %d out of range", i, s.material);
+        if (s.role == ROBAST_ROLE_REFRACT && (s.medium_front < 0 || s.medium_front >= d->n_media ||
+                                              s.medium_back < 0 || s.medium_back >= d->n_media))
+            return fail(ROBAST_E_INVALID, "surface %d: medium index out of range", i);
+        // orthonormal frame
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                const double dp = s.rot[3 * r] * s.rot[3 * c] + s.rot[3 * r + 1] * s.rot[3 * c + 1] +
+                                  s.rot[3 * r + 2] * s.rot[3 * c + 2];
+                if (std::fabs(dp - (r == c ? 1.0 : 0.0)) > 1e-9)
+                    return fail(ROBAST_E_INVALID, "surface %d: rot is not orthonormal", i);
+            }
+        if (s.shape == ROBAST_SHAPE_SAG) {
+            if (s.aperture == ROBAST_AP_SECTOR && !(s.ap[3] > s.ap[2] && s.ap[3] - s.ap[2] <= M_PI + 1e-12))
+                return fail(ROBAST_E_INVALID, "surface %d: sector needs phi0 < phi1 <= phi0 + pi", i);
+            if ((s.aperture == ROBAST_AP_ANNULUS || s.aperture == ROBAST_AP_SECTOR) && !(s.ap[1] > s.ap[0] && s.ap[0] >= 0))
+                return fail(ROBAST_E_INVALID, "surface %d: need 0 <= r_min < r_max", i);
+            if ((s.aperture == ROBAST_AP_CIRCLE || s.aperture == ROBAST_AP_HEXAGON) && !(s.ap[0] > 0))
+                return fail(ROBAST_E_INVALID, "surface %d: aperture size must be > 0", i);
+            if (s.aperture == ROBAST_AP_RECT && !(s.ap[0] > 0 && s.ap[1] > 0))
+                return fail(ROBAST_E_INVALID, "surface %d: rectangle half widths must be > 0", i);
+            if (any_asph(s) && s.aperture == ROBAST_AP_NONE)
+                return fail(ROBAST_E_INVALID, "surface %d: an aspheric surface needs a bounded aperture", i);
+        } else if (s.shape == ROBAST_SHAPE_CYLINDER) {
+            if (!(s.prm[0] > 0 && s.prm[1] > 0))
+                return fail(ROBAST_E_INVALID, "surface %d: cylinder radius and length must be > 0", i);
+        } else if (s.shape == ROBAST_SHAPE_BOX) {
+            if (!(s.prm[0] > 0 && s.prm[1] > 0 && s.prm[2] > 0))
+                return fail(ROBAST_E_INVALID, "surface %d: box half extents must be > 0", i);
+        } else {
+            if (!(s.prm[0] > 0 && s.prm[4] > 0 && s.prm[5] != s.prm[1]))
+                return fail(ROBAST_E_INVALID, "surface %d: Bezier cone needs positive radii and height", i);
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
+static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** out) {
+    if (!out) return fail(ROBAST_E_NULL, "robast_build_geometry: out is NULL");
+    *out = nullptr;
+    int rc = validate(d);
+    if (rc) return rc;
+    const int ns = d->n_surfaces;
+    const int nv = d->variant_offsets ? d->n_variants : 1;
+    const double L = d->length_scale;
+
+    std::vector<double> rec64((size_t)ns * REC, 0.0);
+    std::vector<float> rec32((size_t)ns * REC, 0.0f);
+    std::vector<int4> reci(ns);
+    std::vector<Box> boxes(ns);
+    std::vector<char> bounded(ns, 0);
+    for (int i = 0; i < ns; ++i) {
+        const robast_surface_desc& s = d->surfaces[i];
+        double* R = &rec64[(size_t)i * REC];
+        double rows[9];
+        tilted_rows(s, rows);
+        for (int k = 0; k < 3; ++k) R[F_O + k] = s.origin[k];
+        for (int k = 0; k < 9; ++k) R[F_R + k] = rows[k];
+        const bool asph = s.shape == ROBAST_SHAPE_SAG && any_asph(s);
+        switch (s.shape) {
+            case ROBAST_SHAPE_SAG: {
+                R[F_C] = s.curv;
+                R[F_K1] = 1.0 + s.conic;
+                for (int k = 0; k < 8; ++k) R[F_A + k] = s.asph[k];
+                const double rb = 1.1 * aperture_bound(s);
+                R[F_RB2] = rb * rb;
+                double* A = R + F_AP;
+                switch (s.aperture) {
+                    case ROBAST_AP_CIRCLE: A[0] = s.ap[0] * s.ap[0]; break;
+                    case ROBAST_AP_ANNULUS:
+                        A[0] = s.ap[0] * s.ap[0];
+                        A[1] = s.ap[1] * s.ap[1];
+                        break;
+                    case ROBAST_AP_SECTOR:
+                        A[0] = s.ap[0] * s.ap[0];
+                        A[1] = s.ap[1] * s.ap[1];
+                        A[2] = std::cos(s.ap[2]);
+                        A[3] = std::sin(s.ap[2]);
+                        A[4] = std::cos(s.ap[3]);
+                        A[5] = std::sin(s.ap[3]);
+                        break;
+                    case ROBAST_AP_HEXAGON: A[0] = s.ap[0]; break;
+                    case ROBAST_AP_RECT:
+                        A[0] = s.ap[0];
+                        A[1] = s.ap[1];
+                        break;
+                }
+                break;
+            }
+            case ROBAST_SHAPE_CYLINDER:
+                R[F_C] = s.prm[0];
+                R[F_K1] = s.prm[1];
+                break;
+            case ROBAST_SHAPE_BOX:
+                for (int k = 0; k < 3; ++k) R[F_C + k] = s.prm[k];
+                break;
+            case ROBAST_SHAPE_HEXCONE: {
+                const double r0 = s.prm[0], z0 = s.prm[1], r1 = s.prm[2], z1 = s.prm[3], r2 = s.prm[4], z2 = s.prm[5];
+                R[F_C + 0] = r0;
+                R[F_C + 1] = 2.0 * (r1 - r0);
+                R[F_C + 2] = r0 - 2.0 * r1 + r2;
+                R[F_C + 3] = z0;
+                R[F_C + 4] = 2.0 * (z1 - z0);
+                R[F_C + 5] = z0 - 2.0 * z1 + z2;
+                break;
+            }
+        }
+        for (int k = 0; k < REC; ++k) rec32[(size_t)i * REC + k] = (float)R[k];
+        reci[i] = make_int4(s.shape | (s.role << 4) | (s.aperture << 8) | ((asph ? 1 : 0) << 12), s.material,
+                            s.medium_front, s.medium_back);
+        double lo[3], hi[3];
+        if (local_box(s, lo, hi)) {
+            boxes[i] = world_box(rows, s.origin, lo, hi, 1e-6 * L);
+            bounded[i] = 1;
+        }
+    }
+    // BVH per variant; unbounded surfaces go to a per-variant list
+    std::vector<Node> nodes;
+    std::vector<int> prims, glob;
+    std::vector<int4> vars(nv);
+    for (int v = 0; v < nv; ++v) {
+        const int s0 = d->variant_offsets ? d->variant_offsets[v] : 0;
+        const int s1 = d->variant_offsets ? d->variant_offsets[v + 1] : ns;
+        std::vector<int> ids;
+        const int g0 = (int)glob.size();
+        for (int s = s0; s < s1; ++s) {
+            if (bounded[s])
+                ids.push_back(s);
+            else
+                glob.push_back(s);
+        }
+        int root = -1;
+        if (!ids.empty()) {
+            root = (int)nodes.size();
+            nodes.push_back(Node{});
+            BvhBuilder bb{boxes, nodes, prims};
+            bb.build(root, ids, 0, (int)ids.size());
+        }
+        vars[v] = make_int4(root, g0, (int)glob.size() - g0, s0);
+    }
+    std::vector<double> mats((size_t)std::max(1, d->n_materials) * MAT_REC, 0.0);
+    for (int i = 0; i < d->n_materials; ++i) {
+        const robast_material_desc& m = d->materials[i];
+        double* M = &mats[(size_t)i * MAT_REC];
+        M[0] = m.n;
+        for (int k = 0; k < m.n; ++k) {
+            M[1 + k] = m.lam[k];
+            M[17 + k] = m.refl[k];
+        }
+        M[33] = m.sigma;
+    }
+    std::vector<double> meds((size_t)std::max(1, d->n_media) * MED_REC, 0.0);
+    for (int i = 0; i < d->n_media; ++i) {
+        double* M = &meds[(size_t)i * MED_REC];
+        M[0] = d->media[i].n_const;
+        for (int k = 0; k < 3; ++k) {
+            M[1 + k] = d->media[i].B[k];
+            M[4 + k] = d->media[i].C[k];
+        }
+    }
+    if (glob.empty()) glob.push_back(0);
+    if (prims.empty()) prims.push_back(0);
+    if (nodes.empty()) nodes.push_back(Node{});
+
+    // one device allocation: [rec64 | rec32 | reci | nodes | prims | vars | glob | mats | meds | work]
+    const size_t b64 = align16(rec64.size() * 8), b32 = align16(rec32.size() * 4), bi = align16(reci.size() * 16);
+    const size_t bn = align16(nodes.size() * sizeof(Node)), bp = align16(prims.size() * 4);
+    const size_t bv = align16(vars.size() * 16), bg = align16(glob.size() * 4);
+    const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8);
+    const size_t bw = kWorkSlots * 8;
+    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bw;
+
+    robast_geom* g = new (std::nothrow) robast_geom();
+    if (!g) return fail(ROBAST_E_OOM, "robast_build_geometry: host allocation failed");
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) e = cudaMalloc(&g->dmem, total);
+    if (e != cudaSuccess) {
+        delete g;
+        return e == cudaErrorMemoryAllocation ? fail(ROBAST_E_OOM, "robast_build_geometry: cudaMalloc of %zu bytes failed", total)
+                                              : cuda_fail(e, "robast_build_geometry");
+    }
+    std::vector<unsigned char> host(total, 0);
+    size_t off = 0;
+    auto put = [&](const void* src, size_t bytes, size_t padded) {
+        std::memcpy(host.data() + off, src, bytes);
+        const size_t at = off;
+        off += padded;
+        return at;
+    };
+    const size_t o64 = put(rec64.data(), rec64.size() * 8, b64);
+    const size_t o32 = put(rec32.data(), rec32.size() * 4, b32);
+    const size_t oi = put(reci.data(), reci.size() * 16, bi);
+    const size_t on = put(nodes.data(), nodes.size() * sizeof(Node), bn);
+    const size_t op = put(prims.data(), prims.size() * 4, bp);
+    const size_t ov = put(vars.data(), vars.size() * 16, bv);
+    const size_t og = put(glob.data(), glob.size() * 4, bg);
+    const size_t om = put(mats.data(), mats.size() * 8, bm);
+    const size_t od = put(meds.data(), meds.size() * 8, bd);
+    const size_t ow = off;
+    e = cudaMemcpy(g->dmem, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->dmem);
+        delete g;
+        return cuda_fail(e, "robast_build_geometry: upload");
+    }
+    unsigned char* base = static_cast<unsigned char*>(g->dmem);
+    Tables t{};
+    t.surf_i = reinterpret_cast<const int4*>(base + oi);
+    t.nodes = reinterpret_cast<const Node*>(base + on);
+    t.prims = reinterpret_cast<const int*>(base + op);
+    t.variants = reinterpret_cast<const int4*>(base + ov);
+    t.glob = reinterpret_cast<const int*>(base + og);
+    t.mats = reinterpret_cast<const double*>(base + om);
+    t.meds = reinterpret_cast<const double*>(base + od);
+    t.n_surf = ns;
+    t.n_nodes = (int)nodes.size();
+    t.n_prims = (int)prims.size();
+    t.n_var = nv;
+    t.n_glob = (int)glob.size();
+    t.n_mat = std::max(1, d->n_materials);
+    t.n_med = std::max(1, d->n_media);
+    g->tab64 = t;
+    g->tab64.surf = base + o64;
+    g->tab32 = t;
+    g->tab32.surf = base + o32;
+    g->work = reinterpret_cast<unsigned long long*>(base + ow);
+    g->smem64 = b64 + bi + bn + bp + bv + bg + bm + bd;
+    g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd;
+    g->n_surf = ns;
+    g->n_var = nv;
+    g->n_mat = d->n_materials;
+    g->n_med = d->n_media;
+    g->n_nodes = (int)nodes.size();
+    g->n_prims = (int)prims.size();
+    g->n_glob = (int)glob.size();
+    g->length_scale = L;
+    *out = g;
+    return 0;
+}
+
+extern "C" void robast_free_geometry(robast_geom* g) {
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    cudaFree(g->dmem);
+    if (g->stage) cudaFree(g->stage);
+    if (g->scratch) cudaFree(g->scratch);
+    cudaSetDevice(prev);
+    delete g;
+}
+
+extern "C" int robast_geometry_info(const robast_geom* g, int32_t* n_surfaces, int32_t* n_variants,
+                                    int32_t* n_bvh_nodes) {
+    if (!g) return fail(ROBAST_E_NULL, "robast_geometry_info: g is NULL");
+    if (n_surfaces) *n_surfaces = g->n_surf;
+    if (n_variants) *n_variants = g->n_var;
+    if (n_bvh_nodes) *n_bvh_nodes = g->n_nodes;
+    return 0;
+}
+
+// ------------------------------------------------------------------ trace
+extern "C" void robast_trace_opts_default(robast_trace_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = 32;
+    o->max_bounces = 100;
+}
+
+// Shared memory one block may use for staged tables.
+static const size_t kSmemCap = 200 * 1024;
+
+template <typename T>
+static int do_trace(const robast_geom* g, const void* origins, const void* dirs, const void* wl, int64_t n,
+                    uint64_t seed, const robast_trace_out* out, const robast_trace_opts& o) {
+    TraceArgs<T> a{};
+    a.tab = sizeof(T) == 4 ? g->tab32 : g->tab64;
+    a.o = static_cast<const T*>(origins);
+    a.d = static_cast<const T*>(dirs);
+    a.lam = static_cast<const T*>(wl);
+    a.vop = o.variant_of_photon;
+    a.n = n;
+    a.seed = seed;
+    a.first_id = o.first_photon_id;
+    a.max_bounces = o.max_bounces;
+    const double L = g->length_scale;
+    const double eps = o.eps > 0.0 ? o.eps : (sizeof(T) == 4 ? 1e-6 : 1e-9) * L;
+    a.eps = (T)eps;
+    // Newton stops at |dt| < 1e-4 eps (FP64: 1e-13 L; FP32: then an FP64 step at grazing incidence)
+    a.newton_tol = sizeof(T) == 4 ? (T)(1e-6 * L) : (T)(eps * 1e-4);
+    a.newton_tol64 = eps * 1e-4;
+    a.st = out->status;
+    a.nb = out->bounces;
+    a.hit = static_cast<T*>(out->hit);
+    a.dir = static_cast<T*>(out->dir);
+    a.last = out->last_surface;
+    a.fxy = static_cast<T*>(out->focal_xy);
+    a.counters = out->counters;
+    a.units = o.work_units;
+    cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+    robast_geom* gm = const_cast<robast_geom*>(g);
+    a.work = g->work + (gm->work_slot.fetch_add(1) % kWorkSlots);
+    CU(cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s), "robast_trace: reset work counter");
+    const size_t smem_tab = sizeof(T) == 4 ? g->smem32 : g->smem64;
+    a.stage = smem_tab <= kSmemCap ? 1 : 0;
+    const size_t smem = a.stage ? smem_tab : 0;
+    int block = o.block_size ? o.block_size : 128;
+    if (block != 64 && block != 128 && block != 256)
+        return fail(ROBAST_E_INVALID, "robast_trace: block_size must be 64, 128 or 256 (got %d)", block);
+    if (a.units && block != 128)
+        return fail(ROBAST_E_INVALID, "robast_trace: the counting build (work_units) runs with block_size 128 only");
+    int bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem) : trace_blocks_per_sm_f64(block, smem);
+    if (bps <= 0) return fail(ROBAST_E_CUDA, "robast_trace: kernel cannot launch with %zu bytes of shared memory", smem);
+    if (o.blocks_per_sm > 0) bps = std::min(bps, (int)o.blocks_per_sm);
+    long long grid = (long long)g->num_sms * bps;
+    const long long need = (n + block - 1) / block;
+    if (grid > need) grid = std::max(1LL, need);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4)
+        e = launch_trace_f32(a, block, (int)grid, smem, s);
+    else
+        e = launch_trace_f64(a, block, (int)grid, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "robast_trace: launch");
+    return 0;
+}
+
+static int check_trace_args(const robast_geom* g, const void* o, const void* d, const void* w, int64_t n,
+                            const robast_trace_out* out, const robast_trace_opts& op) {
+    if (!g) return fail(ROBAST_E_NULL, "robast_trace: geometry is NULL");
+    if (!out) return fail(ROBAST_E_NULL, "robast_trace: out is NULL");
+    if (n < 0) return fail(ROBAST_E_INVALID, "robast_trace: n must be >= 0 (got %lld)", (long long)n);
+    if (n > 0 && (!o || !d || !w)) return fail(ROBAST_E_NULL, "robast_trace: origins, dirs and wavelengths are required");
+    if (op.precision != 32 && op.precision != 64)
+        return fail(ROBAST_E_INVALID, "robast_trace: precision must be 32 or 64 (got %d)", op.precision);
+    if (op.max_bounces < 1 || op.max_bounces > 255)
+        return fail(ROBAST_E_INVALID, "robast_trace: max_bounces must be in 1..255 (got %d)", op.max_bounces);
+    if (g->n_var > 1 && !op.variant_of_photon && n > 0) {
+        // allowed: everything traced through variant 0
+    }
+    return 0;
+}
+
+extern "C" int robast_trace_ex(const robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
+                               int64_t n, uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts) {
+    robast_trace_opts o;
+    robast_trace_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_bounces == 0) o.max_bounces = 100;
+    if (o.precision == 0) o.precision = 32;
+    int rc = check_trace_args(g, origins, dirs, wavelengths, n, out, o);
+    if (rc) return rc;
+    if (n == 0) return 0;
+    return o.precision == 32 ? do_trace<float>(g, origins, dirs, wavelengths, n, seed, out, o)
+                             : do_trace<double>(g, origins, dirs, wavelengths, n, seed, out, o);
+}
+
+extern "C" int robast_trace(const robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
+                            int64_t n, uint64_t seed, const robast_trace_out* out) {
+    return robast_trace_ex(g, origins, dirs, wavelengths, n, seed, out, nullptr);
+}
+
+static int grow(void** p, size_t* have, size_t need, const char* what) {
+    if (*have >= need) return 0;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e != cudaSuccess) return fail(ROBAST_E_OOM, "%s: cudaMalloc of %zu bytes failed", what, need);
+    *have = need;
+    return 0;
+}
+
+extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
+                                 int64_t n, uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts) {
+    robast_trace_opts o;
+    robast_trace_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_bounces == 0) o.max_bounces = 100;
+    if (o.precision == 0) o.precision = 32;
+    int rc = check_trace_args(g, origins, dirs, wavelengths, n, out, o);
+    if (rc) return rc;
+    if (n == 0) return 0;
+    std::lock_guard<std::mutex> lk(g->mu);
+    const size_t es = o.precision == 32 ? 4 : 8;
+    const size_t N = (size_t)n;
+    // device layout: in o[3n] d[3n] lam[n] vop[n] | out st[n] nb[n] hit[3n] dir[3n] last[n] fxy[2n] counters[8]
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t at = off;
+        off += align16(bytes);
+        return at;
+    };
+    const size_t xo = carve(3 * N * es), xd = carve(3 * N * es), xl = carve(N * es);
+    const size_t xv = o.variant_of_photon ? carve(N * 4) : 0;
+    const size_t xs = carve(N), xb = carve(N), xh = carve(3 * N * es), xr = carve(3 * N * es), xla = carve(N * 4);
+    const size_t xf = carve(2 * N * es), xc = carve(ROBAST_N_COUNTERS * 8);
+    rc = grow(&g->stage, &g->stage_bytes, off, "robast_trace_host");
+    if (rc) return rc;
+    unsigned char* b = static_cast<unsigned char*>(g->stage);
+    cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+    CU(cudaMemcpyAsync(b + xo, origins, 3 * N * es, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
+    CU(cudaMemcpyAsync(b + xd, dirs, 3 * N * es, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
+    CU(cudaMemcpyAsync(b + xl, wavelengths, N * es, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
+    robast_trace_opts od = o;
+    if (o.variant_of_photon) {
+        CU(cudaMemcpyAsync(b + xv, o.variant_of_photon, N * 4, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
+        od.variant_of_photon = reinterpret_cast<const int32_t*>(b + xv);
+    }
+    robast_trace_out dout{};
+    dout.status = out->status ? b + xs : nullptr;
+    dout.bounces = out->bounces ? b + xb : nullptr;
+    dout.hit = out->hit ? b + xh : nullptr;
+    dout.dir = out->dir ? b + xr : nullptr;
+    dout.last_surface = out->last_surface ? reinterpret_cast<int32_t*>(b + xla) : nullptr;
+    dout.focal_xy = out->focal_xy ? b + xf : nullptr;
+    unsigned long long* dc = reinterpret_cast<unsigned long long*>(b + xc);
+    dout.counters = dc;
+    CU(cudaMemsetAsync(dc, 0, ROBAST_N_COUNTERS * 8, s), "robast_trace_host: counters");
+    rc = robast_trace_ex(g, b + xo, b + xd, b + xl, n, seed, &dout, &od);
+    if (rc) return rc;
+    if (out->status) CU(cudaMemcpyAsync(out->status, dout.status, N, cudaMemcpyDeviceToHost, s), "copy out");
+    if (out->bounces) CU(cudaMemcpyAsync(out->bounces, dout.bounces, N, cudaMemcpyDeviceToHost, s), "copy out");
+    if (out->hit) CU(cudaMemcpyAsync(out->hit, dout.hit, 3 * N * es, cudaMemcpyDeviceToHost, s), "copy out");
+    if (out->dir) CU(cudaMemcpyAsync(out->dir, dout.dir, 3 * N * es, cudaMemcpyDeviceToHost, s), "copy out");
+    if (out->last_surface)
+        CU(cudaMemcpyAsync(out->last_surface, dout.last_surface, N * 4, cudaMemcpyDeviceToHost, s), "copy out");
+    if (out->focal_xy) CU(cudaMemcpyAsync(out->focal_xy, dout.focal_xy, 2 * N * es, cudaMemcpyDeviceToHost, s), "copy out");
+    unsigned long long hc[ROBAST_N_COUNTERS];
+    CU(cudaMemcpyAsync(hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s), "copy out");
+    CU(cudaStreamSynchronize(s), "robast_trace_host: synchronize");
+    if (out->counters)
+        for (int k = 0; k < ROBAST_N_COUNTERS; ++k) out->counters[k] += hc[k];
+    return 0;
+}
+
+// ------------------------------------------------------------- reductions
+// Spot diagram: centroid by fixed-order FP64 block partials, then the exact
+// nearest-rank 80% radius through a 4096-bin histogram and a selection inside
+// the bin that holds the rank.
+namespace {
+constexpr int kRedBlock = 256;
+constexpr int kRedGrid = 304;  // 2 x 152 SMs
+constexpr int kBins = 4096;
+
+template <typename T>
+__global__ void psf_partials(const uint8_t* st, const T* fxy, long long n, long long ld, double* part) {
+    double c = 0, sx = 0, sy = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (st[i] == ROBAST_ST_DETECTED) {
+            c += 1.0;
+            sx += (double)fxy[i];
+            sy += (double)fxy[ld + i];
+        }
+    __shared__ double sh[3][kRedBlock];
+    sh[0][threadIdx.x] = c;
+    sh[1][threadIdx.x] = sx;
+    sh[2][threadIdx.x] = sy;
+    __syncthreads();
+    for (int w = kRedBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) part[3 * blockIdx.x + k] = sh[k][0];
+}
+
+__global__ void psf_finish(const double* part, int nparts, double* res) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double c = 0, sx = 0, sy = 0;
+        for (int b = 0; b < nparts; ++b) {
+            c += part[3 * b];
+            sx += part[3 * b + 1];
+            sy += part[3 * b + 2];
+        }
+        res[0] = c;
+        res[1] = c > 0 ? sx / c : 0.0;
+        res[2] = c > 0 ? sy / c : 0.0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double radius(const T* fxy, long long ld, long long i, const double* res) {
+    const double dx = (double)fxy[i] - res[1], dy = (double)fxy[ld + i] - res[2];
+    return sqrt(dx * dx + dy * dy);
+}
+
+template <typename T>
+__global__ void psf_rmax(const uint8_t* st, const T* fxy, long long n, long long ld, const double* res,
+                         unsigned long long* rmax) {
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (st[i] == ROBAST_ST_DETECTED) m = fmax(m, radius(fxy, ld, i, res));
+    // non-negative doubles order like their bit patterns
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(rmax, bits);
+}
+
+template <typename T>
+__device__ __forceinline__ int bin_of(double r, double rmax) {
+    int b = rmax > 0.0 ? (int)(r / rmax * kBins) : 0;
+    return b < 0 ? 0 : (b >= kBins ? kBins - 1 : b);
+}
+
+template <typename T>
+__global__ void psf_hist(const uint8_t* st, const T* fxy, long long n, long long ld, const double* res,
+                         const unsigned long long* rmax_bits, unsigned long long* hist) {
+    __shared__ unsigned int h[kBins];
+    for (int k = threadIdx.x; k < kBins; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    const double rmax = __longlong_as_double((long long)*rmax_bits);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (st[i] == ROBAST_ST_DETECTED) atomicAdd(&h[bin_of<T>(radius(fxy, ld, i, res), rmax)], 1u);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kBins; k += blockDim.x)
+        if (h[k]) atomicAdd(hist + k, (unsigned long long)h[k]);
+}
+
+template <typename T>
+__global__ void psf_collect(const uint8_t* st, const T* fxy, long long n, long long ld, const double* res,
+                            const unsigned long long* rmax_bits, int bin, double* vals, unsigned long long* cnt,
+                            unsigned long long cap) {
+    const double rmax = __longlong_as_double((long long)*rmax_bits);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (st[i] == ROBAST_ST_DETECTED) {
+            const double r = radius(fxy, ld, i, res);
+            if (bin_of<T>(r, rmax) == bin) {
+                const unsigned long long k = atomicAdd(cnt, 1ull);
+                if (k < cap) vals[k] = r;
+            }
+        }
+}
+
+template <typename T>
+int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long n, long long ld, cudaStream_t s,
+             double* result) {
+    // scratch: parts[3*grid] res[4] rmax[1] cnt[1] hist[kBins] vals[...]
+    const size_t parts = 3 * kRedGrid * 8, fixed = align16(parts) + 64 + kBins * 8;
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = grow(&g->scratch, &g->scratch_bytes, fixed + 1024 * 8, "robast_psf");
+    if (rc) return rc;
+    unsigned char* b = static_cast<unsigned char*>(g->scratch);
+    double* part = reinterpret_cast<double*>(b);
+    double* res = reinterpret_cast<double*>(b + align16(parts));
+    unsigned long long* rmax = reinterpret_cast<unsigned long long*>(b + align16(parts) + 32);
+    unsigned long long* cnt = rmax + 1;
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(b + align16(parts) + 64);
+    CU(cudaMemsetAsync(b + align16(parts), 0, 64 + kBins * 8, s), "robast_psf: clear");
+    psf_partials<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, part);
+    psf_finish<<<1, 32, 0, s>>>(part, kRedGrid, res);
+    psf_rmax<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax);
+    psf_hist<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax, hist);
+    CU(cudaGetLastError(), "robast_psf: launch");
+    double hres[3];
+    std::vector<unsigned long long> hh(kBins);
+    CU(cudaMemcpyAsync(hres, res, sizeof hres, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(hh.data(), hist, kBins * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
+    const long long N = (long long)hres[0];
+    result[0] = hres[0];
+    if (N == 0) {
+        result[1] = result[2] = result[3] = NAN;
+        return 0;
+    }
+    result[1] = hres[1];
+    result[2] = hres[2];
+    const long long k = (long long)std::ceil(0.8 * (double)N) - 1;
+    long long acc = 0;
+    int bin = 0;
+    for (; bin < kBins; ++bin) {
+        if (acc + (long long)hh[bin] > k) break;
+        acc += (long long)hh[bin];
+    }
+    const unsigned long long cap = hh[bin];
+    rc = grow(&g->scratch, &g->scratch_bytes, fixed + cap * 8 + 1024 * 8, "robast_psf");
+    if (rc) return rc;
+    b = static_cast<unsigned char*>(g->scratch);
+    part = reinterpret_cast<double*>(b);
+    res = reinterpret_cast<double*>(b + align16(parts));
+    rmax = reinterpret_cast<unsigned long long*>(b + align16(parts) + 32);
+    cnt = rmax + 1;
+    hist = reinterpret_cast<unsigned long long*>(b + align16(parts) + 64);
+    double* vals = reinterpret_cast<double*>(b + fixed);
+    // the scratch may have moved: restore res and rmax for the collect pass
+    unsigned long long hrmax = 0;
+    {
+        double r4[4] = {hres[0], hres[1], hres[2], 0.0};
+        CU(cudaMemcpyAsync(res, r4, sizeof r4, cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    }
+    // rmax was on the device only; recompute it (cheap) when the scratch moved
+    CU(cudaMemsetAsync(rmax, 0, 16, s), "robast_psf: clear");
+    psf_rmax<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax);
+    psf_collect<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax, bin, vals, cnt, cap);
+    CU(cudaGetLastError(), "robast_psf: launch");
+    std::vector<double> hv(cap);
+    unsigned long long got = 0;
+    CU(cudaMemcpyAsync(&got, cnt, 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(&hrmax, rmax, 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    if (cap) CU(cudaMemcpyAsync(hv.data(), vals, cap * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
+    if (got != cap) return fail(ROBAST_E_CUDA, "robast_psf: histogram and selection disagree (%llu vs %llu)", got, cap);
+    const long long kk = k - acc;
+    std::nth_element(hv.begin(), hv.begin() + kk, hv.end());
+    result[3] = hv[kk];
+    return 0;
+}
+}  // namespace
+
+extern "C" int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t n, int64_t ld,
+                          int32_t precision, void* stream, double* result) {
+    if (!g || !status || !focal_xy || !result) return fail(ROBAST_E_NULL, "robast_psf: NULL argument");
+    if (n <= 0) return fail(ROBAST_E_INVALID, "robast_psf: n must be > 0");
+    if (ld == 0) ld = n;
+    if (ld < n) return fail(ROBAST_E_INVALID, "robast_psf: ld (%lld) must be >= n (%lld)", (long long)ld, (long long)n);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 32) return psf_impl<float>(g, status, static_cast<const float*>(focal_xy), n, ld, s, result);
+    if (precision == 64) return psf_impl<double>(g, status, static_cast<const double*>(focal_xy), n, ld, s, result);
+    return fail(ROBAST_E_INVALID, "robast_psf: precision must be 32 or 64");
+}
+
+// ------------------------------------------------------- ALU peak probe
+// Throughput of dependent-free FMA chains (8 independent accumulators per
+// thread), all SMs busy: the denominator of the ALU roofline.
+namespace {
+template <typename T>
+__global__ void fma_probe(T* sink, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = x[k] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == (T)1234.5678) sink[0] = s;  // keeps the chains alive
+}
+}  // namespace
+
+extern "C" int robast_measure_alu_peak(int32_t precision, void* stream, double* flops_per_s) {
+    if (!flops_per_s) return fail(ROBAST_E_NULL, "robast_measure_alu_peak: result pointer is NULL");
+    if (precision != 32 && precision != 64) return fail(ROBAST_E_INVALID, "robast_measure_alu_peak: precision 32 or 64");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev), "robast_measure_alu_peak");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "robast_measure_alu_peak");
+    void* sink = nullptr;
+    CU(cudaMalloc(&sink, 64), "robast_measure_alu_peak: cudaMalloc");
+    const int block = 256, grid = sms * 8;
+    const int iters = precision == 32 ? 1 << 14 : 1 << 9;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 6; ++rep) {
+        cudaEventRecord(e0, s);
+        if (precision == 32)
+            fma_probe<float><<<grid, block, 0, s>>>((float*)sink, iters, 0.999999f, 1e-7f);
+        else
+            fma_probe<double><<<grid, block, 0, s>>>((double*)sink, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;  // first launch is warm-up
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e, "robast_measure_alu_peak");
+    *flops_per_s = 2.0 * 8.0 * (double)iters * (double)block * (double)grid / (best * 1e-3);
+    return 0;
+}

@@ -1,0 +1,889 @@
+// Device side of the non-sequential photon trace (Okumura et al., ICRC 2015,
+// Sec. 1 and 2.1): for every photon, find the nearest intersection over all
+// surfaces of its optical system, apply the surface's role (mirror: reflect
+// with reflectivity and roughness; refracting face: Snell + Fresnel; focal
+// surface: detect; obscuration: absorb), repeat until the photon terminates.
+//
+// GB300 design:
+//  * one persistent grid (SM count x resident blocks); each warp refills its
+//    idle lanes from a global work counter with ONE atomic per refill round,
+//    so lanes whose photon ended are reused immediately instead of idling
+//    until the longest photon of the warp is done;
+//  * the surface records, the BVH and the material tables are staged in
+//    shared memory once per block (they are read by every lane at every
+//    bounce);
+//  * photon state lives in registers; inputs and outputs are SoA so a warp's
+//    loads and stores of consecutive photons coalesce;
+//  * FP32 form: every intersection is computed in the surface's own local
+//    frame (origin rebased to the vertex) so metre-scale coordinates do not
+//    swamp millimetre-scale sags; FP64 is used only for the reflectivity
+//    threshold (so absorb decisions are identical to the FP64 form) and for
+//    the last Newton step of aspheric / Bezier roots at grazing incidence;
+//  * Philox4x32-10 counter-based streams keyed by (seed, photon id, bounce)
+//    make every photon's result independent of scheduling.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace robast {
+
+// ----------------------------------------------------------------- layout
+enum { SHAPE_SAG = 0, SHAPE_CYL = 1, SHAPE_BOX = 2, SHAPE_HEXCONE = 3 };
+enum { ROLE_MIRROR = 0, ROLE_REFRACT = 1, ROLE_FOCAL = 2, ROLE_OBSC = 3 };
+enum { AP_NONE = 0, AP_CIRCLE = 1, AP_ANNULUS = 2, AP_SECTOR = 3, AP_HEX = 4, AP_RECT = 5 };
+enum { ST_DETECTED = 1, ST_ABSORBED = 2, ST_OBSCURED = 3, ST_ESCAPED = 4, ST_MAXB = 5, ST_ERROR = 6 };
+
+// Surface record: REC values of the working precision T.
+//   [0..2] origin   [3..11] rows of the (tilted) local frame
+//   SAG:     [12] c  [13] 1+k  [14..21] A1..A8  [28] (1.1 r_bound)^2 (Newton seed domain)
+//   CYL:     [12] radius [13] length
+//   BOX:     [12..14] half extents
+//   HEXCONE: [12..14] r power-basis coefficients, [15..17] z coefficients
+//   aperture [22..27]: CIRCLE r^2; ANNULUS rmin^2 rmax^2; SECTOR rmin^2 rmax^2 e0x e0y e1x e1y;
+//                      HEX apothem; RECT hx hy
+enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, REC = 32 };
+// Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12, y = material,
+// z = medium front, w = medium back.
+// Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
+enum { MAT_REC = 34 };
+// Medium record (doubles): [0] n_const, [1..3] B, [4..6] C.
+enum { MED_REC = 7 };
+
+// Work units counted by the counting instantiation (kernel template flag C):
+// the per-unit figures that turn them into algorithmic FLOPs are stated with
+// the benchmark.
+enum {
+    U_AABB = 0,      // ray-box slab tests
+    U_SAG = 1,       // quadric (sag) root solves
+    U_NEWTON = 2,    // aspheric Newton iterations
+    U_APERTURE = 3,  // aperture inclusion tests
+    U_CYL = 4,       // cylinder tests
+    U_BOX = 5,       // box tests
+    U_HEXWALL = 6,   // Bezier wall tests (6 per cone)
+    U_REFLECT = 7,   // reflections
+    U_REFRACT = 8,   // Fresnel + Snell evaluations
+    U_ROUGH = 9,     // roughness perturbations (Box-Muller + basis)
+    U_PHILOX = 10,   // Philox4x32-10 calls (integer pipe)
+    U_REBASE = 11,   // world -> local frame transforms
+    U_N = 12
+};
+#define CNT(k)                         \
+    do {                               \
+        if constexpr (C) cnt[(k)] += 1u; \
+    } while (0)
+
+struct Node {
+    float lo[3], hi[3];
+    int a, b;  // b > 0: leaf with prims [a, a + b); b == 0: internal, children a and a + 1
+};
+
+struct Tables {
+    const void* surf;  // n_surf * REC values of T
+    const int4* surf_i;
+    const Node* nodes;
+    const int* prims;
+    const int4* variants;  // (bvh root or -1, first unbounded index, n unbounded, -)
+    const int* glob;       // surfaces without a bounding box, per variant
+    const double* mats;
+    const double* meds;
+    int n_surf, n_nodes, n_prims, n_var, n_glob, n_mat, n_med, pad;
+};
+
+template <typename T>
+struct TraceArgs {
+    Tables tab;
+    const T* o;
+    const T* d;
+    const T* lam;
+    const int* vop;
+    long long n;
+    unsigned long long seed;
+    long long first_id;
+    int max_bounces;
+    int stage;  // stage tables in shared memory
+    T eps;
+    T newton_tol;
+    double newton_tol64;
+    uint8_t* st;
+    uint8_t* nb;
+    T* hit;
+    T* dir;
+    int* last;
+    T* fxy;
+    unsigned long long* counters;
+    unsigned long long* work;
+    unsigned long long* units;  // [U_N], counting instantiation only
+};
+
+// ------------------------------------------------------------ math helpers
+__device__ __forceinline__ float t_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double t_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float t_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double t_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float t_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double t_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float t_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double t_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float t_log(float x) { return logf(x); }
+__device__ __forceinline__ double t_log(double x) { return log(x); }
+__device__ __forceinline__ void t_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void t_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ bool t_finite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool t_finite(double x) { return isfinite(x); }
+template <typename T> __device__ __forceinline__ T t_inf();
+template <> __device__ __forceinline__ float t_inf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double t_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+template <typename T> __device__ __forceinline__ V3<T> mk(T x, T y, T z) { return V3<T>{x, y, z}; }
+template <typename T> __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <typename T> __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <typename T> __device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return mk(s * a.x, s * a.y, s * a.z); }
+template <typename T> __device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T> __device__ __forceinline__ V3<T> unit(V3<T> a) { return (T(1) / t_sqrt(dot(a, a))) * a; }
+
+// --------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit products, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ T unit_open(uint32_t w) {
+    return (T(w) + T(0.5)) * T(2.3283064365386963e-10);  // 2^-32
+}
+
+// ------------------------------------------------------ frame transforms
+template <typename T>
+__device__ __forceinline__ V3<T> to_local_pt(const T* S, V3<T> p) {
+    const T qx = p.x - S[F_O], qy = p.y - S[F_O + 1], qz = p.z - S[F_O + 2];
+    return mk(S[F_R + 0] * qx + S[F_R + 1] * qy + S[F_R + 2] * qz, S[F_R + 3] * qx + S[F_R + 4] * qy + S[F_R + 5] * qz,
+              S[F_R + 6] * qx + S[F_R + 7] * qy + S[F_R + 8] * qz);
+}
+template <typename T>
+__device__ __forceinline__ V3<T> to_local_vec(const T* S, V3<T> q) {
+    return mk(S[F_R + 0] * q.x + S[F_R + 1] * q.y + S[F_R + 2] * q.z, S[F_R + 3] * q.x + S[F_R + 4] * q.y + S[F_R + 5] * q.z,
+              S[F_R + 6] * q.x + S[F_R + 7] * q.y + S[F_R + 8] * q.z);
+}
+template <typename T>
+__device__ __forceinline__ V3<T> to_world_vec(const T* S, V3<T> q) {
+    return mk(S[F_R + 0] * q.x + S[F_R + 3] * q.y + S[F_R + 6] * q.z, S[F_R + 1] * q.x + S[F_R + 4] * q.y + S[F_R + 7] * q.z,
+              S[F_R + 2] * q.x + S[F_R + 5] * q.y + S[F_R + 8] * q.z);
+}
+
+// ------------------------------------------------------------- apertures
+template <typename T>
+__device__ __forceinline__ bool aperture_inside(const T* S, int ap, T x, T y) {
+    const T* A = S + F_AP;
+    const T r2 = x * x + y * y;
+    switch (ap) {
+        case AP_NONE: return true;
+        case AP_CIRCLE: return r2 <= A[0];
+        case AP_ANNULUS: return r2 >= A[0] && r2 <= A[1];
+        case AP_SECTOR: return r2 >= A[0] && r2 <= A[1] && (A[2] * y - A[3] * x) >= T(0) && (x * A[5] - y * A[4]) >= T(0);
+        case AP_HEX: {
+            const T s60 = T(0.86602540378443864676);
+            const T m = t_max(t_abs(x), t_max(t_abs(T(0.5) * x + s60 * y), t_abs(-T(0.5) * x + s60 * y)));
+            return m <= A[0];
+        }
+        case AP_RECT: return t_abs(x) <= A[0] && t_abs(y) <= A[1];
+    }
+    return false;
+}
+
+template <typename T>
+struct LHit {
+    T t;
+    V3<T> pl;  // local hit point
+    V3<T> nl;  // local front normal (unit)
+};
+
+// sag z(rho) and dz/drho of the even asphere; false outside the conic's domain
+template <typename T>
+__device__ __forceinline__ bool sag_slope(const T* S, T rho, T* z, T* slope) {
+    const T c = S[F_C];
+    const T arg = T(1) - S[F_K1] * c * c * rho;
+    if (arg < T(0)) return false;
+    const T sq = t_sqrt(arg);
+    T poly = T(0), dpoly = T(0);
+#pragma unroll
+    for (int i = 8; i >= 1; --i) {  // Horner in rho
+        poly = poly * rho + S[F_A + i - 1];
+        dpoly = dpoly * rho + T(i) * S[F_A + i - 1];
+    }
+    *z = c * rho / (T(1) + sq) + poly * rho;
+    *slope = c / (T(2) * sq) + dpoly;
+    return true;
+}
+
+// One Newton step on f(t) = z(t) - sag(rho(t)) in FP64 (the final step of an
+// FP32 root at grazing incidence).
+template <typename T>
+__device__ __forceinline__ bool newton_step_fp64(const T* S, V3<T> p, V3<T> d, T* t) {
+    double c = (double)S[F_C], k1 = (double)S[F_K1];
+    double tt = (double)*t;
+    double x = (double)p.x + tt * (double)d.x, y = (double)p.y + tt * (double)d.y, z = (double)p.z + tt * (double)d.z;
+    double rho = x * x + y * y;
+    double arg = 1.0 - k1 * c * c * rho;
+    if (arg < 0.0) return false;
+    double sq = sqrt(arg);
+    double poly = 0.0, dpoly = 0.0;
+#pragma unroll
+    for (int i = 8; i >= 1; --i) {
+        poly = poly * rho + (double)S[F_A + i - 1];
+        dpoly = dpoly * rho + (double)i * (double)S[F_A + i - 1];
+    }
+    double zs = c * rho / (1.0 + sq) + poly * rho;
+    double slope = c / (2.0 * sq) + dpoly;
+    double fp = (double)d.z - slope * 2.0 * (x * (double)d.x + y * (double)d.y);
+    if (fp == 0.0) return false;
+    *t = (T)(tt - (z - zs) / fp);
+    return true;
+}
+
+// Ray vs SAG surface (local frame).  Quadric F = c (x^2 + y^2 + (1+k) z^2) - 2z,
+// sag branch (1+k) c z <= 1; both roots in ascending order, first valid one.
+// Aspheres: Newton from the first on-branch root beyond eps.
+template <bool C, typename T>
+__device__ __forceinline__ bool hit_sag(const T* S, int ap, bool asph, V3<T> p, V3<T> d, T eps, T tmax, T tol, LHit<T>& h,
+                                        bool& err, unsigned* cnt) {
+    CNT(U_SAG);
+    const T c = S[F_C], k1 = S[F_K1];
+    const T a = c * (d.x * d.x + d.y * d.y + k1 * d.z * d.z);
+    const T b = c * (p.x * d.x + p.y * d.y + k1 * p.z * d.z) - d.z;
+    const T g = c * (p.x * p.x + p.y * p.y + k1 * p.z * p.z) - T(2) * p.z;
+    T r[2];
+    int nr = 0;
+    if (a == T(0)) {
+        if (b != T(0)) r[nr++] = -g / (T(2) * b);
+    } else {
+        const T disc = b * b - a * g;
+        if (disc >= T(0)) {
+            const T sq = t_sqrt(disc);
+            const T q = -(b + (b >= T(0) ? sq : -sq));
+            if (q != T(0)) {
+                const T t1 = q / a, t2 = g / q;
+                r[0] = t_min(t1, t2);
+                r[1] = t_max(t1, t2);
+                nr = 2;
+            } else {
+                r[nr++] = T(0);
+            }
+        }
+    }
+    for (int i = 0; i < nr; ++i) {
+        T t = r[i];
+        const V3<T> q = p + t * d;
+        if (k1 * c * q.z > T(1)) continue;
+        if (asph) {
+            if (t <= eps) continue;
+            if (q.x * q.x + q.y * q.y > S[F_RB2]) return false;
+            bool conv = false;
+            T slope = T(0);
+            for (int it = 0; it < 32; ++it) {
+                CNT(U_NEWTON);
+                const V3<T> x = p + t * d;
+                T z;
+                if (!sag_slope(S, x.x * x.x + x.y * x.y, &z, &slope)) return false;
+                const T fp = d.z - slope * T(2) * (x.x * d.x + x.y * d.y);
+                if (fp == T(0)) break;
+                const T dt = (x.z - z) / fp;
+                t -= dt;
+                if (t_abs(dt) < tol) {
+                    conv = true;
+                    break;
+                }
+            }
+            if (!conv) {
+                err = true;
+                return false;
+            }
+            if (sizeof(T) == 4) {
+                // grazing incidence: |d . N| < 0.05 |N| -> last step in FP64
+                const V3<T> x = p + t * d;
+                const T nx = -T(2) * x.x * slope, ny = -T(2) * x.y * slope;
+                const T dn = d.x * nx + d.y * ny + d.z;
+                if (dn * dn < T(0.0025) * (nx * nx + ny * ny + T(1))) {
+                    if (!newton_step_fp64(S, p, d, &t)) return false;
+                }
+            }
+            if (t <= eps || t > tmax) return false;
+            const V3<T> x = p + t * d;
+            T z;
+            if (!sag_slope(S, x.x * x.x + x.y * x.y, &z, &slope)) return false;
+            CNT(U_APERTURE);
+            if (!aperture_inside(S, ap, x.x, x.y)) return false;
+            h.t = t;
+            h.pl = x;
+            h.nl = unit(mk(-T(2) * x.x * slope, -T(2) * x.y * slope, T(1)));
+            return true;
+        }
+        if (t <= eps) continue;
+        if (t > tmax) return false;  // roots ascending: nothing nearer follows
+        CNT(U_APERTURE);
+        if (!aperture_inside(S, ap, q.x, q.y)) continue;
+        h.t = t;
+        h.pl = q;
+        h.nl = unit(mk(-c * q.x, -c * q.y, T(1) - c * k1 * q.z));
+        return true;
+    }
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool hit_cyl(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
+    const T rad = S[F_C], len = S[F_K1];
+    const T a = d.x * d.x + d.y * d.y;
+    if (a == T(0)) return false;
+    const T b = p.x * d.x + p.y * d.y;
+    const T g = p.x * p.x + p.y * p.y - rad * rad;
+    const T disc = b * b - a * g;
+    if (disc < T(0)) return false;
+    const T sq = t_sqrt(disc);
+    const T q = -(b + (b >= T(0) ? sq : -sq));
+    T r[2];
+    int nr;
+    if (q != T(0)) {
+        r[0] = t_min(q / a, g / q);
+        r[1] = t_max(q / a, g / q);
+        nr = 2;
+    } else {
+        r[0] = T(0);
+        nr = 1;
+    }
+    for (int i = 0; i < nr; ++i) {
+        const T t = r[i];
+        if (t <= eps) continue;
+        if (t > tmax) return false;
+        const V3<T> x = p + t * d;
+        if (x.z < T(0) || x.z > len) continue;
+        h.t = t;
+        h.pl = x;
+        h.nl = unit(mk(x.x, x.y, T(0)));
+        return true;
+    }
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool hit_box(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
+    const T pp[3] = {p.x, p.y, p.z}, dd[3] = {d.x, d.y, d.z};
+    T tn = -t_inf<T>(), tf = t_inf<T>();
+    int axn = -1, axf = -1;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const T hw = S[F_C + ax];
+        if (dd[ax] == T(0)) {
+            if (t_abs(pp[ax]) > hw) return false;
+            continue;
+        }
+        const T t1 = (-hw - pp[ax]) / dd[ax], t2 = (hw - pp[ax]) / dd[ax];
+        const T lo = t_min(t1, t2), hi = t_max(t1, t2);
+        if (lo > tn) {
+            tn = lo;
+            axn = ax;
+        }
+        if (hi < tf) {
+            tf = hi;
+            axf = ax;
+        }
+    }
+    if (tn > tf) return false;
+    T t;
+    int ax;
+    if (tn > eps) {
+        t = tn;
+        ax = axn;
+    } else if (tf > eps) {
+        t = tf;
+        ax = axf;
+    } else {
+        return false;
+    }
+    if (t > tmax) return false;
+    h.t = t;
+    h.pl = p + t * d;
+    const T comp = ax == 0 ? h.pl.x : (ax == 1 ? h.pl.y : h.pl.z);
+    const T s = comp >= T(0) ? T(1) : T(-1);
+    h.nl = mk(ax == 0 ? s : T(0), ax == 1 ? s : T(0), ax == 2 ? s : T(0));
+    return true;
+}
+
+// Hexagonal cone with a quadratic-Bezier wall profile (Sec. 2.2; the Winston
+// cone is the case whose control points lie on a parabola).  Wall j faces
+// u_j = (cos j pi/3, sin j pi/3); in its (q, z) half-plane the ray crosses
+// the profile where dz (r(u) - q0) - dq (z(u) - z0) = 0, a quadratic in u.
+template <typename T>
+__device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
+    const T ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
+    const T za0 = S[F_C + 3], za1 = S[F_C + 4], za2 = S[F_C + 5];
+    const T s60 = T(0.86602540378443864676);
+    const T cj[6] = {T(1), T(0.5), T(-0.5), T(-1), T(-0.5), T(0.5)};
+    const T sj[6] = {T(0), s60, s60, T(0), -s60, -s60};
+    bool found = false;
+    T best = tmax;
+    int bj = 0;
+    T bu = T(0);
+    for (int j = 0; j < 6; ++j) {
+        const T q0 = p.x * cj[j] + p.y * sj[j], dq = d.x * cj[j] + d.y * sj[j];
+        const T den = dq * dq + d.z * d.z;
+        if (den == T(0)) continue;
+        const T A = d.z * ra2 - dq * za2;
+        const T B = d.z * ra1 - dq * za1;
+        const T C = d.z * (ra0 - q0) - dq * (za0 - p.z);
+        T us[2];
+        int nu = 0;
+        if (A == T(0)) {
+            if (B != T(0)) us[nu++] = -C / B;
+        } else {
+            const T disc = B * B - T(4) * A * C;
+            if (disc >= T(0)) {
+                const T sq = t_sqrt(disc);
+                const T q = -T(0.5) * (B + (B >= T(0) ? sq : -sq));
+                if (q != T(0)) {
+                    us[nu++] = q / A;
+                    us[nu++] = C / q;
+                } else {
+                    us[nu++] = -B / (T(2) * A);
+                }
+            }
+        }
+        for (int i = 0; i < nu; ++i) {
+            T u = us[i];
+            const T gp = T(2) * A * u + B;
+            // one Newton polish of the root; in FP32 at grazing (|g'| small) it runs in FP64
+            if (sizeof(T) == 4 && t_abs(gp) < T(0.05) * (t_abs(B) + t_abs(A) + t_abs(C) + T(1e-30))) {
+                const double pj_c = (double)cj[j], pj_s = (double)sj[j];
+                const double q0d = (double)p.x * pj_c + (double)p.y * pj_s, dqd = (double)d.x * pj_c + (double)d.y * pj_s;
+                const double Ad = (double)d.z * (double)ra2 - dqd * (double)za2;
+                const double Bd = (double)d.z * (double)ra1 - dqd * (double)za1;
+                const double Cd = (double)d.z * ((double)ra0 - q0d) - dqd * ((double)za0 - (double)p.z);
+                const double ud = (double)u, gpd = 2.0 * Ad * ud + Bd;
+                if (gpd != 0.0) u = (T)(ud - ((Ad * ud + Bd) * ud + Cd) / gpd);
+            } else if (gp != T(0)) {
+                u -= ((A * u + B) * u + C) / gp;
+            }
+            if (u < T(0) || u > T(1)) continue;
+            const T R = ra0 + u * (ra1 + u * ra2);
+            const T Z = za0 + u * (za1 + u * za2);
+            const T t = ((R - q0) * dq + (Z - p.z) * d.z) / den;
+            if (t <= eps || t > best) continue;
+            if (found && !(t < best)) continue;
+            const V3<T> x = p + t * d;
+            const T qj = x.x * cj[j] + x.y * sj[j];
+            bool inwedge = true;
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+                if (m != j && x.x * cj[m] + x.y * sj[m] > qj) inwedge = false;
+            if (!inwedge) continue;
+            found = true;
+            best = t;
+            bj = j;
+            bu = u;
+            h.pl = x;
+        }
+    }
+    if (!found) return false;
+    const T Rp = ra1 + T(2) * ra2 * bu, Zp = za1 + T(2) * za2 * bu;
+    h.t = best;
+    h.nl = unit(mk(-Zp * cj[bj], -Zp * sj[bj], Rp));
+    return true;
+}
+
+template <typename T>
+struct Best {
+    T t;
+    int sid;
+    V3<T> pl;
+    V3<T> nl;
+    bool err;
+};
+
+template <bool C, typename T>
+__device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
+                                             unsigned* cnt) {
+    CNT(U_REBASE);
+    const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)sid * REC;
+    const int flags = tb.surf_i[sid].x;
+    const int shape = flags & 15;
+    const V3<T> pl = to_local_pt(S, p), dl = to_local_vec(S, d);
+    LHit<T> h;
+    bool ok = false, err = false;
+    switch (shape) {
+        case SHAPE_SAG:
+            ok = hit_sag<C>(S, (flags >> 8) & 15, (flags >> 12) & 1, pl, dl, eps, bst.t, tol, h, err, cnt);
+            break;
+        case SHAPE_CYL:
+            CNT(U_CYL);
+            ok = hit_cyl(S, pl, dl, eps, bst.t, h);
+            break;
+        case SHAPE_BOX:
+            CNT(U_BOX);
+            ok = hit_box(S, pl, dl, eps, bst.t, h);
+            break;
+        case SHAPE_HEXCONE:
+            if constexpr (C) cnt[U_HEXWALL] += 6u;
+            ok = hit_hexcone(S, pl, dl, eps, bst.t, h);
+            break;
+    }
+    if (err) bst.err = true;
+    // nearest t wins; an exact tie goes to the lower surface id
+    if (ok && (h.t < bst.t || (h.t == bst.t && sid < bst.sid))) {
+        bst.t = h.t;
+        bst.sid = sid;
+        bst.pl = h.pl;
+        bst.nl = h.nl;
+    }
+}
+
+// slab test against a float box; conservative boxes make the BVH result equal
+// to a brute-force scan over every surface
+__device__ __forceinline__ bool box_hit(const Node& nd, float ox, float oy, float oz, float ix, float iy, float iz,
+                                        float tmax) {
+    const float t0x = (nd.lo[0] - ox) * ix, t1x = (nd.hi[0] - ox) * ix;
+    const float t0y = (nd.lo[1] - oy) * iy, t1y = (nd.hi[1] - oy) * iy;
+    const float t0z = (nd.lo[2] - oz) * iz, t1z = (nd.hi[2] - oz) * iz;
+    const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+    const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    return tn <= tf;
+}
+
+constexpr int STACK = 32;
+
+template <bool C, typename T>
+__device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
+                                            bool& overflow, unsigned* cnt) {
+    bst.t = t_inf<T>();
+    bst.sid = 0x7fffffff;
+    bst.err = false;
+    const int4 vr = tb.variants[var];
+    for (int k = 0; k < vr.z; ++k) test_surface<C>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
+    if (vr.x < 0) return;
+    const float ox = (float)p.x, oy = (float)p.y, oz = (float)p.z;
+    const float ix = 1.0f / (float)d.x, iy = 1.0f / (float)d.y, iz = 1.0f / (float)d.z;
+    int stack[STACK];
+    int sp = 0;
+    int ni = vr.x;
+    // float bound of the current best t, rounded up so that no candidate is lost
+    auto tcap = [&]() -> float { return bst.t == t_inf<T>() ? 3.0e38f : (float)bst.t * 1.0001f + 1e-30f; };
+    CNT(U_AABB);
+    if (!box_hit(tb.nodes[ni], ox, oy, oz, ix, iy, iz, tcap())) return;
+    while (true) {
+        const Node nd = tb.nodes[ni];
+        if (nd.b > 0) {
+            for (int k = 0; k < nd.b; ++k) test_surface<C>(tb, tb.prims[nd.a + k], p, d, eps, tol, bst, cnt);
+        } else {
+            const float tc = tcap();
+            if constexpr (C) cnt[U_AABB] += 2u;
+            const bool h0 = box_hit(tb.nodes[nd.a], ox, oy, oz, ix, iy, iz, tc);
+            const bool h1 = box_hit(tb.nodes[nd.a + 1], ox, oy, oz, ix, iy, iz, tc);
+            if (h0 && h1) {
+                if (sp >= STACK) {
+                    overflow = true;
+                    return;
+                }
+                stack[sp++] = nd.a + 1;
+                ni = nd.a;
+                continue;
+            }
+            if (h0) {
+                ni = nd.a;
+                continue;
+            }
+            if (h1) {
+                ni = nd.a + 1;
+                continue;
+            }
+        }
+        if (sp == 0) break;
+        ni = stack[--sp];
+    }
+}
+
+// Reflectivity threshold floor(R(lambda) 2^32), R piecewise linear, evaluated
+// in FP64 with every operation rounded separately (no contraction) so that the
+// absorb decision is the same in both precisions and in the CPU reference.
+__device__ __forceinline__ unsigned long long refl_threshold(const double* M, double lam) {
+    const int n = (int)M[0];
+    const double* L = M + 1;
+    const double* R = M + 17;
+    double r;
+    if (n <= 1 || lam <= L[0]) {
+        r = R[0];
+    } else if (lam >= L[n - 1]) {
+        r = R[n - 1];
+    } else {
+        int i = 0;
+        while (i + 1 < n - 1 && lam >= L[i + 1]) ++i;
+        const double frac = __ddiv_rn(__dsub_rn(lam, L[i]), __dsub_rn(L[i + 1], L[i]));
+        r = __dadd_rn(R[i], __dmul_rn(__dsub_rn(R[i + 1], R[i]), frac));
+    }
+    const double thr = floor(__dmul_rn(r, 4294967296.0));
+    if (thr <= 0.0) return 0ull;
+    return (unsigned long long)thr;
+}
+
+template <typename T>
+__device__ __forceinline__ T refr_index(const double* Md, T lam_nm) {
+    if (Md[0] > 0.0) return (T)Md[0];
+    const T l = lam_nm * T(1e-3);
+    const T l2 = l * l;
+    T n2 = T(1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n2 += (T)Md[1 + i] * l2 / (l2 - (T)Md[4 + i]);
+    return t_sqrt(n2);
+}
+
+template <typename T>
+__device__ __forceinline__ T fresnel(T n1, T n2, T ci) {
+    const T eta = n1 / n2;
+    const T s2 = eta * eta * (T(1) - ci * ci);
+    if (s2 >= T(1)) return T(1);
+    const T ct = t_sqrt(T(1) - s2);
+    const T rs = (n1 * ci - n2 * ct) / (n1 * ci + n2 * ct);
+    const T rp = (n2 * ci - n1 * ct) / (n2 * ci + n1 * ct);
+    return T(0.5) * (rs * rs + rp * rp);
+}
+
+// ------------------------------------------------------------ the kernel
+template <typename T>
+struct Photon {
+    V3<T> p, d;
+    T lam;
+    long long i;  // local index, -1 = idle
+    int var;
+    int bounces;
+    int mat_cache;
+    int last;  // last surface hit, -1: none
+    unsigned long long thr;
+};
+
+template <typename T, int BLOCK, bool C = false>
+__global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
+    unsigned cnt[U_N];
+    if constexpr (C) {
+#pragma unroll
+        for (int k = 0; k < U_N; ++k) cnt[k] = 0u;
+    }
+    extern __shared__ __align__(16) unsigned char smem[];
+    Tables tb = A.tab;
+    if (A.stage) {
+        // stage every table in shared memory: surfaces, int records, nodes,
+        // prims, variants, unbounded lists, materials, media (16-byte chunks)
+        unsigned char* s = smem;
+        auto stage = [&](const void* src, size_t bytes) -> const void* {
+            const int4* from = reinterpret_cast<const int4*>(src);
+            int4* to = reinterpret_cast<int4*>(s);
+            const size_t n16 = (bytes + 15) / 16;
+            for (size_t k = threadIdx.x; k < n16; k += BLOCK) to[k] = from[k];
+            const void* r = s;
+            s += n16 * 16;
+            return r;
+        };
+        tb.surf = stage(tb.surf, (size_t)tb.n_surf * REC * sizeof(T));
+        tb.surf_i = reinterpret_cast<const int4*>(stage(tb.surf_i, (size_t)tb.n_surf * sizeof(int4)));
+        if (tb.n_nodes) tb.nodes = reinterpret_cast<const Node*>(stage(tb.nodes, (size_t)tb.n_nodes * sizeof(Node)));
+        if (tb.n_prims) tb.prims = reinterpret_cast<const int*>(stage(tb.prims, (size_t)tb.n_prims * sizeof(int)));
+        tb.variants = reinterpret_cast<const int4*>(stage(tb.variants, (size_t)tb.n_var * sizeof(int4)));
+        if (tb.n_glob) tb.glob = reinterpret_cast<const int*>(stage(tb.glob, (size_t)tb.n_glob * sizeof(int)));
+        if (tb.n_mat) tb.mats = reinterpret_cast<const double*>(stage(tb.mats, (size_t)tb.n_mat * MAT_REC * sizeof(double)));
+        if (tb.n_med) tb.meds = reinterpret_cast<const double*>(stage(tb.meds, (size_t)tb.n_med * MED_REC * sizeof(double)));
+        __syncthreads();
+    }
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint2 key = make_uint2((uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+    const long long n = A.n;
+
+    Photon<T> ph;
+    ph.i = -1;
+    bool done = false;
+    unsigned long long my_bounces = 0;
+    unsigned int my_status[7] = {0, 0, 0, 0, 0, 0, 0};
+
+    while (true) {
+        // refill idle lanes: one atomic per warp per round
+        const bool need = ph.i < 0 && !done;
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                const long long idx = (long long)base + __popc(m & lt_mask);
+                if (idx < n) {
+                    ph.i = idx;
+                    ph.p = mk(A.o[idx], A.o[n + idx], A.o[2 * n + idx]);
+                    ph.d = mk(A.d[idx], A.d[n + idx], A.d[2 * n + idx]);
+                    ph.lam = A.lam[idx];
+                    ph.var = A.vop ? A.vop[idx] : 0;
+                    ph.bounces = 0;
+                    ph.mat_cache = -1;
+                    ph.last = -1;
+                    ph.thr = 0;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (__all_sync(FULL, done)) break;
+        if (ph.i < 0) continue;
+
+        // ---- one bounce
+        int status = 0;
+        Best<T> bst;
+        bool overflow = false;
+        V3<T> fpos = mk(T(0), T(0), T(0));
+        const bool bad_var = ph.var < 0 || ph.var >= tb.n_var;  // never index past the variant table
+        if (!bad_var) nearest_hit<C>(tb, ph.var, ph.p, ph.d, A.eps, A.newton_tol, bst, overflow, cnt);
+        if (bad_var || overflow || bst.err) {
+            status = ST_ERROR;
+        } else if (bst.sid == 0x7fffffff) {
+            status = ST_ESCAPED;
+        } else {
+            ph.p = ph.p + bst.t * ph.d;
+            ph.last = bst.sid;
+            const long long pid = A.first_id + ph.i;
+            const uint4 w = philox4x32_10(
+                make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)ph.bounces, 0u), key);
+            ph.bounces += 1;
+            CNT(U_PHILOX);
+            const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)bst.sid * REC;
+            const int4 si = tb.surf_i[bst.sid];
+            const int role = (si.x >> 4) & 15;
+            const V3<T> n = unit(to_world_vec(S, bst.nl));
+            const bool front = dot(ph.d, n) < T(0);
+            if (role == ROLE_OBSC) {
+                status = ST_OBSCURED;
+            } else if (role == ROLE_FOCAL) {
+                if (front) {
+                    status = ST_DETECTED;
+                    fpos = bst.pl;
+                } else {
+                    status = ST_OBSCURED;
+                }
+            } else if (role == ROLE_MIRROR) {
+                if (!front) {
+                    status = ST_OBSCURED;
+                } else {
+                    const double* M = tb.mats + (size_t)si.y * MAT_REC;
+                    if (si.y != ph.mat_cache) {
+                        ph.thr = refl_threshold(M, (double)ph.lam);
+                        ph.mat_cache = si.y;
+                    }
+                    if (!((unsigned long long)w.x < ph.thr)) {
+                        status = ST_ABSORBED;
+                    } else {
+                        V3<T> nn = n;
+                        const T sigma = (T)M[33];
+                        if (sigma > T(0)) {
+                            CNT(U_ROUGH);
+                            const T u1 = unit_open<T>(w.y), u2 = unit_open<T>(w.z);
+                            const T rad = t_sqrt(T(-2) * t_log(u1));
+                            T sn, cs;
+                            t_sincospi(T(2) * u2, &sn, &cs);
+                            const T g1 = rad * cs, g2 = rad * sn;
+                            // Duff et al. 2017 orthonormal basis around n
+                            const T sgn = n.z >= T(0) ? T(1) : T(-1);
+                            const T aa = T(-1) / (sgn + n.z);
+                            const T bb = n.x * n.y * aa;
+                            const V3<T> tt = mk(T(1) + sgn * n.x * n.x * aa, sgn * bb, -sgn * n.x);
+                            const V3<T> bv = mk(bb, sgn + n.y * n.y * aa, -n.y);
+                            nn = unit(n + (sigma * g1) * tt + (sigma * g2) * bv);
+                        }
+                        ph.d = unit(ph.d - (T(2) * dot(ph.d, nn)) * nn);
+                        CNT(U_REFLECT);
+                    }
+                }
+            } else {  // ROLE_REFRACT: Snell + unpolarised Fresnel
+                const T na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, ph.lam);
+                const T nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, ph.lam);
+                const T n1 = front ? na : nb, n2 = front ? nb : na;
+                const V3<T> nf = front ? n : T(-1) * n;
+                const T ci = -dot(ph.d, nf);
+                const T R = fresnel(n1, n2, ci);
+                CNT(U_REFRACT);
+                if (unit_open<T>(w.x) < R) {
+                    ph.d = unit(ph.d - (T(2) * dot(ph.d, nf)) * nf);
+                    CNT(U_REFLECT);
+                } else {
+                    const T eta = n1 / n2;
+                    const T s2 = eta * eta * (T(1) - ci * ci);
+                    const T ct = t_sqrt(T(1) - s2);
+                    ph.d = unit(eta * ph.d + (eta * ci - ct) * nf);
+                }
+            }
+            if (status == 0 && !(t_finite(ph.d.x) && t_finite(ph.d.y) && t_finite(ph.d.z))) status = ST_ERROR;
+            if (status == 0 && ph.bounces >= A.max_bounces) status = ST_MAXB;
+        }
+        if (status == 0) continue;
+        // ---- photon finished: store (SoA)
+        const long long i = ph.i;
+        if (A.st) A.st[i] = (uint8_t)status;
+        if (A.nb) A.nb[i] = (uint8_t)ph.bounces;
+        if (A.hit) {
+            A.hit[i] = ph.p.x;
+            A.hit[n + i] = ph.p.y;
+            A.hit[2 * n + i] = ph.p.z;
+        }
+        if (A.dir) {
+            A.dir[i] = ph.d.x;
+            A.dir[n + i] = ph.d.y;
+            A.dir[2 * n + i] = ph.d.z;
+        }
+        if (A.fxy) {
+            A.fxy[i] = fpos.x;
+            A.fxy[n + i] = fpos.y;
+        }
+        if (A.last) A.last[i] = ph.last;
+        my_bounces += (unsigned long long)ph.bounces;
+        my_status[status] += 1u;
+        ph.i = -1;
+    }
+    if constexpr (C) {
+        // per-thread unit counts -> warp sums -> one atomic per warp and unit
+#pragma unroll
+        for (int k = 0; k < U_N; ++k) {
+            const unsigned v = __reduce_add_sync(FULL, cnt[k]);
+            if (lane == 0 && v) atomicAdd(A.units + k, (unsigned long long)v);
+        }
+    }
+    // warp-aggregated counters
+    if (A.counters) {
+        unsigned long long b = my_bounces;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) b += __shfl_xor_sync(FULL, b, off);
+        unsigned int tot = 0;
+        unsigned int sc[7];
+#pragma unroll
+        for (int k = 1; k < 7; ++k) {
+            sc[k] = __reduce_add_sync(FULL, my_status[k]);
+            tot += sc[k];
+        }
+        if (lane == 0) {
+            if (b) atomicAdd(A.counters + 0, b);
+#pragma unroll
+            for (int k = 1; k < 7; ++k)
+                if (sc[k]) atomicAdd(A.counters + k, (unsigned long long)sc[k]);
+            if (tot) atomicAdd(A.counters + 7, (unsigned long long)tot);
+        }
+    }
+}
+
+}  // namespace robast

@@ -1,0 +1,47 @@
+// float instantiations of the persistent trace kernel (see trace.cuh).
+#include "launch.h"
+
+namespace robast {
+
+template <int BLOCK, bool C = false>
+static cudaError_t launch_one(const TraceArgs<float>& a, int grid, size_t smem, cudaStream_t s) {
+    auto k = trace_kernel<float, BLOCK, C>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int BLOCK>
+static int occupancy_one(size_t smem) {
+    auto k = trace_kernel<float, BLOCK>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, BLOCK, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+int trace_blocks_per_sm_f32(int block, size_t smem) {
+    switch (block) {
+        case 64: return occupancy_one<64>(smem);
+        case 128: return occupancy_one<128>(smem);
+        case 256: return occupancy_one<256>(smem);
+    }
+    return 0;
+}
+
+cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s) {
+    if (a.units) return block == 128 ? launch_one<128, true>(a, grid, smem, s) : cudaErrorInvalidConfiguration;
+    switch (block) {
+        case 64: return launch_one<64>(a, grid, smem, s);
+        case 128: return launch_one<128>(a, grid, smem, s);
+        case 256: return launch_one<256>(a, grid, smem, s);
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace robast

@@ -1,0 +1,226 @@
+"""GPU trace (through the C ABI) against the FP64 oracle, photon by photon.
+
+Sizes here are ones the oracle finishes in seconds but that still span many
+blocks and warps of the persistent launch and end in a ragged tail (photon
+counts are not multiples of 32 or of the block size).  Full-size launches are
+checked on sampled contiguous photon-id windows (test_gpu_fullsize.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import metrics
+
+from parity import compare, oracle_for, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+robast = pytest.importorskip("paper_1508_07803_gb300")
+
+
+def _dev(bundle, precision):
+    dt = torch.float32 if precision == 32 else torch.float64
+    b = bundle if precision == 64 else bundle.rounded_to(np.float32)
+    return (torch.from_numpy(b.origins).to("cuda", dt), torch.from_numpy(b.dirs).to("cuda", dt),
+            torch.from_numpy(b.wavelengths).to("cuda", dt))
+
+
+def _run(scene, bundle, precision, seed, **kw):
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(bundle, precision)
+    out = robast.trace(geom, o, d, w, seed=seed, precision=precision, **kw)
+    torch.cuda.synchronize()
+    res = to_numpy(out)
+    geom.close()
+    return res
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    robast.load()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_sphere_parity(precision):
+    scene, b = W.sphere_workload(100_003, seed=0)
+    g = _run(scene, b, precision, seed=0)
+    r = oracle_for(scene, b, precision, seed=0)
+    rep = compare(g, r, precision, scene.focal_length, f"sphere fp{precision}")
+    print(rep)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_lst_parity(precision):
+    scene, b = W.lst_workload(6_001, seed=3)
+    g = _run(scene, b, precision, seed=11)
+    r = oracle_for(scene, b, precision, seed=11)
+    print(compare(g, r, precision, scene.focal_length, f"lst fp{precision}"))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_sct_parity(precision):
+    scene, b = W.sct_workload(2_501, seed=5)
+    g = _run(scene, b, precision, seed=2)
+    r = oracle_for(scene, b, precision, seed=2)
+    print(compare(g, r, precision, scene.focal_length, f"sct fp{precision}"))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_cone_parity(precision):
+    scene = W.cone_scene()
+    H = W.cone_heights(1)[0]
+    bs = [W.hexagon_bundle(2_003, W.CONE_A_IN, H + W.CONE_WINDOW + 1e-4, math.radians(a), seed=9, stream=300 + k)
+          for k, a in enumerate((0, 15, 25, 32, 40))]
+    b = W.concat(bs)
+    g = _run(scene, b, precision, seed=4, max_bounces=30)
+    r = oracle_for(scene, b, precision, seed=4, max_bounces=30)
+    print(compare(g, r, precision, scene.focal_length, f"cone fp{precision}"))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batched_variants_parity(precision):
+    nv = 8
+    scene = W.cone_scene(n_variants=nv, seed=1)
+    Hs = W.cone_heights(nv, seed=1)
+    bs, vop = [], []
+    for v in range(nv):
+        b = W.hexagon_bundle(777 + 13 * v, W.CONE_A_IN, Hs[v] + W.CONE_WINDOW + 1e-4, math.radians(5 * v), seed=v,
+                             stream=400 + v)
+        bs.append(b)
+        vop.append(np.full(b.n, v, np.int32))
+    b = W.concat(bs)
+    vop = np.concatenate(vop)
+    # shuffle so that one warp mixes variants
+    perm = np.random.default_rng(0).permutation(b.n)
+    b = W.Bundle(np.ascontiguousarray(b.origins[:, perm]), np.ascontiguousarray(b.dirs[:, perm]),
+                 b.wavelengths[perm].copy())
+    vop = vop[perm].copy()
+    g = _run(scene, b, precision, seed=6, max_bounces=30, variant_of_photon=torch.from_numpy(vop).cuda())
+    r = oracle_for(scene, b, precision, seed=6, max_bounces=30, variant_of_photon=vop)
+    print(compare(g, r, precision, scene.focal_length, f"batched fp{precision}"))
+
+
+def test_ideal_winston_cutoff_on_gpu():
+    P0, P1, P2 = W.winston_profile()
+    surfs = [W.Surface("sag", "focal", "hexagon", ap=(W.CONE_A_OUT, 0, 0, 0)),
+             W.Surface("hexcone", "mirror", material=0, prm=(P0[0], P0[1], P1[0], P1[1], P2[0], P2[1], 0, 0))]
+    scene = W.Scene("w2d", surfs, [W.Material([400.0], [1.0])], [W.Medium()], 0.1, 0.05)
+    m = 4001
+    for theta, exp in ((10.0, 1.0), (29.5, 1.0), (30.5, 0.0), (40.0, 0.0)):
+        th = math.radians(theta)
+        x = np.linspace(-W.CONE_A_IN * 0.999, W.CONE_A_IN * 0.999, m)
+        o = np.stack([x, np.zeros(m), np.full(m, P2[1] + 1e-9)])
+        d = np.repeat(np.array([[math.sin(th)], [0.0], [-math.cos(th)]]), m, axis=1)
+        b = W.Bundle(o, d, np.full(m, 400.0))
+        g = _run(scene, b, 64, seed=0, max_bounces=50)
+        assert (g["status"] == W.DETECTED).mean() == exp
+
+
+def test_photon_ids_make_results_independent_of_launch_shape():
+    scene, b = W.lst_workload(3_000, seed=8, angles_deg=(1.0,))
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 32)
+    ref = to_numpy(robast.trace(geom, o, d, w, seed=3, block_size=128))
+    for bs, bps in ((64, 1), (256, 0), (128, 2)):
+        got = to_numpy(robast.trace(geom, o, d, w, seed=3, block_size=bs, blocks_per_sm=bps))
+        for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy"):
+            assert np.array_equal(ref[k], got[k]), (bs, k)
+    # a sub-range traced alone with first_photon_id equals the same photons of the full run
+    lo, hi = 1234, 2345
+    sub = to_numpy(robast.trace(geom, o[:, lo:hi].contiguous(), d[:, lo:hi].contiguous(), w[lo:hi].contiguous(),
+                                seed=3, first_photon_id=lo))
+    for k in ("status", "bounces", "last_surface"):
+        assert np.array_equal(sub[k], ref[k][..., lo:hi])
+    assert np.array_equal(sub["hit"], ref["hit"][:, lo:hi])
+    geom.close()
+
+
+def test_counters_match_outputs():
+    scene, b = W.lst_workload(2_000, seed=2)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 32)
+    out = robast.trace(geom, o, d, w, seed=1)
+    torch.cuda.synchronize()
+    c = out["counters"].cpu().numpy()
+    st = out["status"].cpu().numpy()
+    nb = out["bounces"].cpu().numpy().astype(np.int64)
+    assert c[0] == nb.sum()
+    for k in range(1, 7):
+        assert c[k] == (st == k).sum()
+    assert c[7] == st.shape[0]
+    geom.close()
+
+
+def test_empty_and_single_photon():
+    scene, b = W.sphere_workload(1, seed=0)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 64)
+    out = robast.trace(geom, o[:, :0].contiguous(), d[:, :0].contiguous(), w[:0].contiguous(), precision=64)
+    assert out["status"].numel() == 0
+    out = to_numpy(robast.trace(geom, o, d, w, precision=64, seed=5))
+    ref = oracle.trace(scene, b, seed=5)
+    assert out["status"][0] == ref["status"][0]
+    geom.close()
+
+
+def test_max_bounces_and_error_statuses_are_reported_not_raised():
+    lo = W.Surface("sag", "mirror", "circle", ap=(1.0, 0, 0, 0))
+    hi = W.Surface("sag", "mirror", "circle", origin=(0, 0, 1.0), rot=W.FACING_DOWN, ap=(1.0, 0, 0, 0))
+    scene = W.Scene("cavity", [lo, hi], [W.Material([400.0], [1.0])], [W.Medium()], 2.0, 1.0)
+    o = np.array([[0.0], [0.0], [0.5]])
+    dd = np.array([[1e-3], [0.0], [-1.0]])
+    dd /= np.linalg.norm(dd)
+    b = W.Bundle(o, dd, np.array([400.0]))
+    g = _run(scene, b, 64, seed=0, max_bounces=17)
+    assert g["status"][0] == W.MAX_BOUNCES and g["bounces"][0] == 17
+
+
+def test_psf_reduction_matches_oracle_metrics():
+    scene, b = W.lst_workload(20_000, seed=4, angles_deg=(1.0,))
+    geom = robast.build_geometry(scene)
+    for precision in (64, 32):
+        o, d, w = _dev(b, precision)
+        out = robast.trace(geom, o, d, w, seed=9, precision=precision)
+        n_det, cx, cy, r80 = robast.psf(geom, out["status"], out["focal_xy"], precision=precision)
+        g = to_numpy(out)
+        exact = metrics.psf(g["status"], g["focal_xy"])
+        assert n_det == exact["n_detected"]
+        assert abs(cx - exact["cx"]) < 1e-12 and abs(cy - exact["cy"]) < 1e-12
+        assert r80 == pytest.approx(exact["r80"], rel=1e-12)
+        ref = oracle_for(scene, b, precision, seed=9)
+        want = metrics.psf(ref["status"], ref["focal_xy"])
+        assert r80 == pytest.approx(want["r80"], rel=1e-3)
+        ce_g = (g["status"] == W.DETECTED).mean()
+        ce_r = (ref["status"] == W.DETECTED).mean()
+        assert abs(ce_g - ce_r) <= 1e-3 * ce_r
+    geom.close()
+
+
+def test_host_buffer_entry_point_equals_device_entry_point():
+    scene, b = W.lst_workload(3_001, seed=6, angles_deg=(0.5,))
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 32)
+    dev = to_numpy(robast.trace(geom, o, d, w, seed=2))
+    host = robast.trace_host(geom, o.cpu().pin_memory(), d.cpu().pin_memory(), w.cpu().pin_memory(), seed=2)
+    for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy"):
+        assert np.array_equal(dev[k], host[k].numpy()), k
+    geom.close()
+
+
+def test_bad_arguments_raise():
+    scene, b = W.sphere_workload(100, seed=0)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 64)
+    with pytest.raises(robast.RobastError):
+        robast.trace(geom, o, d, w, precision=32)  # dtype mismatch caught by the binding
+    with pytest.raises(robast.RobastError, match="max_bounces"):
+        robast.trace(geom, o, d, w, precision=64, max_bounces=300)
+    with pytest.raises(robast.RobastError, match="block_size"):
+        robast.trace(geom, o, d, w, precision=64, block_size=96)
+    geom.close()
