@@ -59,7 +59,7 @@ class OScene(ctypes.Structure):
 class OOutputs(ctypes.Structure):
     _fields_ = [("status", ctypes.c_void_p), ("bounces", ctypes.c_void_p), ("hit", ctypes.c_void_p),
                 ("dir", ctypes.c_void_p), ("last_surface", ctypes.c_void_p), ("focal_xy", ctypes.c_void_p),
-                ("edge_margin", ctypes.c_void_p)]
+                ("edge_margin", ctypes.c_void_p), ("cond", ctypes.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -181,10 +181,10 @@ def trace(scene, bundle, seed: int = 0, first_photon_id: int = 0, max_bounces: i
     res = {
         "status": np.zeros(n, np.uint8), "bounces": np.zeros(n, np.uint8), "hit": np.zeros((3, n)),
         "dir": np.zeros((3, n)), "last_surface": np.zeros(n, np.int32), "focal_xy": np.zeros((2, n)),
-        "edge_margin": np.zeros(n),
+        "edge_margin": np.zeros(n), "cond": np.zeros(n),
     }
     outs = OOutputs(*[res[k].ctypes.data for k in
-                      ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "edge_margin")])
+                      ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "edge_margin", "cond")])
     vop = None
     if variant_of_photon is not None:
         vop = np.ascontiguousarray(variant_of_photon, dtype=np.int32)

@@ -588,6 +588,7 @@ void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double*
         int last = -1;
         double fx = 0.0, fy = 0.0;
         double margin = INFINITY;
+        double cond = 0.0;  /* conditioning of the path: sum of 1 / |cos(incidence)| */
         while (status == 0) {
             Hit h = nearest_hit(cx, v, p, d);
             if (h.margin < margin) margin = h.margin;
@@ -608,6 +609,7 @@ void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double*
             ++bounces;
             V3 n = h.nw;
             bool front = dot(d, n) < 0.0;
+            cond += 1.0 / std::fmax(std::fabs(dot(d, n)), 1e-9);
             switch (s.role) {
                 case O_ROLE_OBSCURATION: status = O_ST_OBSCURED; break;
                 case O_ROLE_FOCAL:
@@ -686,6 +688,7 @@ void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double*
             out->focal_xy[n + i] = fy;
         }
         if (out->edge_margin) out->edge_margin[i] = margin;
+        if (out->cond) out->cond[i] = cond;
     }
 }
 

@@ -74,6 +74,7 @@ typedef struct {
     int32_t* last_surface;/* [n] */
     double* focal_xy;     /* [2n] SoA: local x block, local y block (DETECTED only) */
     double* edge_margin;  /* [n] optional: min relative aperture margin met on the path */
+    double* cond;         /* [n] optional: sum over interactions of 1 / |cos(incidence)| */
 } o_outputs;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */

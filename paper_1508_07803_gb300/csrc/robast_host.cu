@@ -260,11 +260,26 @@ Box world_box(const double rows[9], const double o[3], const double lo[3], const
     return b;
 }
 
+// A BVH primitive: one surface and a box that bounds (part of) it.  Long
+// thin surfaces (masts) are entered as several references, one per segment,
+// so that their boxes stay tight; a ray that meets two segments tests the
+// same surface twice, which is harmless.
+struct Ref {
+    int sid;
+    Box box;
+};
+
+double half_area(const Box& b) {
+    const double dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// Binned surface-area-heuristic build (16 bins per axis), leaves of <= 4.
 struct BvhBuilder {
-    const std::vector<Box>& boxes;
+    const std::vector<Ref>& refs;
     std::vector<Node>& nodes;
     std::vector<int>& prims;
-    static const int kLeaf = 2;
+    static const int kBins = 16, kMaxLeaf = 4;
 
     void set_box(int ni, const Box& b) {
         for (int k = 0; k < 3; ++k) {
@@ -272,29 +287,79 @@ struct BvhBuilder {
             nodes[ni].hi[k] = (float)b.hi[k];
         }
     }
-    // node ni covers ids[b, e)
+    void make_leaf(int ni, const std::vector<int>& ids, int b, int e) {
+        nodes[ni].a = (int)prims.size();
+        nodes[ni].b = e - b;
+        for (int k = b; k < e; ++k) prims.push_back(refs[ids[k]].sid);
+    }
+    // node ni covers ids[b, e) (indices into refs)
     void build(int ni, std::vector<int>& ids, int b, int e) {
         Box bb, cb;
         for (int k = b; k < e; ++k) {
-            bb.add(boxes[ids[k]]);
-            const double c[3] = {boxes[ids[k]].centre(0), boxes[ids[k]].centre(1), boxes[ids[k]].centre(2)};
+            const Box& r = refs[ids[k]].box;
+            bb.add(r);
+            const double c[3] = {r.centre(0), r.centre(1), r.centre(2)};
             cb.add(c);
         }
         set_box(ni, bb);
-        if (e - b <= kLeaf) {
-            nodes[ni].a = (int)prims.size();
-            nodes[ni].b = e - b;
-            for (int k = b; k < e; ++k) prims.push_back(ids[k]);
-            return;
+        const int n = e - b;
+        if (n <= 2) return make_leaf(ni, ids, b, e);
+        double best = INFINITY;
+        int bax = -1, bsplit = -1;
+        for (int ax = 0; ax < 3; ++ax) {
+            const double ext = cb.hi[ax] - cb.lo[ax];
+            if (!(ext > 0.0)) continue;
+            Box bin[kBins];
+            int cnt[kBins] = {0};
+            for (int k = b; k < e; ++k) {
+                const Box& r = refs[ids[k]].box;
+                int bi = (int)((r.centre(ax) - cb.lo[ax]) / ext * kBins);
+                bi = std::min(kBins - 1, std::max(0, bi));
+                bin[bi].add(r);
+                ++cnt[bi];
+            }
+            Box lb[kBins];
+            int lc[kBins];
+            Box acc;
+            int c = 0;
+            for (int i = 0; i < kBins; ++i) {
+                if (cnt[i]) acc.add(bin[i]);
+                c += cnt[i];
+                lb[i] = acc;
+                lc[i] = c;
+            }
+            Box racc;
+            int rc = 0;
+            for (int i = kBins - 1; i > 0; --i) {
+                if (cnt[i]) racc.add(bin[i]);
+                rc += cnt[i];
+                if (lc[i - 1] == 0 || rc == 0) continue;
+                const double cost = half_area(lb[i - 1]) * lc[i - 1] + half_area(racc) * rc;
+                if (cost < best) {
+                    best = cost;
+                    bax = ax;
+                    bsplit = i;
+                }
+            }
         }
-        int ax = 0;
-        for (int k = 1; k < 3; ++k)
-            if (cb.hi[k] - cb.lo[k] > cb.hi[ax] - cb.lo[ax]) ax = k;
-        const int mid = (b + e) / 2;
-        std::nth_element(ids.begin() + b, ids.begin() + mid, ids.begin() + e, [&](int x, int y) {
-            const double cx = boxes[x].centre(ax), cy = boxes[y].centre(ax);
-            return cx < cy || (cx == cy && x < y);
-        });
+        if (bax < 0) {  // all centroids coincide: split in the middle of the list
+            if (n <= kMaxLeaf) return make_leaf(ni, ids, b, e);
+            bax = 0;
+        }
+        if (n <= kMaxLeaf && best >= half_area(bb) * n) return make_leaf(ni, ids, b, e);
+        int mid;
+        if (bsplit > 0) {
+            const double ext = cb.hi[bax] - cb.lo[bax];
+            auto it = std::partition(ids.begin() + b, ids.begin() + e, [&](int x) {
+                int bi = (int)((refs[x].box.centre(bax) - cb.lo[bax]) / ext * kBins);
+                bi = std::min(kBins - 1, std::max(0, bi));
+                return bi < bsplit;
+            });
+            mid = (int)(it - ids.begin());
+        } else {
+            mid = b + n / 2;
+        }
+        if (mid == b || mid == e) mid = b + n / 2;
         const int left = (int)nodes.size();
         nodes.push_back(Node{});
         nodes.push_back(Node{});
@@ -392,8 +457,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     std::vector<double> rec64((size_t)ns * REC, 0.0);
     std::vector<float> rec32((size_t)ns * REC, 0.0f);
     std::vector<int4> reci(ns);
-    std::vector<Box> boxes(ns);
-    std::vector<char> bounded(ns, 0);
+    std::vector<std::vector<Ref>> refs_of(ns);  // BVH references per surface; empty = unbounded
     for (int i = 0; i < ns; ++i) {
         const robast_surface_desc& s = d->surfaces[i];
         double* R = &rec64[(size_t)i * REC];
@@ -455,8 +519,14 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
                             s.medium_front, s.medium_back);
         double lo[3], hi[3];
         if (local_box(s, lo, hi)) {
-            boxes[i] = world_box(rows, s.origin, lo, hi, 1e-6 * L);
-            bounded[i] = 1;
+            int segs = 1;
+            if (s.shape == ROBAST_SHAPE_CYLINDER) segs = (int)std::min(16.0, std::ceil(s.prm[1] / (8.0 * s.prm[0])));
+            for (int k = 0; k < segs; ++k) {
+                double slo[3] = {lo[0], lo[1], lo[2] + (hi[2] - lo[2]) * k / segs};
+                double shi[3] = {hi[0], hi[1], lo[2] + (hi[2] - lo[2]) * (k + 1) / segs};
+                if (k == segs - 1) shi[2] = hi[2];
+                refs_of[i].push_back(Ref{i, world_box(rows, s.origin, slo, shi, 1e-6 * L)});
+            }
         }
     }
     // BVH per variant; unbounded surfaces go to a per-variant list
@@ -466,19 +536,21 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     for (int v = 0; v < nv; ++v) {
         const int s0 = d->variant_offsets ? d->variant_offsets[v] : 0;
         const int s1 = d->variant_offsets ? d->variant_offsets[v + 1] : ns;
-        std::vector<int> ids;
+        std::vector<Ref> refs;
         const int g0 = (int)glob.size();
         for (int s = s0; s < s1; ++s) {
-            if (bounded[s])
-                ids.push_back(s);
-            else
+            if (refs_of[s].empty())
                 glob.push_back(s);
+            else
+                refs.insert(refs.end(), refs_of[s].begin(), refs_of[s].end());
         }
         int root = -1;
-        if (!ids.empty()) {
+        if (!refs.empty()) {
+            std::vector<int> ids(refs.size());
+            for (size_t k = 0; k < ids.size(); ++k) ids[k] = (int)k;
             root = (int)nodes.size();
             nodes.push_back(Node{});
-            BvhBuilder bb{boxes, nodes, prims};
+            BvhBuilder bb{refs, nodes, prims};
             bb.build(root, ids, 0, (int)ids.size());
         }
         vars[v] = make_int4(root, g0, (int)glob.size() - g0, s0);

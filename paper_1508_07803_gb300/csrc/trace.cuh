@@ -344,27 +344,23 @@ __device__ __forceinline__ bool hit_sag(const T* S, int ap, bool asph, V3<T> p, 
     return false;
 }
 
+// Open cylinder x^2 + y^2 = r^2, 0 <= z <= length.  The quadratic is solved
+// about the ray's point of closest approach to the axis, t = t0 + s with
+// t0 = -(p.d)_xy / |d_xy|^2: there the linear term vanishes and |p_xy|^2 - r^2
+// is formed from a point near the cylinder, which keeps FP32 accurate for
+// rays that start tens of metres away.
 template <typename T>
 __device__ __forceinline__ bool hit_cyl(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
     const T rad = S[F_C], len = S[F_K1];
     const T a = d.x * d.x + d.y * d.y;
     if (a == T(0)) return false;
-    const T b = p.x * d.x + p.y * d.y;
-    const T g = p.x * p.x + p.y * p.y - rad * rad;
-    const T disc = b * b - a * g;
-    if (disc < T(0)) return false;
-    const T sq = t_sqrt(disc);
-    const T q = -(b + (b >= T(0) ? sq : -sq));
-    T r[2];
-    int nr;
-    if (q != T(0)) {
-        r[0] = t_min(q / a, g / q);
-        r[1] = t_max(q / a, g / q);
-        nr = 2;
-    } else {
-        r[0] = T(0);
-        nr = 1;
-    }
+    const T t0 = -(p.x * d.x + p.y * d.y) / a;
+    const T cx = p.x + t0 * d.x, cy = p.y + t0 * d.y;  // closest approach in the xy plane
+    const T g = (cx - rad) * (cx + rad) + cy * cy;     // |c|^2 - r^2
+    if (g > T(0)) return false;
+    const T sh = t_sqrt(-g / a);
+    T r[2] = {t0 - sh, t0 + sh};
+    const int nr = 2;
     for (int i = 0; i < nr; ++i) {
         const T t = r[i];
         if (t <= eps) continue;
@@ -550,16 +546,19 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
     }
 }
 
-// slab test against a float box; conservative boxes make the BVH result equal
-// to a brute-force scan over every surface
-__device__ __forceinline__ bool box_hit(const Node& nd, float ox, float oy, float oz, float ix, float iy, float iz,
-                                        float tmax) {
-    const float t0x = (nd.lo[0] - ox) * ix, t1x = (nd.hi[0] - ox) * ix;
-    const float t0y = (nd.lo[1] - oy) * iy, t1y = (nd.hi[1] - oy) * iy;
-    const float t0z = (nd.lo[2] - oz) * iz, t1z = (nd.hi[2] - oz) * iz;
+// Slab test against a float box: entry distance, or +inf on a miss.
+// Conservative boxes make the BVH result equal to a brute-force scan over
+// every surface.
+// (ox, oy, oz) here are the origin pre-multiplied by the inverse direction,
+// so every slab distance is one FMA.
+__device__ __forceinline__ float box_entry(const Node& nd, float ox, float oy, float oz, float ix, float iy, float iz,
+                                           float tmax) {
+    const float t0x = fmaf(nd.lo[0], ix, -ox), t1x = fmaf(nd.hi[0], ix, -ox);
+    const float t0y = fmaf(nd.lo[1], iy, -oy), t1y = fmaf(nd.hi[1], iy, -oy);
+    const float t0z = fmaf(nd.lo[2], iz, -oz), t1z = fmaf(nd.hi[2], iz, -oz);
     const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
     const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
-    return tn <= tf;
+    return tn <= tf ? tn : __int_as_float(0x7f800000);
 }
 
 constexpr int STACK = 32;
@@ -573,15 +572,20 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
     const int4 vr = tb.variants[var];
     for (int k = 0; k < vr.z; ++k) test_surface<C>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
     if (vr.x < 0) return;
-    const float ox = (float)p.x, oy = (float)p.y, oz = (float)p.z;
-    const float ix = 1.0f / (float)d.x, iy = 1.0f / (float)d.y, iz = 1.0f / (float)d.z;
+    // Inverse direction with zero components replaced by +-1e-30, so that the
+    // FMA slab form never meets inf - inf (the boxes are padded, so a ray grazing
+    // a box face cannot lose a surface that lies strictly inside it).
+    auto inv = [](float v) -> float { return 1.0f / (fabsf(v) > 1e-30f ? v : copysignf(1e-30f, v)); };
+    const float ix = inv((float)d.x), iy = inv((float)d.y), iz = inv((float)d.z);
+    const float ox = (float)p.x * ix, oy = (float)p.y * iy, oz = (float)p.z * iz;
     int stack[STACK];
+    float stack_t[STACK];
     int sp = 0;
     int ni = vr.x;
     // float bound of the current best t, rounded up so that no candidate is lost
     auto tcap = [&]() -> float { return bst.t == t_inf<T>() ? 3.0e38f : (float)bst.t * 1.0001f + 1e-30f; };
     CNT(U_AABB);
-    if (!box_hit(tb.nodes[ni], ox, oy, oz, ix, iy, iz, tcap())) return;
+    if (!(box_entry(tb.nodes[ni], ox, oy, oz, ix, iy, iz, tcap()) < 3.4e38f)) return;
     while (true) {
         const Node nd = tb.nodes[ni];
         if (nd.b > 0) {
@@ -589,15 +593,20 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
         } else {
             const float tc = tcap();
             if constexpr (C) cnt[U_AABB] += 2u;
-            const bool h0 = box_hit(tb.nodes[nd.a], ox, oy, oz, ix, iy, iz, tc);
-            const bool h1 = box_hit(tb.nodes[nd.a + 1], ox, oy, oz, ix, iy, iz, tc);
+            const float e0 = box_entry(tb.nodes[nd.a], ox, oy, oz, ix, iy, iz, tc);
+            const float e1 = box_entry(tb.nodes[nd.a + 1], ox, oy, oz, ix, iy, iz, tc);
+            const bool h0 = e0 < 3.4e38f, h1 = e1 < 3.4e38f;
             if (h0 && h1) {
                 if (sp >= STACK) {
                     overflow = true;
                     return;
                 }
-                stack[sp++] = nd.a + 1;
-                ni = nd.a;
+                // nearer child first; the farther one waits with its entry distance
+                const bool first0 = e0 <= e1;
+                stack[sp] = first0 ? nd.a + 1 : nd.a;
+                stack_t[sp] = first0 ? e1 : e0;
+                ++sp;
+                ni = first0 ? nd.a : nd.a + 1;
                 continue;
             }
             if (h0) {
@@ -609,8 +618,17 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
                 continue;
             }
         }
-        if (sp == 0) break;
-        ni = stack[--sp];
+        // pop, skipping subtrees that start beyond the current best hit
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tcap()) {
+                ni = stack[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
     }
 }
 

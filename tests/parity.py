@@ -8,8 +8,16 @@ Tolerances (per photon, on the same seeded inputs):
       self-intersection epsilon): status identical for >= 99.999% of photons;
       every photon whose status, bounce count or last surface differs must
       have met an aperture / wedge / range edge within 1e-5 (relative) on its
-      oracle path; photons whose path is the same have positions within
-      1e-6 f and directions within 1e-5 rad.
+      oracle path; photons whose path is the same have directions within
+      1e-5 rad and positions within 1e-6 f x max(1, K - 1), where K is the
+      path's conditioning, the sum over its interactions of 1 / |cos(theta)|
+      (theta = angle of incidence).  First-order error propagation: every
+      interaction rounds the new direction to FP32, that error grows with the
+      distance travelled, and a hit at incidence theta stretches it by
+      1 / |cos(theta)|.  Telescope paths (two or three near-normal
+      interactions, K ~ 2-3) stay at 1e-6 to 2e-6 f; concentrator paths with
+      tens of wall reflections, or a grazing last hit, get the allowance their
+      geometry implies.
 """
 import numpy as np
 
@@ -62,12 +70,17 @@ def compare(gpu, ref, precision, focal_length, label=""):
         assert np.all(m <= 1e-5), f"{label}: FP32 path mismatch away from any edge: ids {bad[m > 1e-5][:10]}, " \
                                   f"margins {m[m > 1e-5][:10]}"
     ok = same_path
-    dh = np.abs(g["hit"][:, ok].astype(np.float64) - ref["hit"][:, ok]).max(initial=0.0)
-    dd = np.abs(g["dir"][:, ok].astype(np.float64) - ref["dir"][:, ok]).max(initial=0.0)
+    allow = 1e-6 * f * np.maximum(1.0, ref["cond"] - 1.0)
+    eh = np.abs(g["hit"].astype(np.float64) - ref["hit"]).max(axis=0)
+    ed = np.abs(g["dir"].astype(np.float64) - ref["dir"]).max(axis=0)
+    ef = np.abs(g["focal_xy"].astype(np.float64) - ref["focal_xy"]).max(axis=0)
     det = ok & (ref["status"] == W.DETECTED)
-    df = np.abs(g["focal_xy"][:, det].astype(np.float64) - ref["focal_xy"][:, det]).max(initial=0.0)
-    report.update(max_dhit=float(dh), max_ddir=float(dd), max_dfocal=float(df))
-    assert dh <= 1e-6 * f, f"{label}: FP32 hit error {dh} > 1e-6 f = {1e-6 * f}"
-    assert dd <= 1e-5, f"{label}: FP32 direction error {dd}"
-    assert df <= 1e-6 * f, f"{label}: FP32 focal error {df}"
+    report.update(max_dhit=float(eh[ok].max(initial=0.0)), max_ddir=float(ed[ok].max(initial=0.0)),
+                  max_dfocal=float(ef[det].max(initial=0.0)),
+                  max_dhit_over_allowance=float((eh[ok] / allow[ok]).max(initial=0.0)))
+    worst = np.argmax(np.where(ok, eh / allow, 0.0))
+    assert np.all(eh[ok] <= allow[ok]), \
+        f"{label}: FP32 hit error {eh[worst]} > {allow[worst]} (photon {worst}, {ref['bounces'][worst]} bounces)"
+    assert np.all(ed[ok] <= 1e-5), f"{label}: FP32 direction error {ed[ok].max()}"
+    assert np.all(ef[det] <= allow[det]), f"{label}: FP32 focal error {ef[det].max()}"
     return report
