@@ -274,19 +274,21 @@ double half_area(const Box& b) {
     return dx * dy + dy * dz + dz * dx;
 }
 
+// Binary build node: box, and either children a, a + 1 (b == 0) or a leaf
+// with prims [a, a + b).
+struct BuildNode {
+    Box box;
+    int a = 0, b = 0;
+};
+
 // Binned surface-area-heuristic build (16 bins per axis), leaves of <= 4.
 struct BvhBuilder {
     const std::vector<Ref>& refs;
-    std::vector<Node>& nodes;
+    std::vector<BuildNode>& nodes;
     std::vector<int>& prims;
     static const int kBins = 16, kMaxLeaf = 4;
 
-    void set_box(int ni, const Box& b) {
-        for (int k = 0; k < 3; ++k) {
-            nodes[ni].lo[k] = (float)b.lo[k];
-            nodes[ni].hi[k] = (float)b.hi[k];
-        }
-    }
+    void set_box(int ni, const Box& b) { nodes[ni].box = b; }
     void make_leaf(int ni, const std::vector<int>& ids, int b, int e) {
         nodes[ni].a = (int)prims.size();
         nodes[ni].b = e - b;
@@ -361,14 +363,63 @@ struct BvhBuilder {
         }
         if (mid == b || mid == e) mid = b + n / 2;
         const int left = (int)nodes.size();
-        nodes.push_back(Node{});
-        nodes.push_back(Node{});
+        nodes.push_back(BuildNode{});
+        nodes.push_back(BuildNode{});
         nodes[ni].a = left;
         nodes[ni].b = 0;
         build(left, ids, b, mid);
         build(left + 1, ids, mid, e);
     }
 };
+
+// Convert the binary build into the device layout (each node carries both
+// children's boxes), preorder so that the root comes first.
+void emit_nodes(const std::vector<BuildNode>& bn, std::vector<Node>& out) {
+    auto child = [&](Node& nd, int k, int c, int ref_internal) {
+        float* lo = k == 0 ? nd.lo0 : nd.lo1;
+        float* hi = k == 0 ? nd.hi0 : nd.hi1;
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = (float)bn[c].box.lo[j];
+            hi[j] = (float)bn[c].box.hi[j];
+        }
+        int& ref = k == 0 ? nd.ref0 : nd.ref1;
+        int& n = k == 0 ? nd.n0 : nd.n1;
+        if (bn[c].b > 0) {
+            ref = bn[c].a;
+            n = bn[c].b;
+        } else {
+            ref = ref_internal;
+            n = 0;
+        }
+    };
+    const int base = (int)out.size();
+    if (bn[0].b > 0) {  // a single leaf: wrap it, the second child empty
+        Node nd{};
+        child(nd, 0, 0, -1);
+        nd.n1 = -1;
+        out.push_back(nd);
+        return;
+    }
+    // index map from build nodes (internal only) to output nodes
+    std::vector<int> map(bn.size(), -1), order;
+    std::vector<int> st{0};
+    while (!st.empty()) {
+        const int i = st.back();
+        st.pop_back();
+        map[i] = base + (int)order.size();
+        order.push_back(i);
+        for (int c : {bn[i].a + 1, bn[i].a})
+            if (bn[c].b == 0) st.push_back(c);
+    }
+    out.resize(base + order.size());
+    for (size_t k = 0; k < order.size(); ++k) {
+        const int i = order[k];
+        Node nd{};
+        child(nd, 0, bn[i].a, map[bn[i].a]);
+        child(nd, 1, bn[i].a + 1, map[bn[i].a + 1]);
+        out[base + k] = nd;
+    }
+}
 
 int validate(const robast_geom_desc* d) {
     if (!d) return fail(ROBAST_E_NULL, "robast_build_geometry: desc is NULL");
@@ -548,10 +599,11 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         if (!refs.empty()) {
             std::vector<int> ids(refs.size());
             for (size_t k = 0; k < ids.size(); ++k) ids[k] = (int)k;
+            std::vector<BuildNode> bn(1);
+            BvhBuilder bb{refs, bn, prims};
+            bb.build(0, ids, 0, (int)ids.size());
             root = (int)nodes.size();
-            nodes.push_back(Node{});
-            BvhBuilder bb{refs, nodes, prims};
-            bb.build(root, ids, 0, (int)ids.size());
+            emit_nodes(bn, nodes);
         }
         vars[v] = make_int4(root, g0, (int)glob.size() - g0, s0);
     }

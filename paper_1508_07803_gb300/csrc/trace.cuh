@@ -72,17 +72,23 @@ enum {
         if constexpr (C) cnt[(k)] += 1u; \
     } while (0)
 
+// BVH node (64 bytes): the boxes of BOTH children and their references, so
+// that one node load serves the two box tests of a level.  Child k is an
+// internal node (n[k] == 0, ref = node index), a leaf (n[k] > 0, prims
+// [ref, ref + n)) or empty (n[k] < 0).
 struct Node {
-    float lo[3], hi[3];
-    int a, b;  // b > 0: leaf with prims [a, a + b); b == 0: internal, children a and a + 1
+    float lo0[3], hi0[3];
+    float lo1[3], hi1[3];
+    int ref0, ref1;
+    int n0, n1;
 };
 
 struct Tables {
     const void* surf;  // n_surf * REC values of T
     const int4* surf_i;
-    const Node* nodes;
+    const Node* nodes;  // node 0 of a variant's BVH is its root
     const int* prims;
-    const int4* variants;  // (bvh root or -1, first unbounded index, n unbounded, -)
+    const int4* variants;  // (bvh root node or -1, first unbounded index, n unbounded, first surface)
     const int* glob;       // surfaces without a bounding box, per variant
     const double* mats;
     const double* meds;
@@ -551,11 +557,11 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
 // every surface.
 // (ox, oy, oz) here are the origin pre-multiplied by the inverse direction,
 // so every slab distance is one FMA.
-__device__ __forceinline__ float box_entry(const Node& nd, float ox, float oy, float oz, float ix, float iy, float iz,
-                                           float tmax) {
-    const float t0x = fmaf(nd.lo[0], ix, -ox), t1x = fmaf(nd.hi[0], ix, -ox);
-    const float t0y = fmaf(nd.lo[1], iy, -oy), t1y = fmaf(nd.hi[1], iy, -oy);
-    const float t0z = fmaf(nd.lo[2], iz, -oz), t1z = fmaf(nd.hi[2], iz, -oz);
+__device__ __forceinline__ float box_entry(const float* lo, const float* hi, float ox, float oy, float oz, float ix,
+                                           float iy, float iz, float tmax) {
+    const float t0x = fmaf(lo[0], ix, -ox), t1x = fmaf(hi[0], ix, -ox);
+    const float t0y = fmaf(lo[1], iy, -oy), t1y = fmaf(hi[1], iy, -oy);
+    const float t0z = fmaf(lo[2], iz, -oz), t1z = fmaf(hi[2], iz, -oz);
     const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
     const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
     return tn <= tf ? tn : __int_as_float(0x7f800000);
@@ -578,23 +584,33 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
     auto inv = [](float v) -> float { return 1.0f / (fabsf(v) > 1e-30f ? v : copysignf(1e-30f, v)); };
     const float ix = inv((float)d.x), iy = inv((float)d.y), iz = inv((float)d.z);
     const float ox = (float)p.x * ix, oy = (float)p.y * iy, oz = (float)p.z * iz;
-    int stack[STACK];
+    // while-while traversal: every lane first walks internal nodes until its
+    // current item is a leaf (or nothing is left), then every lane with a leaf
+    // tests its surfaces; the two code paths do not interleave inside a warp.
+    int stack[STACK];  // packed (ref | n << 24)
     float stack_t[STACK];
     int sp = 0;
-    int ni = vr.x;
     // float bound of the current best t, rounded up so that no candidate is lost
     auto tcap = [&]() -> float { return bst.t == t_inf<T>() ? 3.0e38f : (float)bst.t * 1.0001f + 1e-30f; };
-    CNT(U_AABB);
-    if (!(box_entry(tb.nodes[ni], ox, oy, oz, ix, iy, iz, tcap()) < 3.4e38f)) return;
+    auto pop = [&](int& ref, int& n) {
+        ref = -1;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tcap()) {
+                ref = stack[sp] & 0xffffff;
+                n = stack[sp] >> 24;
+                return;
+            }
+        }
+    };
+    int ref = vr.x, n = 0;  // the root is an internal node
     while (true) {
-        const Node nd = tb.nodes[ni];
-        if (nd.b > 0) {
-            for (int k = 0; k < nd.b; ++k) test_surface<C>(tb, tb.prims[nd.a + k], p, d, eps, tol, bst, cnt);
-        } else {
+        while (n == 0 && ref >= 0) {
+            const Node nd = tb.nodes[ref];
             const float tc = tcap();
             if constexpr (C) cnt[U_AABB] += 2u;
-            const float e0 = box_entry(tb.nodes[nd.a], ox, oy, oz, ix, iy, iz, tc);
-            const float e1 = box_entry(tb.nodes[nd.a + 1], ox, oy, oz, ix, iy, iz, tc);
+            const float e0 = nd.n0 < 0 ? 3.4e38f : box_entry(nd.lo0, nd.hi0, ox, oy, oz, ix, iy, iz, tc);
+            const float e1 = nd.n1 < 0 ? 3.4e38f : box_entry(nd.lo1, nd.hi1, ox, oy, oz, ix, iy, iz, tc);
             const bool h0 = e0 < 3.4e38f, h1 = e1 < 3.4e38f;
             if (h0 && h1) {
                 if (sp >= STACK) {
@@ -603,32 +619,24 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
                 }
                 // nearer child first; the farther one waits with its entry distance
                 const bool first0 = e0 <= e1;
-                stack[sp] = first0 ? nd.a + 1 : nd.a;
+                stack[sp] = first0 ? (nd.ref1 | (nd.n1 << 24)) : (nd.ref0 | (nd.n0 << 24));
                 stack_t[sp] = first0 ? e1 : e0;
                 ++sp;
-                ni = first0 ? nd.a : nd.a + 1;
-                continue;
-            }
-            if (h0) {
-                ni = nd.a;
-                continue;
-            }
-            if (h1) {
-                ni = nd.a + 1;
-                continue;
-            }
-        }
-        // pop, skipping subtrees that start beyond the current best hit
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= tcap()) {
-                ni = stack[sp];
-                found = true;
-                break;
+                ref = first0 ? nd.ref0 : nd.ref1;
+                n = first0 ? nd.n0 : nd.n1;
+            } else if (h0) {
+                ref = nd.ref0;
+                n = nd.n0;
+            } else if (h1) {
+                ref = nd.ref1;
+                n = nd.n1;
+            } else {
+                pop(ref, n);
             }
         }
-        if (!found) break;
+        if (ref < 0) break;
+        for (int k = 0; k < n; ++k) test_surface<C>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
+        pop(ref, n);
     }
 }
 
@@ -690,7 +698,10 @@ struct Photon {
     unsigned long long thr;
 };
 
-template <typename T, int BLOCK, bool C = false>
+// STAGED: the tables fit in shared memory and every table pointer is derived
+// from the shared array (so the loads are shared-memory loads); otherwise the
+// tables are read from global memory through L1.
+template <typename T, int BLOCK, bool C = false, bool STAGED = true>
 __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
     unsigned cnt[U_N];
     if constexpr (C) {
@@ -699,7 +710,7 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
     }
     extern __shared__ __align__(16) unsigned char smem[];
     Tables tb = A.tab;
-    if (A.stage) {
+    if constexpr (STAGED) {
         // stage every table in shared memory: surfaces, int records, nodes,
         // prims, variants, unbounded lists, materials, media (16-byte chunks)
         unsigned char* s = smem;
@@ -712,14 +723,15 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
             s += n16 * 16;
             return r;
         };
+        // every count is >= 1 (the host pads empty tables with one entry)
         tb.surf = stage(tb.surf, (size_t)tb.n_surf * REC * sizeof(T));
         tb.surf_i = reinterpret_cast<const int4*>(stage(tb.surf_i, (size_t)tb.n_surf * sizeof(int4)));
-        if (tb.n_nodes) tb.nodes = reinterpret_cast<const Node*>(stage(tb.nodes, (size_t)tb.n_nodes * sizeof(Node)));
-        if (tb.n_prims) tb.prims = reinterpret_cast<const int*>(stage(tb.prims, (size_t)tb.n_prims * sizeof(int)));
+        tb.nodes = reinterpret_cast<const Node*>(stage(tb.nodes, (size_t)tb.n_nodes * sizeof(Node)));
+        tb.prims = reinterpret_cast<const int*>(stage(tb.prims, (size_t)tb.n_prims * sizeof(int)));
         tb.variants = reinterpret_cast<const int4*>(stage(tb.variants, (size_t)tb.n_var * sizeof(int4)));
-        if (tb.n_glob) tb.glob = reinterpret_cast<const int*>(stage(tb.glob, (size_t)tb.n_glob * sizeof(int)));
-        if (tb.n_mat) tb.mats = reinterpret_cast<const double*>(stage(tb.mats, (size_t)tb.n_mat * MAT_REC * sizeof(double)));
-        if (tb.n_med) tb.meds = reinterpret_cast<const double*>(stage(tb.meds, (size_t)tb.n_med * MED_REC * sizeof(double)));
+        tb.glob = reinterpret_cast<const int*>(stage(tb.glob, (size_t)tb.n_glob * sizeof(int)));
+        tb.mats = reinterpret_cast<const double*>(stage(tb.mats, (size_t)tb.n_mat * MAT_REC * sizeof(double)));
+        tb.meds = reinterpret_cast<const double*>(stage(tb.meds, (size_t)tb.n_med * MED_REC * sizeof(double)));
         __syncthreads();
     }
     const unsigned FULL = 0xffffffffu;

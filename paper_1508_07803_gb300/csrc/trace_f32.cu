@@ -3,9 +3,9 @@
 
 namespace robast {
 
-template <int BLOCK, bool C = false>
+template <int BLOCK, bool C, bool STAGED>
 static cudaError_t launch_one(const TraceArgs<float>& a, int grid, size_t smem, cudaStream_t s) {
-    auto k = trace_kernel<float, BLOCK, C>;
+    auto k = trace_kernel<float, BLOCK, C, STAGED>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -16,7 +16,7 @@ static cudaError_t launch_one(const TraceArgs<float>& a, int grid, size_t smem, 
 
 template <int BLOCK>
 static int occupancy_one(size_t smem) {
-    auto k = trace_kernel<float, BLOCK>;
+    auto k = smem ? trace_kernel<float, BLOCK, false, true> : trace_kernel<float, BLOCK, false, false>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
@@ -35,11 +35,15 @@ int trace_blocks_per_sm_f32(int block, size_t smem) {
 }
 
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s) {
-    if (a.units) return block == 128 ? launch_one<128, true>(a, grid, smem, s) : cudaErrorInvalidConfiguration;
+    const bool st = a.stage != 0;
+    if (a.units) {
+        if (block != 128) return cudaErrorInvalidConfiguration;
+        return st ? launch_one<128, true, true>(a, grid, smem, s) : launch_one<128, true, false>(a, grid, smem, s);
+    }
     switch (block) {
-        case 64: return launch_one<64>(a, grid, smem, s);
-        case 128: return launch_one<128>(a, grid, smem, s);
-        case 256: return launch_one<256>(a, grid, smem, s);
+        case 64: return st ? launch_one<64, false, true>(a, grid, smem, s) : launch_one<64, false, false>(a, grid, smem, s);
+        case 128: return st ? launch_one<128, false, true>(a, grid, smem, s) : launch_one<128, false, false>(a, grid, smem, s);
+        case 256: return st ? launch_one<256, false, true>(a, grid, smem, s) : launch_one<256, false, false>(a, grid, smem, s);
     }
     return cudaErrorInvalidConfiguration;
 }
