@@ -262,7 +262,7 @@ def main():
         o, d, w = inputs(precision)
         out = robast.alloc_outputs(N, precision, dev)
         counters = out["counters"]
-        psf_launches = 6 * len(ANGLES)
+        psf_launches = 4  # sums, finish, histogram, selection (all field angles at once)
 
         def step(ev=None):
             if ev is not None:
@@ -271,9 +271,8 @@ def main():
                          stream=stream)
             if ev is not None:
                 ev[1].record(stream)
-            res = [robast.psf(geom, out["status"], out["focal_xy"], precision=precision, stream=stream,
-                              start=k * npa, count=npa) for k in range(len(ANGLES))]
-            return res
+            return robast.psf(geom, out["status"], out["focal_xy"], precision=precision, stream=stream,
+                              windows=[(k * npa, npa) for k in range(len(ANGLES))])
 
         for _ in range(warmup):
             step()

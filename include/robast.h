@@ -240,18 +240,20 @@ int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, con
 
 /* ----------------------------------------------------------- reductions */
 /*
- * Spot diagram statistics of DETECTED photons (Fig. 1 g-i): centroid of
- * focal_xy and R80 = the nearest-rank 80th percentile (sorted index
- * ceil(0.8 N) - 1) of the radial distance to the centroid.  status [n] and
- * focal_xy are device pointers (precision 32: float, 64: double); the local
- * x of photon i is focal_xy[i] and its y is focal_xy[ld + i] (ld >= n; ld = 0
- * means n), so a window of a larger trace output is reduced in place.
- * result is a HOST array of 4 doubles {N_detected, cx, cy, R80} (NaN when
- * nothing is detected).  Synchronises the stream.  Uses device scratch owned
- * by g.
+ * Spot diagram statistics (Fig. 1 g-i) of the DETECTED photons of each of
+ * n_windows windows of a trace output: window w covers photons starts[w] ..
+ * starts[w] + counts[w] - 1 (host arrays).  status [ld] and focal_xy [2 ld]
+ * are device pointers to the trace output (precision 32: float, 64: double;
+ * local x of photon i at focal_xy[i], y at focal_xy[ld + i]).  Per window,
+ * results (HOST, 4 doubles per window) = {N_detected, cx, cy, R80}: centroid
+ * of focal_xy and R80 = the nearest-rank 80th percentile (sorted index
+ * ceil(0.8 N) - 1) of the distance to the centroid; cx, cy, R80 are NaN when
+ * nothing is detected.  Deterministic (fixed-order FP64 sums, exact
+ * selection).  Synchronises the stream; uses device scratch owned by g.
+ * Errors: ROBAST_E_NULL, ROBAST_E_INVALID (window outside [0, ld), precision).
  */
-int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t n, int64_t ld,
-               int32_t precision, void* stream, double* result);
+int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t ld, int32_t n_windows,
+               const int64_t* starts, const int64_t* counts, int32_t precision, void* stream, double* results);
 
 /* ----------------------------------------------------------- measurement */
 /*

@@ -109,7 +109,7 @@ def load(build_if_missing: bool = True):
                                           ctypes.POINTER(TraceOpts)]
         lib.robast_trace_opts_default.argtypes = [ctypes.POINTER(TraceOpts)]
         lib.robast_trace_opts_default.restype = None
-        lib.robast_psf.argtypes = [vp, vp, vp, i64, i64, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.robast_psf.argtypes = [vp, vp, vp, i64, i32, vp, vp, i32, vp, ctypes.POINTER(ctypes.c_double)]
         lib.robast_last_error.restype = ctypes.c_char_p
         lib.robast_version.restype = ctypes.c_char_p
         _lib = lib
@@ -302,25 +302,32 @@ def trace_host(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precis
     return out
 
 
-def psf(geom: Geometry, status, focal_xy, precision: int = 32, stream=None, start: int = 0, count=None):
-    """robast_psf: (N_detected, cx, cy, R80) of the DETECTED photons' focal-plane points.
+def psf(geom: Geometry, status, focal_xy, precision: int = 32, stream=None, start: int = 0, count=None,
+        windows=None):
+    """robast_psf: spot-diagram statistics (N_detected, cx, cy, R80) of DETECTED photons.
 
-    status [N] and focal_xy [2, N] are trace outputs; photons start .. start+count-1 are reduced.
+    status [N] and focal_xy [2, N] are trace outputs.  Either one window
+    (start, count) -> one tuple, or `windows` = [(start, count), ...] -> a
+    list of tuples, all reduced in one pass.
     """
     import torch
     lib = load()
     N = int(status.shape[0])
-    count = N - start if count is None else int(count)
-    if not (0 <= start and start + count <= N and focal_xy.shape == (2, N) and focal_xy.is_contiguous()):
-        raise RobastError("psf: need status [N], contiguous focal_xy [2, N] and a window inside N")
+    single = windows is None
+    if single:
+        windows = [(start, N - start if count is None else int(count))]
+    if not (tuple(focal_xy.shape) == (2, N) and focal_xy.is_contiguous()):
+        raise RobastError("psf: need status [N] and contiguous focal_xy [2, N]")
     if stream is None:
         stream = torch.cuda.current_stream(status.device)
-    res = (ctypes.c_double * 4)()
-    es = focal_xy.element_size()
-    _check(lib.robast_psf(geom.handle, ctypes.c_void_p(status.data_ptr() + start),
-                          ctypes.c_void_p(focal_xy.data_ptr() + start * es), count, N, int(precision),
+    nw = len(windows)
+    st = (ctypes.c_int64 * nw)(*[int(w[0]) for w in windows])
+    ct = (ctypes.c_int64 * nw)(*[int(w[1]) for w in windows])
+    res = (ctypes.c_double * (4 * nw))()
+    _check(lib.robast_psf(geom.handle, _ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
                           ctypes.c_void_p(stream.cuda_stream), res))
-    return tuple(res)
+    out = [tuple(res[4 * w:4 * w + 4]) for w in range(nw)]
+    return out[0] if single else out
 
 
 def version() -> str:

@@ -905,188 +905,225 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
 }
 
 // ------------------------------------------------------------- reductions
-// Spot diagram: centroid by fixed-order FP64 block partials, then the exact
-// nearest-rank 80% radius through a 4096-bin histogram and a selection inside
-// the bin that holds the rank.
+// Spot diagrams of several photon windows at once.  Per window: centroid
+// from fixed-order FP64 block partials; R80 = exact nearest-rank 80th
+// percentile of the radius to the centroid, found with a histogram over
+// [0, 8 x RMS radius) plus one overflow bin, then a selection inside the bin
+// that holds the rank.  Four launches and two host synchronisations for any
+// number of windows.
 namespace {
 constexpr int kRedBlock = 256;
-constexpr int kRedGrid = 304;  // 2 x 152 SMs
-constexpr int kBins = 4096;
+constexpr int kBins = 4096;  // + 1 overflow bin
+
+struct Win {
+    long long start, count;
+};
 
 template <typename T>
-__global__ void psf_partials(const uint8_t* st, const T* fxy, long long n, long long ld, double* part) {
-    double c = 0, sx = 0, sy = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+__global__ void psf_sums(const uint8_t* st, const T* fxy, long long ld, const Win* win, double* part) {
+    const Win w = win[blockIdx.y];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < w.count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = w.start + k;
         if (st[i] == ROBAST_ST_DETECTED) {
-            c += 1.0;
-            sx += (double)fxy[i];
-            sy += (double)fxy[ld + i];
+            const double x = (double)fxy[i], y = (double)fxy[ld + i];
+            acc[0] += 1.0;
+            acc[1] += x;
+            acc[2] += y;
+            acc[3] += x * x;
+            acc[4] += y * y;
         }
-    __shared__ double sh[3][kRedBlock];
-    sh[0][threadIdx.x] = c;
-    sh[1][threadIdx.x] = sx;
-    sh[2][threadIdx.x] = sy;
+    }
+    __shared__ double sh[5][kRedBlock];
+    for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = acc[c];
     __syncthreads();
-    for (int w = kRedBlock / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    for (int h = kRedBlock / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + h];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) part[3 * blockIdx.x + k] = sh[k][0];
+        for (int c = 0; c < 5; ++c) part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 5 + c] = sh[c][0];
 }
 
-__global__ void psf_finish(const double* part, int nparts, double* res) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double c = 0, sx = 0, sy = 0;
-        for (int b = 0; b < nparts; ++b) {
-            c += part[3 * b];
-            sx += part[3 * b + 1];
-            sy += part[3 * b + 2];
-        }
-        res[0] = c;
-        res[1] = c > 0 ? sx / c : 0.0;
-        res[2] = c > 0 ? sy / c : 0.0;
-    }
+// one thread per window, blocks summed in a fixed order: res = (N, cx, cy, range)
+__global__ void psf_finish(const double* part, int nblocks, int nwin, double* res) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwin) return;
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int c = 0; c < 5; ++c) a[c] += part[((size_t)w * nblocks + b) * 5 + c];
+    const double n = a[0];
+    const double cx = n > 0 ? a[1] / n : 0.0, cy = n > 0 ? a[2] / n : 0.0;
+    const double ms = n > 0 ? fmax(0.0, (a[3] + a[4]) / n - cx * cx - cy * cy) : 0.0;
+    res[4 * w + 0] = n;
+    res[4 * w + 1] = cx;
+    res[4 * w + 2] = cy;
+    res[4 * w + 3] = fmax(8.0 * sqrt(ms), 1e-300);
 }
 
-template <typename T>
-__device__ __forceinline__ double radius(const T* fxy, long long ld, long long i, const double* res) {
-    const double dx = (double)fxy[i] - res[1], dy = (double)fxy[ld + i] - res[2];
-    return sqrt(dx * dx + dy * dy);
-}
-
-template <typename T>
-__global__ void psf_rmax(const uint8_t* st, const T* fxy, long long n, long long ld, const double* res,
-                         unsigned long long* rmax) {
-    double m = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        if (st[i] == ROBAST_ST_DETECTED) m = fmax(m, radius(fxy, ld, i, res));
-    // non-negative doubles order like their bit patterns
-    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-    for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(rmax, bits);
-}
-
-template <typename T>
-__device__ __forceinline__ int bin_of(double r, double rmax) {
-    int b = rmax > 0.0 ? (int)(r / rmax * kBins) : 0;
+__device__ __forceinline__ int psf_bin(double r, double range) {
+    if (!(r < range)) return kBins;  // overflow
+    int b = (int)(r / range * kBins);
     return b < 0 ? 0 : (b >= kBins ? kBins - 1 : b);
 }
 
 template <typename T>
-__global__ void psf_hist(const uint8_t* st, const T* fxy, long long n, long long ld, const double* res,
-                         const unsigned long long* rmax_bits, unsigned long long* hist) {
-    __shared__ unsigned int h[kBins];
-    for (int k = threadIdx.x; k < kBins; k += blockDim.x) h[k] = 0;
+__global__ void psf_hist(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
+                         unsigned long long* hist) {
+    __shared__ unsigned int h[kBins + 1];
+    for (int k = threadIdx.x; k <= kBins; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    const double rmax = __longlong_as_double((long long)*rmax_bits);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        if (st[i] == ROBAST_ST_DETECTED) atomicAdd(&h[bin_of<T>(radius(fxy, ld, i, res), rmax)], 1u);
+    const Win w = win[blockIdx.y];
+    const double* R = res + 4 * blockIdx.y;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < w.count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = w.start + k;
+        if (st[i] == ROBAST_ST_DETECTED) {
+            const double dx = (double)fxy[i] - R[1], dy = (double)fxy[ld + i] - R[2];
+            atomicAdd(&h[psf_bin(sqrt(dx * dx + dy * dy), R[3])], 1u);
+        }
+    }
     __syncthreads();
-    for (int k = threadIdx.x; k < kBins; k += blockDim.x)
-        if (h[k]) atomicAdd(hist + k, (unsigned long long)h[k]);
+    unsigned long long* H = hist + (size_t)blockIdx.y * (kBins + 1);
+    for (int k = threadIdx.x; k <= kBins; k += blockDim.x)
+        if (h[k]) atomicAdd(H + k, (unsigned long long)h[k]);
 }
 
+// sel[w] = (bin, offset into vals); cnt[w] counts the values written
 template <typename T>
-__global__ void psf_collect(const uint8_t* st, const T* fxy, long long n, long long ld, const double* res,
-                            const unsigned long long* rmax_bits, int bin, double* vals, unsigned long long* cnt,
-                            unsigned long long cap) {
-    const double rmax = __longlong_as_double((long long)*rmax_bits);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+__global__ void psf_collect(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
+                            const long long* sel, double* vals, unsigned long long* cnt, const long long* cap) {
+    const Win w = win[blockIdx.y];
+    const double* R = res + 4 * blockIdx.y;
+    const int bin = (int)sel[2 * blockIdx.y];
+    double* out = vals + sel[2 * blockIdx.y + 1];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < w.count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = w.start + k;
         if (st[i] == ROBAST_ST_DETECTED) {
-            const double r = radius(fxy, ld, i, res);
-            if (bin_of<T>(r, rmax) == bin) {
-                const unsigned long long k = atomicAdd(cnt, 1ull);
-                if (k < cap) vals[k] = r;
+            const double dx = (double)fxy[i] - R[1], dy = (double)fxy[ld + i] - R[2];
+            const double r = sqrt(dx * dx + dy * dy);
+            if (psf_bin(r, R[3]) == bin) {
+                const unsigned long long j = atomicAdd(cnt + blockIdx.y, 1ull);
+                if ((long long)j < cap[blockIdx.y]) out[j] = r;
             }
         }
+    }
 }
 
 template <typename T>
-int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long n, long long ld, cudaStream_t s,
-             double* result) {
-    // scratch: parts[3*grid] res[4] rmax[1] cnt[1] hist[kBins] vals[...]
-    const size_t parts = 3 * kRedGrid * 8, fixed = align16(parts) + 64 + kBins * 8;
+int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int nw, const long long* starts,
+             const long long* counts, cudaStream_t s, double* result) {
+    long long maxcount = 0;
+    for (int w = 0; w < nw; ++w) maxcount = std::max(maxcount, counts[w]);
+    const int bx = (int)std::max(1LL, std::min<long long>(std::max(1, 512 / nw), (maxcount + kRedBlock - 1) / kRedBlock));
+    // scratch: win[nw] | part[nw*bx*5] | res[4nw] | hist[nw*(kBins+1)] | sel[2nw] | cnt[nw] | cap[nw] | vals
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t at = off;
+        off += align16(bytes);
+        return at;
+    };
+    const size_t o_win = carve(nw * sizeof(Win)), o_part = carve((size_t)nw * bx * 5 * 8), o_res = carve(nw * 32);
+    const size_t o_hist = carve((size_t)nw * (kBins + 1) * 8), o_sel = carve(nw * 16), o_cnt = carve(nw * 8);
+    const size_t o_cap = carve(nw * 8), o_vals = off;
     std::lock_guard<std::mutex> lk(g->mu);
-    int rc = grow(&g->scratch, &g->scratch_bytes, fixed + 1024 * 8, "robast_psf");
+    int rc = grow(&g->scratch, &g->scratch_bytes, o_vals + 4096 * 8, "robast_psf");
     if (rc) return rc;
     unsigned char* b = static_cast<unsigned char*>(g->scratch);
-    double* part = reinterpret_cast<double*>(b);
-    double* res = reinterpret_cast<double*>(b + align16(parts));
-    unsigned long long* rmax = reinterpret_cast<unsigned long long*>(b + align16(parts) + 32);
-    unsigned long long* cnt = rmax + 1;
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(b + align16(parts) + 64);
-    CU(cudaMemsetAsync(b + align16(parts), 0, 64 + kBins * 8, s), "robast_psf: clear");
-    psf_partials<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, part);
-    psf_finish<<<1, 32, 0, s>>>(part, kRedGrid, res);
-    psf_rmax<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax);
-    psf_hist<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax, hist);
+    std::vector<Win> hw(nw);
+    for (int w = 0; w < nw; ++w) hw[w] = Win{starts[w], counts[w]};
+    CU(cudaMemcpyAsync(b + o_win, hw.data(), nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemsetAsync(b + o_hist, 0, (size_t)nw * (kBins + 1) * 8, s), "robast_psf: clear");
+    const Win* dwin = reinterpret_cast<const Win*>(b + o_win);
+    double* part = reinterpret_cast<double*>(b + o_part);
+    double* res = reinterpret_cast<double*>(b + o_res);
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(b + o_hist);
+    psf_sums<T><<<dim3(bx, nw), kRedBlock, 0, s>>>(st, fxy, ld, dwin, part);
+    psf_finish<<<(nw + 31) / 32, 32, 0, s>>>(part, bx, nw, res);
+    psf_hist<T><<<dim3(bx, nw), kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, hist);
     CU(cudaGetLastError(), "robast_psf: launch");
-    double hres[3];
-    std::vector<unsigned long long> hh(kBins);
-    CU(cudaMemcpyAsync(hres, res, sizeof hres, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
-    CU(cudaMemcpyAsync(hh.data(), hist, kBins * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    std::vector<double> hres(4 * nw);
+    std::vector<unsigned long long> hh((size_t)nw * (kBins + 1));
+    CU(cudaMemcpyAsync(hres.data(), res, nw * 32, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(hh.data(), hist, hh.size() * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
     CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
-    const long long N = (long long)hres[0];
-    result[0] = hres[0];
-    if (N == 0) {
-        result[1] = result[2] = result[3] = NAN;
-        return 0;
+    // the bin holding rank ceil(0.8 N) - 1 of each window
+    std::vector<long long> sel(2 * nw), cap(nw), rank_in_bin(nw);
+    long long total = 0;
+    for (int w = 0; w < nw; ++w) {
+        const long long N = (long long)hres[4 * w];
+        result[4 * w + 0] = hres[4 * w];
+        result[4 * w + 1] = N ? hres[4 * w + 1] : NAN;
+        result[4 * w + 2] = N ? hres[4 * w + 2] : NAN;
+        result[4 * w + 3] = NAN;
+        long long k = N ? (long long)std::ceil(0.8 * (double)N) - 1 : -1, acc = 0;
+        int bin = 0;
+        if (N) {
+            for (; bin <= kBins; ++bin) {
+                const long long c = (long long)hh[(size_t)w * (kBins + 1) + bin];
+                if (acc + c > k) break;
+                acc += c;
+            }
+        }
+        cap[w] = N ? (long long)hh[(size_t)w * (kBins + 1) + bin] : 0;
+        rank_in_bin[w] = k - acc;
+        sel[2 * w] = N ? bin : -1;
+        sel[2 * w + 1] = total;
+        total += cap[w];
     }
-    result[1] = hres[1];
-    result[2] = hres[2];
-    const long long k = (long long)std::ceil(0.8 * (double)N) - 1;
-    long long acc = 0;
-    int bin = 0;
-    for (; bin < kBins; ++bin) {
-        if (acc + (long long)hh[bin] > k) break;
-        acc += (long long)hh[bin];
-    }
-    const unsigned long long cap = hh[bin];
-    rc = grow(&g->scratch, &g->scratch_bytes, fixed + cap * 8 + 1024 * 8, "robast_psf");
+    rc = grow(&g->scratch, &g->scratch_bytes, o_vals + std::max<long long>(total, 1) * 8, "robast_psf");
     if (rc) return rc;
-    b = static_cast<unsigned char*>(g->scratch);
-    part = reinterpret_cast<double*>(b);
-    res = reinterpret_cast<double*>(b + align16(parts));
-    rmax = reinterpret_cast<unsigned long long*>(b + align16(parts) + 32);
-    cnt = rmax + 1;
-    hist = reinterpret_cast<unsigned long long*>(b + align16(parts) + 64);
-    double* vals = reinterpret_cast<double*>(b + fixed);
-    // the scratch may have moved: restore res and rmax for the collect pass
-    unsigned long long hrmax = 0;
-    {
-        double r4[4] = {hres[0], hres[1], hres[2], 0.0};
-        CU(cudaMemcpyAsync(res, r4, sizeof r4, cudaMemcpyHostToDevice, s), "robast_psf: copy");
-    }
-    // rmax was on the device only; recompute it (cheap) when the scratch moved
-    CU(cudaMemsetAsync(rmax, 0, 16, s), "robast_psf: clear");
-    psf_rmax<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax);
-    psf_collect<T><<<kRedGrid, kRedBlock, 0, s>>>(st, fxy, n, ld, res, rmax, bin, vals, cnt, cap);
+    b = static_cast<unsigned char*>(g->scratch);  // may have moved: re-upload what the collect pass reads
+    dwin = reinterpret_cast<const Win*>(b + o_win);
+    res = reinterpret_cast<double*>(b + o_res);
+    CU(cudaMemcpyAsync(b + o_win, hw.data(), nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(res, hres.data(), nw * 32, cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(b + o_sel, sel.data(), nw * 16, cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(b + o_cap, cap.data(), nw * 8, cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemsetAsync(b + o_cnt, 0, nw * 8, s), "robast_psf: clear");
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b + o_cnt);
+    double* vals = reinterpret_cast<double*>(b + o_vals);
+    psf_collect<T><<<dim3(bx, nw), kRedBlock, 0, s>>>(st, fxy, ld, dwin, res,
+                                                      reinterpret_cast<const long long*>(b + o_sel), vals, cnt,
+                                                      reinterpret_cast<const long long*>(b + o_cap));
     CU(cudaGetLastError(), "robast_psf: launch");
-    std::vector<double> hv(cap);
-    unsigned long long got = 0;
-    CU(cudaMemcpyAsync(&got, cnt, 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
-    CU(cudaMemcpyAsync(&hrmax, rmax, 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
-    if (cap) CU(cudaMemcpyAsync(hv.data(), vals, cap * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    std::vector<double> hv(std::max<long long>(total, 1));
+    std::vector<unsigned long long> got(nw);
+    CU(cudaMemcpyAsync(got.data(), cnt, nw * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    if (total) CU(cudaMemcpyAsync(hv.data(), vals, total * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
     CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
-    if (got != cap) return fail(ROBAST_E_CUDA, "robast_psf: histogram and selection disagree (%llu vs %llu)", got, cap);
-    const long long kk = k - acc;
-    std::nth_element(hv.begin(), hv.begin() + kk, hv.end());
-    result[3] = hv[kk];
+    for (int w = 0; w < nw; ++w) {
+        if (sel[2 * w] < 0) continue;
+        if ((long long)got[w] != cap[w])
+            return fail(ROBAST_E_CUDA, "robast_psf: histogram and selection disagree in window %d", w);
+        auto first = hv.begin() + sel[2 * w + 1];
+        std::nth_element(first, first + rank_in_bin[w], first + cap[w]);
+        result[4 * w + 3] = first[rank_in_bin[w]];
+    }
     return 0;
 }
 }  // namespace
 
-extern "C" int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t n, int64_t ld,
-                          int32_t precision, void* stream, double* result) {
-    if (!g || !status || !focal_xy || !result) return fail(ROBAST_E_NULL, "robast_psf: NULL argument");
-    if (n <= 0) return fail(ROBAST_E_INVALID, "robast_psf: n must be > 0");
-    if (ld == 0) ld = n;
-    if (ld < n) return fail(ROBAST_E_INVALID, "robast_psf: ld (%lld) must be >= n (%lld)", (long long)ld, (long long)n);
+extern "C" int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t ld, int32_t n_windows,
+                          const int64_t* starts, const int64_t* counts, int32_t precision, void* stream,
+                          double* results) {
+    if (!g || !status || !focal_xy || !results || !starts || !counts)
+        return fail(ROBAST_E_NULL, "robast_psf: NULL argument");
+    if (n_windows <= 0 || n_windows > 65535) return fail(ROBAST_E_INVALID, "robast_psf: n_windows must be in 1..65535");
+    for (int w = 0; w < n_windows; ++w)
+        if (starts[w] < 0 || counts[w] <= 0 || starts[w] + counts[w] > ld)
+            return fail(ROBAST_E_INVALID, "robast_psf: window %d [%lld, +%lld) must lie inside [0, ld = %lld)", w,
+                        (long long)starts[w], (long long)counts[w], (long long)ld);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (precision == 32) return psf_impl<float>(g, status, static_cast<const float*>(focal_xy), n, ld, s, result);
-    if (precision == 64) return psf_impl<double>(g, status, static_cast<const double*>(focal_xy), n, ld, s, result);
+    const long long* st = reinterpret_cast<const long long*>(starts);
+    const long long* ct = reinterpret_cast<const long long*>(counts);
+    if (precision == 32)
+        return psf_impl<float>(g, status, static_cast<const float*>(focal_xy), ld, n_windows, st, ct, s, results);
+    if (precision == 64)
+        return psf_impl<double>(g, status, static_cast<const double*>(focal_xy), ld, n_windows, st, ct, s, results);
     return fail(ROBAST_E_INVALID, "robast_psf: precision must be 32 or 64");
 }
 

@@ -224,3 +224,26 @@ def test_bad_arguments_raise():
     with pytest.raises(robast.RobastError, match="block_size"):
         robast.trace(geom, o, d, w, precision=64, block_size=96)
     geom.close()
+
+
+def test_psf_windows_each_match_numpy_on_the_same_outputs():
+    npa = 7_001
+    scene, b = W.lst_workload(npa, seed=12)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 32)
+    out = robast.trace(geom, o, d, w, seed=3)
+    wins = [(k * npa, npa) for k in range(5)] + [(0, 5 * npa), (123, 1)]
+    res = robast.psf(geom, out["status"], out["focal_xy"], windows=wins)
+    g = to_numpy(out)
+    for (s0, c), (n_det, cx, cy, r80) in zip(wins, res):
+        sl = slice(s0, s0 + c)
+        exact = metrics.psf(g["status"][sl], g["focal_xy"][:, sl])
+        assert n_det == exact["n_detected"]
+        if n_det == 0:
+            assert math.isnan(r80)
+            continue
+        assert abs(cx - exact["cx"]) < 1e-12 and abs(cy - exact["cy"]) < 1e-12
+        assert r80 == pytest.approx(exact["r80"], rel=1e-12, abs=1e-15)
+    with pytest.raises(robast.RobastError, match="window"):
+        robast.psf(geom, out["status"], out["focal_xy"], windows=[(5 * npa - 10, 11)])
+    geom.close()
