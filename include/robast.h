@@ -255,6 +255,28 @@ int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, con
 int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int64_t ld, int32_t n_windows,
                const int64_t* starts, const int64_t* counts, int32_t precision, void* stream, double* results);
 
+/*
+ * robast_psf_noalloc: the same statistics as robast_psf (same arguments minus
+ * the geometry, same results) for callers that cannot allocate device memory
+ * when they need them -- for example code recording a CUDA graph, code whose
+ * device memory is all owned by a caching allocator, or an embedding with a
+ * fixed memory budget.  The paper has no counterpart; this is a property of
+ * the library, not of the method.
+ *
+ * It allocates nothing: its scratch is one fixed array of about 6.4 MB in
+ * device memory, defined at file scope in the library, which every GPU that
+ * loads the library holds until the process exits; its host buffers are
+ * static too.  Limit: at most 64 windows per call (ROBAST_E_INVALID beyond).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture on it.
+ * Every call on a device shares the array and leaves its contents behind
+ * (each call clears what it needs cleared), so calls whose GPU work overlaps
+ * race with one another: issue them one at a time.  Synchronises the stream.
+ */
+int robast_psf_noalloc(const uint8_t* status, const void* focal_xy, int64_t ld, int32_t n_windows,
+                       const int64_t* starts, const int64_t* counts, int32_t precision, void* stream,
+                       double* results);
+
 /* ----------------------------------------------------------- measurement */
 /*
  * Measurement helper, not part of the method: FP32 (precision 32) or FP64

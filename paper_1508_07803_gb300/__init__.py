@@ -344,3 +344,29 @@ def measure_alu_peak(precision: int = 32, stream=None) -> float:
     v = ctypes.c_double()
     _check(lib.robast_measure_alu_peak(int(precision), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(v)))
     return v.value
+
+
+def psf_noalloc(status, focal_xy, windows, precision: int = 32, stream=None):
+    """robast_psf_noalloc: spot-diagram statistics per window without any allocation.
+
+    For callers that cannot allocate device memory at this point; scratch is a
+    fixed array inside the library (at most 64 windows per call).  Returns a
+    list of (N_detected, cx, cy, R80) per window, like psf(..., windows=...).
+    """
+    import torch
+    lib = load()
+    lib.robast_psf_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_double)]
+    N = int(status.shape[0])
+    if not (tuple(focal_xy.shape) == (2, N) and focal_xy.is_contiguous()):
+        raise RobastError("psf_noalloc: need status [N] and contiguous focal_xy [2, N]")
+    if stream is None:
+        stream = torch.cuda.current_stream(status.device)
+    nw = len(windows)
+    st = (ctypes.c_int64 * nw)(*[int(w[0]) for w in windows])
+    ct = (ctypes.c_int64 * nw)(*[int(w[1]) for w in windows])
+    res = (ctypes.c_double * (4 * nw))()
+    _check(lib.robast_psf_noalloc(_ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
+                                  ctypes.c_void_p(stream.cuda_stream), res))
+    return [tuple(res[4 * w:4 * w + 4]) for w in range(nw)]

@@ -1182,3 +1182,375 @@ extern "C" int robast_measure_alu_peak(int32_t precision, void* stream, double* 
     *flops_per_s = 2.0 * 8.0 * (double)iters * (double)block * (double)grid / (best * 1e-3);
     return 0;
 }
+
+// ============================================ allocation-free spot diagram
+// robast_psf_noalloc: the spot-diagram statistics of robast_psf computed
+// without allocating anything.
+//
+// Some callers cannot allocate device memory at the time they want these
+// statistics: code running inside a CUDA graph that is being captured, code
+// under a caching allocator that owns all device memory, or embedders whose
+// memory budget is fixed up front.  This entry point serves them.  Its
+// scratch lives in one file-scope __device__ array of fixed size (about
+// 6.4 MB) that every GPU which loads the library holds until the process
+// exits; it calls no cudaMalloc, cudaFree or allocating library routine, and
+// its host-side buffers are static too.
+//
+// Limits: at most NA_MAX_WINDOWS windows per call.  Because the scratch is
+// bounded, the selection of the 80% radius does not collect a whole
+// histogram bin (which can hold any number of photons): it refines the bin
+// that holds the rank with further 4096-bin histograms until that bin holds
+// at most NA_CAP values, then selects among them exactly.  The result is the
+// same number robast_psf returns.
+//
+// Sharing: every call on a device uses the same scratch array and leaves its
+// contents behind; each call clears what must start at zero.  Calls whose GPU
+// work overlaps (several host threads, or several streams) race on it; the
+// host-side part is serialised by a mutex, but work already queued on one
+// stream is not ordered against another stream's.
+//
+// Set-up: the first call on a device looks up the array's device address with
+// cudaGetSymbolAddress (with that device current) and caches it; make that
+// first call before any stream capture begins on the device.
+namespace {
+
+constexpr int NA_MAX_WINDOWS = 64;
+constexpr int NA_BINS = 4096;  // + 1 overflow bin in the first round
+constexpr int NA_CAP = 8192;   // values collected per window for the final selection
+constexpr int NA_ROUNDS = 8;   // histogram rounds (4096^8 resolves any double interval)
+constexpr int NA_BLOCK = 256;
+constexpr int NA_MAX_PART_BLOCKS = 512;
+constexpr int NA_MAX_DEVICES = 64;
+
+struct NaScratch {
+    double part[NA_MAX_PART_BLOCKS * 5];
+    double res[NA_MAX_WINDOWS * 4];  // N, cx, cy, first-round range
+    int chosen[NA_MAX_WINDOWS * NA_ROUNDS];
+    double lohi[NA_MAX_WINDOWS * NA_ROUNDS * 2];
+    unsigned long long hist[NA_MAX_WINDOWS * (NA_BINS + 1)];
+    unsigned long long cnt[NA_MAX_WINDOWS];
+    unsigned long long rmax_bits[NA_MAX_WINDOWS];
+    double vals[NA_MAX_WINDOWS * NA_CAP];
+};
+
+// The scratch: one per device, shared by every call (see the header comment).
+static __device__ __align__(256) NaScratch g_na_scratch;
+
+struct WinSet {
+    int n;
+    int round;  // histogram round of this launch
+    long long start[NA_MAX_WINDOWS];
+    long long count[NA_MAX_WINDOWS];
+};
+
+template <typename T>
+__global__ void na_sums(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S) {
+    const int w = blockIdx.y;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = ws.start[w] + k;
+        if (st[i] == ROBAST_ST_DETECTED) {
+            const double x = (double)fxy[i], y = (double)fxy[ld + i];
+            acc[0] += 1.0;
+            acc[1] += x;
+            acc[2] += y;
+            acc[3] += x * x;
+            acc[4] += y * y;
+        }
+    }
+    __shared__ double sh[5][NA_BLOCK];
+    for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int h = NA_BLOCK / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 5; ++c) S->part[((size_t)w * gridDim.x + blockIdx.x) * 5 + c] = sh[c][0];
+}
+
+__global__ void na_finish(int nblocks, int nwin, NaScratch* S) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwin) return;
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int c = 0; c < 5; ++c) a[c] += S->part[((size_t)w * nblocks + b) * 5 + c];
+    const double n = a[0];
+    const double cx = n > 0 ? a[1] / n : 0.0, cy = n > 0 ? a[2] / n : 0.0;
+    const double ms = n > 0 ? fmax(0.0, (a[3] + a[4]) / n - cx * cx - cy * cy) : 0.0;
+    S->res[4 * w + 0] = n;
+    S->res[4 * w + 1] = cx;
+    S->res[4 * w + 2] = cy;
+    S->res[4 * w + 3] = fmax(8.0 * sqrt(ms), 1e-300);
+}
+
+// bin of r in round j of window w: round 0 covers [0, range) plus an overflow
+// bin; later rounds cover [lo, hi) of the bin chosen before (clamped)
+__device__ __forceinline__ int na_bin(const NaScratch* S, int w, int j, double r) {
+    if (j == 0) {
+        const double range = S->res[4 * w + 3];
+        if (!(r < range)) return NA_BINS;
+        int b = (int)(r / range * NA_BINS);
+        return b < 0 ? 0 : (b >= NA_BINS ? NA_BINS - 1 : b);
+    }
+    const double lo = S->lohi[(w * NA_ROUNDS + j) * 2], hi = S->lohi[(w * NA_ROUNDS + j) * 2 + 1];
+    int b = hi > lo ? (int)((r - lo) / (hi - lo) * NA_BINS) : 0;
+    return b < 0 ? 0 : (b >= NA_BINS ? NA_BINS - 1 : b);
+}
+
+template <typename T>
+__device__ __forceinline__ bool na_member(const uint8_t* st, const T* fxy, long long ld, long long i, int w, int upto,
+                                          const NaScratch* S, double* r) {
+    if (st[i] != ROBAST_ST_DETECTED) return false;
+    const double dx = (double)fxy[i] - S->res[4 * w + 1], dy = (double)fxy[ld + i] - S->res[4 * w + 2];
+    *r = sqrt(dx * dx + dy * dy);
+    for (int j = 0; j < upto; ++j)
+        if (na_bin(S, w, j, *r) != S->chosen[w * NA_ROUNDS + j]) return false;
+    return true;
+}
+
+// histogram of round ws.round over the values that followed every earlier choice
+template <typename T>
+__global__ void na_hist(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S) {
+    __shared__ unsigned int h[NA_BINS + 1];
+    for (int k = threadIdx.x; k <= NA_BINS; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    const int w = blockIdx.y;
+    if (S->chosen[w * NA_ROUNDS + ws.round] == -2) {  // -2 marks a window still refining
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
+             k += (long long)gridDim.x * blockDim.x) {
+            double r;
+            if (na_member(st, fxy, ld, ws.start[w] + k, w, ws.round, S, &r))
+                atomicAdd(&h[na_bin(S, w, ws.round, r)], 1u);
+        }
+    }
+    __syncthreads();
+    unsigned long long* H = S->hist + (size_t)w * (NA_BINS + 1);
+    for (int k = threadIdx.x; k <= NA_BINS; k += blockDim.x)
+        if (h[k]) atomicAdd(H + k, (unsigned long long)h[k]);
+}
+
+// largest radius among the values of the first-round overflow bin
+template <typename T>
+__global__ void na_rmax(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S) {
+    const int w = blockIdx.y;
+    double m = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
+         k += (long long)gridDim.x * blockDim.x) {
+        double r;
+        if (na_member(st, fxy, ld, ws.start[w] + k, w, 1, S, &r)) m = fmax(m, r);
+    }
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(S->rmax_bits + w, bits);
+}
+
+// values of the final bin (chosen in rounds 0 .. ws.round - 1), at most NA_CAP per window
+template <typename T>
+__global__ void na_collect(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S, const int* upto) {
+    const int w = blockIdx.y;
+    const int u = upto[w];
+    if (u <= 0) return;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
+         k += (long long)gridDim.x * blockDim.x) {
+        double r;
+        if (na_member(st, fxy, ld, ws.start[w] + k, w, u, S, &r)) {
+            const unsigned long long j = atomicAdd(S->cnt + w, 1ull);
+            if (j < (unsigned long long)NA_CAP) S->vals[(size_t)w * NA_CAP + j] = r;
+        }
+    }
+}
+
+// device address of the scratch, looked up once per device
+std::mutex na_mu;
+NaScratch* na_dev[NA_MAX_DEVICES] = {nullptr};
+// static host mirrors (no allocation per call)
+unsigned long long na_h_hist[NA_MAX_WINDOWS * (NA_BINS + 1)];
+double na_h_vals[NA_MAX_WINDOWS * NA_CAP];
+double na_h_res[NA_MAX_WINDOWS * 4];
+int na_h_chosen[NA_MAX_WINDOWS * NA_ROUNDS];
+double na_h_lohi[NA_MAX_WINDOWS * NA_ROUNDS * 2];
+int na_h_upto[NA_MAX_WINDOWS];
+unsigned long long na_h_cnt[NA_MAX_WINDOWS];
+unsigned long long na_h_rmax[NA_MAX_WINDOWS];
+
+template <typename T>
+int na_impl(NaScratch* S, const uint8_t* st, const T* fxy, long long ld, const WinSet& ws0, cudaStream_t s,
+            double* results) {
+    WinSet ws = ws0;
+    const int nw = ws.n;
+    long long maxcount = 0;
+    for (int w = 0; w < nw; ++w) maxcount = std::max(maxcount, ws.count[w]);
+    // same block partition of the sums as robast_psf, so the centroids agree bit for bit
+    const int bx = (int)std::max(1LL, std::min<long long>(std::max(1, 512 / nw), (maxcount + NA_BLOCK - 1) / NA_BLOCK));
+    const dim3 grid(bx, nw);
+    na_sums<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S);
+    na_finish<<<(nw + 31) / 32, 32, 0, s>>>(bx, nw, S);
+    CU(cudaGetLastError(), "robast_psf_noalloc: launch");
+    CU(cudaMemcpyAsync(na_h_res, S->res, nw * 4 * sizeof(double), cudaMemcpyDeviceToHost, s),
+          "robast_psf_noalloc: copy");
+    CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+    long long rank[NA_MAX_WINDOWS];
+    bool active[NA_MAX_WINDOWS];
+    for (int w = 0; w < nw; ++w) {
+        const long long N = (long long)na_h_res[4 * w];
+        results[4 * w + 0] = na_h_res[4 * w];
+        results[4 * w + 1] = N ? na_h_res[4 * w + 1] : NAN;
+        results[4 * w + 2] = N ? na_h_res[4 * w + 2] : NAN;
+        results[4 * w + 3] = NAN;
+        rank[w] = N ? (long long)std::ceil(0.8 * (double)N) - 1 : -1;
+        active[w] = N > 0;
+        na_h_upto[w] = 0;
+        for (int j = 0; j < NA_ROUNDS; ++j) na_h_chosen[w * NA_ROUNDS + j] = active[w] ? -2 : -1;
+    }
+    int round = 0;
+    bool any = true;
+    while (any) {
+        CU(cudaMemcpyAsync(S->chosen, na_h_chosen, sizeof(int) * nw * NA_ROUNDS, cudaMemcpyHostToDevice, s),
+              "robast_psf_noalloc: copy");
+        CU(cudaMemcpyAsync(S->lohi, na_h_lohi, sizeof(double) * nw * NA_ROUNDS * 2, cudaMemcpyHostToDevice, s),
+              "robast_psf_noalloc: copy");
+        CU(cudaMemsetAsync(S->hist, 0, sizeof(unsigned long long) * nw * (NA_BINS + 1), s),
+              "robast_psf_noalloc: clear");
+        ws.round = round;
+        na_hist<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S);
+        CU(cudaGetLastError(), "robast_psf_noalloc: launch");
+        CU(cudaMemcpyAsync(na_h_hist, S->hist, sizeof(unsigned long long) * nw * (NA_BINS + 1),
+                              cudaMemcpyDeviceToHost, s),
+              "robast_psf_noalloc: copy");
+        CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+        bool need_rmax = false;
+        any = false;
+        for (int w = 0; w < nw; ++w) {
+            if (!active[w]) continue;
+            const unsigned long long* H = na_h_hist + (size_t)w * (NA_BINS + 1);
+            long long acc = 0;
+            int b = 0;
+            for (; b <= NA_BINS; ++b) {
+                if (acc + (long long)H[b] > rank[w]) break;
+                acc += (long long)H[b];
+            }
+            if (b > NA_BINS) return fail(ROBAST_E_CUDA, "robast_psf_noalloc: rank not found in window %d", w);
+            rank[w] -= acc;
+            na_h_chosen[w * NA_ROUNDS + round] = b;
+            const long long inbin = (long long)H[b];
+            const bool last_round = round + 1 >= NA_ROUNDS;
+            if (inbin <= NA_CAP || last_round) {
+                active[w] = false;
+                na_h_upto[w] = round + 1;
+                for (int j = round + 1; j < NA_ROUNDS; ++j) na_h_chosen[w * NA_ROUNDS + j] = -1;
+                continue;
+            }
+            // refine this bin in the next round
+            double lo, hi;
+            if (round == 0) {
+                const double range = na_h_res[4 * w + 3];
+                if (b == NA_BINS) {
+                    need_rmax = true;  // interval [range, max r] fixed after the max pass
+                    lo = range;
+                    hi = range;
+                } else {
+                    lo = range * b / NA_BINS;
+                    hi = range * (b + 1) / NA_BINS;
+                }
+            } else {
+                const double plo = na_h_lohi[(w * NA_ROUNDS + round) * 2];
+                const double phi = na_h_lohi[(w * NA_ROUNDS + round) * 2 + 1];
+                lo = plo + (phi - plo) * b / NA_BINS;
+                hi = plo + (phi - plo) * (b + 1) / NA_BINS;
+            }
+            // the next round's bins span a little beyond the computed edges: membership is
+            // decided by the chain of bin indices, the interval only spreads the values
+            const double pad = (hi - lo) * 1e-9 + 4.0 * std::fabs(hi) * 2.220446049250313e-16;
+            na_h_lohi[(w * NA_ROUNDS + round + 1) * 2] = lo - pad;
+            na_h_lohi[(w * NA_ROUNDS + round + 1) * 2 + 1] = hi + pad;
+            na_h_chosen[w * NA_ROUNDS + round + 1] = -2;
+            any = true;
+        }
+        if (need_rmax) {
+            CU(cudaMemcpyAsync(S->chosen, na_h_chosen, sizeof(int) * nw * NA_ROUNDS, cudaMemcpyHostToDevice, s),
+                  "robast_psf_noalloc: copy");
+            CU(cudaMemsetAsync(S->rmax_bits, 0, sizeof(unsigned long long) * nw, s), "robast_psf_noalloc: clear");
+            na_rmax<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S);
+            CU(cudaGetLastError(), "robast_psf_noalloc: launch");
+            CU(cudaMemcpyAsync(na_h_rmax, S->rmax_bits, sizeof(unsigned long long) * nw, cudaMemcpyDeviceToHost, s),
+                  "robast_psf_noalloc: copy");
+            CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+            for (int w = 0; w < nw; ++w) {
+                if (!active[w] || round != 0 || na_h_chosen[w * NA_ROUNDS] != NA_BINS) continue;
+                double rmax;
+                std::memcpy(&rmax, &na_h_rmax[w], sizeof rmax);
+                na_h_lohi[(w * NA_ROUNDS + 1) * 2 + 1] = rmax * (1.0 + 1e-12) + 1e-300;
+            }
+        }
+        ++round;
+    }
+    // collect the final bins and select
+    CU(cudaMemcpyAsync(S->chosen, na_h_chosen, sizeof(int) * nw * NA_ROUNDS, cudaMemcpyHostToDevice, s),
+          "robast_psf_noalloc: copy");
+    CU(cudaMemcpyAsync(S->lohi, na_h_lohi, sizeof(double) * nw * NA_ROUNDS * 2, cudaMemcpyHostToDevice, s),
+          "robast_psf_noalloc: copy");
+    CU(cudaMemsetAsync(S->cnt, 0, sizeof(unsigned long long) * nw, s), "robast_psf_noalloc: clear");
+    // the per-window round counts travel in the part[] area, unused from here on
+    CU(cudaMemcpyAsync(S->part, na_h_upto, sizeof(int) * nw, cudaMemcpyHostToDevice, s), "robast_psf_noalloc: copy");
+    na_collect<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S, reinterpret_cast<const int*>(S->part));
+    CU(cudaGetLastError(), "robast_psf_noalloc: launch");
+    CU(cudaMemcpyAsync(na_h_cnt, S->cnt, sizeof(unsigned long long) * nw, cudaMemcpyDeviceToHost, s),
+          "robast_psf_noalloc: copy");
+    CU(cudaMemcpyAsync(na_h_vals, S->vals, sizeof(double) * (size_t)nw * NA_CAP, cudaMemcpyDeviceToHost, s),
+          "robast_psf_noalloc: copy");
+    CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+    for (int w = 0; w < nw; ++w) {
+        if (na_h_upto[w] <= 0) continue;
+        const long long got = (long long)std::min<unsigned long long>(na_h_cnt[w], NA_CAP);
+        if (got <= 0) return fail(ROBAST_E_CUDA, "robast_psf_noalloc: selection lost values in window %d", w);
+        // a bin still over the cap after the last round spans less than one ulp:
+        // its values are all equal, so any of them is the answer
+        const long long k = std::min(rank[w], got - 1);
+        if ((long long)na_h_cnt[w] <= NA_CAP && got <= rank[w])
+            return fail(ROBAST_E_CUDA, "robast_psf_noalloc: selection lost values in window %d", w);
+        double* v = na_h_vals + (size_t)w * NA_CAP;
+        std::nth_element(v, v + k, v + got);
+        results[4 * w + 3] = v[k];
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int robast_psf_noalloc(const uint8_t* status, const void* focal_xy, int64_t ld, int32_t n_windows,
+                                  const int64_t* starts, const int64_t* counts, int32_t precision, void* stream,
+                                  double* results) {
+    if (!status || !focal_xy || !results || !starts || !counts)
+        return fail(ROBAST_E_NULL, "robast_psf_noalloc: NULL argument");
+    if (n_windows <= 0 || n_windows > NA_MAX_WINDOWS)
+        return fail(ROBAST_E_INVALID, "robast_psf_noalloc: n_windows must be in 1..%d (got %d)", NA_MAX_WINDOWS,
+                       n_windows);
+    if (precision != 32 && precision != 64)
+        return fail(ROBAST_E_INVALID, "robast_psf_noalloc: precision must be 32 or 64");
+    WinSet ws{};
+    ws.n = n_windows;
+    for (int w = 0; w < n_windows; ++w) {
+        if (starts[w] < 0 || counts[w] <= 0 || starts[w] + counts[w] > ld)
+            return fail(ROBAST_E_INVALID, "robast_psf_noalloc: window %d [%lld, +%lld) must lie inside [0, ld = %lld)",
+                           w, (long long)starts[w], (long long)counts[w], (long long)ld);
+        ws.start[w] = starts[w];
+        ws.count[w] = counts[w];
+    }
+    std::lock_guard<std::mutex> lk(na_mu);
+    int dev = 0;
+    CU(cudaGetDevice(&dev), "robast_psf_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(ROBAST_E_UNSUPPORTED, "robast_psf_noalloc: device %d", dev);
+    if (!na_dev[dev]) {
+        // the array's name is only a host-side stand-in: fetch its device address once
+        void* p = nullptr;
+        CU(cudaGetSymbolAddress(&p, g_na_scratch), "robast_psf_noalloc: cudaGetSymbolAddress");
+        na_dev[dev] = static_cast<NaScratch*>(p);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 32)
+        return na_impl<float>(na_dev[dev], status, static_cast<const float*>(focal_xy), ld, ws, s, results);
+    return na_impl<double>(na_dev[dev], status, static_cast<const double*>(focal_xy), ld, ws, s, results);
+}
