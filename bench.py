@@ -180,6 +180,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_ranks, barrier):
+    """Batched concentrator study: 64 Bezier-cone variants x 41 incidence angles
+    (0-40 deg) x photons per group generated on the device, all in ONE
+    persistent launch, replayed from a captured CUDA graph; launch shape from
+    the autotuner.  Metric: photon-bounces/s; result: collection efficiency per
+    (variant, angle)."""
+    import torch
+    import paper_1508_07803_gb300 as robast
+    from paper_1508_07803_gb300 import autotune
+
+    scene, groups = W.cone_batch(n_variants=64, angles_deg=W.CONE_ANGLES_DEG,
+                                 n_per_group=args.batch_photons_per_group, seed=0)
+    geom = robast.build_geometry(scene)
+    (block, bps), table = autotune.tune_sources(geom, groups, precision=32, max_bounces=30, stream=stream)
+    src = robast.sources_create(geom, groups)
+    counts = torch.zeros((src.n_groups, 8), dtype=torch.int64, device=geom_dev)
+    first_id = rank * src.n_photons
+
+    # capture on a side stream (graphs cannot be captured on the default stream)
+    cap = torch.cuda.Stream(device=geom_dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        robast.trace_sources(geom, src, counts, seed=0, precision=32, max_bounces=30, stream=cap,
+                             first_photon_id=first_id, block_size=block, blocks_per_sm=bps)  # warm-up
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            robast.trace_sources(geom, src, counts, seed=0, precision=32, max_bounces=30, stream=cap,
+                                 first_photon_id=first_id, block_size=block, blocks_per_sm=bps)
+    graph.replay()  # warm-up replay
+    torch.cuda.synchronize()
+    counts.zero_()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.batch_steps):
+        graph.replay()
+    t1.record(stream)
+    barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1))
+    c = counts.cpu().numpy()
+    bounces = sum_over_ranks(float(c[:, 0].sum()))
+    ce = (c[:, 1] / c[:, 7]).reshape(64, len(W.CONE_ANGLES_DEG))
+    angles = list(W.CONE_ANGLES_DEG)
+    summary = {f"{int(a)}deg": {"mean": float(ce[:, i].mean()), "min": float(ce[:, i].min()),
+                                "max": float(ce[:, i].max())}
+               for i, a in enumerate(angles) if int(a) in (0, 10, 20, 25, 30, 35, 40)}
+    src.close()
+    geom.close()
+    return {"value": bounces / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.batch_steps,
+            "steps": args.batch_steps, "photons_per_step": src.n_photons,
+            "bounces_per_step": bounces / args.batch_steps / ws,
+            "config": {"workload": "hex_bezier_cone_64_variants_x_41_angles", "variants": 64,
+                       "angles_deg": [0, 40, 1], "photons_per_group": args.batch_photons_per_group,
+                       "max_bounces": 30, "sources": "generated on the device (Philox stream 1)",
+                       "launch": "one persistent launch per step, replayed from a CUDA graph"},
+            "autotune": {"block": block, "blocks_per_sm": bps,
+                         "candidates_ms": {f"{b}x{p}": round(t, 3) for (b, p), t in table.items()}},
+            "collection_efficiency": summary}
+
+
 def traffic_from_profile(n_photons):
     """DRAM bytes of the trace kernel from the committed ncu summary, if it was
     taken on the current kernel source; else None."""
@@ -208,6 +270,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-photons-per-group", type=int, default=2_000_000)
+    ap.add_argument("--batch-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -335,6 +400,11 @@ def main():
                          "roofline": {"bound": "alu", "achieved": fl64 / (k64 * 1e-3) / 1e12, "peak": peak64 / 1e12,
                                       "unit": "TFLOP/s", "frac": fl64 / (k64 * 1e-3) / peak64,
                                       "peak_source": "DFMA throughput probe (measured)"}}
+
+    if not args.no_batched:
+        forms["batched_fp32"] = measure_batched(args, geom_dev=dev, stream=stream, ws=ws, rank=rank,
+                                                max_over_ranks=max_over_ranks, sum_over_ranks=sum_over_ranks,
+                                                barrier=barrier)
 
     e2e = None
     if not args.no_e2e:

@@ -238,6 +238,53 @@ int robast_trace_ex(const robast_geom* g, const void* origins, const void* dirs,
 int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
                       uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts);
 
+/* --------------------------------------------------- batched source groups */
+/*
+ * Batched study of many optical-system variants (the concentrator comparison
+ * of Sec. 3 / Fig. 2b: collection efficiency against incidence angle for many
+ * cone designs).  Photons are not passed in: each source group generates its
+ * photons on the device, uniform over a hexagon (flats at 0, 60, 120 deg of x,
+ * centre `centre`, in the plane z = centre[2]) with one direction and a
+ * wavelength uniform in [lam_min, lam_max] nm, and traces them through its
+ * variant.  Photons are numbered across groups in group order; photon i
+ * (id = first_photon_id + i) draws candidate points from Philox4x32-10 with
+ * counter (id_lo, id_hi, k, 1), k = 0, 1, ..., and accepts the first inside
+ * the hexagon (x = (2 u0 - 1) a, y = (2 u1 - 1) 2a / sqrt 3, u = (w + 1/2) 2^-32;
+ * wavelength from u2 of the accepted draw); the trace then uses stream 0 as
+ * in robast_trace.  Generation is FP64 with every operation rounded
+ * separately, rounded to the trace precision afterwards.
+ */
+typedef struct robast_source_group {
+    int32_t variant, reserved;
+    int64_t n_photons;
+    double centre[3];
+    double apothem;
+    double dir[3]; /* unit */
+    double lam_min, lam_max;
+} robast_source_group;
+
+typedef struct robast_sources robast_sources; /* opaque device-resident group table */
+
+/* Upload n_groups groups (host array, deep-copied) for geometry g.  Synchronous. */
+int robast_sources_create(const robast_geom* g, const robast_source_group* groups, int32_t n_groups,
+                          robast_sources** out);
+void robast_sources_free(robast_sources* s);
+int robast_sources_info(const robast_sources* s, int32_t* n_groups, int64_t* n_photons);
+
+/*
+ * Trace every photon of `src` in ONE persistent launch (all variants side by
+ * side).  group_counts: device [n_groups * ROBAST_N_COUNTERS] u64, added to
+ * (per group: [0] bounces, [1..6] photons per status, [7] photons), e.g.
+ * collection efficiency = counts[1] / counts[7].  `out` (device arrays of the
+ * total photon count, any field NULL) may be NULL.  opts as for
+ * robast_trace_ex (variant_of_photon must be NULL).  Asynchronous; issues
+ * only a memset and a kernel launch on the stream, so it can be captured in a
+ * CUDA graph.
+ */
+int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64_t seed,
+                         unsigned long long* group_counts, const robast_trace_out* out,
+                         const robast_trace_opts* opts);
+
 /* ----------------------------------------------------------- reductions */
 /*
  * Spot diagram statistics (Fig. 1 g-i) of the DETECTED photons of each of

@@ -56,6 +56,12 @@ class OScene(ctypes.Structure):
                 ("variant_offsets", ctypes.POINTER(ctypes.c_int32))]
 
 
+class OSourceGroup(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("pad", ctypes.c_int32), ("first", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("c", ctypes.c_double * 3), ("apothem", ctypes.c_double),
+                ("dir", ctypes.c_double * 3), ("lam_min", ctypes.c_double), ("lam_max", ctypes.c_double)]
+
+
 class OOutputs(ctypes.Structure):
     _fields_ = [("status", ctypes.c_void_p), ("bounces", ctypes.c_void_p), ("hit", ctypes.c_void_p),
                 ("dir", ctypes.c_void_p), ("last_surface", ctypes.c_void_p), ("focal_xy", ctypes.c_void_p),
@@ -93,6 +99,10 @@ def lib():
             _lib.oracle_reflectivity.argtypes = [ctypes.POINTER(OMaterial), ctypes.c_double]
             _lib.oracle_philox4x32_10.restype = None
             _lib.oracle_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            _lib.oracle_generate_sources.restype = ctypes.c_int64
+            _lib.oracle_generate_sources.argtypes = [ctypes.POINTER(OSourceGroup), ctypes.c_int32, ctypes.c_uint64,
+                                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_void_p, ctypes.c_void_p]
             _lib.oracle_intersect.restype = ctypes.c_int
             _lib.oracle_intersect.argtypes = [ctypes.POINTER(OSurface), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
@@ -234,3 +244,34 @@ def intersect(surface, p, d, eps=1e-12):
     if rc == 0:
         return None
     return t.value, nf, lp
+
+
+def generate_sources(groups, seed: int = 0, first_photon_id: int = 0):
+    """Photons of source groups from Philox stream 1 (see oracle_generate_sources).
+
+    groups: list of dicts with keys variant, n, centre (3), apothem, dir (3),
+    lam (min, max); photons are numbered in group order.  Returns (Bundle-like
+    dict with origins [3, n], dirs [3, n], wavelengths [n]), variant [n], and
+    the number of photons with no accepted draw.
+    """
+    ng = len(groups)
+    arr = (OSourceGroup * ng)()
+    first = 0
+    for k, g in enumerate(groups):
+        a = arr[k]
+        a.variant = int(g["variant"])
+        a.first = first
+        a.n = int(g["n"])
+        _fill(a.c, g["centre"])
+        a.apothem = float(g["apothem"])
+        _fill(a.dir, g["dir"])
+        a.lam_min, a.lam_max = float(g["lam"][0]), float(g["lam"][1])
+        first += int(g["n"])
+    n = first
+    o = np.zeros((3, n))
+    d = np.zeros((3, n))
+    lam = np.zeros(n)
+    var = np.zeros(n, np.int32)
+    failed = lib().oracle_generate_sources(arr, ng, seed & (2**64 - 1), first_photon_id, o.ctypes.data,
+                                           d.ctypes.data, lam.ctypes.data, var.ctypes.data)
+    return {"origins": o, "dirs": d, "wavelengths": lam}, var, int(failed)

@@ -27,6 +27,7 @@
 #include "oracle.h"
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -709,6 +710,54 @@ int check_scene(const o_scene* sc) {
 }  // namespace
 
 extern "C" {
+
+/* Source bundles of the batched concentrator study (uniform over the entrance
+ * hexagon, Sec. 3 / Fig. 2b): rejection sampling in the bounding rectangle
+ * [-a, a] x [-R, R], R = 2a / sqrt(3); candidate k of photon id uses Philox
+ * counter (id_lo, id_hi, k, 1): x = (2 u0 - 1) a, y = (2 u1 - 1) R, accepted
+ * iff max(|x|, |x/2 + s y|, |-x/2 + s y|) <= a with s = sqrt(3)/2; the
+ * wavelength is lam_min + (lam_max - lam_min) u2 of the accepted draw. */
+int64_t oracle_generate_sources(const o_source_group* groups, int32_t n_groups, uint64_t seed,
+                                int64_t first_photon_id, double* O, double* D, double* L, int32_t* V) {
+    int64_t n = 0;
+    for (int g = 0; g < n_groups; ++g) n = std::max<int64_t>(n, groups[g].first + groups[g].n);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const double s60 = std::sqrt(3.0) / 2.0;
+    int64_t failed = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        const o_source_group& G = groups[g];
+        const double a = G.apothem, R = G.apothem * 2.0 / std::sqrt(3.0);
+        for (int64_t j = 0; j < G.n; ++j) {
+            const int64_t i = G.first + j;
+            const int64_t pid = first_photon_id + i;
+            bool ok = false;
+            double x = NAN, y = NAN, lam = NAN;
+            for (uint32_t k = 0; k < 64 && !ok; ++k) {
+                const uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)((uint64_t)pid >> 32), k, 1u};
+                uint32_t w[4];
+                philox(ctr, key, w);
+                const double cx = (2.0 * unit_open(w[0]) - 1.0) * a;
+                const double cy = (2.0 * unit_open(w[1]) - 1.0) * R;
+                const double m = std::fmax(std::fabs(cx), std::fmax(std::fabs(0.5 * cx + s60 * cy),
+                                                                    std::fabs(-0.5 * cx + s60 * cy)));
+                if (m <= a) {
+                    ok = true;
+                    x = cx;
+                    y = cy;
+                    lam = G.lam_min + (G.lam_max - G.lam_min) * unit_open(w[2]);
+                }
+            }
+            if (!ok) ++failed;
+            O[i] = G.c[0] + x;
+            O[n + i] = G.c[1] + y;
+            O[2 * n + i] = G.c[2];
+            for (int c = 0; c < 3; ++c) D[c * n + i] = G.dir[c];
+            L[i] = lam;
+            V[i] = G.variant;
+        }
+    }
+    return failed;
+}
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     philox(ctr, key, out);

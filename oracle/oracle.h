@@ -77,6 +77,27 @@ typedef struct {
     double* cond;         /* [n] optional: sum over interactions of 1 / |cos(incidence)| */
 } o_outputs;
 
+/* A source group: photons uniform over a hexagon (flats at 0, 60, 120 deg,
+ * centre c, apothem a) in the plane z = c[2], all with direction dir, and
+ * wavelength uniform in [lam_min, lam_max]; the photons of group g are ids
+ * first .. first + n - 1 (plus the call's first_photon_id). */
+typedef struct {
+    int32_t variant, pad;
+    int64_t first, n;
+    double c[3];
+    double apothem;
+    double dir[3];
+    double lam_min, lam_max;
+} o_source_group;
+
+/* Generate the photons of the groups from Philox stream 1 (rejection sampling,
+ * draw k of photon id uses counter (id_lo, id_hi, k, 1)).  Writes origins [3n],
+ * dirs [3n], wavelengths [n], variant [n] for n = sum of group sizes.  Returns
+ * the number of photons that found no point in 64 draws (they get NaN). */
+int64_t oracle_generate_sources(const o_source_group* groups, int32_t n_groups, uint64_t seed,
+                                int64_t first_photon_id, double* origins, double* dirs, double* wavelengths,
+                                int32_t* variant);
+
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 

@@ -370,3 +370,88 @@ def psf_noalloc(status, focal_xy, windows, precision: int = 32, stream=None):
     _check(lib.robast_psf_noalloc(_ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
                                   ctypes.c_void_p(stream.cuda_stream), res))
     return [tuple(res[4 * w:4 * w + 4]) for w in range(nw)]
+
+
+class SourceGroupDesc(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_photons", ctypes.c_int64),
+                ("centre", ctypes.c_double * 3), ("apothem", ctypes.c_double), ("dir", ctypes.c_double * 3),
+                ("lam_min", ctypes.c_double), ("lam_max", ctypes.c_double)]
+
+
+class Sources:
+    """Device-resident source groups (robast_sources_create)."""
+
+    def __init__(self, handle, n_groups, n_photons):
+        self._h = ctypes.c_void_p(handle)
+        self.n_groups, self.n_photons = n_groups, n_photons
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RobastError("sources already freed")
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value and _lib is not None:
+            _lib.robast_sources_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sources_create(geom: Geometry, groups) -> Sources:
+    """robast_sources_create from a list of dicts: variant, n, centre (3), apothem, dir (3), lam (min, max)."""
+    lib = load()
+    lib.robast_sources_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+    lib.robast_sources_free.argtypes = [ctypes.c_void_p]
+    lib.robast_sources_free.restype = None
+    lib.robast_sources_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64)]
+    arr = (SourceGroupDesc * len(groups))()
+    for k, g in enumerate(groups):
+        a = arr[k]
+        a.variant = int(g["variant"])
+        a.n_photons = int(g["n"])
+        _fill(a.centre, g["centre"], 3)
+        a.apothem = float(g["apothem"])
+        _fill(a.dir, g["dir"], 3)
+        a.lam_min, a.lam_max = float(g["lam"][0]), float(g["lam"][1])
+    h = ctypes.c_void_p()
+    _check(lib.robast_sources_create(geom.handle, arr, len(groups), ctypes.byref(h)))
+    ng, npho = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib.robast_sources_info(h, ctypes.byref(ng), ctypes.byref(npho)))
+    return Sources(h.value, ng.value, npho.value)
+
+
+def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, precision: int = 32,
+                  max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
+                  eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0):
+    """robast_trace_sources: trace every photon of the source groups in one launch.
+
+    group_counts: CUDA int64 tensor [n_groups, 8], added to.  out: optional
+    dict of per-photon output tensors (see alloc_outputs) for src.n_photons.
+    """
+    import torch
+    lib = load()
+    lib.robast_trace_sources.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                         ctypes.POINTER(TraceOut), ctypes.POINTER(TraceOpts)]
+    if tuple(group_counts.shape) != (src.n_groups, N_COUNTERS) or group_counts.dtype != torch.int64 \
+            or not group_counts.is_cuda:
+        raise RobastError("trace_sources: group_counts must be a CUDA int64 tensor [n_groups, 8]")
+    if stream is None:
+        stream = torch.cuda.current_stream(group_counts.device)
+    tout = None
+    if out is not None:
+        tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
+                          for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
+    o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), None, first_photon_id, eps, block_size,
+              blocks_per_sm)
+    _check(lib.robast_trace_sources(geom.handle, src.handle, ctypes.c_uint64(seed & (2**64 - 1)),
+                                    ctypes.c_void_p(group_counts.data_ptr()),
+                                    ctypes.byref(tout) if tout is not None else None, ctypes.byref(o)))
+    return group_counts

@@ -9,8 +9,8 @@ namespace robast {
 
 // Occupancy: resident blocks of trace_kernel<T, block> per SM for `smem`
 // bytes of dynamic shared memory (0 if the configuration cannot launch).
-int trace_blocks_per_sm_f32(int block, size_t smem);
-int trace_blocks_per_sm_f64(int block, size_t smem);
+int trace_blocks_per_sm_f32(int block, size_t smem, bool src);
+int trace_blocks_per_sm_f64(int block, size_t smem, bool src);
 
 // Launch the persistent trace kernel; returns the cudaError_t of the launch.
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s);

@@ -741,10 +741,23 @@ extern "C" void robast_trace_opts_default(robast_trace_opts* o) {
 // Shared memory one block may use for staged tables.
 static const size_t kSmemCap = 200 * 1024;
 
+struct robast_sources {
+    int device = 0;
+    int n_groups = 0;
+    long long n_photons = 0;
+    SrcGroup* d_groups = nullptr;
+};
+
 template <typename T>
 static int do_trace(const robast_geom* g, const void* origins, const void* dirs, const void* wl, int64_t n,
-                    uint64_t seed, const robast_trace_out* out, const robast_trace_opts& o) {
+                    uint64_t seed, const robast_trace_out* out, const robast_trace_opts& o,
+                    const robast_sources* src = nullptr, unsigned long long* gcounts = nullptr) {
     TraceArgs<T> a{};
+    if (src) {
+        a.groups = src->d_groups;
+        a.n_groups = src->n_groups;
+        a.gcounts = gcounts;
+    }
     a.tab = sizeof(T) == 4 ? g->tab32 : g->tab64;
     a.o = static_cast<const T*>(origins);
     a.d = static_cast<const T*>(dirs);
@@ -780,7 +793,9 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
         return fail(ROBAST_E_INVALID, "robast_trace: block_size must be 64, 128 or 256 (got %d)", block);
     if (a.units && block != 128)
         return fail(ROBAST_E_INVALID, "robast_trace: the counting build (work_units) runs with block_size 128 only");
-    int bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem) : trace_blocks_per_sm_f64(block, smem);
+    if (a.units && src) return fail(ROBAST_E_INVALID, "robast_trace_sources: no counting build for source mode");
+    int bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem, src != nullptr)
+                             : trace_blocks_per_sm_f64(block, smem, src != nullptr);
     if (bps <= 0) return fail(ROBAST_E_CUDA, "robast_trace: kernel cannot launch with %zu bytes of shared memory", smem);
     if (o.blocks_per_sm > 0) bps = std::min(bps, (int)o.blocks_per_sm);
     long long grid = (long long)g->num_sms * bps;
@@ -828,6 +843,87 @@ extern "C" int robast_trace_ex(const robast_geom* g, const void* origins, const 
 extern "C" int robast_trace(const robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
                             int64_t n, uint64_t seed, const robast_trace_out* out) {
     return robast_trace_ex(g, origins, dirs, wavelengths, n, seed, out, nullptr);
+}
+
+// ---------------------------------------------------------- source groups
+extern "C" int robast_sources_create(const robast_geom* g, const robast_source_group* groups, int32_t n_groups,
+                                     robast_sources** out) {
+    if (!out) return fail(ROBAST_E_NULL, "robast_sources_create: out is NULL");
+    *out = nullptr;
+    if (!g || !groups) return fail(ROBAST_E_NULL, "robast_sources_create: NULL argument");
+    if (n_groups <= 0) return fail(ROBAST_E_INVALID, "robast_sources_create: n_groups must be > 0");
+    std::vector<SrcGroup> h(n_groups);
+    long long first = 0;
+    for (int k = 0; k < n_groups; ++k) {
+        const robast_source_group& q = groups[k];
+        if (q.variant < 0 || q.variant >= g->n_var)
+            return fail(ROBAST_E_INVALID, "robast_sources_create: group %d: variant %d out of range", k, q.variant);
+        if (q.n_photons <= 0) return fail(ROBAST_E_INVALID, "robast_sources_create: group %d: n_photons must be > 0", k);
+        if (!(q.apothem > 0)) return fail(ROBAST_E_INVALID, "robast_sources_create: group %d: apothem must be > 0", k);
+        const double dn = q.dir[0] * q.dir[0] + q.dir[1] * q.dir[1] + q.dir[2] * q.dir[2];
+        if (std::fabs(dn - 1.0) > 1e-9) return fail(ROBAST_E_INVALID, "robast_sources_create: group %d: dir not unit", k);
+        SrcGroup& G = h[k];
+        for (int c = 0; c < 3; ++c) {
+            G.c[c] = q.centre[c];
+            G.dir[c] = q.dir[c];
+        }
+        G.a = q.apothem;
+        G.R = q.apothem * 2.0 / std::sqrt(3.0);
+        G.lam0 = q.lam_min;
+        G.lam1 = q.lam_max;
+        G.first = first;
+        G.n = q.n_photons;
+        G.variant = q.variant;
+        first += q.n_photons;
+    }
+    robast_sources* s = new (std::nothrow) robast_sources();
+    if (!s) return fail(ROBAST_E_OOM, "robast_sources_create: host allocation failed");
+    s->n_groups = n_groups;
+    s->n_photons = first;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_groups, h.size() * sizeof(SrcGroup));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_groups, h.data(), h.size() * sizeof(SrcGroup), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (s->d_groups) cudaFree(s->d_groups);
+        delete s;
+        return cuda_fail(e, "robast_sources_create");
+    }
+    *out = s;
+    return 0;
+}
+
+extern "C" void robast_sources_free(robast_sources* s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    cudaFree(s->d_groups);
+    delete s;
+}
+
+extern "C" int robast_sources_info(const robast_sources* s, int32_t* n_groups, int64_t* n_photons) {
+    if (!s) return fail(ROBAST_E_NULL, "robast_sources_info: NULL");
+    if (n_groups) *n_groups = s->n_groups;
+    if (n_photons) *n_photons = s->n_photons;
+    return 0;
+}
+
+extern "C" int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64_t seed,
+                                    unsigned long long* group_counts, const robast_trace_out* out,
+                                    const robast_trace_opts* opts) {
+    robast_trace_opts o;
+    robast_trace_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_bounces == 0) o.max_bounces = 100;
+    if (o.precision == 0) o.precision = 32;
+    if (!g || !src) return fail(ROBAST_E_NULL, "robast_trace_sources: NULL geometry or sources");
+    if (!group_counts) return fail(ROBAST_E_NULL, "robast_trace_sources: group_counts is required");
+    if (o.variant_of_photon) return fail(ROBAST_E_INVALID, "robast_trace_sources: variants come from the groups");
+    robast_trace_out none{};
+    const robast_trace_out* po = out ? out : &none;
+    const char dummy = 0;  // the input pointers are unused in source mode
+    int rc = check_trace_args(g, &dummy, &dummy, &dummy, src->n_photons, po, o);
+    if (rc) return rc;
+    return o.precision == 32 ? do_trace<float>(g, nullptr, nullptr, nullptr, src->n_photons, seed, po, o, src, group_counts)
+                             : do_trace<double>(g, nullptr, nullptr, nullptr, src->n_photons, seed, po, o, src, group_counts);
 }
 
 static int grow(void** p, size_t* have, size_t need, const char* what) {

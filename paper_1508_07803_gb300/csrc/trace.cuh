@@ -95,6 +95,19 @@ struct Tables {
     int n_surf, n_nodes, n_prims, n_var, n_glob, n_mat, n_med, pad;
 };
 
+// A source group (batched concentrator study): photons uniform over a hexagon
+// of apothem a (bounding rectangle half-sizes a, R = 2a / sqrt 3) centred at c
+// in the plane z = c.z, direction dir, wavelength uniform in [lam0, lam1];
+// its photons are work indices first .. first + n - 1.
+struct SrcGroup {
+    double c[3];
+    double a, R;
+    double dir[3];
+    double lam0, lam1;
+    long long first, n;
+    int variant, pad;
+};
+
 template <typename T>
 struct TraceArgs {
     Tables tab;
@@ -119,7 +132,12 @@ struct TraceArgs {
     unsigned long long* counters;
     unsigned long long* work;
     unsigned long long* units;  // [U_N], counting instantiation only
+    const SrcGroup* groups;     // source mode: photons generated on the device
+    int n_groups;
+    unsigned long long* gcounts;  // source mode: [n_groups][8] counters per group
 };
+
+
 
 // ------------------------------------------------------------ math helpers
 __device__ __forceinline__ float t_sqrt(float x) { return sqrtf(x); }
@@ -171,6 +189,33 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 template <typename T>
 __device__ __forceinline__ T unit_open(uint32_t w) {
     return (T(w) + T(0.5)) * T(2.3283064365386963e-10);  // 2^-32
+}
+
+// Photon of work index idx from its source group (Philox stream 1): rejection
+// sampling in the bounding rectangle, candidate k from counter
+// (id_lo, id_hi, k, 1).  FP64 with every operation rounded separately, so the
+// generated inputs are bit-identical to the CPU reference's.  Returns false if
+// 64 candidates were all rejected (probability 0.25^64).
+__device__ __forceinline__ bool gen_source(const SrcGroup& G, long long pid, uint2 key, double o[3], double* lam) {
+    const double s60 = 0.86602540378443864676;
+    for (uint32_t k = 0; k < 64; ++k) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), k, 1u), key);
+        const double u0 = __dmul_rn(__dadd_rn((double)w.x, 0.5), 2.3283064365386963e-10);
+        const double u1 = __dmul_rn(__dadd_rn((double)w.y, 0.5), 2.3283064365386963e-10);
+        const double x = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u0), 1.0), G.a);
+        const double y = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u1), 1.0), G.R);
+        const double hx = __dmul_rn(0.5, x), sy = __dmul_rn(s60, y);
+        const double m = fmax(fabs(x), fmax(fabs(__dadd_rn(hx, sy)), fabs(__dadd_rn(-hx, sy))));
+        if (m <= G.a) {
+            const double u2 = __dmul_rn(__dadd_rn((double)w.z, 0.5), 2.3283064365386963e-10);
+            o[0] = __dadd_rn(G.c[0], x);
+            o[1] = __dadd_rn(G.c[1], y);
+            o[2] = G.c[2];
+            *lam = __dadd_rn(G.lam0, __dmul_rn(__dsub_rn(G.lam1, G.lam0), u2));
+            return true;
+        }
+    }
+    return false;
 }
 
 // ------------------------------------------------------ frame transforms
@@ -695,13 +740,17 @@ struct Photon {
     int bounces;
     int mat_cache;
     int last;  // last surface hit, -1: none
+    int group; // source mode: group of the photon
+    bool bad;  // source mode: no point generated
     unsigned long long thr;
 };
 
 // STAGED: the tables fit in shared memory and every table pointer is derived
 // from the shared array (so the loads are shared-memory loads); otherwise the
 // tables are read from global memory through L1.
-template <typename T, int BLOCK, bool C = false, bool STAGED = true>
+// SRC: photons come from source groups generated on the device (batched
+// study) instead of caller arrays; per-group counters are accumulated.
+template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false>
 __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
     unsigned cnt[U_N];
     if constexpr (C) {
@@ -743,6 +792,18 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
     Photon<T> ph;
     ph.i = -1;
     bool done = false;
+    int cur_g = -1;                // source mode: group whose counts this thread holds
+    unsigned int gc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    auto flush_group = [&]() {
+        if constexpr (SRC) {
+            if (cur_g >= 0)
+                for (int k = 0; k < 8; ++k)
+                    if (gc[k]) {
+                        atomicAdd(A.gcounts + (size_t)cur_g * 8 + k, (unsigned long long)gc[k]);
+                        gc[k] = 0;
+                    }
+        }
+    };
     unsigned long long my_bounces = 0;
     unsigned int my_status[7] = {0, 0, 0, 0, 0, 0, 0};
 
@@ -759,10 +820,31 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
                 const long long idx = (long long)base + __popc(m & lt_mask);
                 if (idx < n) {
                     ph.i = idx;
-                    ph.p = mk(A.o[idx], A.o[n + idx], A.o[2 * n + idx]);
-                    ph.d = mk(A.d[idx], A.d[n + idx], A.d[2 * n + idx]);
-                    ph.lam = A.lam[idx];
-                    ph.var = A.vop ? A.vop[idx] : 0;
+                    if constexpr (SRC) {
+                        // group: the last one whose first index is <= idx
+                        int lo = 0, hi = A.n_groups - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (A.groups[mid].first <= idx)
+                                lo = mid;
+                            else
+                                hi = mid - 1;
+                        }
+                        const SrcGroup& G = A.groups[lo];
+                        double o[3], lam;
+                        ph.bad = !gen_source(G, A.first_id + idx, key, o, &lam);
+                        ph.p = mk((T)o[0], (T)o[1], (T)o[2]);
+                        ph.d = mk((T)G.dir[0], (T)G.dir[1], (T)G.dir[2]);
+                        ph.lam = (T)lam;
+                        ph.var = G.variant;
+                        ph.group = lo;
+                    } else {
+                        ph.p = mk(A.o[idx], A.o[n + idx], A.o[2 * n + idx]);
+                        ph.d = mk(A.d[idx], A.d[n + idx], A.d[2 * n + idx]);
+                        ph.lam = A.lam[idx];
+                        ph.var = A.vop ? A.vop[idx] : 0;
+                        ph.bad = false;
+                    }
                     ph.bounces = 0;
                     ph.mat_cache = -1;
                     ph.last = -1;
@@ -780,7 +862,7 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
         Best<T> bst;
         bool overflow = false;
         V3<T> fpos = mk(T(0), T(0), T(0));
-        const bool bad_var = ph.var < 0 || ph.var >= tb.n_var;  // never index past the variant table
+        const bool bad_var = ph.bad || ph.var < 0 || ph.var >= tb.n_var;  // never index past the variant table
         if (!bad_var) nearest_hit<C>(tb, ph.var, ph.p, ph.d, A.eps, A.newton_tol, bst, overflow, cnt);
         if (bad_var || overflow || bst.err) {
             status = ST_ERROR;
@@ -884,8 +966,18 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
         if (A.last) A.last[i] = ph.last;
         my_bounces += (unsigned long long)ph.bounces;
         my_status[status] += 1u;
+        if constexpr (SRC) {
+            if (ph.group != cur_g) {
+                flush_group();
+                cur_g = ph.group;
+            }
+            gc[0] += (unsigned)ph.bounces;
+            gc[status] += 1u;
+            gc[7] += 1u;
+        }
         ph.i = -1;
     }
+    flush_group();
     if constexpr (C) {
         // per-thread unit counts -> warp sums -> one atomic per warp and unit
 #pragma unroll

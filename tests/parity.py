@@ -9,15 +9,16 @@ Tolerances (per photon, on the same seeded inputs):
       every photon whose status, bounce count or last surface differs must
       have met an aperture / wedge / range edge within 1e-5 (relative) on its
       oracle path; photons whose path is the same have directions within
-      1e-5 rad and positions within 1e-6 f x max(1, K - 1), where K is the
+      max(1e-5, 1e-6 (K - 1)) rad and positions within 1e-6 f x max(1, K - 1), where K is the
       path's conditioning, the sum over its interactions of 1 / |cos(theta)|
       (theta = angle of incidence).  First-order error propagation: every
       interaction rounds the new direction to FP32, that error grows with the
       distance travelled, and a hit at incidence theta stretches it by
-      1 / |cos(theta)|.  Telescope paths (two or three near-normal
-      interactions, K ~ 2-3) stay at 1e-6 to 2e-6 f; concentrator paths with
-      tens of wall reflections, or a grazing last hit, get the allowance their
-      geometry implies.
+      1 / |cos(theta)|; a position error on a curved wall turns the next
+      normal, so direction errors accumulate per redirection too.  Telescope
+      paths (two or three near-normal interactions, K ~ 2-3) stay at 1e-5 rad
+      and 1e-6 to 2e-6 f; concentrator paths with tens of wall reflections, or
+      a grazing last hit, get the allowance their geometry implies.
 """
 import numpy as np
 
@@ -81,6 +82,11 @@ def compare(gpu, ref, precision, focal_length, label=""):
     worst = np.argmax(np.where(ok, eh / allow, 0.0))
     assert np.all(eh[ok] <= allow[ok]), \
         f"{label}: FP32 hit error {eh[worst]} > {allow[worst]} (photon {worst}, {ref['bounces'][worst]} bounces)"
-    assert np.all(ed[ok] <= 1e-5), f"{label}: FP32 direction error {ed[ok].max()}"
+    dallow = np.maximum(1e-5, 1e-6 * (ref["cond"] - 1.0))
+    worst_d = np.argmax(np.where(ok, ed / dallow, 0.0))
+    report["max_ddir_over_allowance"] = float((ed[ok] / dallow[ok]).max(initial=0.0))
+    assert np.all(ed[ok] <= dallow[ok]), \
+        f"{label}: FP32 direction error {ed[worst_d]} > {dallow[worst_d]} (photon {worst_d}, " \
+        f"{ref['bounces'][worst_d]} bounces, K = {ref['cond'][worst_d]:.1f})"
     assert np.all(ef[det] <= allow[det]), f"{label}: FP32 focal error {ef[det].max()}"
     return report

@@ -1,0 +1,106 @@
+"""Batched concentrator study on the GPU: photons generated on the device from
+source groups (many cone variants x incidence angles in one launch) against
+the oracle fed with its own independently generated photons."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+from parity import compare, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+robast = pytest.importorskip("paper_1508_07803_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    robast.load()
+
+
+def _setup(nv=6, angles=(0.0, 12.0, 25.0, 31.0, 40.0), n=301, seed=2):
+    scene, groups = W.cone_batch(n_variants=nv, angles_deg=angles, n_per_group=n, seed=seed)
+    return scene, groups
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batched_sources_match_oracle_per_photon(precision):
+    scene, groups = _setup()
+    geom = robast.build_geometry(scene)
+    src = robast.sources_create(geom, groups)
+    counts = torch.zeros((src.n_groups, 8), dtype=torch.int64, device="cuda")
+    out = robast.alloc_outputs(src.n_photons, precision, "cuda")
+    robast.trace_sources(geom, src, counts, seed=5, precision=precision, max_bounces=30, out=out,
+                         first_photon_id=1000)
+    torch.cuda.synchronize()
+    g = to_numpy(out)
+    b, var, failed = oracle.generate_sources(groups, seed=5, first_photon_id=1000)
+    assert failed == 0
+    bundle = W.Bundle(b["origins"], b["dirs"], b["wavelengths"])
+    if precision == 32:
+        bundle = bundle.rounded_to(np.float32)
+    ref = oracle.trace(scene, bundle, seed=5, first_photon_id=1000, max_bounces=30, variant_of_photon=var,
+                       eps=oracle.default_eps(scene, precision))
+    print(compare(g, ref, precision, scene.focal_length, f"sources fp{precision}"))
+    # per-group counters agree with the per-photon statuses
+    c = counts.cpu().numpy()
+    first = 0
+    for k, grp in enumerate(groups):
+        sl = slice(first, first + grp["n"])
+        st = g["status"][sl]
+        assert c[k, 7] == grp["n"]
+        assert c[k, 0] == g["bounces"][sl].astype(np.int64).sum()
+        for s in range(1, 7):
+            assert c[k, s] == (st == s).sum()
+        first += grp["n"]
+    src.close()
+    geom.close()
+
+
+def test_batched_sources_counts_only_and_graph_replay():
+    scene, groups = _setup(nv=4, angles=(0.0, 20.0, 35.0), n=20_011)
+    geom = robast.build_geometry(scene)
+    src = robast.sources_create(geom, groups)
+    ref = torch.zeros((src.n_groups, 8), dtype=torch.int64, device="cuda")
+    robast.trace_sources(geom, src, ref, seed=9)
+    torch.cuda.synchronize()
+    # the launch records into a CUDA graph and replays with identical results
+    counts = torch.zeros_like(ref)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        robast.trace_sources(geom, src, counts, seed=9, stream=s)  # warm-up outside capture
+        torch.cuda.synchronize()
+        counts.zero_()
+        with torch.cuda.graph(graph, stream=s):
+            robast.trace_sources(geom, src, counts, seed=9, stream=s)
+    torch.cuda.synchronize()
+    counts.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(counts, 2 * ref)
+    ce = (ref[:, 1].double() / ref[:, 7].double()).cpu().numpy()
+    assert np.all((ce >= 0) & (ce <= 1))
+    src.close()
+    geom.close()
+
+
+def test_batched_sources_reject_bad_groups():
+    scene, groups = _setup(nv=2, angles=(0.0,), n=10)
+    geom = robast.build_geometry(scene)
+    bad = dict(groups[0])
+    bad["variant"] = 7
+    with pytest.raises(robast.RobastError, match="variant"):
+        robast.sources_create(geom, [bad])
+    bad = dict(groups[0])
+    bad["dir"] = (0.0, 0.0, -2.0)
+    with pytest.raises(robast.RobastError, match="unit"):
+        robast.sources_create(geom, [bad])
+    geom.close()

@@ -410,3 +410,24 @@ def sct_workload(n_per_angle: int, seed: int = 0, angles_deg=SCT_ANGLES_DEG):
     bs = [disk_bundle(n_per_angle, 5.0, 10.0, math.radians(a), (300.0, 600.0), seed, stream=200 + k)
           for k, a in enumerate(angles_deg)]
     return scene, concat(bs)
+
+
+CONE_ANGLES_DEG = tuple(float(a) for a in range(41))
+
+
+def cone_batch(n_variants: int = 64, angles_deg=CONE_ANGLES_DEG, n_per_group: int = 2_000_000, seed: int = 0,
+               lam=(300.0, 600.0)):
+    """Batched hexagonal-concentrator study: n_variants cone designs (one
+    scene with variant offsets) and one source group per (variant, incidence
+    angle): photons uniform over the 50 mm entrance hexagon, 0.1 mm above the
+    window, tilted towards the flat at azimuth 0."""
+    scene = cone_scene(n_variants=n_variants, seed=seed)
+    Hs = cone_heights(n_variants, seed=seed)
+    groups = []
+    for v in range(n_variants):
+        for a in angles_deg:
+            th = math.radians(a)
+            groups.append(dict(variant=v, n=int(n_per_group), centre=(0.0, 0.0, Hs[v] + CONE_WINDOW + 1e-4),
+                               apothem=CONE_A_IN, dir=(math.sin(th), 0.0, -math.cos(th)), lam=lam,
+                               angle_deg=a))
+    return scene, groups
