@@ -103,6 +103,12 @@ def lib():
             _lib.oracle_generate_sources.argtypes = [ctypes.POINTER(OSourceGroup), ctypes.c_int32, ctypes.c_uint64,
                                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                      ctypes.c_void_p, ctypes.c_void_p]
+            _lib.oracle_objective.restype = ctypes.c_int
+            _lib.oracle_objective.argtypes = [ctypes.POINTER(OScene), ctypes.c_int64, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                              ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p]
             _lib.oracle_intersect.restype = ctypes.c_int
             _lib.oracle_intersect.argtypes = [ctypes.POINTER(OSurface), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
@@ -275,3 +281,41 @@ def generate_sources(groups, seed: int = 0, first_photon_id: int = 0):
     failed = lib().oracle_generate_sources(arr, ng, seed & (2**64 - 1), first_photon_id, o.ctypes.data,
                                            d.ctypes.data, lam.ctypes.data, var.ctypes.data)
     return {"origins": o, "dirs": d, "wavelengths": lam}, var, int(failed)
+
+
+N_PARAM = 16
+OBJECTIVES = {"msr": 0, "soft_ce": 1, "centroid_x": 2, "centroid_y": 3}
+
+
+def objective(scene, bundle, objective="msr", seed=0, first_photon_id=0, max_bounces=100, eps=None,
+              variant_of_photon=None, tau=0.5e-3, delta=None, grad=True, n_threads=0):
+    """Frozen-path objective (and its gradient by dual numbers) -- see oracle.h.
+
+    delta: optional [n_surfaces, 16] parameter offsets (tilt x, y; A1..A8;
+    Bezier P0r, P0z, P1r, P1z, P2r, P2z).  Returns (value, grad [n_surfaces, 16] or None).
+    """
+    L = lib()
+    n = bundle.n
+    o = np.ascontiguousarray(bundle.origins, dtype=np.float64).reshape(3, n)
+    d = np.ascontiguousarray(bundle.dirs, dtype=np.float64).reshape(3, n)
+    wl = np.ascontiguousarray(bundle.wavelengths, dtype=np.float64)
+    if eps is None:
+        eps = default_eps(scene, 64)
+    if n_threads <= 0:
+        n_threads = os.cpu_count() or 1
+    ns = len(scene.surfaces)
+    dl = None
+    if delta is not None:
+        dl = np.ascontiguousarray(delta, dtype=np.float64).reshape(ns, N_PARAM)
+    g = np.zeros((ns, N_PARAM)) if grad else None
+    vop = None if variant_of_photon is None else np.ascontiguousarray(variant_of_photon, dtype=np.int32)
+    val = ctypes.c_double()
+    ps = PackedScene(scene)
+    rc = L.oracle_objective(ctypes.byref(ps.s), n, o.ctypes.data, d.ctypes.data, wl.ctypes.data,
+                            vop.ctypes.data if vop is not None else None, seed & (2**64 - 1), first_photon_id,
+                            max_bounces, float(eps), n_threads, OBJECTIVES[objective], float(tau),
+                            dl.ctypes.data if dl is not None else None, ctypes.byref(val),
+                            g.ctypes.data if g is not None else None)
+    if rc != 0:
+        raise ValueError(f"oracle_objective failed (code {rc})")
+    return val.value, g

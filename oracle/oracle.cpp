@@ -707,6 +707,516 @@ int check_scene(const o_scene* sc) {
     return 0;
 }
 
+
+/* ==================================================== frozen-path gradients
+ * Forward-mode dual numbers: every quantity carries its value and its
+ * derivatives with respect to up to NT parameters (the parameters of the one
+ * differentiable surface a photon's path meets, see oracle.h). */
+constexpr int NT = 10;
+
+struct Dual {
+    double v;
+    double d[NT];
+};
+Dual dconst(double v) {
+    Dual r;
+    r.v = v;
+    for (int k = 0; k < NT; ++k) r.d[k] = 0.0;
+    return r;
+}
+Dual operator+(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v + b.v;
+    for (int k = 0; k < NT; ++k) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+Dual operator-(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v - b.v;
+    for (int k = 0; k < NT; ++k) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+Dual operator-(const Dual& a) {
+    Dual r;
+    r.v = -a.v;
+    for (int k = 0; k < NT; ++k) r.d[k] = -a.d[k];
+    return r;
+}
+Dual operator*(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v * b.v;
+    for (int k = 0; k < NT; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+Dual operator/(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v / b.v;
+    for (int k = 0; k < NT; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) / b.v;
+    return r;
+}
+Dual operator+(const Dual& a, double b) { return a + dconst(b); }
+Dual operator+(double a, const Dual& b) { return dconst(a) + b; }
+Dual operator-(const Dual& a, double b) { return a - dconst(b); }
+Dual operator-(double a, const Dual& b) { return dconst(a) - b; }
+Dual operator*(const Dual& a, double b) { return a * dconst(b); }
+Dual operator*(double a, const Dual& b) { return dconst(a) * b; }
+Dual operator/(const Dual& a, double b) { return a / dconst(b); }
+Dual operator/(double a, const Dual& b) { return dconst(a) / b; }
+
+double val(double x) { return x; }
+double val(const Dual& x) { return x.v; }
+double nsqrt(double x) { return std::sqrt(x); }
+Dual nsqrt(const Dual& x) {
+    Dual r;
+    r.v = std::sqrt(x.v);
+    for (int k = 0; k < NT; ++k) r.d[k] = x.d[k] / (2.0 * r.v);
+    return r;
+}
+double ncos(double x) { return std::cos(x); }
+double nsin(double x) { return std::sin(x); }
+Dual ncos(const Dual& x) {
+    Dual r;
+    r.v = std::cos(x.v);
+    const double s = -std::sin(x.v);
+    for (int k = 0; k < NT; ++k) r.d[k] = s * x.d[k];
+    return r;
+}
+Dual nsin(const Dual& x) {
+    Dual r;
+    r.v = std::sin(x.v);
+    const double c = std::cos(x.v);
+    for (int k = 0; k < NT; ++k) r.d[k] = c * x.d[k];
+    return r;
+}
+template <class N>
+N nlit(double v);
+template <>
+double nlit<double>(double v) { return v; }
+template <>
+Dual nlit<Dual>(double v) { return dconst(v); }
+
+template <class N>
+struct NV3 {
+    N x, y, z;
+};
+template <class N>
+NV3<N> nv3(N x, N y, N z) { return NV3<N>{x, y, z}; }
+template <class N>
+NV3<N> operator+(const NV3<N>& a, const NV3<N>& b) { return nv3<N>(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class N>
+NV3<N> operator-(const NV3<N>& a, const NV3<N>& b) { return nv3<N>(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class N>
+NV3<N> scale(const N& s, const NV3<N>& a) { return nv3<N>(s * a.x, s * a.y, s * a.z); }
+template <class N>
+N ndot(const NV3<N>& a, const NV3<N>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class N>
+NV3<N> nunit(const NV3<N>& a) { return scale<N>(1.0 / nsqrt(ndot(a, a)), a); }
+
+/* The surface with its parameters as numbers of type N. */
+template <class N>
+struct PSurf {
+    const o_surface* s;
+    N rows[9];  /* tilted frame */
+    N asph[8];
+    N bz[6];    /* Bezier control points (r, z) x 3 */
+};
+
+/* params: 16 numbers in the layout of oracle.h */
+template <class N>
+PSurf<N> make_psurf(const o_surface& s, const N* prm) {
+    PSurf<N> P;
+    P.s = &s;
+    const N ca = ncos(prm[0]), sa = nsin(prm[0]);
+    const N cb = ncos(prm[1]), sb = nsin(prm[1]);
+    const N z0 = nlit<N>(0.0), one = nlit<N>(1.0);
+    const N rxT[9] = {one, z0, z0, z0, ca, sa, z0, -sa, ca};
+    const N ryT[9] = {cb, z0, -sb, z0, one, z0, sb, z0, cb};
+    N tmp[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            N acc = nlit<N>(0.0);
+            for (int k = 0; k < 3; ++k) acc = acc + rxT[3 * i + k] * s.rot[3 * k + j];
+            tmp[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            N acc = nlit<N>(0.0);
+            for (int k = 0; k < 3; ++k) acc = acc + ryT[3 * i + k] * tmp[3 * k + j];
+            P.rows[3 * i + j] = acc;
+        }
+    for (int k = 0; k < 8; ++k) P.asph[k] = prm[2 + k];
+    for (int k = 0; k < 6; ++k) P.bz[k] = prm[10 + k];
+    return P;
+}
+
+template <class N>
+NV3<N> p_local_pt(const PSurf<N>& P, const NV3<N>& p) {
+    const NV3<N> q = nv3<N>(p.x - P.s->origin[0], p.y - P.s->origin[1], p.z - P.s->origin[2]);
+    return nv3<N>(P.rows[0] * q.x + P.rows[1] * q.y + P.rows[2] * q.z, P.rows[3] * q.x + P.rows[4] * q.y + P.rows[5] * q.z,
+                  P.rows[6] * q.x + P.rows[7] * q.y + P.rows[8] * q.z);
+}
+template <class N>
+NV3<N> p_local_vec(const PSurf<N>& P, const NV3<N>& q) {
+    return nv3<N>(P.rows[0] * q.x + P.rows[1] * q.y + P.rows[2] * q.z, P.rows[3] * q.x + P.rows[4] * q.y + P.rows[5] * q.z,
+                  P.rows[6] * q.x + P.rows[7] * q.y + P.rows[8] * q.z);
+}
+template <class N>
+NV3<N> p_world_vec(const PSurf<N>& P, const NV3<N>& q) {
+    return nv3<N>(P.rows[0] * q.x + P.rows[3] * q.y + P.rows[6] * q.z, P.rows[1] * q.x + P.rows[4] * q.y + P.rows[7] * q.z,
+                  P.rows[2] * q.x + P.rows[5] * q.y + P.rows[8] * q.z);
+}
+
+/* sag and dsag/drho with the surface's conic and the parameter asphere */
+template <class N>
+bool p_sag(const PSurf<N>& P, const N& rho, N* z, N* slope) {
+    const double c = P.s->curv, k1 = 1.0 + P.s->conic;
+    const N arg = 1.0 - k1 * c * c * rho;
+    if (val(arg) < 0.0) return false;
+    const N sq = nsqrt(arg);
+    N zz = c * rho / (1.0 + sq), sl = c / (2.0 * sq);
+    N rp = rho, rpm = nlit<N>(1.0);
+    for (int i = 1; i <= 8; ++i) {
+        zz = zz + P.asph[i - 1] * rp;
+        sl = sl + (double)i * P.asph[i - 1] * rpm;
+        rpm = rp;
+        rp = rp * rho;
+    }
+    *z = zz;
+    *slope = sl;
+    return true;
+}
+
+/* Re-intersect a recorded SAG surface: conic roots, the on-branch root
+ * nearest the recorded distance t0, then Newton on the full sag (value
+ * converged, plus one step so the derivatives are those of the exact root). */
+template <class N>
+bool p_hit_sag(const PSurf<N>& P, const NV3<N>& p, const NV3<N>& d, double t0, N* t, NV3<N>* pl, NV3<N>* nl) {
+    const double c = P.s->curv, k1 = 1.0 + P.s->conic;
+    const N a = c * (d.x * d.x + d.y * d.y + k1 * d.z * d.z);
+    const N b = c * (p.x * d.x + p.y * d.y + k1 * p.z * d.z) - d.z;
+    const N g = c * (p.x * p.x + p.y * p.y + k1 * p.z * p.z) - 2.0 * p.z;
+    N roots[2];
+    int nr = 0;
+    if (val(a) == 0.0) {
+        if (val(b) != 0.0) roots[nr++] = -g / (2.0 * b);
+    } else {
+        const N disc = b * b - a * g;
+        if (val(disc) >= 0.0) {
+            const N sq = nsqrt(disc);
+            const N q = -(b + (val(b) >= 0.0 ? sq : -sq));
+            if (val(q) != 0.0) {
+                roots[nr++] = q / a;
+                roots[nr++] = g / q;
+            } else {
+                roots[nr++] = nlit<N>(0.0) * b;
+            }
+        }
+    }
+    int best = -1;
+    for (int i = 0; i < nr; ++i) {
+        const NV3<N> x = p + scale<N>(roots[i], d);
+        if (k1 * c * val(x.z) > 1.0) continue;
+        if (best < 0 || std::fabs(val(roots[i]) - t0) < std::fabs(val(roots[best]) - t0)) best = i;
+    }
+    N tt = best >= 0 ? roots[best] : nlit<N>(t0) + nlit<N>(0.0) * a;
+    for (int it = 0; it < 40; ++it) {
+        const NV3<N> x = p + scale<N>(tt, d);
+        N z, sl;
+        if (!p_sag(P, x.x * x.x + x.y * x.y, &z, &sl)) return false;
+        const N f = x.z - z;
+        const N fp = d.z - sl * 2.0 * (x.x * d.x + x.y * d.y);
+        const N dt = f / fp;
+        tt = tt - dt;
+        if (std::fabs(val(dt)) < 1e-15 * (1.0 + std::fabs(val(tt))) && it > 0) break;
+    }
+    const NV3<N> x = p + scale<N>(tt, d);
+    N z, sl;
+    if (!p_sag(P, x.x * x.x + x.y * x.y, &z, &sl)) return false;
+    *t = tt;
+    *pl = x;
+    *nl = nunit(nv3<N>(-2.0 * x.x * sl, -2.0 * x.y * sl, nlit<N>(1.0)));
+    return true;
+}
+
+/* Re-intersect a recorded Bezier hex cone: the wall/root whose distance is
+ * nearest the recorded one. */
+template <class N>
+bool p_hit_hexcone(const PSurf<N>& P, const NV3<N>& p, const NV3<N>& d, double t0, N* t, NV3<N>* pl, NV3<N>* nl) {
+    const N ra0 = P.bz[0], ra1 = 2.0 * (P.bz[2] - P.bz[0]), ra2 = P.bz[0] - 2.0 * P.bz[2] + P.bz[4];
+    const N za0 = P.bz[1], za1 = 2.0 * (P.bz[3] - P.bz[1]), za2 = P.bz[1] - 2.0 * P.bz[3] + P.bz[5];
+    bool found = false;
+    double bestd = INFINITY;
+    for (int j = 0; j < 6; ++j) {
+        const double cj = std::cos(j * M_PI / 3.0), sj = std::sin(j * M_PI / 3.0);
+        const N q0 = p.x * cj + p.y * sj, dq = d.x * cj + d.y * sj;
+        const N den = dq * dq + d.z * d.z;
+        if (val(den) == 0.0) continue;
+        const N A = d.z * ra2 - dq * za2, B = d.z * ra1 - dq * za1, C = d.z * (ra0 - q0) - dq * (za0 - p.z);
+        N us[2];
+        int nu = 0;
+        if (val(A) == 0.0) {
+            if (val(B) != 0.0) us[nu++] = -C / B;
+        } else {
+            const N disc = B * B - 4.0 * A * C;
+            if (val(disc) >= 0.0) {
+                const N sq = nsqrt(disc);
+                const N q = -0.5 * (B + (val(B) >= 0.0 ? sq : -sq));
+                if (val(q) != 0.0) {
+                    us[nu++] = q / A;
+                    us[nu++] = C / q;
+                } else {
+                    us[nu++] = -B / (2.0 * A);
+                }
+            }
+        }
+        for (int i = 0; i < nu; ++i) {
+            N u = us[i];
+            const N gp = 2.0 * A * u + B;
+            if (val(gp) != 0.0) u = u - ((A * u + B) * u + C) / gp;
+            const N R = ra0 + u * (ra1 + u * ra2), Z = za0 + u * (za1 + u * za2);
+            const N tt = ((R - q0) * dq + (Z - p.z) * d.z) / den;
+            const double dist = std::fabs(val(tt) - t0);
+            if (dist < bestd) {
+                bestd = dist;
+                found = true;
+                *t = tt;
+                *pl = p + scale<N>(tt, d);
+                const N Rp = ra1 + 2.0 * ra2 * u, Zp = za1 + 2.0 * za2 * u;
+                *nl = nunit(nv3<N>(-Zp * cj, -Zp * sj, Rp));
+            }
+        }
+    }
+    return found;
+}
+
+enum { ACT_REFLECT = 0, ACT_REFRACT = 1, ACT_DETECT = 2, ACT_STOP = 3 };
+struct Step {
+    int sid, act;
+    double t;
+};
+
+/* Nominal trace in expected-weight mode, recording the path. */
+int record_path(const Ctx& cx, int v, V3 p, V3 d, double lam, int64_t pid, const uint32_t key[2], int max_bounces,
+                std::vector<Step>* path, double* w) {
+    const o_scene* sc = cx.sc;
+    *w = 1.0;
+    path->clear();
+    int bounces = 0;
+    while (true) {
+        Hit h = nearest_hit(cx, v, p, d);
+        if (h.error) return O_ST_ERROR;
+        if (!h.any) return O_ST_ESCAPED;
+        p = p + h.t * d;
+        const o_surface& s = sc->surfaces[h.sid];
+        uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)((uint64_t)pid >> 32), (uint32_t)bounces, 0u};
+        uint32_t wd[4];
+        philox(ctr, key, wd);
+        ++bounces;
+        V3 n = h.nw;
+        bool front = dot(d, n) < 0.0;
+        Step st{h.sid, ACT_STOP, h.t};
+        if (s.role == O_ROLE_OBSCURATION) {
+            path->push_back(st);
+            return O_ST_OBSCURED;
+        }
+        if (s.role == O_ROLE_FOCAL) {
+            st.act = front ? ACT_DETECT : ACT_STOP;
+            path->push_back(st);
+            return front ? O_ST_DETECTED : O_ST_OBSCURED;
+        }
+        if (s.role == O_ROLE_MIRROR) {
+            if (!front) {
+                path->push_back(st);
+                return O_ST_OBSCURED;
+            }
+            const o_material& m = sc->materials[s.material];
+            *w *= reflectivity(m, lam);
+            V3 nn = n;
+            if (m.sigma > 0.0) {
+                double u1 = unit_open(wd[1]), u2 = unit_open(wd[2]);
+                double rad = std::sqrt(-2.0 * std::log(u1));
+                V3 t, b;
+                onb(n, &t, &b);
+                nn = normalize(n + (m.sigma * rad * std::cos(2.0 * M_PI * u2)) * t +
+                               (m.sigma * rad * std::sin(2.0 * M_PI * u2)) * b);
+            }
+            d = normalize(reflect(d, nn));
+            st.act = ACT_REFLECT;
+        } else {
+            double na = refr_index(sc->media[s.medium_front], lam), nb = refr_index(sc->media[s.medium_back], lam);
+            double n1 = front ? na : nb, n2 = front ? nb : na;
+            V3 nf = front ? n : (-1.0) * n;
+            double ci = -dot(d, nf);
+            if (unit_open(wd[0]) < fresnel(n1, n2, ci)) {
+                d = normalize(reflect(d, nf));
+                st.act = ACT_REFLECT;
+            } else {
+                double eta = n1 / n2, s2 = eta * eta * (1.0 - ci * ci);
+                d = normalize(eta * d + (eta * ci - std::sqrt(1.0 - s2)) * nf);
+                st.act = ACT_REFRACT;
+            }
+        }
+        path->push_back(st);
+        if (bounces >= max_bounces) return O_ST_MAX_BOUNCES;
+    }
+}
+
+bool differentiable(const o_surface& s) {
+    return s.role == O_ROLE_MIRROR && (s.shape == O_SHAPE_SAG || s.shape == O_SHAPE_HEXCONE);
+}
+
+/* Replay one recorded path with parameters as numbers of type N.  `tracked`
+ * is the surface whose parameters carry the derivative slots (Dual only). */
+template <class N>
+struct Replay {
+    bool ok;
+    NV3<N> p, d;  /* final point and direction */
+    N qx, qy;     /* focal-surface local point (DETECTED) */
+};
+
+template <class N>
+N param_number(double v, int slot);
+template <>
+double param_number<double>(double v, int) { return v; }
+template <>
+Dual param_number<Dual>(double v, int slot) {
+    Dual r = dconst(v);
+    if (slot >= 0 && slot < NT) r.d[slot] = 1.0;
+    return r;
+}
+
+template <class N>
+PSurf<N> psurf_for(const o_surface& s, int sid, int tracked, const double* delta) {
+    N prm[O_N_PARAM];
+    double nom[O_N_PARAM];
+    nom[0] = s.tilt[0];
+    nom[1] = s.tilt[1];
+    for (int k = 0; k < 8; ++k) nom[2 + k] = s.asph[k];
+    for (int k = 0; k < 6; ++k) nom[10 + k] = s.prm[k];
+    for (int k = 0; k < O_N_PARAM; ++k) {
+        const double v = nom[k] + (delta ? delta[(size_t)sid * O_N_PARAM + k] : 0.0);
+        int slot = -1;
+        if (sid == tracked) slot = s.shape == O_SHAPE_SAG ? (k < 10 ? k : -1) : (k >= 10 ? k - 10 : -1);
+        prm[k] = param_number<N>(v, slot);
+    }
+    return make_psurf<N>(s, prm);
+}
+
+template <class N>
+Replay<N> replay(const Ctx& cx, const std::vector<Step>& path, V3 p0, V3 d0, double lam, int64_t pid,
+                 const uint32_t key[2], int tracked, const double* delta) {
+    const o_scene* sc = cx.sc;
+    Replay<N> R;
+    R.ok = true;
+    NV3<N> p = nv3<N>(nlit<N>(p0.x), nlit<N>(p0.y), nlit<N>(p0.z));
+    NV3<N> d = nv3<N>(nlit<N>(d0.x), nlit<N>(d0.y), nlit<N>(d0.z));
+    R.qx = nlit<N>(0.0);
+    R.qy = nlit<N>(0.0);
+    for (size_t b = 0; b < path.size(); ++b) {
+        const Step& st = path[b];
+        const o_surface& s = sc->surfaces[st.sid];
+        const PSurf<N> P = psurf_for<N>(s, st.sid, tracked, delta);
+        const NV3<N> pl = p_local_pt(P, p), dl = p_local_vec(P, d);
+        N t;
+        NV3<N> xl, nl;
+        bool ok = false;
+        if (s.shape == O_SHAPE_SAG) ok = p_hit_sag(P, pl, dl, st.t, &t, &xl, &nl);
+        else if (s.shape == O_SHAPE_HEXCONE) ok = p_hit_hexcone(P, pl, dl, st.t, &t, &xl, &nl);
+        else ok = false;
+        if (!ok) {
+            R.ok = false;
+            return R;
+        }
+        p = p + scale<N>(t, d);
+        if (st.act == ACT_DETECT) {
+            R.qx = xl.x;
+            R.qy = xl.y;
+            break;
+        }
+        if (st.act == ACT_STOP) break;
+        const NV3<N> n = p_world_vec(P, nl);
+        const bool front = val(ndot(d, n)) < 0.0;
+        uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)((uint64_t)pid >> 32), (uint32_t)b, 0u};
+        uint32_t wd[4];
+        philox(ctr, key, wd);
+        if (s.role == O_ROLE_MIRROR) {
+            const o_material& m = sc->materials[s.material];
+            NV3<N> nn = n;
+            if (m.sigma > 0.0) {
+                const double u1 = unit_open(wd[1]), u2 = unit_open(wd[2]);
+                const double rad = std::sqrt(-2.0 * std::log(u1));
+                const double g1 = rad * std::cos(2.0 * M_PI * u2), g2 = rad * std::sin(2.0 * M_PI * u2);
+                const double sign = val(n.z) >= 0.0 ? 1.0 : -1.0;
+                const N a = -1.0 / (sign + n.z);
+                const N bb = n.x * n.y * a;
+                const NV3<N> tt = nv3<N>(1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+                const NV3<N> bv = nv3<N>(bb, sign + n.y * n.y * a, -n.y);
+                nn = nunit(n + scale<N>(nlit<N>(m.sigma * g1), tt) + scale<N>(nlit<N>(m.sigma * g2), bv));
+            }
+            d = nunit(d - scale<N>(2.0 * ndot(d, nn), nn));
+        } else {
+            const double na = refr_index(sc->media[s.medium_front], lam);
+            const double nb = refr_index(sc->media[s.medium_back], lam);
+            const double n1 = front ? na : nb, n2 = front ? nb : na;
+            const NV3<N> nf = front ? n : scale<N>(nlit<N>(-1.0), n);
+            if (st.act == ACT_REFLECT) {
+                d = nunit(d - scale<N>(2.0 * ndot(d, nf), nf));
+            } else {
+                const double eta = n1 / n2;
+                const N ci = -ndot(d, nf);
+                const N s2 = eta * eta * (1.0 - ci * ci);
+                d = nunit(scale<N>(nlit<N>(eta), d) + scale<N>(eta * ci - nsqrt(1.0 - s2), nf));
+            }
+        }
+    }
+    R.p = p;
+    R.d = d;
+    return R;
+}
+
+/* signed hexagon margin of the last segment's crossing of the variant's focal plane */
+template <class N>
+bool exit_margin(const o_scene* sc, int v, const NV3<N>& p, const NV3<N>& d, N* m) {
+    int s0 = 0, s1 = sc->n_surfaces;
+    if (sc->variant_offsets) {
+        s0 = sc->variant_offsets[v];
+        s1 = sc->variant_offsets[v + 1];
+    }
+    for (int s = s0; s < s1; ++s) {
+        const o_surface& f = sc->surfaces[s];
+        if (f.role != O_ROLE_FOCAL || f.shape != O_SHAPE_SAG || f.aperture != O_AP_HEXAGON) continue;
+        const N zero[O_N_PARAM] = {};
+        N prm[O_N_PARAM];
+        for (int k = 0; k < O_N_PARAM; ++k) prm[k] = nlit<N>(0.0);
+        prm[0] = nlit<N>(f.tilt[0]);
+        prm[1] = nlit<N>(f.tilt[1]);
+        (void)zero;
+        const PSurf<N> P = make_psurf<N>(f, prm);
+        const NV3<N> pl = p_local_pt(P, p), dl = p_local_vec(P, d);
+        if (!(val(dl.z) < 0.0)) return false;
+        const N t = -pl.z / dl.z;
+        const NV3<N> x = pl + scale<N>(t, dl);
+        const double s60 = std::sqrt(3.0) / 2.0;
+        const N c0 = x.x, c1 = 0.5 * x.x + s60 * x.y, c2 = -0.5 * x.x + s60 * x.y;
+        const N cand[3] = {c0, c1, c2};
+        int km = 0;
+        for (int k = 1; k < 3; ++k)
+            if (std::fabs(val(cand[k])) > std::fabs(val(cand[km]))) km = k;
+        const N mk = val(cand[km]) >= 0.0 ? cand[km] : -cand[km];
+        *m = f.ap[0] - mk;
+        return true;
+    }
+    return false;
+}
+
+struct PhotonRec {
+    int status;
+    double w;
+    int tracked;
+    std::vector<Step> path;
+};
+
+double sigmoid(double x) { return 1.0 / (1.0 + std::exp(-x)); }
 }  // namespace
 
 extern "C" {
@@ -757,6 +1267,147 @@ int64_t oracle_generate_sources(const o_source_group* groups, int32_t n_groups, 
         }
     }
     return failed;
+}
+
+
+int oracle_objective(const o_scene* scene, int64_t n, const double* O, const double* D, const double* L,
+                     const int32_t* vop, uint64_t seed, int64_t first_photon_id, int32_t max_bounces, double eps,
+                     int32_t n_threads, int32_t objective, double tau, const double* delta, double* value,
+                     double* grad) {
+    int rc = check_scene(scene);
+    if (rc) return rc;
+    if (n <= 0 || max_bounces <= 0 || max_bounces > 255 || !value || objective < 0 || objective > 3) return -10;
+    /* objectives 2 and 3 (pins only): w-weighted centroid x, y of the DETECTED photons */
+    const bool centroid = objective >= 2;
+    const int cax = objective - 2;
+    Ctx cx;
+    cx.sc = scene;
+    cx.frames.resize(scene->n_surfaces);
+    for (int s = 0; s < scene->n_surfaces; ++s) cx.frames[s] = make_frame(scene->surfaces[s]);
+    cx.eps = eps;
+    cx.newton_tol = eps * 1e-4;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    if (n_threads <= 0) n_threads = 1;
+    if ((int64_t)n_threads > n) n_threads = (int32_t)n;
+    const size_t NP = (size_t)scene->n_surfaces * O_N_PARAM;
+    // per photon: value-pass results
+    std::vector<int> status(n), tracked(n, -1);
+    std::vector<double> w(n, 0.0), qx(n, 0.0), qy(n, 0.0), mval(n, 0.0);
+    std::vector<char> valid(n, 0);
+    auto photon = [&](int64_t i, std::vector<Step>& path) {
+        V3 p = v3(O[i], O[n + i], O[2 * n + i]), d = v3(D[i], D[n + i], D[2 * n + i]);
+        const int v = vop ? vop[i] : 0;
+        const int64_t pid = first_photon_id + i;
+        status[i] = record_path(cx, v, p, d, L[i], pid, key, max_bounces, &path, &w[i]);
+        for (const Step& st : path)
+            if (differentiable(scene->surfaces[st.sid])) {
+                tracked[i] = st.sid;
+                break;
+            }
+    };
+    // pass 1: values with the perturbed parameters
+    {
+        std::vector<std::thread> th;
+        for (int k = 0; k < n_threads; ++k)
+            th.emplace_back([&, k]() {
+                std::vector<Step> path;
+                for (int64_t i = n * k / n_threads; i < n * (k + 1) / n_threads; ++i) {
+                    photon(i, path);
+                    V3 p = v3(O[i], O[n + i], O[2 * n + i]), d = v3(D[i], D[n + i], D[2 * n + i]);
+                    Replay<double> R = replay<double>(cx, path, p, d, L[i], first_photon_id + i, key, -1, delta);
+                    if (!R.ok) continue;
+                    valid[i] = 1;
+                    qx[i] = R.qx;
+                    qy[i] = R.qy;
+                    if (objective == 1 && status[i] != O_ST_OBSCURED && status[i] != O_ST_ERROR &&
+                        status[i] != O_ST_MAX_BOUNCES) {
+                        double m;
+                        if (exit_margin<double>(scene, vop ? vop[i] : 0, R.p, R.d, &m)) mval[i] = m;
+                        else valid[i] = 2;  // heading away: contributes 0
+                    } else if (objective == 1) {
+                        valid[i] = 2;
+                    }
+                }
+            });
+        for (auto& t : th) t.join();
+    }
+    double W = 0.0, sx = 0.0, sy = 0.0;
+    if (centroid) {
+        for (int64_t i = 0; i < n; ++i)
+            if (valid[i] == 1 && status[i] == O_ST_DETECTED) {
+                W += w[i];
+                sx += w[i] * (cax == 0 ? qx[i] : qy[i]);
+            }
+        *value = W > 0.0 ? sx / W : 0.0;
+    } else if (objective == 0) {
+        for (int64_t i = 0; i < n; ++i)
+            if (valid[i] == 1 && status[i] == O_ST_DETECTED) {
+                W += w[i];
+                sx += w[i] * qx[i];
+                sy += w[i] * qy[i];
+            }
+        if (W <= 0.0) {
+            *value = 0.0;
+            if (grad) std::fill(grad, grad + NP, 0.0);
+            return 0;
+        }
+        const double cxm = sx / W, cym = sy / W;
+        double acc = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            if (valid[i] == 1 && status[i] == O_ST_DETECTED)
+                acc += w[i] * ((qx[i] - cxm) * (qx[i] - cxm) + (qy[i] - cym) * (qy[i] - cym));
+        *value = acc / W;
+        sx = cxm;
+        sy = cym;
+    } else {
+        double acc = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            if (valid[i] == 1) acc += w[i] * sigmoid(mval[i] / tau);
+        *value = acc / (double)n;
+    }
+    if (!grad) return 0;
+    // pass 2: dual numbers along the same frozen paths, one thread-partial vector each
+    std::vector<std::vector<double>> part(n_threads, std::vector<double>(NP, 0.0));
+    {
+        std::vector<std::thread> th;
+        for (int k = 0; k < n_threads; ++k)
+            th.emplace_back([&, k]() {
+                std::vector<Step> path;
+                std::vector<double>& g = part[k];
+                double dummy_w;
+                for (int64_t i = n * k / n_threads; i < n * (k + 1) / n_threads; ++i) {
+                    if (valid[i] != 1 || tracked[i] < 0) continue;
+                    if (objective != 1 && status[i] != O_ST_DETECTED) continue;
+                    V3 p = v3(O[i], O[n + i], O[2 * n + i]), d = v3(D[i], D[n + i], D[2 * n + i]);
+                    const int v = vop ? vop[i] : 0;
+                    record_path(cx, v, p, d, L[i], first_photon_id + i, key, max_bounces, &path, &dummy_w);
+                    Replay<Dual> R = replay<Dual>(cx, path, p, d, L[i], first_photon_id + i, key, tracked[i], delta);
+                    if (!R.ok) continue;
+                    const o_surface& ts = scene->surfaces[tracked[i]];
+                    const int base = ts.shape == O_SHAPE_SAG ? 0 : 10;
+                    const int nslots = ts.shape == O_SHAPE_SAG ? 10 : 6;
+                    for (int k2 = 0; k2 < nslots; ++k2) {
+                        double c;
+                        if (centroid) {
+                            c = w[i] / W * (cax == 0 ? R.qx.d[k2] : R.qy.d[k2]);
+                        } else if (objective == 0) {
+                            c = 2.0 * w[i] / W * ((qx[i] - sx) * R.qx.d[k2] + (qy[i] - sy) * R.qy.d[k2]);
+                        } else {
+                            Dual m;
+                            if (!exit_margin<Dual>(scene, v, R.p, R.d, &m)) continue;
+                            const double sg = sigmoid(m.v / tau);
+                            c = w[i] * sg * (1.0 - sg) / tau * m.d[k2] / (double)n;
+                        }
+                        g[(size_t)tracked[i] * O_N_PARAM + base + k2] += c;
+                    }
+                }
+            });
+        for (auto& t : th) t.join();
+    }
+    std::fill(grad, grad + NP, 0.0);
+    for (int k = 0; k < n_threads; ++k)
+        for (size_t j = 0; j < NP; ++j) grad[j] += part[k][j];
+    return 0;
 }
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {

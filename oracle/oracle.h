@@ -98,6 +98,33 @@ int64_t oracle_generate_sources(const o_source_group* groups, int32_t n_groups, 
                                 int64_t first_photon_id, double* origins, double* dirs, double* wavelengths,
                                 int32_t* variant);
 
+/* ------------------------------------------------------------ gradients
+ * Frozen-path objectives (a reading: the paper defines no objective).  A
+ * nominal trace in expected-weight mode (mirrors always reflect, the photon
+ * carries w = product of R(lambda) instead of an absorb draw) records each
+ * photon's surface sequence, distances and reflect/refract decisions; the
+ * objective is then evaluated on those paths with the parameters moved by
+ * `delta`, re-intersecting the recorded surfaces (apertures ignored, the root
+ * nearest the recorded distance), so that it is smooth in the parameters.
+ *   objective 0, MSR: detected photons, W = sum w, qbar = sum w q / W,
+ *                     MSR = sum w |q - qbar|^2 / W (q = focal-surface x, y);
+ *   objective 1, soft CE: (1/N) sum w sigmoid(m / tau), m = apothem - max_k
+ *                     |x . u_k| at the crossing of the photon's last segment
+ *                     with the plane of its variant's (hexagonal) focal
+ *                     surface, 0 if the segment does not head into it or the
+ *                     photon was obscured;
+ *   objectives 2, 3 (closed-form pins only): the w-weighted centroid of the
+ *                     DETECTED photons' focal x (2) or y (3).
+ * Parameters: 16 per surface -- [0..1] tilt about local x, y; [2..9] A1..A8
+ * (SAG mirrors); [10..15] Bezier control points P0r, P0z, P1r, P1z, P2r, P2z
+ * (HEXCONE mirrors).  grad (may be NULL): d objective / d parameter by
+ * forward-mode dual numbers along the frozen paths. */
+#define O_N_PARAM 16
+int oracle_objective(const o_scene* scene, int64_t n, const double* origins, const double* dirs,
+                     const double* wavelengths, const int32_t* variant_of_photon, uint64_t seed,
+                     int64_t first_photon_id, int32_t max_bounces, double eps, int32_t n_threads,
+                     int32_t objective, double tau, const double* delta, double* value, double* grad);
+
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
