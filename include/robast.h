@@ -285,6 +285,51 @@ int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64
                          unsigned long long* group_counts, const robast_trace_out* out,
                          const robast_trace_opts* opts);
 
+/* -------------------------------------------------------------- gradients */
+/*
+ * Differentiable objectives (an addition to the paper's method, which
+ * optimises designs by hand: tolerance and design studies of Sec. 3).
+ * Reading: each photon's path is the one robast_trace takes in
+ * expected-weight mode -- mirrors always reflect and the photon carries
+ * w = product of R(lambda) instead of an absorb draw; Fresnel choices and
+ * roughness use the same Philox draws -- and is held fixed while the
+ * parameters move (boundary terms of path changes are excluded).
+ *   ROBAST_OBJ_MSR: sum w |q - qbar|^2 / W over DETECTED photons, q = local
+ *       (x, y) on the focal surface, W = sum w, qbar = sum w q / W;
+ *   ROBAST_OBJ_SOFT_CE: (1/N) sum w sigmoid(m / tau) over all photons, m =
+ *       apothem - max_k |x . u_k| at the crossing of the photon's last
+ *       segment with its variant's hexagonal focal plane (0 if it heads away
+ *       or the photon was obscured);
+ *   ROBAST_OBJ_CENTROID_X / _Y: sum w q_x / W (resp. q_y) over DETECTED.
+ * Parameters: ROBAST_N_PARAM per surface, [0..1] tilt about local x, y
+ * (as robast_surface_desc.tilt), [2..9] A1..A8 (SAG mirrors), [10..15]
+ * Bezier control points P0r, P0z, P1r, P1z, P2r, P2z (HEXCONE mirrors); a
+ * path carries derivatives for the first such mirror it meets.
+ */
+#define ROBAST_OBJ_MSR 0
+#define ROBAST_OBJ_SOFT_CE 1
+#define ROBAST_OBJ_CENTROID_X 2
+#define ROBAST_OBJ_CENTROID_Y 3
+#define ROBAST_N_PARAM 16
+
+/* Number of parameters of g (ROBAST_N_PARAM x surfaces); 0 for NULL. */
+int robast_param_count(const robast_geom* g);
+
+/*
+ * Objective value (HOST *value) and, if d_params (device, FP64,
+ * [robast_param_count]) is not NULL, d_params += d_obj * d value / d param.
+ * Inputs as robast_trace_ex (device, the precision's element type).  One
+ * pass: each photon's path is re-traced (nothing per bounce is stored) and
+ * every surface it meets is re-intersected in forward-mode dual numbers;
+ * sums over photons are FP64.  info (HOST, 8 doubles, may be NULL):
+ * W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid, N_detected, photons
+ * meeting a second differentiable mirror (untracked), N.  Synchronises the
+ * stream; uses device scratch owned by g.
+ */
+int robast_trace_grad(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
+                      uint64_t seed, int32_t objective, double tau, double d_obj, double* value, double* d_params,
+                      const robast_trace_opts* opts, double* info);
+
 /* ----------------------------------------------------------- reductions */
 /*
  * Spot diagram statistics (Fig. 1 g-i) of the DETECTED photons of each of

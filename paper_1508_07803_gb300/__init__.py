@@ -455,3 +455,102 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
                                     ctypes.c_void_p(group_counts.data_ptr()),
                                     ctypes.byref(tout) if tout is not None else None, ctypes.byref(o)))
     return group_counts
+
+
+N_PARAM = 16
+OBJECTIVES = {"msr": 0, "soft_ce": 1, "centroid_x": 2, "centroid_y": 3}
+
+
+def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed: int = 0, precision: int = 32,
+               tau: float = 0.5e-3, d_obj: float = 1.0, grad=True, max_bounces: int = 100, stream=None,
+               variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None, out=None):
+    """robast_trace_grad: frozen-path objective value and d_obj * gradient.
+
+    Returns (value, grad [n_surfaces, 16] float64 CUDA tensor or None, info dict).
+    `out`, if given, is a float64 CUDA tensor [n_surfaces, 16] the gradient is added to.
+    """
+    import torch
+    lib = load()
+    lib.robast_param_count.argtypes = [ctypes.c_void_p]
+    lib.robast_trace_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                      ctypes.POINTER(TraceOpts), ctypes.POINTER(ctypes.c_double)]
+    dt = torch.float32 if precision == 32 else torch.float64
+    n = int(wavelengths.shape[0])
+    for name, t, shape in (("origins", origins, (3, n)), ("dirs", dirs, (3, n)), ("wavelengths", wavelengths, (n,))):
+        if t.dtype != dt or tuple(t.shape) != shape or not t.is_cuda or not t.is_contiguous():
+            raise RobastError(f"{name}: need a contiguous CUDA {dt} tensor of shape {shape}")
+    g = out
+    if grad and g is None:
+        g = torch.zeros((geom.n_surfaces, N_PARAM), dtype=torch.float64, device=origins.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(origins.device)
+    vop = ctypes.c_void_p(variant_of_photon.data_ptr()) if variant_of_photon is not None else None
+    o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), vop, first_photon_id, eps, 0, 0)
+    val = ctypes.c_double()
+    info = (ctypes.c_double * 8)()
+    _check(lib.robast_trace_grad(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,
+                                 ctypes.c_uint64(seed & (2**64 - 1)), OBJECTIVES[objective], float(tau), float(d_obj),
+                                 ctypes.byref(val), ctypes.c_void_p(g.data_ptr()) if g is not None else None,
+                                 ctypes.byref(o), info))
+    keys = ("W", "sum_wqx", "sum_wqy", "sum_wq2", "sum_soft", "n_detected", "n_untracked", "n")
+    return val.value, g, dict(zip(keys, list(info)))
+
+
+def apply_params(scene, params):
+    """A copy of `scene` with the 16 parameters per surface set from `params`
+    ([n_surfaces, 16]: tilt x, y; A1..A8; Bezier P0r, P0z, P1r, P1z, P2r, P2z)."""
+    import copy
+    import numpy as np_
+    p = np_.asarray(params, dtype=np_.float64).reshape(len(scene.surfaces), N_PARAM)
+    sc = copy.copy(scene)
+    sc.surfaces = []
+    for s, row in zip(scene.surfaces, p):
+        t = copy.copy(s)
+        t.tilt = (float(row[0]), float(row[1]))
+        if s.shape == "sag":
+            t.asph = tuple(float(x) for x in row[2:10])
+        if s.shape == "hexcone":
+            t.prm = tuple(float(x) for x in row[10:16]) + tuple(s.prm[6:8])
+        sc.surfaces.append(t)
+    return sc
+
+
+def scene_params(scene):
+    """The [n_surfaces, 16] parameter array of a scene (see apply_params)."""
+    import numpy as np_
+    p = np_.zeros((len(scene.surfaces), N_PARAM))
+    for i, s in enumerate(scene.surfaces):
+        p[i, 0:2] = s.tilt
+        p[i, 2:10] = list(s.asph) + [0.0] * (8 - len(s.asph))
+        if s.shape == "hexcone":
+            p[i, 10:16] = list(s.prm)[:6]
+    return p
+
+
+def objective_function():
+    """torch.autograd.Function computing a frozen-path objective of a scene's
+    parameters on the GPU; backward returns the gradient the same launch
+    produced (scaled by the incoming gradient).
+
+    Usage: FrozenPathObjective.apply(params, scene, origins, dirs, wavelengths, options_dict)
+    with params a float64 tensor [n_surfaces, 16] (requires_grad).
+    """
+    import torch
+
+    class FrozenPathObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params, scene, origins, dirs, wavelengths, options):
+            geom = build_geometry(apply_params(scene, params.detach().cpu().numpy()))
+            value, grad, _ = trace_grad(geom, origins, dirs, wavelengths, **options)
+            geom.close()
+            ctx.save_for_backward(grad.to(params.device))
+            return torch.tensor(value, dtype=torch.float64, device=params.device)
+
+        @staticmethod
+        def backward(ctx, grad_output):
+            (grad,) = ctx.saved_tensors
+            return grad_output * grad, None, None, None, None, None
+
+    return FrozenPathObjective

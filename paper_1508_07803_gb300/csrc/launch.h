@@ -12,6 +12,34 @@ namespace robast {
 int trace_blocks_per_sm_f32(int block, size_t smem, bool src);
 int trace_blocks_per_sm_f64(int block, size_t smem, bool src);
 
+// Gradient pass (grad.cu): frozen-path objective sums and per-parameter sums.
+template <typename T>
+struct GradArgs {
+    Tables tab;              // precision T: the nearest-hit search
+    const double* surf64;    // FP64 surface records: the dual-number re-intersection
+    const double* grec;      // per surface: d rows / d tilt_x (9), d rows / d tilt_y (9)
+    const T* o;
+    const T* d;
+    const T* lam;
+    const int* vop;
+    long long n;
+    unsigned long long seed;
+    long long first_id;
+    int max_bounces;
+    int stage;
+    T eps;
+    T newton_tol;
+    double newton_tol64;  // Newton tolerance of the FP64 dual re-intersection
+    int objective;
+    double tau;
+    double* acc;   // [n_surf * 16 * 3]
+    double* vals;  // [8]
+};
+cudaError_t launch_grad_f32(const GradArgs<float>& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_grad_finish(const double* acc, const double* vals, int n_params, int objective, double d_obj,
+                               double* out, cudaStream_t s);
+
 // Launch the persistent trace kernel; returns the cudaError_t of the launch.
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceArgs<double>& a, int block, int grid, size_t smem, cudaStream_t s);

@@ -51,6 +51,8 @@ struct robast_geom {
     double length_scale = 1.0;
     void* dmem = nullptr;  // one allocation holding every table
     Tables tab32{}, tab64{};
+    const float* grec32 = nullptr;    // per surface: d rows / d tilt_x, d rows / d tilt_y
+    const double* grec64 = nullptr;
     size_t smem32 = 0, smem64 = 0;  // bytes to stage each precision's tables
     int num_sms = 0;
     // per-launch work counters (a ring, so launches on several streams do not share one)
@@ -509,6 +511,8 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     std::vector<float> rec32((size_t)ns * REC, 0.0f);
     std::vector<int4> reci(ns);
     std::vector<std::vector<Ref>> refs_of(ns);  // BVH references per surface; empty = unbounded
+    std::vector<double> grec64((size_t)ns * 18, 0.0);
+    std::vector<float> grec32((size_t)ns * 18, 0.0f);
     for (int i = 0; i < ns; ++i) {
         const robast_surface_desc& s = d->surfaces[i];
         double* R = &rec64[(size_t)i * REC];
@@ -566,6 +570,21 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
             }
         }
         for (int k = 0; k < REC; ++k) rec32[(size_t)i * REC + k] = (float)R[k];
+        {
+            // derivatives of the tilted rows Ry(b)^T Rx(a)^T R with respect to a and b
+            const double ca = std::cos(s.tilt[0]), sa = std::sin(s.tilt[0]);
+            const double cb = std::cos(s.tilt[1]), sb = std::sin(s.tilt[1]);
+            const double rxT[9] = {1, 0, 0, 0, ca, sa, 0, -sa, ca}, drxT[9] = {0, 0, 0, 0, -sa, ca, 0, -ca, -sa};
+            const double ryT[9] = {cb, 0, -sb, 0, 1, 0, sb, 0, cb}, dryT[9] = {-sb, 0, -cb, 0, 0, 0, cb, 0, -sb};
+            double t1[9], t2[9];
+            mat3_mul(drxT, s.rot, t1);
+            mat3_mul(ryT, t1, t2);  // d/da
+            for (int k = 0; k < 9; ++k) grec64[(size_t)i * 18 + k] = t2[k];
+            mat3_mul(rxT, s.rot, t1);
+            mat3_mul(dryT, t1, t2);  // d/db
+            for (int k = 0; k < 9; ++k) grec64[(size_t)i * 18 + 9 + k] = t2[k];
+            for (int k = 0; k < 18; ++k) grec32[(size_t)i * 18 + k] = (float)grec64[(size_t)i * 18 + k];
+        }
         reci[i] = make_int4(s.shape | (s.role << 4) | (s.aperture << 8) | ((asph ? 1 : 0) << 12), s.material,
                             s.medium_front, s.medium_back);
         double lo[3], hi[3];
@@ -605,7 +624,15 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
             root = (int)nodes.size();
             emit_nodes(bn, nodes);
         }
-        vars[v] = make_int4(root, g0, (int)glob.size() - g0, s0);
+        // .w: the variant's exit surface (first focal plane with a hexagonal aperture), for soft CE
+        int exit_sid = -1;
+        for (int s = s0; s < s1 && exit_sid < 0; ++s) {
+            const robast_surface_desc& q = d->surfaces[s];
+            if (q.role == ROBAST_ROLE_FOCAL && q.shape == ROBAST_SHAPE_SAG && q.aperture == ROBAST_AP_HEXAGON &&
+                q.curv == 0.0 && !any_asph(q))
+                exit_sid = s;
+        }
+        vars[v] = make_int4(root, g0, (int)glob.size() - g0, exit_sid);
     }
     std::vector<double> mats((size_t)std::max(1, d->n_materials) * MAT_REC, 0.0);
     for (int i = 0; i < d->n_materials; ++i) {
@@ -637,7 +664,8 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t bv = align16(vars.size() * 16), bg = align16(glob.size() * 4);
     const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8);
     const size_t bw = kWorkSlots * 8;
-    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bw;
+    const size_t bg64 = align16(grec64.size() * 8), bg32 = align16(grec32.size() * 4);
+    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bw + bg64 + bg32;
 
     robast_geom* g = new (std::nothrow) robast_geom();
     if (!g) return fail(ROBAST_E_OOM, "robast_build_geometry: host allocation failed");
@@ -667,6 +695,9 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t om = put(mats.data(), mats.size() * 8, bm);
     const size_t od = put(meds.data(), meds.size() * 8, bd);
     const size_t ow = off;
+    off += bw;
+    const size_t og64 = put(grec64.data(), grec64.size() * 8, bg64);
+    const size_t og32 = put(grec32.data(), grec32.size() * 4, bg32);
     e = cudaMemcpy(g->dmem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->dmem);
@@ -694,6 +725,8 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->tab32 = t;
     g->tab32.surf = base + o32;
     g->work = reinterpret_cast<unsigned long long*>(base + ow);
+    g->grec64 = reinterpret_cast<const double*>(base + og64);
+    g->grec32 = reinterpret_cast<const float*>(base + og32);
     g->smem64 = b64 + bi + bn + bp + bv + bg + bm + bd;
     g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd;
     g->n_surf = ns;
@@ -998,6 +1031,96 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
     if (out->counters)
         for (int k = 0; k < ROBAST_N_COUNTERS; ++k) out->counters[k] += hc[k];
     return 0;
+}
+
+// -------------------------------------------------------------- gradients
+extern "C" int robast_param_count(const robast_geom* g) { return g ? g->n_surf * ROBAST_N_PARAM : 0; }
+
+template <typename T>
+static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl, int64_t n, uint64_t seed,
+                   int objective, double tau, double d_obj, double* value, double* d_params,
+                   const robast_trace_opts& op, double* info) {
+    GradArgs<T> a{};
+    a.tab = sizeof(T) == 4 ? g->tab32 : g->tab64;
+    a.surf64 = static_cast<const double*>(g->tab64.surf);
+    a.grec = g->grec64;
+    a.o = static_cast<const T*>(o);
+    a.d = static_cast<const T*>(d);
+    a.lam = static_cast<const T*>(wl);
+    a.vop = op.variant_of_photon;
+    a.n = n;
+    a.seed = seed;
+    a.first_id = op.first_photon_id;
+    a.max_bounces = op.max_bounces;
+    const double L = g->length_scale;
+    const double eps = op.eps > 0.0 ? op.eps : (sizeof(T) == 4 ? 1e-6 : 1e-9) * L;
+    a.eps = (T)eps;
+    a.newton_tol = sizeof(T) == 4 ? (T)(1e-6 * L) : (T)(eps * 1e-4);
+    a.newton_tol64 = 1e-13 * L;
+    a.objective = objective;
+    a.tau = tau;
+    const size_t NP = (size_t)g->n_surf * ROBAST_N_PARAM;
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = grow(&g->scratch, &g->scratch_bytes, (NP * 3 + 8) * sizeof(double), "robast_trace_grad");
+    if (rc) return rc;
+    double* acc = static_cast<double*>(g->scratch);
+    double* vals = acc + NP * 3;
+    a.acc = acc;
+    a.vals = vals;
+    cudaStream_t s = static_cast<cudaStream_t>(op.stream);
+    CU(cudaMemsetAsync(acc, 0, (NP * 3 + 8) * sizeof(double), s), "robast_trace_grad: clear");
+    const size_t smem_tab = sizeof(T) == 4 ? g->smem32 : g->smem64;
+    a.stage = smem_tab <= kSmemCap ? 1 : 0;
+    const size_t smem = a.stage ? smem_tab : 0;
+    const long long grid = std::max(1LL, std::min<long long>((long long)g->num_sms * 4, (n + 127) / 128));
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4)
+        e = launch_grad_f32(a, (int)grid, smem, s);
+    else
+        e = launch_grad_f64(a, (int)grid, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "robast_trace_grad: launch");
+    if (d_params) {
+        e = launch_grad_finish(acc, vals, (int)NP, objective, d_obj, d_params, s);
+        if (e != cudaSuccess) return cuda_fail(e, "robast_trace_grad: launch");
+    }
+    double hv[8];
+    CU(cudaMemcpyAsync(hv, vals, sizeof hv, cudaMemcpyDeviceToHost, s), "robast_trace_grad: copy");
+    CU(cudaStreamSynchronize(s), "robast_trace_grad: synchronize");
+    if (objective == 1) {
+        *value = hv[7] > 0 ? hv[4] / hv[7] : 0.0;
+    } else if (hv[0] > 0) {
+        const double qx = hv[1] / hv[0], qy = hv[2] / hv[0];
+        if (objective == 0) *value = hv[3] / hv[0] - qx * qx - qy * qy;
+        if (objective == 2) *value = qx;
+        if (objective == 3) *value = qy;
+    } else {
+        *value = 0.0;
+    }
+    if (info)
+        for (int k = 0; k < 8; ++k) info[k] = hv[k];
+    return 0;
+}
+
+extern "C" int robast_trace_grad(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
+                                 int64_t n, uint64_t seed, int32_t objective, double tau, double d_obj, double* value,
+                                 double* d_params, const robast_trace_opts* opts, double* info) {
+    robast_trace_opts o;
+    robast_trace_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_bounces == 0) o.max_bounces = 100;
+    if (o.precision == 0) o.precision = 32;
+    if (!value) return fail(ROBAST_E_NULL, "robast_trace_grad: value is NULL");
+    robast_trace_out none{};
+    int rc = check_trace_args(g, origins, dirs, wavelengths, n, &none, o);
+    if (rc) return rc;
+    if (n <= 0) return fail(ROBAST_E_INVALID, "robast_trace_grad: n must be > 0");
+    if (objective < 0 || objective > 3) return fail(ROBAST_E_INVALID, "robast_trace_grad: unknown objective %d", objective);
+    if (objective == 1 && !(tau > 0.0)) return fail(ROBAST_E_INVALID, "robast_trace_grad: tau must be > 0");
+    robast_geom* gm = const_cast<robast_geom*>(g);
+    return o.precision == 32 ? do_grad<float>(gm, origins, dirs, wavelengths, n, seed, objective, tau, d_obj, value,
+                                              d_params, o, info)
+                             : do_grad<double>(gm, origins, dirs, wavelengths, n, seed, objective, tau, d_obj, value,
+                                               d_params, o, info);
 }
 
 // ------------------------------------------------------------- reductions

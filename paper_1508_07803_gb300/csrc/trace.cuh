@@ -261,6 +261,7 @@ struct LHit {
     T t;
     V3<T> pl;  // local hit point
     V3<T> nl;  // local front normal (unit)
+    T u;       // Bezier parameter of a cone-wall hit
 };
 
 // sag z(rho) and dz/drho of the even asphere; false outside the conic's domain
@@ -363,7 +364,7 @@ __device__ __forceinline__ bool hit_sag(const T* S, int ap, bool asph, V3<T> p, 
                 err = true;
                 return false;
             }
-            if (sizeof(T) == 4) {
+            if constexpr (sizeof(T) == 4) {
                 // grazing incidence: |d . N| < 0.05 |N| -> last step in FP64
                 const V3<T> x = p + t * d;
                 const T nx = -T(2) * x.x * slope, ny = -T(2) * x.y * slope;
@@ -513,17 +514,21 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
             T u = us[i];
             const T gp = T(2) * A * u + B;
             // one Newton polish of the root; in FP32 at grazing (|g'| small) it runs in FP64
-            if (sizeof(T) == 4 && t_abs(gp) < T(0.05) * (t_abs(B) + t_abs(A) + t_abs(C) + T(1e-30))) {
-                const double pj_c = (double)cj[j], pj_s = (double)sj[j];
-                const double q0d = (double)p.x * pj_c + (double)p.y * pj_s, dqd = (double)d.x * pj_c + (double)d.y * pj_s;
-                const double Ad = (double)d.z * (double)ra2 - dqd * (double)za2;
-                const double Bd = (double)d.z * (double)ra1 - dqd * (double)za1;
-                const double Cd = (double)d.z * ((double)ra0 - q0d) - dqd * ((double)za0 - (double)p.z);
-                const double ud = (double)u, gpd = 2.0 * Ad * ud + Bd;
-                if (gpd != 0.0) u = (T)(ud - ((Ad * ud + Bd) * ud + Cd) / gpd);
-            } else if (gp != T(0)) {
-                u -= ((A * u + B) * u + C) / gp;
+            bool polished = false;
+            if constexpr (sizeof(T) == 4) {
+                if (t_abs(gp) < T(0.05) * (t_abs(B) + t_abs(A) + t_abs(C) + T(1e-30))) {
+                    const double pj_c = (double)cj[j], pj_s = (double)sj[j];
+                    const double q0d = (double)p.x * pj_c + (double)p.y * pj_s,
+                                 dqd = (double)d.x * pj_c + (double)d.y * pj_s;
+                    const double Ad = (double)d.z * (double)ra2 - dqd * (double)za2;
+                    const double Bd = (double)d.z * (double)ra1 - dqd * (double)za1;
+                    const double Cd = (double)d.z * ((double)ra0 - q0d) - dqd * ((double)za0 - (double)p.z);
+                    const double ud = (double)u, gpd = 2.0 * Ad * ud + Bd;
+                    if (gpd != 0.0) u = (T)(ud - ((Ad * ud + Bd) * ud + Cd) / gpd);
+                    polished = true;
+                }
             }
+            if (!polished && gp != T(0)) u = u - ((A * u + B) * u + C) / gp;
             if (u < T(0) || u > T(1)) continue;
             const T R = ra0 + u * (ra1 + u * ra2);
             const T Z = za0 + u * (za1 + u * za2);
@@ -546,6 +551,7 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
     }
     if (!found) return false;
     const T Rp = ra1 + T(2) * ra2 * bu, Zp = za1 + T(2) * za2 * bu;
+    h.u = bu;
     h.t = best;
     h.nl = unit(mk(-Zp * cj[bj], -Zp * sj[bj], Rp));
     return true;

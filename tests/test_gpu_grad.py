@@ -1,0 +1,109 @@
+"""GPU frozen-path gradients (robast_trace_grad, through the C ABI) against
+the oracle's dual-number gradients and central finite differences.
+
+Tolerances: GPU vs oracle duals 1e-3 relative (FP32 trace) and 1e-8 (FP64);
+GPU (FP64) vs oracle central differences (h = 1e-6) 1e-4.  Relative error is
+|g - g_ref| / max(|g_ref|, 1e-3 max|g_ref|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+robast = pytest.importorskip("paper_1508_07803_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    robast.load()
+
+
+def _rel(g, ref):
+    scale = max(np.max(np.abs(ref)), 1e-300)
+    return np.abs(g - ref) / np.maximum(np.abs(ref), 1e-3 * scale)
+
+
+def _dev(bundle, precision):
+    dt = torch.float32 if precision == 32 else torch.float64
+    b = bundle if precision == 64 else bundle.rounded_to(np.float32)
+    return (torch.from_numpy(b.origins).to("cuda", dt), torch.from_numpy(b.dirs).to("cuda", dt),
+            torch.from_numpy(b.wavelengths).to("cuda", dt))
+
+
+def _gpu(scene, b, objective, precision, **kw):
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, precision)
+    v, g, info = robast.trace_grad(geom, o, d, w, objective=objective, precision=precision, **kw)
+    geom.close()
+    return v, g.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-8), (32, 1e-3)])
+def test_dish_msr_gradient_matches_oracle_duals(precision, tol):
+    scene, b = W.lst_workload(4_001, seed=5, angles_deg=(0.0, 1.0))
+    v, g, info = _gpu(scene, b, "msr", precision, seed=7)
+    ref_b = b if precision == 64 else b.rounded_to(np.float32)
+    rv, rg = oracle.objective(scene, ref_b, "msr", seed=7, eps=oracle.default_eps(scene, precision))
+    assert v == pytest.approx(rv, rel=1e-9 if precision == 64 else 1e-5)
+    assert info["n_untracked"] == 0
+    mask = np.abs(rg).sum(axis=1) > 0
+    assert mask.sum() > 50
+    assert np.max(_rel(g[mask], rg[mask])) < tol
+
+
+def test_dish_gradient_matches_central_differences():
+    scene, b = W.lst_workload(1_500, seed=6, angles_deg=(1.5,))
+    _, g, _ = _gpu(scene, b, "msr", 64, seed=8)
+    ns = len(scene.surfaces)
+    picks = np.argsort(-np.abs(g[:, 0]))[:3]
+    for sid in picks:
+        for k in (0, 1, 2, 5):
+            dp = np.zeros((ns, 16))
+            dp[sid, k] = 1e-6
+            vp, _ = oracle.objective(scene, b, "msr", seed=8, delta=dp, grad=False)
+            vm, _ = oracle.objective(scene, b, "msr", seed=8, delta=-dp, grad=False)
+            fd = (vp - vm) / 2e-6
+            scale = np.max(np.abs(g))
+            assert abs(g[sid, k] - fd) / max(abs(fd), 1e-3 * scale) < 1e-4, (sid, k, g[sid, k], fd)
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-8), (32, 1e-3)])
+def test_cone_soft_ce_gradient_matches_oracle_duals(precision, tol):
+    scene = W.cone_scene(n_variants=1, seed=0)
+    H = W.cone_heights(1)[0]
+    b = W.concat([W.hexagon_bundle(3_001, W.CONE_A_IN, H + W.CONE_WINDOW + 1e-4, math.radians(a), seed=3,
+                                   stream=60 + i) for i, a in enumerate((5.0, 20.0, 28.0, 33.0))])
+    v, g, _ = _gpu(scene, b, "soft_ce", precision, seed=4, max_bounces=30)
+    ref_b = b if precision == 64 else b.rounded_to(np.float32)
+    rv, rg = oracle.objective(scene, ref_b, "soft_ce", seed=4, max_bounces=30, eps=oracle.default_eps(scene, precision))
+    assert v == pytest.approx(rv, rel=1e-9 if precision == 64 else 1e-4)
+    assert np.max(_rel(g[1, 10:16], rg[1, 10:16])) < tol, (g[1, 10:16], rg[1, 10:16])
+
+
+def test_autograd_function_returns_the_launch_gradient():
+    scene, b = W.lst_workload(2_000, seed=9, angles_deg=(0.5,))
+    F = robast.objective_function()
+    params = torch.tensor(robast.scene_params(scene), dtype=torch.float64, requires_grad=True)
+    o, d, w = _dev(b, 64)
+    val = F.apply(params, scene, o, d, w, dict(objective="msr", precision=64, seed=2))
+    (2.0 * val).backward()
+    rv, rg = oracle.objective(scene, b, "msr", seed=2)
+    assert float(val) == pytest.approx(rv, rel=1e-9)
+    got = params.grad.numpy()
+    mask = np.abs(rg).sum(axis=1) > 0
+    assert np.max(_rel(got[mask], 2.0 * rg[mask])) < 1e-8
+    # a central difference along a step matches the gradient's directional derivative
+    step = 1e-6 * got / np.max(np.abs(got))
+    p0 = robast.scene_params(scene)
+    opts = dict(objective="msr", precision=64, seed=2)
+    vp = float(F.apply(torch.tensor(p0 + step), scene, o, d, w, opts))
+    vm = float(F.apply(torch.tensor(p0 - step), scene, o, d, w, opts))
+    pred = 0.5 * np.sum(got * step)
+    assert abs((vp - vm) / 2 - pred) < 1e-4 * abs(pred)
