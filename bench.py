@@ -242,6 +242,49 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
             "collection_efficiency": summary}
 
 
+def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
+    """Differentiable batch: 32 LST-like dishes with 60-198 facets, 1e6
+    photons each over field angles 0-2 deg, one evaluation = the summed
+    mean-squared spot radius of the 32 dishes AND its gradient with respect to
+    every facet's two tilts and eight aspheric coefficients, in one launch
+    (FP32 trace, FP64 dual re-intersection and sums).  Dish v is lit at the
+    field angle 2 v / 31 deg.  Metric: gradient evaluations/s."""
+    import torch
+    import paper_1508_07803_gb300 as robast
+
+    scene, b, vop, counts = W.dish_batch(n_dishes=32, photons_per_dish=args.grad_photons_per_dish, seed=rank)
+    geom = robast.build_geometry(scene)
+    o = torch.from_numpy(b.origins).to(dev, torch.float32)
+    d = torch.from_numpy(b.dirs).to(dev, torch.float32)
+    w = torch.from_numpy(b.wavelengths).to(dev, torch.float32)
+    v = torch.from_numpy(vop).to(dev)
+    g = torch.zeros((geom.n_surfaces, robast.N_PARAM), dtype=torch.float64, device=dev)
+
+    def evaluate():
+        g.zero_()
+        return robast.trace_grad(geom, o, d, w, objective="msr", precision=32, seed=0, variant_of_photon=v,
+                                 stream=stream, out=g)
+
+    for _ in range(2):
+        evaluate()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.grad_steps):
+        value, _, info = evaluate()
+    barrier()
+    dt = max_over_ranks(time.perf_counter() - t0)
+    gn = float(torch.linalg.vector_norm(g).item())
+    geom.close()
+    return {"value": ws * args.grad_steps / dt, "unit": "grad evals/s", "ms_per_eval": 1e3 * dt / args.grad_steps,
+            "photons_per_eval": int(b.n), "photons_per_s": ws * args.grad_steps * b.n / dt,
+            "objective": "sum over 32 dishes of the mean-squared spot radius (frozen path, expected weights)",
+            "objective_value_m2": value, "gradient_norm": gn, "n_params": int(geom.n_surfaces * robast.N_PARAM),
+            "n_detected": int(info["n_detected"]), "untracked_photons": int(info["n_untracked"]),
+            "config": {"workload": "dish_batch_32_dishes_60_to_198_facets", "facets": [counts[0], counts[-1]],
+                       "photons_per_dish": args.grad_photons_per_dish, "field_angle_deg": "2 v / 31 for dish v",
+                       "timing": "host wall clock around the synchronous call (value returned to the host)"}}
+
+
 def traffic_from_profile(n_photons):
     """DRAM bytes of the trace kernel from the committed ncu summary, if it was
     taken on the current kernel source; else None."""
@@ -271,6 +314,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--grad-photons-per-dish", type=int, default=1_000_000)
+    ap.add_argument("--grad-steps", type=int, default=3)
     ap.add_argument("--batch-photons-per-group", type=int, default=2_000_000)
     ap.add_argument("--batch-steps", type=int, default=2)
     args = ap.parse_args()
@@ -405,6 +451,10 @@ def main():
         forms["batched_fp32"] = measure_batched(args, geom_dev=dev, stream=stream, ws=ws, rank=rank,
                                                 max_over_ranks=max_over_ranks, sum_over_ranks=sum_over_ranks,
                                                 barrier=barrier)
+
+    if not args.no_grad:
+        forms["grad_fp32"] = measure_grad(args, dev=dev, stream=stream, ws=ws, rank=rank,
+                                          max_over_ranks=max_over_ranks, barrier=barrier)
 
     e2e = None
     if not args.no_e2e:

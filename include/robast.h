@@ -304,7 +304,9 @@ int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64
  * Parameters: ROBAST_N_PARAM per surface, [0..1] tilt about local x, y
  * (as robast_surface_desc.tilt), [2..9] A1..A8 (SAG mirrors), [10..15]
  * Bezier control points P0r, P0z, P1r, P1z, P2r, P2z (HEXCONE mirrors); a
- * path carries derivatives for the first such mirror it meets.
+ * path carries derivatives for the first such mirror it meets.  With several
+ * variants the objective is the sum of the variants' objectives, each over
+ * its own photons (a batch of designs evaluated in one launch).
  */
 #define ROBAST_OBJ_MSR 0
 #define ROBAST_OBJ_SOFT_CE 1
@@ -321,9 +323,10 @@ int robast_param_count(const robast_geom* g);
  * Inputs as robast_trace_ex (device, the precision's element type).  One
  * pass: each photon's path is re-traced (nothing per bounce is stored) and
  * every surface it meets is re-intersected in forward-mode dual numbers;
- * sums over photons are FP64.  info (HOST, 8 doubles, may be NULL):
- * W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid, N_detected, photons
- * meeting a second differentiable mirror (untracked), N.  Synchronises the
+ * sums over photons are FP64.  info (HOST, 8 doubles, may be NULL; totals
+ * over variants): W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid,
+ * N_detected, photons meeting a second differentiable mirror (untracked), N
+ * (photons with an invalid variant index are skipped).  Synchronises the
  * stream; uses device scratch owned by g.
  */
 int robast_trace_grad(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,

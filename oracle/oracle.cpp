@@ -1331,40 +1331,44 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* O, const dou
             });
         for (auto& t : th) t.join();
     }
-    double W = 0.0, sx = 0.0, sy = 0.0;
-    if (centroid) {
-        for (int64_t i = 0; i < n; ++i)
-            if (valid[i] == 1 && status[i] == O_ST_DETECTED) {
-                W += w[i];
-                sx += w[i] * (cax == 0 ? qx[i] : qy[i]);
-            }
-        *value = W > 0.0 ? sx / W : 0.0;
-    } else if (objective == 0) {
-        for (int64_t i = 0; i < n; ++i)
-            if (valid[i] == 1 && status[i] == O_ST_DETECTED) {
-                W += w[i];
-                sx += w[i] * qx[i];
-                sy += w[i] * qy[i];
-            }
-        if (W <= 0.0) {
-            *value = 0.0;
-            if (grad) std::fill(grad, grad + NP, 0.0);
-            return 0;
+    /* per-variant sums; with several variants the objective is the sum of the
+     * variants' objectives, each over its own photons */
+    const int nvar = scene->variant_offsets ? scene->n_variants : 1;
+    std::vector<double> Wv(nvar, 0.0), cxv(nvar, 0.0), cyv(nvar, 0.0), nv(nvar, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int v = vop ? vop[i] : 0;
+        nv[v] += 1.0;
+        if (valid[i] == 1 && status[i] == O_ST_DETECTED) {
+            Wv[v] += w[i];
+            cxv[v] += w[i] * qx[i];
+            cyv[v] += w[i] * qy[i];
         }
-        const double cxm = sx / W, cym = sy / W;
-        double acc = 0.0;
-        for (int64_t i = 0; i < n; ++i)
-            if (valid[i] == 1 && status[i] == O_ST_DETECTED)
-                acc += w[i] * ((qx[i] - cxm) * (qx[i] - cxm) + (qy[i] - cym) * (qy[i] - cym));
-        *value = acc / W;
-        sx = cxm;
-        sy = cym;
-    } else {
-        double acc = 0.0;
-        for (int64_t i = 0; i < n; ++i)
-            if (valid[i] == 1) acc += w[i] * sigmoid(mval[i] / tau);
-        *value = acc / (double)n;
     }
+    for (int v = 0; v < nvar; ++v)
+        if (Wv[v] > 0.0) {
+            cxv[v] /= Wv[v];
+            cyv[v] /= Wv[v];
+        }
+    std::vector<double> part_v(nvar, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int v = vop ? vop[i] : 0;
+        if (valid[i] != 1) continue;
+        if (objective == 1) {
+            part_v[v] += w[i] * sigmoid(mval[i] / tau);
+        } else if (status[i] == O_ST_DETECTED) {
+            if (centroid) part_v[v] += w[i] * (cax == 0 ? qx[i] : qy[i]);
+            else part_v[v] += w[i] * ((qx[i] - cxv[v]) * (qx[i] - cxv[v]) + (qy[i] - cyv[v]) * (qy[i] - cyv[v]));
+        }
+    }
+    double total = 0.0;
+    for (int v = 0; v < nvar; ++v) {
+        if (objective == 1) {
+            if (nv[v] > 0.0) total += part_v[v] / nv[v];
+        } else if (Wv[v] > 0.0) {
+            total += part_v[v] / Wv[v];
+        }
+    }
+    *value = total;
     if (!grad) return 0;
     // pass 2: dual numbers along the same frozen paths, one thread-partial vector each
     std::vector<std::vector<double>> part(n_threads, std::vector<double>(NP, 0.0));
@@ -1386,17 +1390,17 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* O, const dou
                     const o_surface& ts = scene->surfaces[tracked[i]];
                     const int base = ts.shape == O_SHAPE_SAG ? 0 : 10;
                     const int nslots = ts.shape == O_SHAPE_SAG ? 10 : 6;
+                    Dual m;
+                    if (objective == 1 && !exit_margin<Dual>(scene, v, R.p, R.d, &m)) continue;
                     for (int k2 = 0; k2 < nslots; ++k2) {
                         double c;
                         if (centroid) {
-                            c = w[i] / W * (cax == 0 ? R.qx.d[k2] : R.qy.d[k2]);
+                            c = w[i] / Wv[v] * (cax == 0 ? R.qx.d[k2] : R.qy.d[k2]);
                         } else if (objective == 0) {
-                            c = 2.0 * w[i] / W * ((qx[i] - sx) * R.qx.d[k2] + (qy[i] - sy) * R.qy.d[k2]);
+                            c = 2.0 * w[i] / Wv[v] * ((qx[i] - cxv[v]) * R.qx.d[k2] + (qy[i] - cyv[v]) * R.qy.d[k2]);
                         } else {
-                            Dual m;
-                            if (!exit_margin<Dual>(scene, v, R.p, R.d, &m)) continue;
                             const double sg = sigmoid(m.v / tau);
-                            c = w[i] * sg * (1.0 - sg) / tau * m.d[k2] / (double)n;
+                            c = w[i] * sg * (1.0 - sg) / tau * m.d[k2] / nv[v];
                         }
                         g[(size_t)tracked[i] * O_N_PARAM + base + k2] += c;
                     }

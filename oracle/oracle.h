@@ -115,6 +115,8 @@ int64_t oracle_generate_sources(const o_source_group* groups, int32_t n_groups, 
  *                     photon was obscured;
  *   objectives 2, 3 (closed-form pins only): the w-weighted centroid of the
  *                     DETECTED photons' focal x (2) or y (3).
+ * With several variants the objective is the sum of the variants' objectives,
+ * each over its own photons.
  * Parameters: 16 per surface -- [0..1] tilt about local x, y; [2..9] A1..A8
  * (SAG mirrors); [10..15] Bezier control points P0r, P0z, P1r, P1z, P2r, P2z
  * (HEXCONE mirrors).  grad (may be NULL): d objective / d parameter by

@@ -111,7 +111,19 @@ __global__ void __launch_bounds__(BLOCK) grad_kernel(GradArgs<T> A) {
     }
     const uint2 key = make_uint2((uint32_t)A.seed, (uint32_t)(A.seed >> 32));
     const long long n = A.n;
-    double vs[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // W, sum w qx, sum w qy, sum w |q|^2, sum soft CE, n_det, untracked, n
+    // per-variant sums held for the variant of this thread's current photons (photons of a
+    // variant are contiguous, so a thread changes variant rarely): W, sum w qx, sum w qy,
+    // sum w |q|^2, sum soft CE, n_det, untracked, n
+    double vs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cur_var = -1;
+    auto flush = [&]() {
+        if (cur_var < 0) return;
+        for (int k = 0; k < 8; ++k)
+            if (vs[k] != 0.0) {
+                atomicAdd(A.vals + (size_t)cur_var * 8 + k, vs[k]);
+                vs[k] = 0.0;
+            }
+    };
     DD Sd[REC];
     for (long long i = blockIdx.x * (long long)BLOCK + threadIdx.x; i < n; i += (long long)gridDim.x * BLOCK) {
         V3<DD> p = lift(mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]));
@@ -122,7 +134,11 @@ __global__ void __launch_bounds__(BLOCK) grad_kernel(GradArgs<T> A) {
         double w = 1.0;
         int tracked = -1, status = 0, extra = 0;
         DD qx(0), qy(0);
-        if (var < 0 || var >= tb.n_var) status = ST_ERROR;
+        if (var < 0 || var >= tb.n_var) continue;  // no variant to account it to
+        if (var != cur_var) {
+            flush();
+            cur_var = var;
+        }
         for (int b = 0; status == 0; ++b) {
             Best<T> bst;
             bool overflow = false;
@@ -273,19 +289,16 @@ __global__ void __launch_bounds__(BLOCK) grad_kernel(GradArgs<T> A) {
             }
         }
     }
-    // value sums: warp shuffles, then one atomic per warp and entry
-    for (int k = 0; k < 8; ++k) {
-        double v = vs[k];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(A.vals + k, v);
-    }
+    flush();
 }
 
-// d_params[p] += d_obj * gradient, from the sums of the pass
-__global__ void grad_finish(const double* acc, const double* vals, int n_params, int objective, double d_obj,
-                            double* out) {
+// d_params[p] += d_obj * gradient, from the sums of the pass (the sums of the
+// variant the parameter's surface belongs to)
+__global__ void grad_finish(const double* acc, const double* vals_all, const int* surf_var, int n_params,
+                            int objective, double d_obj, double* out) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_params) return;
+    const double* vals = vals_all + (size_t)surf_var[p / 16] * 8;
     const double W = vals[0];
     double g = 0.0;
     if (objective == 1) {
@@ -317,9 +330,9 @@ cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cu
     return a.stage ? launch_grad_one<double, 128, true>(a, grid, smem, s)
                    : launch_grad_one<double, 128, false>(a, grid, 0, s);
 }
-cudaError_t launch_grad_finish(const double* acc, const double* vals, int n_params, int objective, double d_obj,
-                               double* out, cudaStream_t s) {
-    grad_finish<<<(n_params + 255) / 256, 256, 0, s>>>(acc, vals, n_params, objective, d_obj, out);
+cudaError_t launch_grad_finish(const double* acc, const double* vals, const int* surf_var, int n_params, int objective,
+                               double d_obj, double* out, cudaStream_t s) {
+    grad_finish<<<(n_params + 255) / 256, 256, 0, s>>>(acc, vals, surf_var, n_params, objective, d_obj, out);
     return cudaGetLastError();
 }
 

@@ -33,12 +33,12 @@ struct GradArgs {
     int objective;
     double tau;
     double* acc;   // [n_surf * 16 * 3]
-    double* vals;  // [8]
+    double* vals;  // [n_variants * 8]
 };
 cudaError_t launch_grad_f32(const GradArgs<float>& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_grad_finish(const double* acc, const double* vals, int n_params, int objective, double d_obj,
-                               double* out, cudaStream_t s);
+cudaError_t launch_grad_finish(const double* acc, const double* vals, const int* surf_var, int n_params, int objective,
+                               double d_obj, double* out, cudaStream_t s);
 
 // Launch the persistent trace kernel; returns the cudaError_t of the launch.
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s);

@@ -53,6 +53,7 @@ struct robast_geom {
     Tables tab32{}, tab64{};
     const float* grec32 = nullptr;    // per surface: d rows / d tilt_x, d rows / d tilt_y
     const double* grec64 = nullptr;
+    const int* surf_var = nullptr;    // variant of each surface
     size_t smem32 = 0, smem64 = 0;  // bytes to stage each precision's tables
     int num_sms = 0;
     // per-launch work counters (a ring, so launches on several streams do not share one)
@@ -665,7 +666,14 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8);
     const size_t bw = kWorkSlots * 8;
     const size_t bg64 = align16(grec64.size() * 8), bg32 = align16(grec32.size() * 4);
-    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bw + bg64 + bg32;
+    std::vector<int> surf_var(ns, 0);
+    for (int v = 0; v < nv; ++v) {
+        const int s0 = d->variant_offsets ? d->variant_offsets[v] : 0;
+        const int s1 = d->variant_offsets ? d->variant_offsets[v + 1] : ns;
+        for (int s = s0; s < s1; ++s) surf_var[s] = v;
+    }
+    const size_t bsv = align16(surf_var.size() * 4);
+    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bw + bg64 + bg32 + bsv;
 
     robast_geom* g = new (std::nothrow) robast_geom();
     if (!g) return fail(ROBAST_E_OOM, "robast_build_geometry: host allocation failed");
@@ -698,6 +706,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     off += bw;
     const size_t og64 = put(grec64.data(), grec64.size() * 8, bg64);
     const size_t og32 = put(grec32.data(), grec32.size() * 4, bg32);
+    const size_t osv = put(surf_var.data(), surf_var.size() * 4, bsv);
     e = cudaMemcpy(g->dmem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->dmem);
@@ -727,6 +736,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->work = reinterpret_cast<unsigned long long*>(base + ow);
     g->grec64 = reinterpret_cast<const double*>(base + og64);
     g->grec32 = reinterpret_cast<const float*>(base + og32);
+    g->surf_var = reinterpret_cast<const int*>(base + osv);
     g->smem64 = b64 + bi + bn + bp + bv + bg + bm + bd;
     g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd;
     g->n_surf = ns;
@@ -1060,15 +1070,16 @@ static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl,
     a.objective = objective;
     a.tau = tau;
     const size_t NP = (size_t)g->n_surf * ROBAST_N_PARAM;
+    const size_t NV = (size_t)g->n_var;
     std::lock_guard<std::mutex> lk(g->mu);
-    int rc = grow(&g->scratch, &g->scratch_bytes, (NP * 3 + 8) * sizeof(double), "robast_trace_grad");
+    int rc = grow(&g->scratch, &g->scratch_bytes, (NP * 3 + 8 * NV) * sizeof(double), "robast_trace_grad");
     if (rc) return rc;
     double* acc = static_cast<double*>(g->scratch);
     double* vals = acc + NP * 3;
     a.acc = acc;
     a.vals = vals;
     cudaStream_t s = static_cast<cudaStream_t>(op.stream);
-    CU(cudaMemsetAsync(acc, 0, (NP * 3 + 8) * sizeof(double), s), "robast_trace_grad: clear");
+    CU(cudaMemsetAsync(acc, 0, (NP * 3 + 8 * NV) * sizeof(double), s), "robast_trace_grad: clear");
     const size_t smem_tab = sizeof(T) == 4 ? g->smem32 : g->smem64;
     a.stage = smem_tab <= kSmemCap ? 1 : 0;
     const size_t smem = a.stage ? smem_tab : 0;
@@ -1080,24 +1091,32 @@ static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl,
         e = launch_grad_f64(a, (int)grid, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "robast_trace_grad: launch");
     if (d_params) {
-        e = launch_grad_finish(acc, vals, (int)NP, objective, d_obj, d_params, s);
+        e = launch_grad_finish(acc, vals, g->surf_var, (int)NP, objective, d_obj, d_params, s);
         if (e != cudaSuccess) return cuda_fail(e, "robast_trace_grad: launch");
     }
-    double hv[8];
-    CU(cudaMemcpyAsync(hv, vals, sizeof hv, cudaMemcpyDeviceToHost, s), "robast_trace_grad: copy");
+    std::vector<double> hv(8 * NV);
+    CU(cudaMemcpyAsync(hv.data(), vals, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "robast_trace_grad: copy");
     CU(cudaStreamSynchronize(s), "robast_trace_grad: synchronize");
-    if (objective == 1) {
-        *value = hv[7] > 0 ? hv[4] / hv[7] : 0.0;
-    } else if (hv[0] > 0) {
-        const double qx = hv[1] / hv[0], qy = hv[2] / hv[0];
-        if (objective == 0) *value = hv[3] / hv[0] - qx * qx - qy * qy;
-        if (objective == 2) *value = qx;
-        if (objective == 3) *value = qy;
-    } else {
-        *value = 0.0;
+    // the objective of several variants is the sum of their objectives
+    double total = 0.0;
+    for (size_t v = 0; v < NV; ++v) {
+        const double* V = &hv[8 * v];
+        if (objective == 1) {
+            if (V[7] > 0) total += V[4] / V[7];
+        } else if (V[0] > 0) {
+            const double qx = V[1] / V[0], qy = V[2] / V[0];
+            if (objective == 0) total += V[3] / V[0] - qx * qx - qy * qy;
+            if (objective == 2) total += qx;
+            if (objective == 3) total += qy;
+        }
     }
-    if (info)
-        for (int k = 0; k < 8; ++k) info[k] = hv[k];
+    *value = total;
+    if (info) {
+        for (int k = 0; k < 8; ++k) info[k] = 0.0;
+        for (size_t v = 0; v < NV; ++v)
+            for (int k = 0; k < 8; ++k) info[k] += hv[8 * v + k];
+    }
     return 0;
 }
 

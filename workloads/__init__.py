@@ -431,3 +431,31 @@ def cone_batch(n_variants: int = 64, angles_deg=CONE_ANGLES_DEG, n_per_group: in
                                apothem=CONE_A_IN, dir=(math.sin(th), 0.0, -math.cos(th)), lam=lam,
                                angle_deg=a))
     return scene, groups
+
+
+def dish_batch(n_dishes: int = 32, n_min: int = 60, n_max: int = 198, photons_per_dish: int = 1_000_000,
+               angles_deg=None, seed: int = 0):
+    """Differentiable batch: n_dishes LST-like dishes with facet counts evenly
+    spaced over [n_min, n_max] (the first N lattice facets by radius), each
+    with its own focal plane, masts and camera box, as the variants of one
+    scene.  Photons: photons_per_dish per dish, split over angles_deg, or by
+    default all at ONE field angle per dish, the angles spread evenly over
+    0-2 deg across the dishes (so each dish's spot is one spot).
+    Returns (scene, bundle, variant_of_photon, facet counts)."""
+    surfs: List[Surface] = []
+    offs = [0]
+    bundles, vop = [], []
+    counts = [int(round(n_min + (n_max - n_min) * v / max(n_dishes - 1, 1))) for v in range(n_dishes)]
+    for v, nf in enumerate(counts):
+        sc = lst_scene(seed=seed * 1000 + v, n_facets=nf)
+        surfs += sc.surfaces
+        offs.append(len(surfs))
+        angles = angles_deg if angles_deg is not None else (2.0 * v / max(n_dishes - 1, 1),)
+        per_angle = max(1, photons_per_dish // len(angles))
+        for k, a in enumerate(angles):
+            b = disk_bundle(per_angle, 12.0, 32.0, math.radians(a), (300.0, 600.0), seed * 1000 + v, stream=500 + k)
+            bundles.append(b)
+            vop.append(np.full(b.n, v, np.int32))
+    scene = Scene("dish_batch", surfs, [lst_reflectivity()], [Medium()], length_scale=46.6, focal_length=LST_F,
+                  variant_offsets=offs)
+    return scene, concat(bundles), np.concatenate(vop), counts
