@@ -202,6 +202,10 @@ typedef struct robast_trace_opts {
     unsigned long long* work_units; /* device [ROBAST_N_UNITS] or NULL; non-NULL runs the
                                        counting build of the kernel (block 128, slower) and
                                        adds the work units below to it */
+    int32_t coherent_order;   /* 0: library default (on for n >= 65536), 1: on, -1: off.  On, the
+                                 photons are first sorted by origin cell (stream-ordered scratch
+                                 of ~4n bytes) so that each warp traces neighbouring rays; the
+                                 results are identical either way */
 } robast_trace_opts;
 
 /* Work units counted when opts.work_units is set: ray-box tests, quadric root

@@ -73,7 +73,7 @@ class TraceOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_bounces", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("variant_of_photon", ctypes.c_void_p), ("first_photon_id", ctypes.c_int64),
                 ("eps", ctypes.c_double), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("work_units", ctypes.c_void_p)]
+                ("work_units", ctypes.c_void_p), ("coherent_order", ctypes.c_int32)]
 
 N_UNITS = 12
 UNIT_NAMES = ("aabb", "sag", "newton", "aperture", "cylinder", "box", "hexwall", "reflect", "refract", "rough",
@@ -213,7 +213,8 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_size, blocks_per_sm, units=None):
+def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_size, blocks_per_sm, units=None,
+          coherent_order=0):
     o = TraceOpts()
     _lib.robast_trace_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -225,6 +226,7 @@ def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_s
     o.block_size = int(block_size)
     o.blocks_per_sm = int(blocks_per_sm)
     o.work_units = ctypes.c_void_p(units.data_ptr()) if units is not None else None
+    o.coherent_order = int(coherent_order)
     return o
 
 
@@ -247,7 +249,8 @@ def alloc_outputs(n: int, precision: int = 32, device="cuda", fields=None):
 
 def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32, max_bounces: int = 100,
           stream=None, variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None,
-          block_size: int = 0, blocks_per_sm: int = 0, out: Optional[dict] = None, work_units=None):
+          block_size: int = 0, blocks_per_sm: int = 0, out: Optional[dict] = None, work_units=None,
+          coherent_order: int = 0):
     """robast_trace_ex on CUDA tensors; returns the dict of output tensors.
 
     work_units: optional CUDA int64 tensor [N_UNITS]; when given, the counting
@@ -272,7 +275,8 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
         if variant_of_photon.dtype != torch.int32 or not variant_of_photon.is_cuda:
             raise RobastError("variant_of_photon: need a CUDA int32 tensor")
         vop = ctypes.c_void_p(variant_of_photon.data_ptr())
-    o = _opts(precision, max_bounces, sp, vop, first_photon_id, eps, block_size, blocks_per_sm, work_units)
+    o = _opts(precision, max_bounces, sp, vop, first_photon_id, eps, block_size, blocks_per_sm, work_units,
+              coherent_order)
     _check(lib.robast_trace_ex(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,
                                ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(tout), ctypes.byref(o)))
     return out

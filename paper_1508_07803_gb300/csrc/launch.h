@@ -40,6 +40,12 @@ cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cu
 cudaError_t launch_grad_finish(const double* acc, const double* vals, const int* surf_var, int n_params, int objective,
                                double d_obj, double* out, cudaStream_t s);
 
+// Coherent processing order (order.cu): scratch bytes for n photons, and the
+// permutation (work index -> photon index) built in `scratch` on stream s.
+long long order_scratch_bytes(long long n);
+cudaError_t build_order_f32(const float* o, long long n, void* scratch, int** order, int sms, cudaStream_t s);
+cudaError_t build_order_f64(const double* o, long long n, void* scratch, int** order, int sms, cudaStream_t s);
+
 // Launch the persistent trace kernel; returns the cudaError_t of the launch.
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceArgs<double>& a, int block, int grid, size_t smem, cudaStream_t s);

@@ -1,0 +1,143 @@
+// Coherent processing order for the trace: a counting sort of the photon
+// indices by (chunk of the input order, cell of the origin in a 256 x 256 grid
+// over the origins' x-y bounding box).  Rays of one warp then start close
+// together (and, within a chunk of the caller's order, usually share a
+// direction), so they walk the same BVH nodes and hit the same surfaces, and
+// the warp's lanes diverge far less.  Results do not depend on the order:
+// every photon keeps its index, its random stream and its output slot.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "launch.h"
+
+namespace robast {
+
+constexpr int ORD_G = 256;             // grid cells per axis
+constexpr int ORD_CHUNK_BITS = 22;     // chunks of 4M photons keep the caller's coarse order
+
+__device__ __forceinline__ int ordered_int(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unordered_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void ord_init(int* box) {
+    if (threadIdx.x == 0) {
+        box[0] = 0x7fffffff;
+        box[1] = (int)0x80000000;
+        box[2] = 0x7fffffff;
+        box[3] = (int)0x80000000;
+    }
+}
+
+template <typename T>
+__global__ void ord_bounds(const T* o, long long n, int* box) {
+    float lo0 = 3.4e38f, lo1 = 3.4e38f, hi0 = -3.4e38f, hi1 = -3.4e38f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float x = (float)o[i], y = (float)o[n + i];
+        lo0 = fminf(lo0, x);
+        hi0 = fmaxf(hi0, x);
+        lo1 = fminf(lo1, y);
+        hi1 = fmaxf(hi1, y);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, off));
+        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, off));
+        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, off));
+        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(box + 0, ordered_int(lo0));
+        atomicMax(box + 1, ordered_int(hi0));
+        atomicMin(box + 2, ordered_int(lo1));
+        atomicMax(box + 3, ordered_int(hi1));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned ord_key(const T* o, long long n, long long i, const int* box) {
+    const float x0 = unordered_float(box[0]), x1 = unordered_float(box[1]);
+    const float y0 = unordered_float(box[2]), y1 = unordered_float(box[3]);
+    const float fx = x1 > x0 ? ((float)o[i] - x0) / (x1 - x0) : 0.0f;
+    const float fy = y1 > y0 ? ((float)o[n + i] - y0) / (y1 - y0) : 0.0f;
+    int cx = (int)(fx * ORD_G), cy = (int)(fy * ORD_G);
+    cx = cx < 0 ? 0 : (cx >= ORD_G ? ORD_G - 1 : cx);
+    cy = cy < 0 ? 0 : (cy >= ORD_G ? ORD_G - 1 : cy);
+    // serpentine rows keep consecutive cells adjacent
+    const int c = cy * ORD_G + ((cy & 1) ? ORD_G - 1 - cx : cx);
+    return (unsigned)((i >> ORD_CHUNK_BITS) * (ORD_G * ORD_G) + c);
+}
+
+template <typename T>
+__global__ void ord_hist(const T* o, long long n, const int* box, unsigned* hist) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(hist + ord_key(o, n, i, box), 1u);
+}
+
+// exclusive prefix sum of nbins counts, one block
+__global__ void ord_scan(unsigned* hist, long long nbins) {
+    __shared__ unsigned long long part[1024];
+    const int t = threadIdx.x;
+    const long long per = (nbins + blockDim.x - 1) / blockDim.x;
+    const long long b0 = t * per, b1 = b0 + per < nbins ? b0 + per : nbins;
+    unsigned long long s = 0;
+    for (long long k = b0; k < b1; ++k) s += hist[k];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long acc = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const unsigned long long v = part[k];
+            part[k] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    unsigned long long acc = part[t];
+    for (long long k = b0; k < b1; ++k) {
+        const unsigned v = hist[k];
+        hist[k] = (unsigned)acc;
+        acc += v;
+    }
+}
+
+template <typename T>
+__global__ void ord_scatter(const T* o, long long n, const int* box, unsigned* offs, int* order) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned pos = atomicAdd(offs + ord_key(o, n, i, box), 1u);
+        order[pos] = (int)i;
+    }
+}
+
+long long order_scratch_bytes(long long n) {
+    const long long nbins = ((n - 1) >> ORD_CHUNK_BITS) * (long long)(ORD_G * ORD_G) + ORD_G * ORD_G;
+    return 16 + nbins * 4 + n * 4 + 256;
+}
+
+template <typename T>
+static cudaError_t build_order_t(const T* o, long long n, void* scratch, int** order_out, int sms, cudaStream_t s) {
+    const long long nbins = ((n - 1) >> ORD_CHUNK_BITS) * (long long)(ORD_G * ORD_G) + ORD_G * ORD_G;
+    unsigned char* b = static_cast<unsigned char*>(scratch);
+    int* box = reinterpret_cast<int*>(b);
+    unsigned* hist = reinterpret_cast<unsigned*>(b + 16);
+    int* order = reinterpret_cast<int*>(b + 16 + ((nbins * 4 + 255) / 256) * 256);
+    ord_init<<<1, 32, 0, s>>>(box);
+    cudaError_t e = cudaMemsetAsync(hist, 0, nbins * 4, s);
+    if (e != cudaSuccess) return e;
+    const int grid = sms * 4;
+    ord_bounds<T><<<grid, 256, 0, s>>>(o, n, box);
+    ord_hist<T><<<grid, 256, 0, s>>>(o, n, box, hist);
+    ord_scan<<<1, 1024, 0, s>>>(hist, nbins);
+    ord_scatter<T><<<grid, 256, 0, s>>>(o, n, box, hist, order);
+    *order_out = order;
+    return cudaGetLastError();
+}
+
+cudaError_t build_order_f32(const float* o, long long n, void* scratch, int** order, int sms, cudaStream_t s) {
+    return build_order_t<float>(o, n, scratch, order, sms, s);
+}
+cudaError_t build_order_f64(const double* o, long long n, void* scratch, int** order, int sms, cudaStream_t s) {
+    return build_order_t<double>(o, n, scratch, order, sms, s);
+}
+
+}  // namespace robast

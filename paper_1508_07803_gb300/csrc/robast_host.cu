@@ -844,11 +844,30 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     long long grid = (long long)g->num_sms * bps;
     const long long need = (n + block - 1) / block;
     if (grid > need) grid = std::max(1LL, need);
+    // coherent processing order (stream-ordered scratch, so concurrent launches do not share it)
+    void* ord_scratch = nullptr;
+    const bool want_order =
+        !src && n < (1LL << 31) && (o.coherent_order > 0 || (o.coherent_order == 0 && n >= 65536));
+    if (want_order) {
+        CU(cudaMallocAsync(&ord_scratch, (size_t)order_scratch_bytes(n), s), "robast_trace: order scratch");
+        int* order = nullptr;
+        cudaError_t eo;
+        if constexpr (sizeof(T) == 4)
+            eo = build_order_f32(a.o, n, ord_scratch, &order, g->num_sms, s);
+        else
+            eo = build_order_f64(a.o, n, ord_scratch, &order, g->num_sms, s);
+        if (eo != cudaSuccess) {
+            cudaFreeAsync(ord_scratch, s);
+            return cuda_fail(eo, "robast_trace: order");
+        }
+        a.order = order;
+    }
     cudaError_t e;
     if constexpr (sizeof(T) == 4)
         e = launch_trace_f32(a, block, (int)grid, smem, s);
     else
         e = launch_trace_f64(a, block, (int)grid, smem, s);
+    if (ord_scratch) cudaFreeAsync(ord_scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "robast_trace: launch");
     return 0;
 }

@@ -115,6 +115,7 @@ struct TraceArgs {
     const T* d;
     const T* lam;
     const int* vop;
+    const int* order;  // optional processing order: work index -> photon index
     long long n;
     unsigned long long seed;
     long long first_id;
@@ -714,6 +715,23 @@ __device__ __forceinline__ unsigned long long refl_threshold(const double* M, do
     return (unsigned long long)thr;
 }
 
+// Survive iff w0 < floor(R(lambda) 2^32).  The FP32 form first compares with
+// an FP32 estimate of the threshold (cached per photon and material) and
+// falls back to the exact FP64 threshold only when the draw lies within the
+// estimate's error band (relative 1e-5, probability ~1e-5 per reflection), so
+// the decision is exactly the FP64 one at FP32 cost.
+__device__ __forceinline__ float refl_estimate32(const double* M, float lam) {
+    const int n = (int)M[0];
+    const double* L = M + 1;
+    const double* R = M + 17;
+    if (n <= 1 || lam <= (float)L[0]) return (float)R[0];
+    if (lam >= (float)L[n - 1]) return (float)R[n - 1];
+    int i = 0;
+    while (i + 1 < n - 1 && lam >= (float)L[i + 1]) ++i;
+    const float frac = (lam - (float)L[i]) / ((float)L[i + 1] - (float)L[i]);
+    return (float)R[i] + ((float)R[i + 1] - (float)R[i]) * frac;
+}
+
 template <typename T>
 __device__ __forceinline__ T refr_index(const double* Md, T lam_nm) {
     if (Md[0] > 0.0) return (T)Md[0];
@@ -745,6 +763,7 @@ struct Photon {
     int var;
     int bounces;
     int mat_cache;
+    float refl32;  // FP32 estimate of R(lambda) for mat_cache (FP32 form)
     int last;  // last surface hit, -1: none
     int group; // source mode: group of the photon
     bool bad;  // source mode: no point generated
@@ -756,8 +775,20 @@ struct Photon {
 // tables are read from global memory through L1.
 // SRC: photons come from source groups generated on the device (batched
 // study) instead of caller arrays; per-group counters are accumulated.
+// Resident 128-thread blocks per SM the FP32 kernel must fit (a register cap:
+// 4 blocks = 128 registers, the most that fits 16 warps per SM without
+// spilling); the FP64 form is bound by its FP64 pipe and keeps its registers.
+#ifndef ROBAST_TRACE_MIN_BLOCKS
+#define ROBAST_TRACE_MIN_BLOCKS 4
+#endif
+template <typename T, int BLOCK>
+struct TraceBounds {
+    static constexpr int min_blocks =
+        sizeof(T) == 4 && (ROBAST_TRACE_MIN_BLOCKS * 128) / BLOCK > 0 ? (ROBAST_TRACE_MIN_BLOCKS * 128) / BLOCK : 1;
+};
+
 template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false>
-__global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
+__global__ void __launch_bounds__(BLOCK, TraceBounds<T, BLOCK>::min_blocks) trace_kernel(TraceArgs<T> A) {
     unsigned cnt[U_N];
     if constexpr (C) {
 #pragma unroll
@@ -823,8 +854,9 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
             if (lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(m));
             base = __shfl_sync(FULL, base, leader);
             if (need) {
-                const long long idx = (long long)base + __popc(m & lt_mask);
-                if (idx < n) {
+                const long long widx = (long long)base + __popc(m & lt_mask);
+                if (widx < n) {
+                    const long long idx = A.order ? (long long)A.order[widx] : widx;
                     ph.i = idx;
                     if constexpr (SRC) {
                         // group: the last one whose first index is <= idx
@@ -901,11 +933,26 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs<T> A) {
                     status = ST_OBSCURED;
                 } else {
                     const double* M = tb.mats + (size_t)si.y * MAT_REC;
-                    if (si.y != ph.mat_cache) {
-                        ph.thr = refl_threshold(M, (double)ph.lam);
-                        ph.mat_cache = si.y;
+                    bool survive;
+                    if constexpr (sizeof(T) == 4) {
+                        if (si.y != ph.mat_cache) {
+                            ph.refl32 = refl_estimate32(M, (float)ph.lam);
+                            ph.mat_cache = si.y;
+                        }
+                        const float est = ph.refl32 * 4294967296.0f;
+                        const float wf = (float)w.x;
+                        if (fabsf(wf - est) > est * 1e-5f + 1024.0f)
+                            survive = wf < est;
+                        else
+                            survive = (unsigned long long)w.x < refl_threshold(M, (double)ph.lam);
+                    } else {
+                        if (si.y != ph.mat_cache) {
+                            ph.thr = refl_threshold(M, (double)ph.lam);
+                            ph.mat_cache = si.y;
+                        }
+                        survive = (unsigned long long)w.x < ph.thr;
                     }
-                    if (!((unsigned long long)w.x < ph.thr)) {
+                    if (!survive) {
                         status = ST_ABSORBED;
                     } else {
                         V3<T> nn = n;

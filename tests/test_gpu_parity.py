@@ -247,3 +247,15 @@ def test_psf_windows_each_match_numpy_on_the_same_outputs():
     with pytest.raises(robast.RobastError, match="window"):
         robast.psf(geom, out["status"], out["focal_xy"], windows=[(5 * npa - 10, 11)])
     geom.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_coherent_order_does_not_change_results(precision):
+    scene, b = W.lst_workload(40_000, seed=13)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, precision)
+    off = to_numpy(robast.trace(geom, o, d, w, seed=5, precision=precision, coherent_order=-1))
+    on = to_numpy(robast.trace(geom, o, d, w, seed=5, precision=precision, coherent_order=1))
+    for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters"):
+        assert np.array_equal(off[k], on[k]), k
+    geom.close()
