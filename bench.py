@@ -123,6 +123,7 @@ def workload_config(n_per_angle):
     return {"workload": "lst_dish_198_facets_masts_camera_5_field_angles", "photons_per_step": n_per_angle * len(ANGLES),
             "photons_per_angle": n_per_angle, "field_angles_deg": list(ANGLES), "wavelength_nm": [300, 600],
             "facet_tilt_sigma_mrad": 0.1, "roughness_sigma_mrad": 0.3, "max_bounces": 100,
+            "outputs": "status, bounce count, focal-plane (x, y) per photon; per-angle centroid and R80",
             "l2": "inputs larger than L2 (no flush)"}
 
 
@@ -371,7 +372,8 @@ def main():
 
     def measure(precision, steps, warmup, want_clocks):
         o, d, w = inputs(precision)
-        out = robast.alloc_outputs(N, precision, dev)
+        # per-photon outputs the spot diagram and the metric need: status, bounce count, focal (x, y)
+        out = robast.alloc_outputs(N, precision, dev, fields=("status", "bounces", "focal_xy", "counters"))
         counters = out["counters"]
         psf_launches = 4  # sums, finish, histogram, selection (all field angles at once)
 

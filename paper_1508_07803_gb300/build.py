@@ -61,8 +61,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(sources())) as ex:
-        objs = list(ex.map(compile_one, sources()))
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+        glob.glob(os.path.join(INCLUDE, "*.h"))
+    newest_header = max([os.path.getmtime(h) for h in headers] + [0.0])
+
+    def stale(src):
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        return force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header)
+
+    todo = [src for src in sources() if stale(src)]
+    if todo:
+        with cf.ThreadPoolExecutor(max_workers=len(todo)) as ex:
+            list(ex.map(compile_one, todo))
+    objs = [os.path.join(BUILD, os.path.basename(src)[:-3] + ".o") for src in sources()]
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

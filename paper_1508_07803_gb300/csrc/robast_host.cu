@@ -1164,10 +1164,12 @@ extern "C" int robast_trace_grad(robast_geom* g, const void* origins, const void
 // ------------------------------------------------------------- reductions
 // Spot diagrams of several photon windows at once.  Per window: centroid
 // from fixed-order FP64 block partials; R80 = exact nearest-rank 80th
-// percentile of the radius to the centroid, found with a histogram over
-// [0, 8 x RMS radius) plus one overflow bin, then a selection inside the bin
-// that holds the rank.  Four launches and two host synchronisations for any
-// number of windows.
+// percentile of the radius to the centroid, found with a histogram of the
+// SQUARED radius over [0, (8 x RMS radius)^2) plus one overflow bin, then a
+// selection inside the bin that holds the rank (ordering by r^2 is ordering
+// by r, and r = sqrt(r^2) of the selected photon, so no square root or
+// division is taken per photon).  Four launches and two host synchronisations
+// for any number of windows.
 namespace {
 constexpr int kRedBlock = 256;
 constexpr int kBins = 4096;  // + 1 overflow bin
@@ -1204,7 +1206,7 @@ __global__ void psf_sums(const uint8_t* st, const T* fxy, long long ld, const Wi
         for (int c = 0; c < 5; ++c) part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 5 + c] = sh[c][0];
 }
 
-// one thread per window, blocks summed in a fixed order: res = (N, cx, cy, range)
+// one thread per window, blocks summed in a fixed order: res = (N, cx, cy, bins / range^2)
 __global__ void psf_finish(const double* part, int nblocks, int nwin, double* res) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwin) return;
@@ -1217,13 +1219,16 @@ __global__ void psf_finish(const double* part, int nblocks, int nwin, double* re
     res[4 * w + 0] = n;
     res[4 * w + 1] = cx;
     res[4 * w + 2] = cy;
-    res[4 * w + 3] = fmax(8.0 * sqrt(ms), 1e-300);
+    const double range2 = fmax(64.0 * ms, 1e-300);  // (8 x RMS radius)^2
+    res[4 * w + 3] = (double)kBins / range2;
 }
 
-__device__ __forceinline__ int psf_bin(double r, double range) {
-    if (!(r < range)) return kBins;  // overflow
-    int b = (int)(r / range * kBins);
-    return b < 0 ? 0 : (b >= kBins ? kBins - 1 : b);
+// bin of r^2: scale = kBins / range^2; values beyond the range -> overflow bin
+__device__ __forceinline__ int psf_bin(double r2, double scale) {
+    const double f = r2 * scale;
+    if (!(f < (double)kBins)) return kBins;
+    const int b = (int)f;
+    return b < 0 ? 0 : b;
 }
 
 template <typename T>
@@ -1239,7 +1244,7 @@ __global__ void psf_hist(const uint8_t* st, const T* fxy, long long ld, const Wi
         const long long i = w.start + k;
         if (st[i] == ROBAST_ST_DETECTED) {
             const double dx = (double)fxy[i] - R[1], dy = (double)fxy[ld + i] - R[2];
-            atomicAdd(&h[psf_bin(sqrt(dx * dx + dy * dy), R[3])], 1u);
+            atomicAdd(&h[psf_bin(dx * dx + dy * dy, R[3])], 1u);
         }
     }
     __syncthreads();
@@ -1261,10 +1266,10 @@ __global__ void psf_collect(const uint8_t* st, const T* fxy, long long ld, const
         const long long i = w.start + k;
         if (st[i] == ROBAST_ST_DETECTED) {
             const double dx = (double)fxy[i] - R[1], dy = (double)fxy[ld + i] - R[2];
-            const double r = sqrt(dx * dx + dy * dy);
-            if (psf_bin(r, R[3]) == bin) {
+            const double r2 = dx * dx + dy * dy;
+            if (psf_bin(r2, R[3]) == bin) {
                 const unsigned long long j = atomicAdd(cnt + blockIdx.y, 1ull);
-                if ((long long)j < cap[blockIdx.y]) out[j] = r;
+                if ((long long)j < cap[blockIdx.y]) out[j] = r2;
             }
         }
     }
@@ -1358,7 +1363,7 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
             return fail(ROBAST_E_CUDA, "robast_psf: histogram and selection disagree in window %d", w);
         auto first = hv.begin() + sel[2 * w + 1];
         std::nth_element(first, first + rank_in_bin[w], first + cap[w]);
-        result[4 * w + 3] = first[rank_in_bin[w]];
+        result[4 * w + 3] = std::sqrt(first[rank_in_bin[w]]);  // the selected photon's radius
     }
     return 0;
 }
