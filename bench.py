@@ -328,6 +328,7 @@ def main():
 
     import torch
     import paper_1508_07803_gb300 as robast
+    from paper_1508_07803_gb300 import shard
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -343,7 +344,7 @@ def main():
     N = npa * len(ANGLES)
     scene, bundle = W.lst_workload(npa, seed=rank)
     geom = robast.build_geometry(scene)
-    first_id = rank * N
+    first_id = shard.replica_first_id(rank, N)
     stream = torch.cuda.current_stream(dev)
 
     def inputs(precision):
@@ -357,18 +358,10 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return shard.all_reduce_scalar(x, "max", device=dev)
 
     def sum_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t)
-        return float(t.item())
+        return shard.all_reduce_scalar(x, "sum", device=dev)
 
     def measure(precision, steps, warmup, want_clocks):
         o, d, w = inputs(precision)
