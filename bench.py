@@ -305,8 +305,8 @@ def traffic_from_profile(n_photons):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--photons-per-angle", type=int, default=10_000_000)
     ap.add_argument("--fp64-steps", type=int, default=3)

@@ -128,10 +128,18 @@ typedef struct robast_material_desc {
 } robast_material_desc;
 
 /* Refractive medium: n_const > 0 gives a constant index, otherwise the
- * Sellmeier form n^2 = 1 + sum B_i l^2 / (l^2 - C_i), l in micrometres. */
+ * Sellmeier form n^2 = 1 + sum B_i l^2 / (l^2 - C_i), l in micrometres.
+ * Bulk absorption (n_abs > 0): absorption length abs_len (m) piecewise linear
+ * in abs_lam (nm), clamped; a photon that reaches a refracting face after a
+ * path s through this medium (the medium on its side of that face) survives
+ * with probability exp(-s / len), decided by Philox word 3 of that
+ * interaction, else it is ABSORBED there. */
 typedef struct robast_medium_desc {
     double n_const;
     double B[3], C[3];
+    int32_t n_abs, reserved;
+    double abs_lam[ROBAST_MAX_TABLE];
+    double abs_len[ROBAST_MAX_TABLE];
 } robast_medium_desc;
 
 /*

@@ -46,7 +46,9 @@ class OMaterial(ctypes.Structure):
 
 
 class OMedium(ctypes.Structure):
-    _fields_ = [("n_const", ctypes.c_double), ("B", ctypes.c_double * 3), ("C", ctypes.c_double * 3)]
+    _fields_ = [("n_const", ctypes.c_double), ("B", ctypes.c_double * 3), ("C", ctypes.c_double * 3),
+                ("n_abs", ctypes.c_int32), ("pad", ctypes.c_int32), ("abs_lam", ctypes.c_double * 16),
+                ("abs_len", ctypes.c_double * 16)]
 
 
 class OScene(ctypes.Structure):
@@ -95,6 +97,8 @@ def lib():
             _lib.oracle_fresnel_unpolarised.argtypes = [ctypes.c_double] * 3
             _lib.oracle_refractive_index.restype = ctypes.c_double
             _lib.oracle_refractive_index.argtypes = [ctypes.POINTER(OMedium), ctypes.c_double]
+            _lib.oracle_absorption_length.restype = ctypes.c_double
+            _lib.oracle_absorption_length.argtypes = [ctypes.POINTER(OMedium), ctypes.c_double]
             _lib.oracle_reflectivity.restype = ctypes.c_double
             _lib.oracle_reflectivity.argtypes = [ctypes.POINTER(OMaterial), ctypes.c_double]
             _lib.oracle_philox4x32_10.restype = None
@@ -151,6 +155,11 @@ def pack_medium(m) -> OMedium:
     o.n_const = float(m.n_const)
     _fill(o.B, m.B)
     _fill(o.C, m.C)
+    lam = list(getattr(m, "abs_lam", ()) or ())
+    ln = list(getattr(m, "abs_len", ()) or ())
+    o.n_abs = len(lam)
+    _fill(o.abs_lam, lam)
+    _fill(o.abs_len, ln)
     return o
 
 

@@ -512,6 +512,18 @@ double refr_index(const o_medium& m, double lam_nm) {
     return std::sqrt(n2);
 }
 
+/* Absorption length of a medium at lambda: piecewise linear in its table,
+ * clamped; INFINITY without a table (no bulk absorption). */
+double abs_length(const o_medium& m, double lam) {
+    if (m.n_abs <= 0) return INFINITY;
+    if (m.n_abs == 1 || lam <= m.abs_lam[0]) return m.abs_len[0];
+    if (lam >= m.abs_lam[m.n_abs - 1]) return m.abs_len[m.n_abs - 1];
+    int i = 0;
+    while (i + 1 < m.n_abs - 1 && lam >= m.abs_lam[i + 1]) ++i;
+    double frac = (lam - m.abs_lam[i]) / (m.abs_lam[i + 1] - m.abs_lam[i]);
+    return m.abs_len[i] + (m.abs_len[i + 1] - m.abs_len[i]) * frac;
+}
+
 /* Unpolarised Fresnel reflectance: mean of |r_s|^2 and |r_p|^2; 1 under TIR. */
 double fresnel(double n1, double n2, double cos_i) {
     double eta = n1 / n2;
@@ -648,6 +660,21 @@ void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double*
                     break;
                 }
                 case O_ROLE_REFRACT: {
+                    /* bulk absorption over the segment just travelled, which lies in the
+                     * medium on the photon's side of this face: survive with probability
+                     * exp(-t / len(lambda)), draw u3 */
+                    const o_medium& m_in = sc->media[front ? s.medium_front : s.medium_back];
+                    const double len = abs_length(m_in, lam);
+                    if (len < INFINITY) {
+                        const double surv = std::exp(-h.t / len);
+                        const double u3 = unit_open(w[3]);
+                        const double am = std::fabs(u3 - surv);
+                        if (am < margin) margin = am;
+                        if (!(u3 < surv)) {
+                            status = O_ST_ABSORBED;
+                            break;
+                        }
+                    }
                     double na = refr_index(sc->media[s.medium_front], lam);
                     double nb = refr_index(sc->media[s.medium_back], lam);
                     double n1 = front ? na : nb, n2 = front ? nb : na;
@@ -655,6 +682,7 @@ void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double*
                     double cos_i = -dot(d, nf);
                     double R = fresnel(n1, n2, cos_i);
                     double u0 = unit_open(w[0]);
+                    if (std::fabs(u0 - R) < margin) margin = std::fabs(u0 - R);
                     if (u0 < R) {
                         d = normalize(reflect(d, nf));
                     } else {
@@ -1043,6 +1071,9 @@ int record_path(const Ctx& cx, int v, V3 p, V3 d, double lam, int64_t pid, const
             d = normalize(reflect(d, nn));
             st.act = ACT_REFLECT;
         } else {
+            /* expected-weight mode: bulk absorption multiplies the weight */
+            const double len = abs_length(sc->media[front ? s.medium_front : s.medium_back], lam);
+            if (len < INFINITY) *w *= std::exp(-h.t / len);
             double na = refr_index(sc->media[s.medium_front], lam), nb = refr_index(sc->media[s.medium_back], lam);
             double n1 = front ? na : nb, n2 = front ? nb : na;
             V3 nf = front ? n : (-1.0) * n;
@@ -1420,6 +1451,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 
 double oracle_fresnel_unpolarised(double n1, double n2, double cos_i) { return fresnel(n1, n2, cos_i); }
 double oracle_refractive_index(const o_medium* m, double lambda_nm) { return refr_index(*m, lambda_nm); }
+double oracle_absorption_length(const o_medium* m, double lambda_nm) { return abs_length(*m, lambda_nm); }
 double oracle_reflectivity(const o_material* m, double lambda_nm) { return reflectivity(*m, lambda_nm); }
 
 int oracle_intersect(const o_surface* s, const double p[3], const double d[3], double eps, double* t,

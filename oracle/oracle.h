@@ -56,6 +56,9 @@ typedef struct {
 typedef struct {
     double n_const;     /* > 0: constant index */
     double B[3], C[3];  /* Sellmeier, lambda in micrometres, C in um^2 */
+    int32_t n_abs, pad; /* bulk absorption: 0 = none, else a table of n_abs points */
+    double abs_lam[16]; /* nm, ascending */
+    double abs_len[16]; /* absorption length (m): survival exp(-s / len) over a path s */
 } o_medium;
 
 typedef struct {
@@ -139,6 +142,7 @@ int oracle_trace(const o_scene* scene, int64_t n, const double* origins, const d
 /* Building blocks exposed for the pin tests. */
 double oracle_fresnel_unpolarised(double n1, double n2, double cos_i);
 double oracle_refractive_index(const o_medium* m, double lambda_nm);
+double oracle_absorption_length(const o_medium* m, double lambda_nm);
 double oracle_reflectivity(const o_material* m, double lambda_nm);
 /* Nearest hit of one ray against one surface, world frame.  Returns 1 on hit. */
 int oracle_intersect(const o_surface* s, const double p[3], const double d[3], double eps,

@@ -53,7 +53,9 @@ class MaterialDesc(ctypes.Structure):
 
 
 class MediumDesc(ctypes.Structure):
-    _fields_ = [("n_const", ctypes.c_double), ("B", ctypes.c_double * 3), ("C", ctypes.c_double * 3)]
+    _fields_ = [("n_const", ctypes.c_double), ("B", ctypes.c_double * 3), ("C", ctypes.c_double * 3),
+                ("n_abs", ctypes.c_int32), ("reserved", ctypes.c_int32), ("abs_lam", ctypes.c_double * 16),
+                ("abs_len", ctypes.c_double * 16)]
 
 
 class GeomDesc(ctypes.Structure):
@@ -152,6 +154,10 @@ def _pack(scene):
         meds[k].n_const = float(m.n_const)
         _fill(meds[k].B, m.B, 3)
         _fill(meds[k].C, m.C, 3)
+        lam = list(getattr(m, "abs_lam", ()) or ())
+        meds[k].n_abs = len(lam)
+        _fill(meds[k].abs_lam, lam, 16)
+        _fill(meds[k].abs_len, list(getattr(m, "abs_len", ()) or ()), 16)
     desc = GeomDesc()
     desc.n_surfaces = len(scene.surfaces)
     desc.n_materials = len(scene.materials)

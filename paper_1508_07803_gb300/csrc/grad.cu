@@ -230,7 +230,9 @@ __global__ void __launch_bounds__(BLOCK) grad_kernel(GradArgs<T> A) {
                     nn = unit(nw + g1 * tt + g2 * bv);
                 }
                 d = unit(d - (DD(2) * dot(d, nn)) * nn);
-            } else {  // refracting face: the trace's Fresnel decision, then reflect or Snell
+            } else {  // refracting face: bulk absorption weight, the trace's Fresnel decision, reflect or Snell
+                const T len = abs_length<T>(tb.meds + (size_t)(front ? si.z : si.w) * MED_REC, lam);
+                if (len > T(0)) w *= exp(-h.t.v / (double)len);
                 const T na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, lam);
                 const T nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, lam);
                 const T n1 = front ? na : nb, n2 = front ? nb : na;

@@ -451,6 +451,16 @@ int validate(const robast_geom_desc* d) {
                 return fail(ROBAST_E_INVALID, "material %d: wavelengths must increase", i);
         if (!(m.sigma >= 0.0)) return fail(ROBAST_E_INVALID, "material %d: sigma must be >= 0", i);
     }
+    for (int i = 0; i < d->n_media; ++i) {
+        const robast_medium_desc& m = d->media[i];
+        if (m.n_abs < 0 || m.n_abs > ROBAST_MAX_TABLE)
+            return fail(ROBAST_E_INVALID, "medium %d: absorption table size %d outside 0..%d", i, m.n_abs, ROBAST_MAX_TABLE);
+        for (int k = 0; k < m.n_abs; ++k) {
+            if (!(m.abs_len[k] > 0.0)) return fail(ROBAST_E_INVALID, "medium %d: absorption lengths must be > 0", i);
+            if (k + 1 < m.n_abs && !(m.abs_lam[k + 1] > m.abs_lam[k]))
+                return fail(ROBAST_E_INVALID, "medium %d: absorption wavelengths must increase", i);
+        }
+    }
     for (int i = 0; i < d->n_surfaces; ++i) {
         const robast_surface_desc& s = d->surfaces[i];
         if (s.shape < 0 || s.shape > 3) return fail(ROBAST_E_INVALID, "surface %d: unknown shape %d", i, s.shape);
@@ -653,6 +663,11 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         for (int k = 0; k < 3; ++k) {
             M[1 + k] = d->media[i].B[k];
             M[4 + k] = d->media[i].C[k];
+        }
+        M[7] = d->media[i].n_abs;
+        for (int k = 0; k < d->media[i].n_abs; ++k) {
+            M[8 + k] = d->media[i].abs_lam[k];
+            M[24 + k] = d->media[i].abs_len[k];
         }
     }
     if (glob.empty()) glob.push_back(0);

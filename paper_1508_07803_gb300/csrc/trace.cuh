@@ -46,8 +46,9 @@ enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, R
 // z = medium front, w = medium back.
 // Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
 enum { MAT_REC = 34 };
-// Medium record (doubles): [0] n_const, [1..3] B, [4..6] C.
-enum { MED_REC = 7 };
+// Medium record (doubles): [0] n_const, [1..3] B, [4..6] C, [7] n_abs,
+// [8..23] absorption-table wavelengths, [24..39] absorption lengths.
+enum { MED_REC = 40 };
 
 // Work units counted by the counting instantiation (kernel template flag C):
 // the per-unit figures that turn them into algorithmic FLOPs are stated with
@@ -743,6 +744,21 @@ __device__ __forceinline__ T refr_index(const double* Md, T lam_nm) {
     return t_sqrt(n2);
 }
 
+// Absorption length at lambda (piecewise linear, clamped); <= 0: no absorption.
+template <typename T>
+__device__ __forceinline__ T abs_length(const double* Md, T lam) {
+    const int n = (int)Md[7];
+    if (n <= 0) return T(-1);
+    const double* L = Md + 8;
+    const double* A = Md + 24;
+    if (n == 1 || lam <= (T)L[0]) return (T)A[0];
+    if (lam >= (T)L[n - 1]) return (T)A[n - 1];
+    int i = 0;
+    while (i + 1 < n - 1 && lam >= (T)L[i + 1]) ++i;
+    const T frac = (lam - (T)L[i]) / ((T)L[i + 1] - (T)L[i]);
+    return (T)A[i] + ((T)A[i + 1] - (T)A[i]) * frac;
+}
+
 template <typename T>
 __device__ __forceinline__ T fresnel(T n1, T n2, T ci) {
     const T eta = n1 / n2;
@@ -781,14 +797,17 @@ struct Photon {
 #ifndef ROBAST_TRACE_MIN_BLOCKS
 #define ROBAST_TRACE_MIN_BLOCKS 4
 #endif
-template <typename T, int BLOCK>
+#ifndef ROBAST_TRACE_MIN_BLOCKS_SRC
+#define ROBAST_TRACE_MIN_BLOCKS_SRC 1  // source mode: uncapped (swept 1, 3, 4; the 128-register cap spills and runs 25% slower)
+#endif
+template <typename T, int BLOCK, bool SRC = false>
 struct TraceBounds {
-    static constexpr int min_blocks =
-        sizeof(T) == 4 && (ROBAST_TRACE_MIN_BLOCKS * 128) / BLOCK > 0 ? (ROBAST_TRACE_MIN_BLOCKS * 128) / BLOCK : 1;
+    static constexpr int mb = SRC ? ROBAST_TRACE_MIN_BLOCKS_SRC : ROBAST_TRACE_MIN_BLOCKS;
+    static constexpr int min_blocks = sizeof(T) == 4 && (mb * 128) / BLOCK > 0 ? (mb * 128) / BLOCK : 1;
 };
 
 template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false>
-__global__ void __launch_bounds__(BLOCK, TraceBounds<T, BLOCK>::min_blocks) trace_kernel(TraceArgs<T> A) {
+__global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks)) trace_kernel(TraceArgs<T> A) {
     unsigned cnt[U_N];
     if constexpr (C) {
 #pragma unroll
@@ -976,7 +995,14 @@ __global__ void __launch_bounds__(BLOCK, TraceBounds<T, BLOCK>::min_blocks) trac
                         CNT(U_REFLECT);
                     }
                 }
-            } else {  // ROLE_REFRACT: Snell + unpolarised Fresnel
+            } else {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
+                const T len = abs_length<T>(tb.meds + (size_t)(front ? si.z : si.w) * MED_REC, ph.lam);
+                if (len > T(0)) {
+                    const T surv = (sizeof(T) == 4) ? (T)expf(-(float)(bst.t / len)) : (T)exp(-(double)(bst.t / len));
+                    if (!(unit_open<T>(w.w) < surv)) status = ST_ABSORBED;
+                }
+            }
+            if (status == 0 && role == ROLE_REFRACT) {
                 const T na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, ph.lam);
                 const T nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, ph.lam);
                 const T n1 = front ? na : nb, n2 = front ? nb : na;

@@ -259,3 +259,19 @@ def test_coherent_order_does_not_change_results(precision):
     for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters"):
         assert np.array_equal(off[k], on[k]), k
     geom.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_thick_absorbing_lens_parity(precision):
+    """Refraction beyond a window: a thick aspheric plano-convex PMMA-like lens
+    with bulk absorption, imaging onto a focal plane."""
+    scene = W.lens_scene(R1=0.1, thickness=0.01, aperture=0.02, n=1.49,
+                         abs_len=((300.0, 450.0, 600.0), (0.004, 0.02, 0.05)),
+                         asph=(2e-1, -5.0) + (0.0,) * 6, focal_z=-0.19)
+    bs = [W.disk_bundle(4_001, 0.019, 0.05, math.radians(a), (300.0, 600.0), seed=2, stream=70 + k)
+          for k, a in enumerate((0.0, 1.5, 3.0))]
+    b = W.concat(bs)
+    g = _run(scene, b, precision, seed=8)
+    r = oracle_for(scene, b, precision, seed=8)
+    assert (r["status"] == W.ABSORBED).sum() > 500 and (r["status"] == W.DETECTED).sum() > 5000
+    print(compare(g, r, precision, scene.focal_length, f"lens fp{precision}"))

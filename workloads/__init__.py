@@ -57,6 +57,8 @@ class Medium:
     n_const: float = 1.0
     B: Sequence[float] = (0.0, 0.0, 0.0)
     C: Sequence[float] = (0.0, 0.0, 0.0)
+    abs_lam: Sequence[float] = ()  # bulk absorption: wavelengths (nm) of the table, empty = none
+    abs_len: Sequence[float] = ()  # absorption lengths (m) at abs_lam
 
 
 @dataclasses.dataclass
@@ -459,3 +461,24 @@ def dish_batch(n_dishes: int = 32, n_min: int = 60, n_max: int = 198, photons_pe
     scene = Scene("dish_batch", surfs, [lst_reflectivity()], [Medium()], length_scale=46.6, focal_length=LST_F,
                   variant_offsets=offs)
     return scene, concat(bundles), np.concatenate(vop), counts
+
+
+def lens_scene(R1: float = 0.1, thickness: float = 0.01, aperture: float = 0.02, n: float = 1.49,
+               abs_len=None, asph=(0.0,) * 8, focal_z=None) -> Scene:
+    """A thick plano-convex lens (the refracting counterpart of the mirrors,
+    Sec. 2.1 ALens): convex spherical (or even-aspheric) front of radius R1
+    facing +z with its vertex at z = thickness, flat back face at z = 0,
+    medium 1 of constant index n (optionally absorbing: abs_len = (lam list,
+    length list)); optionally a focal plane facing +z at z = focal_z."""
+    med = Medium(n_const=n)
+    if abs_len is not None:
+        med = Medium(n_const=n, abs_lam=tuple(abs_len[0]), abs_len=tuple(abs_len[1]))
+    surfs = [Surface("sag", "refract", "circle", origin=(0.0, 0.0, thickness), curv=-1.0 / R1, asph=tuple(asph),
+                     medium_front=0, medium_back=1, ap=(aperture, 0, 0, 0)),
+             Surface("sag", "refract", "circle", origin=(0.0, 0.0, 0.0), medium_front=1, medium_back=0,
+                     ap=(aperture, 0, 0, 0))]
+    if focal_z is not None:
+        surfs.append(Surface("sag", "focal", "circle", origin=(0.0, 0.0, focal_z), ap=(aperture, 0, 0, 0)))
+    fl = R1 / (n - 1.0)
+    return Scene("lens", surfs, [Material([400.0], [1.0])], [Medium(), med], length_scale=max(0.1, 2 * fl),
+                 focal_length=fl)
