@@ -243,6 +243,53 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
             "collection_efficiency": summary}
 
 
+def measure_tolerance(args, dev, stream, ws, rank, max_over_ranks, sum_over_ranks, barrier):
+    """Misalignment study: 64 realisations of the dish with Gaussian facet-tilt
+    errors (0.5 mrad per axis), 1e6 photons each at a 1 deg field, all
+    realisations in one launch (variants); the step includes the R80 of every
+    realisation.  Reports photon-bounces/s and the R80 distribution."""
+    import torch
+    import paper_1508_07803_gb300 as robast
+
+    nr, m = 64, 1_000_000
+    scene, b, vop = W.tolerance_sweep(n_realizations=nr, tilt_sigma=0.5e-3, photons_per_realization=m, seed=rank)
+    geom = robast.build_geometry(scene)
+    o = torch.from_numpy(b.origins).to(dev, torch.float32)
+    d = torch.from_numpy(b.dirs).to(dev, torch.float32)
+    w = torch.from_numpy(b.wavelengths).to(dev, torch.float32)
+    v = torch.from_numpy(vop).to(dev)
+    out = robast.alloc_outputs(b.n, 32, dev, fields=("status", "bounces", "focal_xy", "counters"))
+    wins = [(k * m, m) for k in range(nr)]
+
+    def step():
+        robast.trace(geom, o, d, w, seed=0, variant_of_photon=v, out=out, stream=stream,
+                     first_photon_id=rank * b.n)
+        return robast.psf(geom, out["status"], out["focal_xy"], windows=wins, stream=stream)
+
+    for _ in range(3):
+        step()
+    out["counters"].zero_()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    steps = 5
+    t0.record(stream)
+    for _ in range(steps):
+        res = step()
+    t1.record(stream)
+    barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1))
+    bounces = sum_over_ranks(float(out["counters"][0].item()))
+    r80 = np.array([r[3] for r in res])
+    geom.close()
+    return {"value": bounces / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "photons_per_step": int(b.n),
+            "r80_m": {"mean": float(r80.mean()), "std": float(r80.std()), "min": float(r80.min()),
+                      "max": float(r80.max())},
+            "config": {"workload": "lst_tolerance_64_realisations_tilt_0.5mrad", "realisations": nr,
+                       "photons_per_realisation": m, "field_deg": 1.0}}
+
+
 def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
     """Differentiable batch: 32 LST-like dishes with 60-198 facets, 1e6
     photons each over field angles 0-2 deg, one evaluation = the summed
@@ -316,6 +363,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-tolerance", action="store_true")
     ap.add_argument("--grad-photons-per-dish", type=int, default=1_000_000)
     ap.add_argument("--grad-steps", type=int, default=3)
     ap.add_argument("--batch-photons-per-group", type=int, default=2_000_000)
@@ -446,6 +494,11 @@ def main():
         forms["batched_fp32"] = measure_batched(args, geom_dev=dev, stream=stream, ws=ws, rank=rank,
                                                 max_over_ranks=max_over_ranks, sum_over_ranks=sum_over_ranks,
                                                 barrier=barrier)
+
+    if not args.no_tolerance:
+        forms["tolerance_fp32"] = measure_tolerance(args, dev=dev, stream=stream, ws=ws, rank=rank,
+                                                    max_over_ranks=max_over_ranks, sum_over_ranks=sum_over_ranks,
+                                                    barrier=barrier)
 
     if not args.no_grad:
         forms["grad_fp32"] = measure_grad(args, dev=dev, stream=stream, ws=ws, rank=rank,

@@ -198,6 +198,24 @@ typedef struct robast_trace_out {
     unsigned long long* counters;
 } robast_trace_out;
 
+/*
+ * Photon tracks (Fig. 2a of the paper shows simulated tracks through a cone;
+ * this records them without rendering).  Every interaction of the photons
+ * with index first .. first + count - 1 appends one record: points[4k..4k+3]
+ * = interaction point x, y, z and 0 (trace precision), info[4k..4k+3] =
+ * photon index, bounce index (0-based), surface id, status after the
+ * interaction (0 = still travelling).  Records are appended in no particular
+ * order (sort by photon, then bounce); *n_records (device u64, zero it before
+ * the call) counts every interaction, records beyond cap are dropped.  All
+ * pointers are device pointers.
+ */
+typedef struct robast_track_opts {
+    int64_t first, count, cap;
+    void* points;
+    int32_t* info;
+    unsigned long long* n_records;
+} robast_track_opts;
+
 typedef struct robast_trace_opts {
     int32_t precision;        /* 32 (default) or 64 */
     int32_t max_bounces;      /* 1..255; 0 = 100 */
@@ -214,6 +232,7 @@ typedef struct robast_trace_opts {
                                  photons are first sorted by origin cell (stream-ordered scratch
                                  of ~4n bytes) so that each warp traces neighbouring rays; the
                                  results are identical either way */
+    const robast_track_opts* track; /* host pointer or NULL: record photon tracks */
 } robast_trace_opts;
 
 /* Work units counted when opts.work_units is set: ray-box tests, quadric root

@@ -113,6 +113,11 @@ def lib():
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p]
+            _lib.oracle_track.restype = ctypes.c_int64
+            _lib.oracle_track.argtypes = [ctypes.POINTER(OScene), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             _lib.oracle_intersect.restype = ctypes.c_int
             _lib.oracle_intersect.argtypes = [ctypes.POINTER(OSurface), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
@@ -328,3 +333,27 @@ def objective(scene, bundle, objective="msr", seed=0, first_photon_id=0, max_bou
     if rc != 0:
         raise ValueError(f"oracle_objective failed (code {rc})")
     return val.value, g
+
+
+def track(scene, bundle, first, count, seed=0, first_photon_id=0, max_bounces=100, eps=None, variant_of_photon=None,
+          cap=100_000):
+    """Interaction records of photons first .. first+count-1: (points [k, 3], info [k, 4] =
+    photon index, bounce, surface id, status after), photon then bounce order."""
+    L = lib()
+    n = bundle.n
+    o = np.ascontiguousarray(bundle.origins, dtype=np.float64).reshape(3, n)
+    d = np.ascontiguousarray(bundle.dirs, dtype=np.float64).reshape(3, n)
+    wl = np.ascontiguousarray(bundle.wavelengths, dtype=np.float64)
+    if eps is None:
+        eps = default_eps(scene, 64)
+    pts = np.zeros((cap, 3))
+    info = np.zeros((cap, 4), np.int32)
+    vop = None if variant_of_photon is None else np.ascontiguousarray(variant_of_photon, dtype=np.int32)
+    ps = PackedScene(scene)
+    k = L.oracle_track(ctypes.byref(ps.s), n, o.ctypes.data, d.ctypes.data, wl.ctypes.data,
+                       vop.ctypes.data if vop is not None else None, seed & (2**64 - 1), first_photon_id,
+                       max_bounces, float(eps), first, count, pts.ctypes.data, info.ctypes.data, cap)
+    if k < 0:
+        raise ValueError("oracle_track: bad arguments")
+    k = min(int(k), cap)
+    return pts[:k], info[:k]

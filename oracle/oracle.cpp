@@ -585,9 +585,16 @@ Hit nearest_hit(const Ctx& cx, int v, V3 p, V3 d) {
     return best;
 }
 
+/* One interaction of a recorded photon track (Fig. 2a shows such tracks). */
+struct TrackRec {
+    int64_t photon;
+    int bounce, sid, status;
+    V3 p;
+};
+
 void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double* O, const double* D,
                  const double* L, const int32_t* vop, uint64_t seed, int64_t first_id, int32_t max_bounces,
-                 const o_outputs* out) {
+                 const o_outputs* out, std::vector<TrackRec>* track = nullptr) {
     const o_scene* sc = cx.sc;
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int64_t i = i0; i < i1; ++i) {
@@ -698,6 +705,7 @@ void trace_range(const Ctx& cx, int64_t i0, int64_t i1, int64_t n, const double*
             if (status == 0 && !(std::isfinite(d.x) && std::isfinite(d.y) && std::isfinite(d.z)))
                 status = O_ST_ERROR;
             if (status == 0 && bounces >= max_bounces) status = O_ST_MAX_BOUNCES;
+            if (track) track->push_back(TrackRec{i, bounces - 1, last, status, p});
         }
         out->status[i] = (uint8_t)status;
         out->bounces[i] = (uint8_t)bounces;
@@ -1449,6 +1457,35 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     philox(ctr, key, out);
 }
 
+int64_t oracle_track(const o_scene* scene, int64_t n, const double* O, const double* D, const double* L,
+                     const int32_t* vop, uint64_t seed, int64_t first_photon_id, int32_t max_bounces, double eps,
+                     int64_t track_first, int64_t track_count, double* points, int32_t* info, int64_t cap) {
+    if (check_scene(scene) || n <= 0 || track_first < 0 || track_count < 0 || track_first + track_count > n) return -1;
+    Ctx cx;
+    cx.sc = scene;
+    cx.frames.resize(scene->n_surfaces);
+    for (int s = 0; s < scene->n_surfaces; ++s) cx.frames[s] = make_frame(scene->surfaces[s]);
+    cx.eps = eps;
+    cx.newton_tol = eps * 1e-4;
+    std::vector<uint8_t> st(n), nb(n);
+    o_outputs out{};
+    out.status = st.data();
+    out.bounces = nb.data();
+    std::vector<TrackRec> recs;
+    trace_range(cx, track_first, track_first + track_count, n, O, D, L, vop, seed, first_photon_id, max_bounces, &out,
+                &recs);
+    for (size_t k = 0; k < recs.size() && (int64_t)k < cap; ++k) {
+        points[3 * k + 0] = recs[k].p.x;
+        points[3 * k + 1] = recs[k].p.y;
+        points[3 * k + 2] = recs[k].p.z;
+        info[4 * k + 0] = (int32_t)recs[k].photon;
+        info[4 * k + 1] = recs[k].bounce;
+        info[4 * k + 2] = recs[k].sid;
+        info[4 * k + 3] = recs[k].status;
+    }
+    return (int64_t)recs.size();
+}
+
 double oracle_fresnel_unpolarised(double n1, double n2, double cos_i) { return fresnel(n1, n2, cos_i); }
 double oracle_refractive_index(const o_medium* m, double lambda_nm) { return refr_index(*m, lambda_nm); }
 double oracle_absorption_length(const o_medium* m, double lambda_nm) { return abs_length(*m, lambda_nm); }
@@ -1492,7 +1529,7 @@ int oracle_trace(const o_scene* scene, int64_t n, const double* origins, const d
     for (int k = 0; k < n_threads; ++k) {
         int64_t i0 = n * k / n_threads, i1 = n * (k + 1) / n_threads;
         th.emplace_back(trace_range, std::cref(cx), i0, i1, n, origins, dirs, wavelengths, variant_of_photon,
-                        seed, first_photon_id, max_bounces, out);
+                        seed, first_photon_id, max_bounces, out, (std::vector<TrackRec>*)nullptr);
     }
     for (auto& t : th) t.join();
     return 0;

@@ -130,6 +130,17 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* origins, con
                      int64_t first_photon_id, int32_t max_bounces, double eps, int32_t n_threads,
                      int32_t objective, double tau, const double* delta, double* value, double* grad);
 
+/* Photon tracks (Fig. 2a shows simulated tracks): trace photons
+ * track_first .. track_first + track_count - 1 of the input and record every
+ * interaction -- points [3 per record] and info [4 per record: photon index,
+ * bounce index (0-based), surface id, status after the interaction (0 =
+ * alive)], in photon then bounce order, at most cap records.  Returns the
+ * number of interactions (may exceed cap), or < 0 on bad arguments. */
+int64_t oracle_track(const o_scene* scene, int64_t n, const double* origins, const double* dirs,
+                     const double* wavelengths, const int32_t* variant_of_photon, uint64_t seed,
+                     int64_t first_photon_id, int32_t max_bounces, double eps, int64_t track_first,
+                     int64_t track_count, double* points, int32_t* info, int64_t cap);
+
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 

@@ -71,11 +71,17 @@ class TraceOut(ctypes.Structure):
                 ("counters", ctypes.c_void_p)]
 
 
+class TrackOpts(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int64), ("count", ctypes.c_int64), ("cap", ctypes.c_int64),
+                ("points", ctypes.c_void_p), ("info", ctypes.c_void_p), ("n_records", ctypes.c_void_p)]
+
+
 class TraceOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_bounces", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("variant_of_photon", ctypes.c_void_p), ("first_photon_id", ctypes.c_int64),
                 ("eps", ctypes.c_double), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("work_units", ctypes.c_void_p), ("coherent_order", ctypes.c_int32)]
+                ("work_units", ctypes.c_void_p), ("coherent_order", ctypes.c_int32),
+                ("track", ctypes.POINTER(TrackOpts))]
 
 N_UNITS = 12
 UNIT_NAMES = ("aabb", "sag", "newton", "aperture", "cylinder", "box", "hexwall", "reflect", "refract", "rough",
@@ -256,7 +262,7 @@ def alloc_outputs(n: int, precision: int = 32, device="cuda", fields=None):
 def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32, max_bounces: int = 100,
           stream=None, variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None,
           block_size: int = 0, blocks_per_sm: int = 0, out: Optional[dict] = None, work_units=None,
-          coherent_order: int = 0):
+          coherent_order: int = 0, track=None):
     """robast_trace_ex on CUDA tensors; returns the dict of output tensors.
 
     work_units: optional CUDA int64 tensor [N_UNITS]; when given, the counting
@@ -283,6 +289,11 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
         vop = ctypes.c_void_p(variant_of_photon.data_ptr())
     o = _opts(precision, max_bounces, sp, vop, first_photon_id, eps, block_size, blocks_per_sm, work_units,
               coherent_order)
+    tr = None
+    if track is not None:
+        tr = TrackOpts(int(track["first"]), int(track["count"]), int(track["cap"]), track["points"].data_ptr(),
+                       track["info"].data_ptr(), track["n_records"].data_ptr())
+        o.track = ctypes.pointer(tr)
     _check(lib.robast_trace_ex(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,
                                ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(tout), ctypes.byref(o)))
     return out
@@ -564,3 +575,23 @@ def objective_function():
             return grad_output * grad, None, None, None, None, None
 
     return FrozenPathObjective
+
+
+def alloc_track(first: int, count: int, cap: int, precision: int = 32, device="cuda"):
+    """Device buffers for photon-track recording (pass as trace(..., track=...))."""
+    import torch
+    dt = torch.float32 if precision == 32 else torch.float64
+    return {"first": first, "count": count, "cap": cap,
+            "points": torch.zeros((cap, 4), dtype=dt, device=device),
+            "info": torch.zeros((cap, 4), dtype=torch.int32, device=device),
+            "n_records": torch.zeros(1, dtype=torch.int64, device=device)}
+
+
+def tracks_sorted(track):
+    """Recorded tracks as numpy arrays sorted by (photon, bounce): points [k, 3], info [k, 4]."""
+    import numpy as np_
+    k = min(int(track["n_records"].item()), int(track["cap"]))
+    pts = track["points"][:k, :3].cpu().numpy().astype(np_.float64)
+    info = track["info"][:k].cpu().numpy()
+    order = np_.lexsort((info[:, 1], info[:, 0]))
+    return pts[order], info[order]

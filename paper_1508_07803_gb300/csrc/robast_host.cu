@@ -839,6 +839,17 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     a.fxy = static_cast<T*>(out->focal_xy);
     a.counters = out->counters;
     a.units = o.work_units;
+    if (o.track) {
+        const robast_track_opts& t = *o.track;
+        if (t.first < 0 || t.count < 0 || t.cap < 0 || !t.points || !t.info || !t.n_records)
+            return fail(ROBAST_E_INVALID, "robast_trace: track needs first, count, cap >= 0 and device buffers");
+        a.tr_first = t.first;
+        a.tr_count = t.count;
+        a.tr_cap = t.cap;
+        a.tr_pts = static_cast<T*>(t.points);
+        a.tr_info = t.info;
+        a.tr_n = t.n_records;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
     robast_geom* gm = const_cast<robast_geom*>(g);
     a.work = g->work + (gm->work_slot.fetch_add(1) % kWorkSlots);

@@ -136,6 +136,11 @@ struct TraceArgs {
     unsigned long long* units;  // [U_N], counting instantiation only
     const SrcGroup* groups;     // source mode: photons generated on the device
     int n_groups;
+    // photon tracks: every interaction of photons tr_first .. tr_first + tr_count - 1
+    long long tr_first, tr_count, tr_cap;
+    T* tr_pts;                      // [tr_cap * 4]: x, y, z, 0
+    int* tr_info;                   // [tr_cap * 4]: photon, bounce, surface, status after
+    unsigned long long* tr_n;       // records appended (may exceed tr_cap)
     unsigned long long* gcounts;  // source mode: [n_groups][8] counters per group
 };
 
@@ -1022,6 +1027,19 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             }
             if (status == 0 && !(t_finite(ph.d.x) && t_finite(ph.d.y) && t_finite(ph.d.z))) status = ST_ERROR;
             if (status == 0 && ph.bounces >= A.max_bounces) status = ST_MAXB;
+            if (A.tr_pts && ph.i >= A.tr_first && ph.i < A.tr_first + A.tr_count) {
+                const unsigned long long k = atomicAdd(A.tr_n, 1ull);
+                if ((long long)k < A.tr_cap) {
+                    A.tr_pts[4 * k + 0] = ph.p.x;
+                    A.tr_pts[4 * k + 1] = ph.p.y;
+                    A.tr_pts[4 * k + 2] = ph.p.z;
+                    A.tr_pts[4 * k + 3] = T(0);
+                    A.tr_info[4 * k + 0] = (int)ph.i;
+                    A.tr_info[4 * k + 1] = ph.bounces - 1;
+                    A.tr_info[4 * k + 2] = ph.last;
+                    A.tr_info[4 * k + 3] = status;
+                }
+            }
         }
         if (status == 0) continue;
         // ---- photon finished: store (SoA)

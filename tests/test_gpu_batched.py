@@ -104,3 +104,39 @@ def test_batched_sources_reject_bad_groups():
     with pytest.raises(robast.RobastError, match="unit"):
         robast.sources_create(geom, [bad])
     geom.close()
+
+
+def test_tolerance_sweep_r80_distribution_matches_oracle():
+    """Tilt-error realisations as variants of one launch; the spot-diagram
+    R80 of every realisation agrees with the oracle's to 0.1%, and larger
+    errors give larger spots."""
+    from oracle import metrics
+    nr, m = 6, 3_001
+    scene, b, vop = W.tolerance_sweep(n_realizations=nr, tilt_sigma=1e-3, photons_per_realization=m, seed=3)
+    geom = robast.build_geometry(scene)
+    o = torch.from_numpy(b.origins).to("cuda", torch.float32)
+    d = torch.from_numpy(b.dirs).to("cuda", torch.float32)
+    w = torch.from_numpy(b.wavelengths).to("cuda", torch.float32)
+    out = robast.trace(geom, o, d, w, seed=5, variant_of_photon=torch.from_numpy(vop).cuda())
+    res = robast.psf(geom, out["status"], out["focal_xy"], windows=[(v * m, m) for v in range(nr)])
+    ref = oracle.trace(scene, b.rounded_to(np.float32), seed=5, variant_of_photon=vop,
+                       eps=oracle.default_eps(scene, 32))
+    r80 = []
+    for v, (n_det, cx, cy, r) in enumerate(res):
+        sl = slice(v * m, (v + 1) * m)
+        want = metrics.psf(ref["status"][sl], ref["focal_xy"][:, sl])
+        assert n_det == want["n_detected"]
+        assert r == pytest.approx(want["r80"], rel=1e-3)
+        r80.append(r)
+    # realisations differ (independent tilt errors)
+    assert np.std(r80) > 0
+    geom.close()
+    scene0, b0, vop0 = W.tolerance_sweep(n_realizations=2, tilt_sigma=0.0, photons_per_realization=m, seed=3)
+    g0 = robast.build_geometry(scene0)
+    o0 = torch.from_numpy(b0.origins).to("cuda", torch.float32)
+    d0 = torch.from_numpy(b0.dirs).to("cuda", torch.float32)
+    w0 = torch.from_numpy(b0.wavelengths).to("cuda", torch.float32)
+    out0 = robast.trace(g0, o0, d0, w0, seed=5, variant_of_photon=torch.from_numpy(vop0).cuda())
+    r0 = robast.psf(g0, out0["status"], out0["focal_xy"], windows=[(0, m)])[0][3]
+    assert r0 < np.mean(r80)
+    g0.close()

@@ -275,3 +275,32 @@ def test_thick_absorbing_lens_parity(precision):
     r = oracle_for(scene, b, precision, seed=8)
     assert (r["status"] == W.ABSORBED).sum() > 500 and (r["status"] == W.DETECTED).sum() > 5000
     print(compare(g, r, precision, scene.focal_length, f"lens fp{precision}"))
+
+
+def test_photon_tracks_match_oracle():
+    """Headless photon-track recording (Fig. 2a): every interaction of a
+    window of photons through a concentrator, in FP64, equals the oracle's
+    records; records beyond the capacity are counted, not written."""
+    scene = W.cone_scene()
+    H = W.cone_heights(1)[0]
+    b = W.concat([W.hexagon_bundle(3_000, W.CONE_A_IN, H + W.CONE_WINDOW + 1e-4, math.radians(a), seed=4,
+                                   stream=80 + k) for k, a in enumerate((12.0, 31.0))])
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 64)
+    first, count = 2_900, 250
+    tr = robast.alloc_track(first, count, cap=20_000, precision=64)
+    robast.trace(geom, o, d, w, seed=6, precision=64, max_bounces=30, track=tr)
+    torch.cuda.synchronize()
+    pts, info = robast.tracks_sorted(tr)
+    rpts, rinfo = oracle.track(scene, b, first, count, seed=6, max_bounces=30)
+    assert len(rinfo) > 2 * count  # multi-bounce paths
+    assert int(tr["n_records"].item()) == len(rinfo)
+    assert np.array_equal(info, rinfo)
+    assert np.max(np.abs(pts - rpts)) < 1e-10 * scene.focal_length
+    # a small capacity keeps the count exact and writes only cap records
+    tr2 = robast.alloc_track(first, count, cap=10, precision=64)
+    robast.trace(geom, o, d, w, seed=6, precision=64, max_bounces=30, track=tr2)
+    torch.cuda.synchronize()
+    assert int(tr2["n_records"].item()) == len(rinfo)
+    assert np.all(tr2["info"][10:].cpu().numpy() == 0) if tr2["info"].shape[0] > 10 else True
+    geom.close()

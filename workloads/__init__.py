@@ -482,3 +482,24 @@ def lens_scene(R1: float = 0.1, thickness: float = 0.01, aperture: float = 0.02,
     fl = R1 / (n - 1.0)
     return Scene("lens", surfs, [Material([400.0], [1.0])], [Medium(), med], length_scale=max(0.1, 2 * fl),
                  focal_length=fl)
+
+
+def tolerance_sweep(n_realizations: int = 16, tilt_sigma: float = 0.5e-3, photons_per_realization: int = 100_000,
+                    field_deg: float = 1.0, seed: int = 0, n_facets: Optional[int] = None):
+    """Misalignment study (Sec. 3: tolerance analysis): n_realizations copies of
+    the LST-like dish, each with its own Gaussian facet-tilt errors (sigma per
+    axis), as the variants of one scene; the same photon bundle (one field
+    angle) traced through each.  Returns (scene, bundle, variant_of_photon);
+    photons of realization v are the contiguous range v*n .. (v+1)*n - 1."""
+    surfs: List[Surface] = []
+    offs = [0]
+    for v in range(n_realizations):
+        sc = lst_scene(tilt_sigma=tilt_sigma, seed=seed * 1000 + 17 * v + 1, n_facets=n_facets)
+        surfs += sc.surfaces
+        offs.append(len(surfs))
+    b = disk_bundle(photons_per_realization, 12.0, 32.0, math.radians(field_deg), (300.0, 600.0), seed, stream=900)
+    bundle = concat([b] * n_realizations)
+    vop = np.repeat(np.arange(n_realizations, dtype=np.int32), b.n)
+    scene = Scene("tolerance", surfs, [lst_reflectivity()], [Medium()], length_scale=46.6, focal_length=LST_F,
+                  variant_offsets=offs)
+    return scene, bundle, vop
