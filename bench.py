@@ -416,7 +416,7 @@ def main():
         # per-photon outputs the spot diagram and the metric need: status, bounce count, focal (x, y)
         out = robast.alloc_outputs(N, precision, dev, fields=("status", "bounces", "focal_xy", "counters"))
         counters = out["counters"]
-        psf_launches = 4  # sums, finish, histogram, selection (all field angles at once)
+        psf_launches = 8  # sums, finish, histogram, pick, sub-histogram, pick, collect, select (all angles at once)
 
         def step(ev=None):
             if ev is not None:

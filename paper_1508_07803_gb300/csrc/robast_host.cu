@@ -656,6 +656,8 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         }
         M[33] = m.sigma;
     }
+    std::vector<float> mats32(mats.size());
+    for (size_t k = 0; k < mats.size(); ++k) mats32[k] = (float)mats[k];
     std::vector<double> meds((size_t)std::max(1, d->n_media) * MED_REC, 0.0);
     for (int i = 0; i < d->n_media; ++i) {
         double* M = &meds[(size_t)i * MED_REC];
@@ -674,11 +676,11 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     if (prims.empty()) prims.push_back(0);
     if (nodes.empty()) nodes.push_back(Node{});
 
-    // one device allocation: [rec64 | rec32 | reci | nodes | prims | vars | glob | mats | meds | work]
+    // one device allocation: [rec64 | rec32 | reci | nodes | prims | vars | glob | mats | meds | mats32 | work | ...]
     const size_t b64 = align16(rec64.size() * 8), b32 = align16(rec32.size() * 4), bi = align16(reci.size() * 16);
     const size_t bn = align16(nodes.size() * sizeof(Node)), bp = align16(prims.size() * 4);
     const size_t bv = align16(vars.size() * 16), bg = align16(glob.size() * 4);
-    const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8);
+    const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8), bm32 = align16(mats32.size() * 4);
     const size_t bw = kWorkSlots * 8;
     const size_t bg64 = align16(grec64.size() * 8), bg32 = align16(grec32.size() * 4);
     std::vector<int> surf_var(ns, 0);
@@ -688,7 +690,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         for (int s = s0; s < s1; ++s) surf_var[s] = v;
     }
     const size_t bsv = align16(surf_var.size() * 4);
-    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bw + bg64 + bg32 + bsv;
+    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bw + bg64 + bg32 + bsv;
 
     robast_geom* g = new (std::nothrow) robast_geom();
     if (!g) return fail(ROBAST_E_OOM, "robast_build_geometry: host allocation failed");
@@ -717,6 +719,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t og = put(glob.data(), glob.size() * 4, bg);
     const size_t om = put(mats.data(), mats.size() * 8, bm);
     const size_t od = put(meds.data(), meds.size() * 8, bd);
+    const size_t om32 = put(mats32.data(), mats32.size() * 4, bm32);
     const size_t ow = off;
     off += bw;
     const size_t og64 = put(grec64.data(), grec64.size() * 8, bg64);
@@ -737,6 +740,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     t.glob = reinterpret_cast<const int*>(base + og);
     t.mats = reinterpret_cast<const double*>(base + om);
     t.meds = reinterpret_cast<const double*>(base + od);
+    t.mats32 = reinterpret_cast<const float*>(base + om32);
     t.n_surf = ns;
     t.n_nodes = (int)nodes.size();
     t.n_prims = (int)prims.size();
@@ -753,7 +757,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->grec32 = reinterpret_cast<const float*>(base + og32);
     g->surf_var = reinterpret_cast<const int*>(base + osv);
     g->smem64 = b64 + bi + bn + bp + bv + bg + bm + bd;
-    g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd;
+    g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd + bm32;
     g->n_surf = ns;
     g->n_var = nv;
     g->n_mat = d->n_materials;
@@ -1189,30 +1193,114 @@ extern "C" int robast_trace_grad(robast_geom* g, const void* origins, const void
 
 // ------------------------------------------------------------- reductions
 // Spot diagrams of several photon windows at once.  Per window: centroid
-// from fixed-order FP64 block partials; R80 = exact nearest-rank 80th
-// percentile of the radius to the centroid, found with a histogram of the
-// SQUARED radius over [0, (8 x RMS radius)^2) plus one overflow bin, then a
-// selection inside the bin that holds the rank (ordering by r^2 is ordering
-// by r, and r = sqrt(r^2) of the selected photon, so no square root or
-// division is taken per photon).  Four launches and two host synchronisations
-// for any number of windows.
+// from fixed-order block partials; R80 = exact nearest-rank 80th percentile
+// of the radius to the centroid.  Ordering by r^2 is ordering by r, and r =
+// sqrt(r^2) of the selected photon, so no square root or division is taken
+// per photon.  The rank is located on the device in two histogram rounds:
+//   1. r^2 over [0, (8 x RMS radius)^2) in kBins bins plus an overflow bin;
+//      the bins lo..hi around the bin b that holds the rank are kept;
+//   2. the exact FP64 r^2 of the photons kept, in kSub sub-bins of an
+//      interval that covers them (indices clamped, so the sub-bin is a
+//      non-decreasing function of r^2 whatever the interval);
+// then the values of the sub-bin that holds the rank (a handful) are
+// collected and the rank is selected among them by counting.  One host
+// synchronisation per call; a sub-bin with more than kSel distinct values
+// (a spot far more concentrated than its RMS radius suggests) falls back to
+// collecting bins lo..hi and selecting on the host.
+//
+// FP64 issues at a small fraction of the FP32 rate on this GPU, so with FP32
+// positions the first round takes no FP64 operation per photon: the sums are
+// float pairs, and the histogram bins an FP32 r^2 whose error, in bins, is
+// bounded by delta in psf_finish.  When delta < 1/2, every photon outside the
+// bins b-1..b+1 lies on the correct side of the rank photon in exact
+// arithmetic (approximate and exact bin positions differ by at most delta),
+// so lo..hi = b-1..b+1 holds the rank photon and the photons below lo are
+// exactly those ranked below the kept ones.  Otherwise (a spot tiny against
+// its distance from the origin) the window is binned in FP64 and lo = hi = b.
 namespace {
 constexpr int kRedBlock = 256;
-constexpr int kBins = 4096;  // + 1 overflow bin
+constexpr int kPartBlocks = 1216;  // blocks of a per-photon pass over all windows (8 per SM)
+constexpr int kBins = 4096;        // + 1 overflow bin
+constexpr int kSub = 4096;         // second-round sub-bins
+constexpr int kSel = 2048;         // values the device selects among
+constexpr int kScanBlock = 1024;
+constexpr int kRes = 8;            // per window: N, cx, cy, bins / range^2, fast, delta, -, -
+constexpr int kUnroll = 4;         // photons in flight per thread
+
+// blocks per window of the per-photon passes (robast_psf and robast_psf_noalloc alike)
+int psf_blocks_per_window(int nw, long long maxcount) {
+    return (int)std::max(1LL, std::min<long long>(std::max(1, kPartBlocks / nw), (maxcount + kRedBlock - 1) / kRedBlock));
+}
 
 struct Win {
     long long start, count;
 };
 
-template <typename T>
-__global__ void psf_sums(const uint8_t* st, const T* fxy, long long ld, const Win* win, double* part) {
-    const Win w = win[blockIdx.y];
+// unevaluated float pair hi + lo; two-sum (Knuth) keeps every addition exact
+// in the pair, the product error comes from a fused multiply-add (Dekker)
+struct F2 {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_sq(float x) {
+        const float p = __fmul_rn(x, x);
+        add(p);
+        lo = __fadd_rn(lo, __fmaf_rn(x, x, -p));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Per-thread partial sums over photons start + k, k = tid, tid + stride, ...:
+// (detected count, sum x, sum y, sum x^2, sum y^2), loads kUnroll photons
+// ahead.  Shared by robast_psf and robast_psf_noalloc, so their centroids
+// agree bit for bit.
+__device__ __forceinline__ void psf_thread_sums(const uint8_t* st, const float* fxy, long long ld, long long start,
+                                                long long count, long long tid, long long stride, double out[5]) {
+    unsigned n = 0;
+    F2 sx, sy, sxx, syy;
+    for (long long k0 = tid; k0 < count; k0 += kUnroll * stride) {
+        uint8_t s[kUnroll];
+        float x[kUnroll], y[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+            const long long k = k0 + j * stride;
+            s[j] = 0;
+            x[j] = y[j] = 0.0f;
+            if (k < count) {
+                s[j] = st[start + k];
+                x[j] = fxy[start + k];
+                y[j] = fxy[ld + start + k];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j)
+            if (s[j] == ROBAST_ST_DETECTED) {
+                ++n;
+                sx.add(x[j]);
+                sy.add(y[j]);
+                sxx.add_sq(x[j]);
+                syy.add_sq(y[j]);
+            }
+    }
+    out[0] = (double)n;
+    out[1] = sx.value();
+    out[2] = sy.value();
+    out[3] = sxx.value();
+    out[4] = syy.value();
+}
+
+__device__ __forceinline__ void psf_thread_sums(const uint8_t* st, const double* fxy, long long ld, long long start,
+                                                long long count, long long tid, long long stride, double out[5]) {
     double acc[5] = {0, 0, 0, 0, 0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < w.count;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long i = w.start + k;
+    for (long long k = tid; k < count; k += stride) {
+        const long long i = start + k;
         if (st[i] == ROBAST_ST_DETECTED) {
-            const double x = (double)fxy[i], y = (double)fxy[ld + i];
+            const double x = fxy[i], y = fxy[ld + i];
             acc[0] += 1.0;
             acc[1] += x;
             acc[2] += y;
@@ -1220,6 +1308,15 @@ __global__ void psf_sums(const uint8_t* st, const T* fxy, long long ld, const Wi
             acc[4] += y * y;
         }
     }
+    for (int c = 0; c < 5; ++c) out[c] = acc[c];
+}
+
+template <typename T>
+__global__ void psf_sums(const uint8_t* st, const T* fxy, long long ld, const Win* win, double* part) {
+    const Win w = win[blockIdx.y];
+    double acc[5];
+    psf_thread_sums(st, fxy, ld, w.start, w.count, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                    (long long)gridDim.x * blockDim.x, acc);
     __shared__ double sh[5][kRedBlock];
     for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = acc[c];
     __syncthreads();
@@ -1232,29 +1329,144 @@ __global__ void psf_sums(const uint8_t* st, const T* fxy, long long ld, const Wi
         for (int c = 0; c < 5; ++c) part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 5 + c] = sh[c][0];
 }
 
-// one thread per window, blocks summed in a fixed order: res = (N, cx, cy, bins / range^2)
-__global__ void psf_finish(const double* part, int nblocks, int nwin, double* res) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nwin) return;
-    double a[5] = {0, 0, 0, 0, 0};
-    for (int b = 0; b < nblocks; ++b)
+// Window sums from the block partials in a fixed order: lane l adds the
+// partials l, l + 32, ... in turn, then a butterfly (each step adds the same
+// two numbers on both lanes, so all lanes end with the same bits).  One full
+// warp per window; robast_psf and robast_psf_noalloc share it, so their
+// centroids agree bit for bit.
+__device__ __forceinline__ void psf_window_sums(const double* part, int nblocks, int w, double a[5]) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < 5; ++c) a[c] = 0.0;
+    for (int b = lane; b < nblocks; b += 32)
         for (int c = 0; c < 5; ++c) a[c] += part[((size_t)w * nblocks + b) * 5 + c];
+    for (int off = 16; off > 0; off >>= 1)
+        for (int c = 0; c < 5; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], off);
+}
+
+// One warp per window.  res = (N, cx, cy, bins / range^2, fast, delta).
+// delta bounds |approximate - exact| bin position of the FP32 binning
+// (psf_fbin) for every photon with exact r^2 < (kBins + 2) / scale; fast = 1
+// when FP32 binning may be used.
+__global__ void psf_finish(const double* part, int nblocks, int allow_fast, double* res) {
+    const int w = blockIdx.x;
+    double a[5];
+    psf_window_sums(part, nblocks, w, a);
+    if (threadIdx.x != 0) return;
     const double n = a[0];
     const double cx = n > 0 ? a[1] / n : 0.0, cy = n > 0 ? a[2] / n : 0.0;
     const double ms = n > 0 ? fmax(0.0, (a[3] + a[4]) / n - cx * cx - cy * cy) : 0.0;
-    res[4 * w + 0] = n;
-    res[4 * w + 1] = cx;
-    res[4 * w + 2] = cy;
     const double range2 = fmax(64.0 * ms, 1e-300);  // (8 x RMS radius)^2
-    res[4 * w + 3] = (double)kBins / range2;
+    const double scale = (double)kBins / range2;
+    // Error of psf_fbin for |dx|, |dy| <= R (u = unit roundoff of FP32):
+    //   dxf = fl(x - fl(cx)) differs from x - cx by ex <= u|cx|(1+u) + uR,
+    //   |dxf^2 - dx^2| <= ex(2R + ex), the fma and product add (2u+u^2) E^2
+    //   with E = R + ex + ey, and the scaling by fl(scale) another (2u+u^2).
+    const double u = 0x1p-24, R2 = (kBins + 2) / scale, R = sqrt(R2);
+    const double ex = u * fabs(cx) * (1 + u) + u * R, ey = u * fabs(cy) * (1 + u) + u * R;
+    const double E = R + ex + ey;
+    const double err = ex * (2 * R + ex) + ey * (2 * R + ey) + (2 * u + u * u) * E * E;
+    const double delta = scale * err + (2 * u + u * u) * scale * (R2 + err);
+    const bool fast = allow_fast && n > 0 && scale < 1e37 && fabs(cx) < 1e37 && fabs(cy) < 1e37 &&
+                      1.5 * delta < 0.25;  // margin of 2 against the bound 1/2
+    double* r = res + kRes * w;
+    r[0] = n;
+    r[1] = cx;
+    r[2] = cy;
+    r[3] = scale;
+    r[4] = fast ? 1.0 : 0.0;
+    r[5] = delta;
+    r[6] = r[7] = 0.0;
 }
 
-// bin of r^2: scale = kBins / range^2; values beyond the range -> overflow bin
+// exact bin of r^2: scale = kBins / range^2; values beyond the range -> overflow bin
 __device__ __forceinline__ int psf_bin(double r2, double scale) {
     const double f = r2 * scale;
     if (!(f < (double)kBins)) return kBins;
     const int b = (int)f;
     return b < 0 ? 0 : b;
+}
+
+// approximate bin in FP32, each rounding explicit (the error bound above
+// follows these operations)
+__device__ __forceinline__ int psf_fbin(float x, float y, float cx, float cy, float scale) {
+    const float dx = __fsub_rn(x, cx), dy = __fsub_rn(y, cy);
+    const float f = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), scale);
+    if (!(f < (float)kBins)) return kBins;
+    return (int)f;
+}
+
+template <typename T>
+__device__ __forceinline__ double psf_r2(T x, T y, const double* R) {
+    const double dx = (double)x - R[1], dy = (double)y - R[2];
+    return dx * dx + dy * dy;
+}
+
+// Bin of each photon of one window, kUnroll photons in flight per thread;
+// body(bin, x, y) runs for the detected ones.  FAST: FP32 bins (psf_fbin).
+template <bool FAST, typename T, typename F>
+__device__ __forceinline__ void psf_loop(const uint8_t* st, const T* fxy, long long ld, const Win& w, const double* R,
+                                         F body) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    const float cxf = __double2float_rn(R[1]), cyf = __double2float_rn(R[2]), sf = __double2float_rn(R[3]);
+    for (long long k0 = tid; k0 < w.count; k0 += kUnroll * stride) {
+        uint8_t s[kUnroll];
+        T x[kUnroll], y[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+            const long long k = k0 + j * stride;
+            s[j] = 0;
+            x[j] = y[j] = T(0);
+            if (k < w.count) {
+                s[j] = st[w.start + k];
+                x[j] = fxy[w.start + k];
+                y[j] = fxy[ld + w.start + k];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j)
+            if (s[j] == ROBAST_ST_DETECTED) {
+                int b;
+                if constexpr (FAST)
+                    b = psf_fbin((float)x[j], (float)y[j], cxf, cyf, sf);
+                else
+                    b = psf_bin(psf_r2(x[j], y[j], R), R[3]);
+                body(b, x[j], y[j]);
+            }
+    }
+}
+
+// The window's binning is chosen once per block (a uniform branch), so the
+// FP32 loop carries no FP64 operation.
+template <typename T, typename F>
+__device__ __forceinline__ void psf_for_bins(const uint8_t* st, const T* fxy, long long ld, const Win& w,
+                                             const double* R, F body) {
+    if constexpr (sizeof(T) == 4) {
+        if (R[4] != 0.0) {
+            psf_loop<true>(st, fxy, ld, w, R, body);
+            return;
+        }
+    }
+    psf_loop<false>(st, fxy, ld, w, R, body);
+}
+
+// sub-bin of r^2 in round 2 (non-decreasing in r^2 for any a and s2 >= 0)
+__device__ __forceinline__ int psf_sub(double r2, double a, double s2) {
+    const double f = (r2 - a) * s2;
+    if (!(f > 0.0)) return 0;  // also NaN
+    return f >= (double)kSub ? kSub - 1 : (int)f;
+}
+
+// Exact r^2 and its sub-bin, for the few photons of the kept bins: out of
+// line, so that the compiler cannot turn the rare branch into predicated
+// FP64 work on every photon.
+struct Cand {
+    double r2;
+    int sub;
+};
+template <typename T>
+__device__ __noinline__ Cand psf_cand(T x, T y, const double* R, double a, double s2) {
+    const double r2 = psf_r2(x, y, R);
+    return Cand{r2, psf_sub(r2, a, s2)};
 }
 
 template <typename T>
@@ -1264,40 +1476,243 @@ __global__ void psf_hist(const uint8_t* st, const T* fxy, long long ld, const Wi
     for (int k = threadIdx.x; k <= kBins; k += blockDim.x) h[k] = 0;
     __syncthreads();
     const Win w = win[blockIdx.y];
-    const double* R = res + 4 * blockIdx.y;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < w.count;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long i = w.start + k;
-        if (st[i] == ROBAST_ST_DETECTED) {
-            const double dx = (double)fxy[i] - R[1], dy = (double)fxy[ld + i] - R[2];
-            atomicAdd(&h[psf_bin(dx * dx + dy * dy, R[3])], 1u);
-        }
-    }
+    psf_for_bins(st, fxy, ld, w, res + kRes * blockIdx.y, [&](int b, T, T) { atomicAdd(&h[b], 1u); });
     __syncthreads();
     unsigned long long* H = hist + (size_t)blockIdx.y * (kBins + 1);
     for (int k = threadIdx.x; k <= kBins; k += blockDim.x)
         if (h[k]) atomicAdd(H + k, (unsigned long long)h[k]);
 }
 
-// sel[w] = (bin, offset into vals); cnt[w] counts the values written
+// Fallback selection: the values of bins lo..hi.  sel[4w..] = (first bin,
+// last bin, offset into vals, -); cnt[w] counts the values written; each
+// value is the photon's exact FP64 r^2.
 template <typename T>
 __global__ void psf_collect(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
                             const long long* sel, double* vals, unsigned long long* cnt, const long long* cap) {
     const Win w = win[blockIdx.y];
-    const double* R = res + 4 * blockIdx.y;
-    const int bin = (int)sel[2 * blockIdx.y];
-    double* out = vals + sel[2 * blockIdx.y + 1];
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < w.count;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long i = w.start + k;
-        if (st[i] == ROBAST_ST_DETECTED) {
-            const double dx = (double)fxy[i] - R[1], dy = (double)fxy[ld + i] - R[2];
-            const double r2 = dx * dx + dy * dy;
-            if (psf_bin(r2, R[3]) == bin) {
-                const unsigned long long j = atomicAdd(cnt + blockIdx.y, 1ull);
-                if ((long long)j < cap[blockIdx.y]) out[j] = r2;
+    const double* R = res + kRes * blockIdx.y;
+    const int lo = (int)sel[4 * blockIdx.y], hi = (int)sel[4 * blockIdx.y + 1];
+    double* out = vals + sel[4 * blockIdx.y + 2];
+    const long long c = cap[blockIdx.y];
+    unsigned long long* cw = cnt + blockIdx.y;
+    psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y) {
+        if (b >= lo && b <= hi) {
+            const unsigned long long j = atomicAdd(cw, 1ull);
+            if ((long long)j < c) out[j] = psf_r2(x, y, R);
+        }
+    });
+}
+
+// Device-side selection state of one window.
+struct Sel {
+    long long k;      // rank of the 80% photon among the window's detected photons
+    long long rank1;  // its rank among the photons of first-round bins lo..hi
+    long long cap1;   // photons in bins lo..hi
+    long long rank2;  // its rank among the values of sub-bin sub
+    long long cap2;   // values in sub-bin sub
+    double a, s2;     // sub-bin of r^2: clamp(floor((r^2 - a) s2), 0, kSub - 1)
+    int lo, hi;       // first-round bins kept
+    int sub;          // chosen sub-bin
+    int status;       // 0 in progress / resolved, 1 unresolved, 2 no detected photon, 3 counts disagree
+};
+
+// Block of kScanBlock threads: the bin j of H[0..nb) with
+// sum(H[0..j)) <= k < sum(H[0..j]) (-1 if k >= total), sum(H[0..j)) and the
+// total, to every thread.
+__device__ void block_find_rank(const unsigned long long* H, int nb, long long k, int* bin, long long* below,
+                                long long* total) {
+    __shared__ unsigned long long csum[kScanBlock];
+    __shared__ int s_bin;
+    __shared__ long long s_below;
+    const int per = (nb + kScanBlock - 1) / kScanBlock;
+    const int j0 = min(nb, (int)threadIdx.x * per), j1 = min(nb, j0 + per);
+    unsigned long long my = 0;
+    for (int j = j0; j < j1; ++j) my += H[j];
+    csum[threadIdx.x] = my;
+    if (threadIdx.x == 0) {
+        s_bin = -1;
+        s_below = 0;
+    }
+    __syncthreads();
+    for (int off = 1; off < kScanBlock; off <<= 1) {  // inclusive scan
+        const unsigned long long v = (int)threadIdx.x >= off ? csum[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        csum[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const long long before = (long long)(csum[threadIdx.x] - my);
+    if (before <= k && k < before + (long long)my) {  // one thread at most
+        long long acc = before;
+        for (int j = j0; j < j1; ++j) {
+            if (acc + (long long)H[j] > k) {
+                s_bin = j;
+                s_below = acc;
+                break;
+            }
+            acc += (long long)H[j];
+        }
+    }
+    __syncthreads();
+    *bin = s_bin;
+    *below = s_below;
+    *total = (long long)csum[kScanBlock - 1];
+}
+
+// Round 1 decision: rank k, bin b, bins lo..hi kept, the sub-bin interval.
+__global__ void psf_pick1(const unsigned long long* hist, const double* res, Sel* sel) {
+    const int w = blockIdx.x;
+    const double* R = res + kRes * w;
+    const long long N = (long long)R[0];
+    Sel z{};
+    z.k = -1;
+    z.lo = -1;
+    z.hi = -2;
+    z.sub = -1;
+    if (N == 0) {
+        if (threadIdx.x == 0) {
+            z.status = 2;
+            sel[w] = z;
+        }
+        return;
+    }
+    const long long k = (long long)ceil(0.8 * (double)N) - 1;
+    const unsigned long long* H = hist + (size_t)w * (kBins + 1);
+    int b;
+    long long below, total;
+    block_find_rank(H, kBins + 1, k, &b, &below, &total);
+    if (threadIdx.x != 0) return;
+    z.k = k;
+    if (b < 0 || total != N) {
+        z.status = 3;
+        sel[w] = z;
+        return;
+    }
+    const bool fast = R[4] != 0.0;
+    const int lo = fast ? max(b - 1, 0) : b, hi = fast ? min(b + 1, kBins) : b;
+    long long below1 = below, cap1 = 0;
+    for (int j = lo; j < b; ++j) below1 -= (long long)H[j];
+    for (int j = lo; j <= hi; ++j) cap1 += (long long)H[j];
+    z.lo = lo;
+    z.hi = hi;
+    z.rank1 = k - below1;
+    z.cap1 = cap1;
+    // exact r^2 of the kept photons lies in [(lo - delta) / scale, (hi + 1 + delta) / scale]
+    const double scale = R[3];
+    z.a = fmax(0.0, ((double)lo - 0.5) / scale);
+    z.s2 = (double)kSub / (((double)hi + 1.5) / scale - z.a);
+    z.status = 0;
+    sel[w] = z;
+}
+
+// Round 2: sub-bin histogram of the exact r^2 of the kept photons.
+template <typename T>
+__global__ void psf_hist2(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
+                          const Sel* sel, unsigned long long* hist2) {
+    __shared__ unsigned int h[kSub];
+    for (int k = threadIdx.x; k < kSub; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    const Win w = win[blockIdx.y];
+    const Sel S = sel[blockIdx.y];
+    const double* R = res + kRes * blockIdx.y;
+    if (S.status == 0)
+        psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y) {
+            if (b >= S.lo && b <= S.hi) atomicAdd(&h[psf_cand(x, y, R, S.a, S.s2).sub], 1u);
+        });
+    __syncthreads();
+    unsigned long long* H = hist2 + (size_t)blockIdx.y * kSub;
+    for (int k = threadIdx.x; k < kSub; k += blockDim.x)
+        if (h[k]) atomicAdd(H + k, (unsigned long long)h[k]);
+}
+
+// Round 2 decision: the sub-bin that holds rank1.
+__global__ void psf_pick2(const unsigned long long* hist2, Sel* sel) {
+    const int w = blockIdx.x;
+    const Sel S = sel[w];
+    if (S.status != 0) return;
+    const unsigned long long* H = hist2 + (size_t)w * kSub;
+    int sub;
+    long long below, total;
+    block_find_rank(H, kSub, S.rank1, &sub, &below, &total);
+    if (threadIdx.x != 0) return;
+    if (sub < 0 || total != S.cap1) {
+        sel[w].status = 3;
+        return;
+    }
+    sel[w].sub = sub;
+    sel[w].rank2 = S.rank1 - below;
+    sel[w].cap2 = (long long)H[sub];
+}
+
+// The exact r^2 of the sub-bin's photons (at most kSel kept), their count
+// and the bit patterns of their minimum (stored complemented) and maximum.
+template <typename T>
+__global__ void psf_collect2(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
+                             const Sel* sel, double* vals2, unsigned long long* cnt2, unsigned long long* mm) {
+    const Win w = win[blockIdx.y];
+    const Sel S = sel[blockIdx.y];
+    if (S.status != 0) return;
+    const double* R = res + kRes * blockIdx.y;
+    double* out = vals2 + (size_t)blockIdx.y * kSel;
+    unsigned long long* cw = cnt2 + blockIdx.y;
+    unsigned long long* m = mm + 2 * blockIdx.y;
+    psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y) {
+        if (b >= S.lo && b <= S.hi) {
+            const Cand c = psf_cand(x, y, R, S.a, S.s2);
+            const double r2 = c.r2;
+            if (c.sub == S.sub) {
+                const unsigned long long j = atomicAdd(cw, 1ull);
+                if (j < (unsigned long long)kSel) out[j] = r2;
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(r2);  // r2 >= +0
+                atomicMax(m, ~bits);
+                atomicMax(m + 1, bits);
             }
         }
+    });
+}
+
+// Final selection by counting: the value v with #(< v) <= rank2 < #(<= v).
+// out[4w..] = (N, cx, cy, R80); stat[w] = final status.
+__global__ void psf_select(const double* res, const Sel* sel, const double* vals2, const unsigned long long* cnt2,
+                           const unsigned long long* mm, double* out, int* stat) {
+    __shared__ double v[kSel];
+    const int w = blockIdx.x;
+    const Sel S = sel[w];
+    const double* R = res + kRes * w;
+    const bool any = R[0] > 0.0;
+    if (threadIdx.x == 0) {
+        out[4 * w + 0] = R[0];
+        out[4 * w + 1] = any ? R[1] : NAN;
+        out[4 * w + 2] = any ? R[2] : NAN;
+        out[4 * w + 3] = NAN;
+        stat[w] = S.status;
+    }
+    if (S.status != 0) return;
+    const long long c = (long long)cnt2[w];
+    if (c != S.cap2 || S.rank2 < 0 || S.rank2 >= c) {
+        if (threadIdx.x == 0) stat[w] = 3;
+        return;
+    }
+    const double vmin = __longlong_as_double((long long)~mm[2 * w]), vmax = __longlong_as_double((long long)mm[2 * w + 1]);
+    if (c > kSel) {
+        if (threadIdx.x == 0) {
+            if (vmin == vmax)
+                out[4 * w + 3] = sqrt(vmin);  // all equal
+            else
+                stat[w] = 1;
+        }
+        return;
+    }
+    const int n = (int)c;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = vals2[(size_t)w * kSel + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = v[i];
+        int less = 0, leq = 0;
+        for (int j = 0; j < n; ++j) {
+            less += v[j] < x;
+            leq += v[j] <= x;
+        }
+        if (less <= S.rank2 && S.rank2 < leq) out[4 * w + 3] = sqrt(x);  // equal values: same result
     }
 }
 
@@ -1306,17 +1721,25 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
              const long long* counts, cudaStream_t s, double* result) {
     long long maxcount = 0;
     for (int w = 0; w < nw; ++w) maxcount = std::max(maxcount, counts[w]);
-    const int bx = (int)std::max(1LL, std::min<long long>(std::max(1, 512 / nw), (maxcount + kRedBlock - 1) / kRedBlock));
-    // scratch: win[nw] | part[nw*bx*5] | res[4nw] | hist[nw*(kBins+1)] | sel[2nw] | cnt[nw] | cap[nw] | vals
+    const int bx = psf_blocks_per_window(nw, maxcount);
+    // scratch: win | part | {res, out, stat, sel} (read back together) |
+    //          {hist, hist2, cnt2, mm} (cleared together) | vals2 | fallback: sel4, cnt, cap, vals
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         const size_t at = off;
         off += align16(bytes);
         return at;
     };
-    const size_t o_win = carve(nw * sizeof(Win)), o_part = carve((size_t)nw * bx * 5 * 8), o_res = carve(nw * 32);
-    const size_t o_hist = carve((size_t)nw * (kBins + 1) * 8), o_sel = carve(nw * 16), o_cnt = carve(nw * 8);
-    const size_t o_cap = carve(nw * 8), o_vals = off;
+    const size_t o_win = carve(nw * sizeof(Win)), o_part = carve((size_t)nw * bx * 5 * 8);
+    const size_t o_back = off, o_res = carve((size_t)nw * kRes * 8), o_out = carve((size_t)nw * 32),
+                 o_stat = carve((size_t)nw * 4), o_sel = carve((size_t)nw * sizeof(Sel));
+    const size_t back_bytes = off - o_back;
+    const size_t o_zero = off, o_hist = carve((size_t)nw * (kBins + 1) * 8), o_hist2 = carve((size_t)nw * kSub * 8),
+                 o_cnt2 = carve((size_t)nw * 8), o_mm = carve((size_t)nw * 16);
+    const size_t zero_bytes = off - o_zero;
+    const size_t o_vals2 = carve((size_t)nw * kSel * 8);
+    const size_t o_sel4 = carve((size_t)nw * 32), o_cnt = carve((size_t)nw * 8), o_cap = carve((size_t)nw * 8);
+    const size_t o_vals = off;
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = grow(&g->scratch, &g->scratch_bytes, o_vals + 4096 * 8, "robast_psf");
     if (rc) return rc;
@@ -1324,72 +1747,77 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
     std::vector<Win> hw(nw);
     for (int w = 0; w < nw; ++w) hw[w] = Win{starts[w], counts[w]};
     CU(cudaMemcpyAsync(b + o_win, hw.data(), nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
-    CU(cudaMemsetAsync(b + o_hist, 0, (size_t)nw * (kBins + 1) * 8, s), "robast_psf: clear");
+    CU(cudaMemsetAsync(b + o_zero, 0, zero_bytes, s), "robast_psf: clear");
     const Win* dwin = reinterpret_cast<const Win*>(b + o_win);
     double* part = reinterpret_cast<double*>(b + o_part);
     double* res = reinterpret_cast<double*>(b + o_res);
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(b + o_hist);
-    psf_sums<T><<<dim3(bx, nw), kRedBlock, 0, s>>>(st, fxy, ld, dwin, part);
-    psf_finish<<<(nw + 31) / 32, 32, 0, s>>>(part, bx, nw, res);
-    psf_hist<T><<<dim3(bx, nw), kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, hist);
+    Sel* sel = reinterpret_cast<Sel*>(b + o_sel);
+    auto u64 = [&](size_t o) { return reinterpret_cast<unsigned long long*>(b + o); };
+    const dim3 grid(bx, nw);
+    psf_sums<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, part);
+    psf_finish<<<nw, 32, 0, s>>>(part, bx, sizeof(T) == 4 ? 1 : 0, res);
+    psf_hist<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, u64(o_hist));
+    psf_pick1<<<nw, kScanBlock, 0, s>>>(u64(o_hist), res, sel);
+    psf_hist2<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, sel, u64(o_hist2));
+    psf_pick2<<<nw, kScanBlock, 0, s>>>(u64(o_hist2), sel);
+    psf_collect2<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, sel, reinterpret_cast<double*>(b + o_vals2),
+                                               u64(o_cnt2), u64(o_mm));
+    psf_select<<<nw, kScanBlock, 0, s>>>(res, sel, reinterpret_cast<const double*>(b + o_vals2), u64(o_cnt2), u64(o_mm),
+                                         reinterpret_cast<double*>(b + o_out), reinterpret_cast<int*>(b + o_stat));
     CU(cudaGetLastError(), "robast_psf: launch");
-    std::vector<double> hres(4 * nw);
-    std::vector<unsigned long long> hh((size_t)nw * (kBins + 1));
-    CU(cudaMemcpyAsync(hres.data(), res, nw * 32, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
-    CU(cudaMemcpyAsync(hh.data(), hist, hh.size() * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    std::vector<unsigned char> back(back_bytes);
+    CU(cudaMemcpyAsync(back.data(), b + o_back, back_bytes, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
     CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
-    // the bin holding rank ceil(0.8 N) - 1 of each window
-    std::vector<long long> sel(2 * nw), cap(nw), rank_in_bin(nw);
+    const double* hout = reinterpret_cast<const double*>(back.data() + (o_out - o_back));
+    const int* hstat = reinterpret_cast<const int*>(back.data() + (o_stat - o_back));
+    const Sel* hsel = reinterpret_cast<const Sel*>(back.data() + (o_sel - o_back));
+    bool fallback = false;
+    for (int w = 0; w < nw; ++w) {
+        for (int c = 0; c < 4; ++c) result[4 * w + c] = hout[4 * w + c];
+        if (hstat[w] == 3) return fail(ROBAST_E_CUDA, "robast_psf: histogram and selection disagree in window %d", w);
+        fallback = fallback || hstat[w] == 1;
+    }
+    if (!fallback) return 0;
+
+    // fallback for unresolved windows: collect bins lo..hi, select on the host
+    std::vector<long long> sel4(4 * nw), cap(nw);
     long long total = 0;
     for (int w = 0; w < nw; ++w) {
-        const long long N = (long long)hres[4 * w];
-        result[4 * w + 0] = hres[4 * w];
-        result[4 * w + 1] = N ? hres[4 * w + 1] : NAN;
-        result[4 * w + 2] = N ? hres[4 * w + 2] : NAN;
-        result[4 * w + 3] = NAN;
-        long long k = N ? (long long)std::ceil(0.8 * (double)N) - 1 : -1, acc = 0;
-        int bin = 0;
-        if (N) {
-            for (; bin <= kBins; ++bin) {
-                const long long c = (long long)hh[(size_t)w * (kBins + 1) + bin];
-                if (acc + c > k) break;
-                acc += c;
-            }
-        }
-        cap[w] = N ? (long long)hh[(size_t)w * (kBins + 1) + bin] : 0;
-        rank_in_bin[w] = k - acc;
-        sel[2 * w] = N ? bin : -1;
-        sel[2 * w + 1] = total;
+        const bool on = hstat[w] == 1;
+        sel4[4 * w] = on ? hsel[w].lo : -1;
+        sel4[4 * w + 1] = on ? hsel[w].hi : -2;
+        sel4[4 * w + 2] = total;
+        sel4[4 * w + 3] = 0;
+        cap[w] = on ? hsel[w].cap1 : 0;
         total += cap[w];
     }
     rc = grow(&g->scratch, &g->scratch_bytes, o_vals + std::max<long long>(total, 1) * 8, "robast_psf");
     if (rc) return rc;
     b = static_cast<unsigned char*>(g->scratch);  // may have moved: re-upload what the collect pass reads
-    dwin = reinterpret_cast<const Win*>(b + o_win);
-    res = reinterpret_cast<double*>(b + o_res);
     CU(cudaMemcpyAsync(b + o_win, hw.data(), nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
-    CU(cudaMemcpyAsync(res, hres.data(), nw * 32, cudaMemcpyHostToDevice, s), "robast_psf: copy");
-    CU(cudaMemcpyAsync(b + o_sel, sel.data(), nw * 16, cudaMemcpyHostToDevice, s), "robast_psf: copy");
-    CU(cudaMemcpyAsync(b + o_cap, cap.data(), nw * 8, cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(b + o_res, back.data() + (o_res - o_back), (size_t)nw * kRes * 8, cudaMemcpyHostToDevice, s),
+       "robast_psf: copy");
     CU(cudaMemsetAsync(b + o_cnt, 0, nw * 8, s), "robast_psf: clear");
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b + o_cnt);
+    CU(cudaMemcpyAsync(b + o_sel4, sel4.data(), nw * 32, cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(b + o_cap, cap.data(), nw * 8, cudaMemcpyHostToDevice, s), "robast_psf: copy");
     double* vals = reinterpret_cast<double*>(b + o_vals);
-    psf_collect<T><<<dim3(bx, nw), kRedBlock, 0, s>>>(st, fxy, ld, dwin, res,
-                                                      reinterpret_cast<const long long*>(b + o_sel), vals, cnt,
-                                                      reinterpret_cast<const long long*>(b + o_cap));
+    psf_collect<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, reinterpret_cast<const Win*>(b + o_win),
+                                              reinterpret_cast<const double*>(b + o_res),
+                                              reinterpret_cast<const long long*>(b + o_sel4), vals, u64(o_cnt),
+                                              reinterpret_cast<const long long*>(b + o_cap));
     CU(cudaGetLastError(), "robast_psf: launch");
     std::vector<double> hv(std::max<long long>(total, 1));
     std::vector<unsigned long long> got(nw);
-    CU(cudaMemcpyAsync(got.data(), cnt, nw * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(got.data(), u64(o_cnt), nw * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
     if (total) CU(cudaMemcpyAsync(hv.data(), vals, total * 8, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
     CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
     for (int w = 0; w < nw; ++w) {
-        if (sel[2 * w] < 0) continue;
+        if (hstat[w] != 1) continue;
         if ((long long)got[w] != cap[w])
             return fail(ROBAST_E_CUDA, "robast_psf: histogram and selection disagree in window %d", w);
-        auto first = hv.begin() + sel[2 * w + 1];
-        std::nth_element(first, first + rank_in_bin[w], first + cap[w]);
-        result[4 * w + 3] = std::sqrt(first[rank_in_bin[w]]);  // the selected photon's radius
+        auto first = hv.begin() + sel4[4 * w + 2];
+        std::nth_element(first, first + hsel[w].rank1, first + cap[w]);
+        result[4 * w + 3] = std::sqrt(first[hsel[w].rank1]);  // the selected photon's radius
     }
     return 0;
 }
@@ -1507,7 +1935,7 @@ constexpr int NA_BINS = 4096;  // + 1 overflow bin in the first round
 constexpr int NA_CAP = 8192;   // values collected per window for the final selection
 constexpr int NA_ROUNDS = 8;   // histogram rounds (4096^8 resolves any double interval)
 constexpr int NA_BLOCK = 256;
-constexpr int NA_MAX_PART_BLOCKS = 512;
+constexpr int NA_MAX_PART_BLOCKS = kPartBlocks;
 constexpr int NA_MAX_DEVICES = 64;
 
 struct NaScratch {
@@ -1534,19 +1962,9 @@ struct WinSet {
 template <typename T>
 __global__ void na_sums(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S) {
     const int w = blockIdx.y;
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long i = ws.start[w] + k;
-        if (st[i] == ROBAST_ST_DETECTED) {
-            const double x = (double)fxy[i], y = (double)fxy[ld + i];
-            acc[0] += 1.0;
-            acc[1] += x;
-            acc[2] += y;
-            acc[3] += x * x;
-            acc[4] += y * y;
-        }
-    }
+    double acc[5];
+    psf_thread_sums(st, fxy, ld, ws.start[w], ws.count[w], blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                    (long long)gridDim.x * blockDim.x, acc);
     __shared__ double sh[5][NA_BLOCK];
     for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = acc[c];
     __syncthreads();
@@ -1559,12 +1977,12 @@ __global__ void na_sums(const uint8_t* st, const T* fxy, long long ld, WinSet ws
         for (int c = 0; c < 5; ++c) S->part[((size_t)w * gridDim.x + blockIdx.x) * 5 + c] = sh[c][0];
 }
 
-__global__ void na_finish(int nblocks, int nwin, NaScratch* S) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nwin) return;
-    double a[5] = {0, 0, 0, 0, 0};
-    for (int b = 0; b < nblocks; ++b)
-        for (int c = 0; c < 5; ++c) a[c] += S->part[((size_t)w * nblocks + b) * 5 + c];
+// one warp per window, the same fixed-order sums as robast_psf
+__global__ void na_finish(int nblocks, NaScratch* S) {
+    const int w = blockIdx.x;
+    double a[5];
+    psf_window_sums(S->part, nblocks, w, a);
+    if (threadIdx.x != 0) return;
     const double n = a[0];
     const double cx = n > 0 ? a[1] / n : 0.0, cy = n > 0 ? a[2] / n : 0.0;
     const double ms = n > 0 ? fmax(0.0, (a[3] + a[4]) / n - cx * cx - cy * cy) : 0.0;
@@ -1672,10 +2090,10 @@ int na_impl(NaScratch* S, const uint8_t* st, const T* fxy, long long ld, const W
     long long maxcount = 0;
     for (int w = 0; w < nw; ++w) maxcount = std::max(maxcount, ws.count[w]);
     // same block partition of the sums as robast_psf, so the centroids agree bit for bit
-    const int bx = (int)std::max(1LL, std::min<long long>(std::max(1, 512 / nw), (maxcount + NA_BLOCK - 1) / NA_BLOCK));
+    const int bx = psf_blocks_per_window(nw, maxcount);
     const dim3 grid(bx, nw);
     na_sums<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S);
-    na_finish<<<(nw + 31) / 32, 32, 0, s>>>(bx, nw, S);
+    na_finish<<<nw, 32, 0, s>>>(bx, S);
     CU(cudaGetLastError(), "robast_psf_noalloc: launch");
     CU(cudaMemcpyAsync(na_h_res, S->res, nw * 4 * sizeof(double), cudaMemcpyDeviceToHost, s),
           "robast_psf_noalloc: copy");

@@ -93,6 +93,7 @@ struct Tables {
     const int* glob;       // surfaces without a bounding box, per variant
     const double* mats;
     const double* meds;
+    const float* mats32;  // the material records rounded to FP32 (the FP32 kernel's reads)
     int n_surf, n_nodes, n_prims, n_var, n_glob, n_mat, n_med, pad;
 };
 
@@ -726,16 +727,17 @@ __device__ __forceinline__ unsigned long long refl_threshold(const double* M, do
 // falls back to the exact FP64 threshold only when the draw lies within the
 // estimate's error band (relative 1e-5, probability ~1e-5 per reflection), so
 // the decision is exactly the FP64 one at FP32 cost.
-__device__ __forceinline__ float refl_estimate32(const double* M, float lam) {
+// M: the material record rounded to FP32 (no FP64 operation on this path).
+__device__ __forceinline__ float refl_estimate32(const float* M, float lam) {
     const int n = (int)M[0];
-    const double* L = M + 1;
-    const double* R = M + 17;
-    if (n <= 1 || lam <= (float)L[0]) return (float)R[0];
-    if (lam >= (float)L[n - 1]) return (float)R[n - 1];
+    const float* L = M + 1;
+    const float* R = M + 17;
+    if (n <= 1 || lam <= L[0]) return R[0];
+    if (lam >= L[n - 1]) return R[n - 1];
     int i = 0;
-    while (i + 1 < n - 1 && lam >= (float)L[i + 1]) ++i;
-    const float frac = (lam - (float)L[i]) / ((float)L[i + 1] - (float)L[i]);
-    return (float)R[i] + ((float)R[i + 1] - (float)R[i]) * frac;
+    while (i + 1 < n - 1 && lam >= L[i + 1]) ++i;
+    const float frac = (lam - L[i]) / (L[i + 1] - L[i]);
+    return R[i] + (R[i + 1] - R[i]) * frac;
 }
 
 template <typename T>
@@ -842,6 +844,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         tb.glob = reinterpret_cast<const int*>(stage(tb.glob, (size_t)tb.n_glob * sizeof(int)));
         tb.mats = reinterpret_cast<const double*>(stage(tb.mats, (size_t)tb.n_mat * MAT_REC * sizeof(double)));
         tb.meds = reinterpret_cast<const double*>(stage(tb.meds, (size_t)tb.n_med * MED_REC * sizeof(double)));
+        if constexpr (sizeof(T) == 4)
+            tb.mats32 = reinterpret_cast<const float*>(stage(tb.mats32, (size_t)tb.n_mat * MAT_REC * sizeof(float)));
         __syncthreads();
     }
     const unsigned FULL = 0xffffffffu;
@@ -960,7 +964,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     bool survive;
                     if constexpr (sizeof(T) == 4) {
                         if (si.y != ph.mat_cache) {
-                            ph.refl32 = refl_estimate32(M, (float)ph.lam);
+                            ph.refl32 = refl_estimate32(tb.mats32 + (size_t)si.y * MAT_REC, (float)ph.lam);
                             ph.mat_cache = si.y;
                         }
                         const float est = ph.refl32 * 4294967296.0f;
@@ -980,7 +984,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         status = ST_ABSORBED;
                     } else {
                         V3<T> nn = n;
-                        const T sigma = (T)M[33];
+                        const T sigma = sizeof(T) == 4 ? (T)tb.mats32[(size_t)si.y * MAT_REC + 33] : (T)M[33];
                         if (sigma > T(0)) {
                             CNT(U_ROUGH);
                             const T u1 = unit_open<T>(w.y), u2 = unit_open<T>(w.z);

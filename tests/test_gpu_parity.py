@@ -249,6 +249,64 @@ def test_psf_windows_each_match_numpy_on_the_same_outputs():
     geom.close()
 
 
+def _spots(rng):
+    """Synthetic focal-plane spots that exercise every branch of the R80 selection."""
+    n = 200_003
+    out = {}
+    # broad spot far off axis (FP32 binning with its guard band)
+    out["offaxis"] = (rng.normal(0, 0.02, (2, n)) + np.array([[0.3], [-1.02]]), rng.random(n) < 0.97)
+    # spot of a few FP32 ulps at 1 m: the error bound rejects FP32 binning (FP64 fallback), ties everywhere
+    out["tiny"] = (rng.normal(0, 2e-7, (2, n)) + np.array([[1.0], [0.5]]), rng.random(n) < 0.9)
+    # a thin ring: nearly all photons in one or two bins
+    phi = rng.uniform(0, 2 * np.pi, n)
+    r = 0.05 + rng.normal(0, 1e-9, n)
+    out["ring"] = (np.stack([r * np.cos(phi), r * np.sin(phi)]), np.ones(n, bool))
+    # 30% far outliers: the spread is set by them, the rank falls among them
+    xy = rng.normal(0, 0.01, (2, n))
+    far = rng.random(n) < 0.3
+    xy[:, far] *= 1000.0
+    out["outliers"] = (xy, np.ones(n, bool))
+    # a lattice: many photons at exactly equal radii
+    g = rng.integers(-20, 21, (2, n)).astype(np.float64) * 0.001
+    out["lattice"] = (g, rng.random(n) < 0.8)
+    # every photon at one point: zero spread
+    out["point"] = (np.tile(np.array([[0.25], [-0.125]]), (1, n)), rng.random(n) < 0.5)
+    # one detected photon
+    one = np.zeros(n, bool)
+    one[n // 2] = True
+    out["single"] = (rng.normal(0, 0.1, (2, n)), one)
+    return out
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_psf_selection_on_synthetic_spots(precision):
+    """R80, centroid and count against numpy on spots built to reach the FP32
+    guard band, the FP64 fallback, ties, a one-bin ring and a zero spread."""
+    scene, _ = W.lst_workload(10, seed=0, angles_deg=(0.0,))
+    geom = robast.build_geometry(scene)
+    npdt = np.float32 if precision == 32 else np.float64
+    dt = torch.float32 if precision == 32 else torch.float64
+    for name, (xy, det) in _spots(np.random.default_rng(21)).items():
+        xy = np.ascontiguousarray(xy.astype(npdt))
+        st = np.where(det, W.DETECTED, 3).astype(np.uint8)
+        st_d = torch.from_numpy(st).cuda()
+        xy_d = torch.from_numpy(xy).cuda()
+        n = st.shape[0]
+        wins = [(0, n), (17, n // 3), (n - 5000, 5000)]
+        got = robast.psf(geom, st_d, xy_d, precision=precision, windows=wins)
+        got_na = robast.psf_noalloc(st_d, xy_d, windows=wins, precision=precision)
+        for (s0, c), g, gn in zip(wins, got, got_na):
+            exact = metrics.psf(st[s0:s0 + c], xy[:, s0:s0 + c])
+            assert g[0] == exact["n_detected"], name
+            if g[0] == 0:
+                continue
+            assert abs(g[1] - exact["cx"]) < 1e-12 and abs(g[2] - exact["cy"]) < 1e-12, name
+            assert g[3] == pytest.approx(exact["r80"], rel=1e-12, abs=1e-15), name
+            assert gn[:3] == g[:3], name  # same partition of the sums: identical centroids
+            assert gn[3] == pytest.approx(g[3], rel=1e-12, abs=1e-15), name
+    geom.close()
+
+
 @pytest.mark.parametrize("precision", [32, 64])
 def test_coherent_order_does_not_change_results(precision):
     scene, b = W.lst_workload(40_000, seed=13)
