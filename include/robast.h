@@ -223,7 +223,8 @@ typedef struct robast_trace_opts {
     const int32_t* variant_of_photon; /* device [n] or NULL (all variant 0) */
     int64_t first_photon_id;  /* photon i uses random stream id first_photon_id + i */
     double eps;               /* self-intersection epsilon; 0 = 1e-6 L_sys (FP32) / 1e-9 L_sys (FP64) */
-    int32_t block_size;       /* 64, 128 or 256; 0 = library choice (128) */
+    int32_t block_size;       /* 64, 128 or 256; 0 = library choice (FP32: 256, FP64, source
+                                 mode and counting build: 128) */
     int32_t blocks_per_sm;    /* 0 = as many as fit */
     unsigned long long* work_units; /* device [ROBAST_N_UNITS] or NULL; non-NULL runs the
                                        counting build of the kernel (block 128, slower) and
@@ -233,6 +234,12 @@ typedef struct robast_trace_opts {
                                  of ~4n bytes) so that each warp traces neighbouring rays; the
                                  results are identical either way */
     const robast_track_opts* track; /* host pointer or NULL: record photon tracks */
+    int32_t refill_min;       /* 0..32; 0 = library default (24).  A warp takes new photons for its
+                                 idle lanes once at least refill_min of its 32 lanes are idle, or all
+                                 of its lanes that still have work to do are.  Waiting keeps the
+                                 lanes of a warp on the same bounce of neighbouring photons (coherent
+                                 traversal) at the cost of idle lanes; 1 refills at once.  The
+                                 results do not depend on it */
 } robast_trace_opts;
 
 /* Work units counted when opts.work_units is set: ray-box tests, quadric root

@@ -81,7 +81,7 @@ class TraceOpts(ctypes.Structure):
                 ("variant_of_photon", ctypes.c_void_p), ("first_photon_id", ctypes.c_int64),
                 ("eps", ctypes.c_double), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("work_units", ctypes.c_void_p), ("coherent_order", ctypes.c_int32),
-                ("track", ctypes.POINTER(TrackOpts))]
+                ("track", ctypes.POINTER(TrackOpts)), ("refill_min", ctypes.c_int32)]
 
 N_UNITS = 12
 UNIT_NAMES = ("aabb", "sag", "newton", "aperture", "cylinder", "box", "hexwall", "reflect", "refract", "rough",
@@ -226,7 +226,7 @@ def _ptr(t):
 
 
 def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_size, blocks_per_sm, units=None,
-          coherent_order=0):
+          coherent_order=0, refill_min=0):
     o = TraceOpts()
     _lib.robast_trace_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -239,6 +239,7 @@ def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_s
     o.blocks_per_sm = int(blocks_per_sm)
     o.work_units = ctypes.c_void_p(units.data_ptr()) if units is not None else None
     o.coherent_order = int(coherent_order)
+    o.refill_min = int(refill_min)
     return o
 
 
@@ -262,7 +263,7 @@ def alloc_outputs(n: int, precision: int = 32, device="cuda", fields=None):
 def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32, max_bounces: int = 100,
           stream=None, variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None,
           block_size: int = 0, blocks_per_sm: int = 0, out: Optional[dict] = None, work_units=None,
-          coherent_order: int = 0, track=None):
+          coherent_order: int = 0, track=None, refill_min: int = 0):
     """robast_trace_ex on CUDA tensors; returns the dict of output tensors.
 
     work_units: optional CUDA int64 tensor [N_UNITS]; when given, the counting
@@ -288,7 +289,7 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
             raise RobastError("variant_of_photon: need a CUDA int32 tensor")
         vop = ctypes.c_void_p(variant_of_photon.data_ptr())
     o = _opts(precision, max_bounces, sp, vop, first_photon_id, eps, block_size, blocks_per_sm, work_units,
-              coherent_order)
+              coherent_order, refill_min)
     tr = None
     if track is not None:
         tr = TrackOpts(int(track["first"]), int(track["count"]), int(track["cap"]), track["points"].data_ptr(),
@@ -451,7 +452,7 @@ def sources_create(geom: Geometry, groups) -> Sources:
 
 def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, precision: int = 32,
                   max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
-                  eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0):
+                  eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0):
     """robast_trace_sources: trace every photon of the source groups in one launch.
 
     group_counts: CUDA int64 tensor [n_groups, 8], added to.  out: optional
@@ -471,7 +472,7 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
         tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
                           for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
     o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), None, first_photon_id, eps, block_size,
-              blocks_per_sm)
+              blocks_per_sm, refill_min=refill_min)
     _check(lib.robast_trace_sources(geom.handle, src.handle, ctypes.c_uint64(seed & (2**64 - 1)),
                                     ctypes.c_void_p(group_counts.data_ptr()),
                                     ctypes.byref(tout) if tout is not None else None, ctypes.byref(o)))

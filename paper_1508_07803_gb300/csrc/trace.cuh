@@ -122,7 +122,8 @@ struct TraceArgs {
     unsigned long long seed;
     long long first_id;
     int max_bounces;
-    int stage;  // stage tables in shared memory
+    int stage;       // stage tables in shared memory
+    int refill_min;  // a warp refills when this many lanes are idle (or all of its live lanes are)
     T eps;
     T newton_tol;
     double newton_tol64;
@@ -876,7 +877,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         // refill idle lanes: one atomic per warp per round
         const bool need = ph.i < 0 && !done;
         const unsigned m = __ballot_sync(FULL, need);
-        if (m) {
+        const unsigned live = __ballot_sync(FULL, !done);
+        if (m && (m == live || __popc(m) >= A.refill_min)) {
             const int leader = __ffs(m) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(m));

@@ -82,3 +82,39 @@ def test_valid_descriptor_without_gpu_fails_cleanly():
     with pytest.raises(robast.RobastError) as ei:
         robast.build_geometry(W.lst_scene())
     assert "robast error -3" in str(ei.value) or "robast error -4" in str(ei.value)
+
+
+_STRUCTS = {
+    "robast_surface_desc": "SurfaceDesc", "robast_material_desc": "MaterialDesc", "robast_medium_desc": "MediumDesc",
+    "robast_geom_desc": "GeomDesc", "robast_trace_out": "TraceOut", "robast_track_opts": "TrackOpts",
+    "robast_trace_opts": "TraceOpts", "robast_source_group": "SourceGroupDesc",
+}
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "robast.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(robast, pyname)
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("    return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(robast, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

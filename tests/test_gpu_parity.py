@@ -127,10 +127,10 @@ def test_photon_ids_make_results_independent_of_launch_shape():
     geom = robast.build_geometry(scene)
     o, d, w = _dev(b, 32)
     ref = to_numpy(robast.trace(geom, o, d, w, seed=3, block_size=128))
-    for bs, bps in ((64, 1), (256, 0), (128, 2)):
-        got = to_numpy(robast.trace(geom, o, d, w, seed=3, block_size=bs, blocks_per_sm=bps))
+    for bs, bps, rm in ((64, 1, 0), (256, 0, 0), (128, 2, 0), (128, 0, 1), (256, 0, 32), (64, 3, 7)):
+        got = to_numpy(robast.trace(geom, o, d, w, seed=3, block_size=bs, blocks_per_sm=bps, refill_min=rm))
         for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy"):
-            assert np.array_equal(ref[k], got[k]), (bs, k)
+            assert np.array_equal(ref[k], got[k]), (bs, rm, k)
     # a sub-range traced alone with first_photon_id equals the same photons of the full run
     lo, hi = 1234, 2345
     sub = to_numpy(robast.trace(geom, o[:, lo:hi].contiguous(), d[:, lo:hi].contiguous(), w[lo:hi].contiguous(),
@@ -223,6 +223,8 @@ def test_bad_arguments_raise():
         robast.trace(geom, o, d, w, precision=64, max_bounces=300)
     with pytest.raises(robast.RobastError, match="block_size"):
         robast.trace(geom, o, d, w, precision=64, block_size=96)
+    with pytest.raises(robast.RobastError, match="refill_min"):
+        robast.trace(geom, o, d, w, precision=64, refill_min=33)
     geom.close()
 
 
