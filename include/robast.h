@@ -355,6 +355,19 @@ int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64
 /* Number of parameters of g (ROBAST_N_PARAM x surfaces); 0 for NULL. */
 int robast_param_count(const robast_geom* g);
 
+/* What parameter p = surface * ROBAST_N_PARAM + slot of d_params means. */
+typedef struct robast_param_info {
+    int32_t surface; /* surface index (the order of robast_geom_desc.surfaces) */
+    int32_t variant; /* the surface's variant */
+    int32_t slot;    /* 0, 1 tilt about local x, y; 2..9 A1..A8; 10..15 P0r P0z P1r P1z P2r P2z */
+    int32_t active;  /* 1 if robast_trace_grad can give it a nonzero derivative: slots 0..9 of
+                        SAG mirrors, slots 10..15 of HEXCONE mirrors; 0 otherwise */
+} robast_param_info;
+
+/* Fills out[robast_param_count(g)] (HOST array, caller-owned).  0 or
+ * ROBAST_E_NULL. */
+int robast_param_layout(const robast_geom* g, robast_param_info* out);
+
 /*
  * Objective value (HOST *value) and, if d_params (device, FP64,
  * [robast_param_count]) is not NULL, d_params += d_obj * d value / d param.

@@ -483,6 +483,26 @@ N_PARAM = 16
 OBJECTIVES = {"msr": 0, "soft_ce": 1, "centroid_x": 2, "centroid_y": 3}
 
 
+class ParamInfo(ctypes.Structure):
+    _fields_ = [("surface", ctypes.c_int32), ("variant", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("active", ctypes.c_int32)]
+
+
+PARAM_SLOTS = ("tilt_x", "tilt_y", "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8",
+               "P0r", "P0z", "P1r", "P1z", "P2r", "P2z")
+
+
+def param_layout(geom: Geometry):
+    """robast_param_layout: per gradient parameter (surface, variant, slot name, active)."""
+    lib = load()
+    lib.robast_param_count.argtypes = [ctypes.c_void_p]
+    lib.robast_param_layout.argtypes = [ctypes.c_void_p, ctypes.POINTER(ParamInfo)]
+    n = lib.robast_param_count(geom.handle)
+    arr = (ParamInfo * max(n, 1))()
+    _check(lib.robast_param_layout(geom.handle, arr))
+    return [(p.surface, p.variant, PARAM_SLOTS[p.slot], bool(p.active)) for p in arr[:n]]
+
+
 def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed: int = 0, precision: int = 32,
                tau: float = 0.5e-3, d_obj: float = 1.0, grad=True, max_bounces: int = 100, stream=None,
                variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None, out=None):

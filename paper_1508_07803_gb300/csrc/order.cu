@@ -72,10 +72,22 @@ __device__ __forceinline__ unsigned ord_key(const T* o, long long n, long long i
     return (unsigned)((i >> ORD_CHUNK_BITS) * (ORD_G * ORD_G) + c);
 }
 
+constexpr int ORD_UNROLL = 8;  // photons per thread per iteration: independent atomics in flight
+
 template <typename T>
 __global__ void ord_hist(const T* o, long long n, const int* box, unsigned* hist) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        atomicAdd(hist + ord_key(o, n, i, box), 1u);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += ORD_UNROLL * stride) {
+        unsigned key[ORD_UNROLL];
+#pragma unroll
+        for (int j = 0; j < ORD_UNROLL; ++j) {
+            const long long i = i0 + j * stride;
+            key[j] = i < n ? ord_key(o, n, i, box) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int j = 0; j < ORD_UNROLL; ++j)
+            if (key[j] != 0xffffffffu) atomicAdd(hist + key[j], 1u);
+    }
 }
 
 // Exclusive prefix sum of nbins counts in three launches: per-tile sums,
@@ -135,9 +147,17 @@ __global__ void ord_tile_scan(unsigned* hist, long long nbins, const unsigned* t
 
 template <typename T>
 __global__ void ord_scatter(const T* o, long long n, const int* box, unsigned* offs, int* order) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned pos = atomicAdd(offs + ord_key(o, n, i, box), 1u);
-        order[pos] = (int)i;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += ORD_UNROLL * stride) {
+        unsigned pos[ORD_UNROLL];
+#pragma unroll
+        for (int j = 0; j < ORD_UNROLL; ++j) {
+            const long long i = i0 + j * stride;
+            pos[j] = i < n ? atomicAdd(offs + ord_key(o, n, i, box), 1u) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int j = 0; j < ORD_UNROLL; ++j)
+            if (pos[j] != 0xffffffffu) order[pos[j]] = (int)(i0 + j * stride);
     }
 }
 
@@ -159,7 +179,7 @@ static cudaError_t build_order_t(const T* o, long long n, void* scratch, int** o
     ord_init<<<1, 32, 0, s>>>(box);
     cudaError_t e = cudaMemsetAsync(hist, 0, nbins * 4, s);
     if (e != cudaSuccess) return e;
-    const int grid = sms * 4;
+    const int grid = sms * 8;
     ord_bounds<T><<<grid, 256, 0, s>>>(o, n, box);
     ord_hist<T><<<grid, 256, 0, s>>>(o, n, box, hist);
     ord_tile_sums<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(hist, nbins, tiles);

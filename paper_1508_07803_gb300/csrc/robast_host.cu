@@ -54,6 +54,7 @@ struct robast_geom {
     const float* grec32 = nullptr;    // per surface: d rows / d tilt_x, d rows / d tilt_y
     const double* grec64 = nullptr;
     const int* surf_var = nullptr;    // variant of each surface
+    std::vector<int> h_var, h_flags;  // host copies: variant, shape | role << 4 of each surface
     size_t smem32 = 0, smem64 = 0;  // bytes to stage each precision's tables
     int num_sms = 0;
     // per-launch work counters (a ring, so launches on several streams do not share one)
@@ -753,6 +754,9 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd + bm32;
     g->n_surf = ns;
     g->n_var = nv;
+    g->h_var = surf_var;
+    g->h_flags.resize(ns);
+    for (int i = 0; i < ns; ++i) g->h_flags[i] = d->surfaces[i].shape | (d->surfaces[i].role << 4);
     g->n_mat = d->n_materials;
     g->n_med = d->n_media;
     g->n_nodes = (int)nodes.size();
@@ -1092,6 +1096,23 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
 
 // -------------------------------------------------------------- gradients
 extern "C" int robast_param_count(const robast_geom* g) { return g ? g->n_surf * ROBAST_N_PARAM : 0; }
+
+extern "C" int robast_param_layout(const robast_geom* g, robast_param_info* out) {
+    if (!g || !out) return fail(ROBAST_E_NULL, "robast_param_layout: NULL argument");
+    for (int s = 0; s < g->n_surf; ++s) {
+        const int shape = g->h_flags[s] & 15, role = (g->h_flags[s] >> 4) & 15;
+        const bool mirror = role == ROBAST_ROLE_MIRROR;
+        for (int k = 0; k < ROBAST_N_PARAM; ++k) {
+            robast_param_info& p = out[(size_t)s * ROBAST_N_PARAM + k];
+            p.surface = s;
+            p.variant = g->h_var[s];
+            p.slot = k;
+            // the gradient pass differentiates SAG mirrors (tilts, A1..A8) and HEXCONE mirrors (Bezier points)
+            p.active = mirror && ((shape == ROBAST_SHAPE_SAG && k < 10) || (shape == ROBAST_SHAPE_HEXCONE && k >= 10));
+        }
+    }
+    return 0;
+}
 
 template <typename T>
 static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl, int64_t n, uint64_t seed,

@@ -87,7 +87,7 @@ def test_valid_descriptor_without_gpu_fails_cleanly():
 _STRUCTS = {
     "robast_surface_desc": "SurfaceDesc", "robast_material_desc": "MaterialDesc", "robast_medium_desc": "MediumDesc",
     "robast_geom_desc": "GeomDesc", "robast_trace_out": "TraceOut", "robast_track_opts": "TrackOpts",
-    "robast_trace_opts": "TraceOpts", "robast_source_group": "SourceGroupDesc",
+    "robast_trace_opts": "TraceOpts", "robast_source_group": "SourceGroupDesc", "robast_param_info": "ParamInfo",
 }
 
 

@@ -126,3 +126,24 @@ def test_batched_dishes_gradient_matches_oracle():
     mask = np.abs(rg).sum(axis=1) > 0
     assert mask.sum() > 100
     assert np.max(_rel(g[mask], rg[mask])) < 1e-8
+
+
+def test_param_layout_marks_the_differentiated_slots():
+    scene, _ = W.lst_workload(10, seed=0, angles_deg=(0.0,))
+    geom = robast.build_geometry(scene)
+    lay = robast.param_layout(geom)
+    assert len(lay) == len(scene.surfaces) * robast.N_PARAM
+    for k, (sid, var, slot, active) in enumerate(lay):
+        assert sid == k // robast.N_PARAM and var == 0 and slot == robast.PARAM_SLOTS[k % robast.N_PARAM]
+        s = scene.surfaces[sid]
+        want = s.role == "mirror" and ((s.shape == "sag" and k % 16 < 10) or (s.shape == "hexcone" and k % 16 >= 10))
+        assert active == want, (sid, slot)
+    assert sum(a for *_, a in lay) == 10 * sum(1 for s in scene.surfaces if s.role == "mirror" and s.shape == "sag")
+    geom.close()
+    cone = W.cone_scene(n_variants=3, seed=1)
+    geom = robast.build_geometry(cone)
+    lay = robast.param_layout(geom)
+    assert {v for _, v, _, _ in lay} == {0, 1, 2}
+    act = [(sid, slot) for sid, _, slot, a in lay if a]
+    assert act and all(cone.surfaces[sid].shape == "hexcone" and slot.startswith("P") for sid, slot in act)
+    geom.close()
