@@ -1,14 +1,23 @@
 // Coherent processing order for the trace: a counting sort of the photon
-// indices by (chunk of 4M photons of the input order, cell of the origin in a
-// 512 x 512 grid over the origins' x-y bounding box).  Rays of one warp then
-// start close together (and, within a chunk of the caller's order, usually
-// share a direction), so they walk the same BVH nodes and hit the same
-// surfaces and the warp's lanes diverge far less.  The reordered loads and
-// stores touch scattered sectors (more DRAM traffic than the I/O itself), but
-// on the dish workload the divergence saved outweighs it: measured over grids
-// of 16..1024 cells and chunks of 2^16..2^26 photons, this setting gave the
-// fastest step.  Results do not depend on the order: every photon keeps its
-// index, its random stream and its output slot.
+// indices by (chunk of 2^20 photons of the input order, cell of the origin in
+// a 128 x 128 grid over the origins' x-y bounding box).  Rays of one warp
+// then start close together (and, within a chunk of the caller's order,
+// usually share a direction), so they walk the same BVH nodes and hit the
+// same surfaces and the warp's lanes diverge far less.  A chunk's inputs
+// (28 MB in FP32) stay in L2 while the trace reads them in cell order, so the
+// reordered loads cost little DRAM traffic.  Results do not depend on the
+// order: every photon keeps its index, its random stream and its output slot.
+//
+// Chunk size and grid were swept on the dish workload (chunks 2^17..2^23,
+// grids 64..1024 cells per axis): 2^20 photons per chunk was fastest (the
+// trace's DRAM reads fall from 24 GB to 2 GB per 5e7 photons against 2^22),
+// and grids of 128..512 cells per axis traced within 1% of each other.
+//
+// The sort is one pass of a block-local counting sort: every block of
+// 2^ORD_TILE_BITS photons (one tile of a chunk) counts its photons per cell
+// in shared memory; the counts, laid out [chunk][cell][tile of the chunk],
+// are scanned once; a second pass places each photon at its block's offset
+// for its cell (shared-memory atomics only).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,8 +25,12 @@
 
 namespace robast {
 
-constexpr int ORD_G = 512;            // grid cells per axis (swept: 16..1024; 512 fastest)
-constexpr int ORD_CHUNK_BITS = 22;    // chunks of 4M photons keep the caller's order (swept 16..26)
+constexpr int ORD_G = 128;                // grid cells per axis
+constexpr int ORD_CELLS = ORD_G * ORD_G;  // 16384 cells: 64 KB of counters per block
+constexpr int ORD_CHUNK_BITS = 20;        // chunks of 2^20 photons keep the caller's order
+constexpr int ORD_TILE_BITS = 16;         // photons per block
+constexpr int ORD_TILES_PER_CHUNK = 1 << (ORD_CHUNK_BITS - ORD_TILE_BITS);
+constexpr int ORD_BLOCK = 1024;
 
 __device__ __forceinline__ int ordered_int(float f) {
     const int i = __float_as_int(f);
@@ -58,41 +71,63 @@ __global__ void ord_bounds(const T* o, long long n, int* box) {
     }
 }
 
-template <typename T>
-__device__ __forceinline__ unsigned ord_key(const T* o, long long n, long long i, const int* box) {
+struct OrdMap {
+    float x0, sx, y0, sy;  // cell = (coordinate - origin) * scale
+};
+
+__device__ __forceinline__ OrdMap ord_map(const int* box) {
     const float x0 = unordered_float(box[0]), x1 = unordered_float(box[1]);
     const float y0 = unordered_float(box[2]), y1 = unordered_float(box[3]);
-    const float fx = x1 > x0 ? ((float)o[i] - x0) / (x1 - x0) : 0.0f;
-    const float fy = y1 > y0 ? ((float)o[n + i] - y0) / (y1 - y0) : 0.0f;
-    int cx = (int)(fx * ORD_G), cy = (int)(fy * ORD_G);
-    cx = cx < 0 ? 0 : (cx >= ORD_G ? ORD_G - 1 : cx);
-    cy = cy < 0 ? 0 : (cy >= ORD_G ? ORD_G - 1 : cy);
-    // serpentine rows keep consecutive cells adjacent
-    const int c = cy * ORD_G + ((cy & 1) ? ORD_G - 1 - cx : cx);
-    return (unsigned)((i >> ORD_CHUNK_BITS) * (ORD_G * ORD_G) + c);
+    return OrdMap{x0, x1 > x0 ? (float)ORD_G / (x1 - x0) : 0.0f, y0, y1 > y0 ? (float)ORD_G / (y1 - y0) : 0.0f};
 }
 
-constexpr int ORD_UNROLL = 8;  // photons per thread per iteration: independent atomics in flight
-
+// cell of photon i; serpentine rows keep consecutive cells adjacent
 template <typename T>
-__global__ void ord_hist(const T* o, long long n, const int* box, unsigned* hist) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += ORD_UNROLL * stride) {
-        unsigned key[ORD_UNROLL];
-#pragma unroll
-        for (int j = 0; j < ORD_UNROLL; ++j) {
-            const long long i = i0 + j * stride;
-            key[j] = i < n ? ord_key(o, n, i, box) : 0xffffffffu;
-        }
-#pragma unroll
-        for (int j = 0; j < ORD_UNROLL; ++j)
-            if (key[j] != 0xffffffffu) atomicAdd(hist + key[j], 1u);
+__device__ __forceinline__ int ord_cell(const T* o, long long n, long long i, const OrdMap& m) {
+    int cx = (int)(((float)o[i] - m.x0) * m.sx), cy = (int)(((float)o[n + i] - m.y0) * m.sy);
+    cx = cx < 0 ? 0 : (cx >= ORD_G ? ORD_G - 1 : cx);
+    cy = cy < 0 ? 0 : (cy >= ORD_G ? ORD_G - 1 : cy);
+    return cy * ORD_G + ((cy & 1) ? ORD_G - 1 - cx : cx);
+}
+
+// Pass 1: per-block cell counts, to counts[(chunk * CELLS + cell) * TILES + tile].
+// Blocks past n (in the last chunk) write zeros.
+template <typename T>
+__global__ void __launch_bounds__(ORD_BLOCK) ord_count(const T* o, long long n, const int* box, unsigned* counts) {
+    extern __shared__ unsigned h[];
+    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) h[c] = 0;
+    __syncthreads();
+    const OrdMap m = ord_map(box);
+    const long long b0 = (long long)blockIdx.x << ORD_TILE_BITS;
+    const long long b1 = min(n, b0 + (1LL << ORD_TILE_BITS));
+    for (long long i = b0 + threadIdx.x; i < b1; i += ORD_BLOCK) atomicAdd(&h[ord_cell(o, n, i, m)], 1u);
+    __syncthreads();
+    const long long chunk = blockIdx.x / ORD_TILES_PER_CHUNK, tile = blockIdx.x % ORD_TILES_PER_CHUNK;
+    unsigned* dst = counts + chunk * (long long)ORD_CELLS * ORD_TILES_PER_CHUNK + tile;
+    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) dst[(long long)c * ORD_TILES_PER_CHUNK] = h[c];
+}
+
+// Pass 2: each photon at its block's running offset for its cell.
+template <typename T>
+__global__ void __launch_bounds__(ORD_BLOCK) ord_place(const T* o, long long n, const int* box, const unsigned* offs,
+                                                      int* order) {
+    extern __shared__ unsigned h[];
+    const long long chunk = blockIdx.x / ORD_TILES_PER_CHUNK, tile = blockIdx.x % ORD_TILES_PER_CHUNK;
+    const unsigned* src = offs + chunk * (long long)ORD_CELLS * ORD_TILES_PER_CHUNK + tile;
+    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) h[c] = src[(long long)c * ORD_TILES_PER_CHUNK];
+    __syncthreads();
+    const OrdMap m = ord_map(box);
+    const long long b0 = (long long)blockIdx.x << ORD_TILE_BITS;
+    const long long b1 = min(n, b0 + (1LL << ORD_TILE_BITS));
+    for (long long i = b0 + threadIdx.x; i < b1; i += ORD_BLOCK) {
+        const unsigned pos = atomicAdd(&h[ord_cell(o, n, i, m)], 1u);
+        order[pos] = (int)i;
     }
 }
 
 // Exclusive prefix sum of nbins counts in three launches: per-tile sums,
 // a scan of the tile sums, per-tile scans with the tile offset.
-constexpr int ORD_TILE = 1024;  // bins per tile (one block of 1024 threads)
+constexpr int ORD_TILE = 1024;  // counts per scan tile (one block of 1024 threads)
 
 __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* total) {
     __shared__ unsigned warp_sums[32];
@@ -145,47 +180,41 @@ __global__ void ord_tile_scan(unsigned* hist, long long nbins, const unsigned* t
     if (k < nbins) hist[k] = tiles[blockIdx.x] + ex;
 }
 
-template <typename T>
-__global__ void ord_scatter(const T* o, long long n, const int* box, unsigned* offs, int* order) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += ORD_UNROLL * stride) {
-        unsigned pos[ORD_UNROLL];
-#pragma unroll
-        for (int j = 0; j < ORD_UNROLL; ++j) {
-            const long long i = i0 + j * stride;
-            pos[j] = i < n ? atomicAdd(offs + ord_key(o, n, i, box), 1u) : 0xffffffffu;
-        }
-#pragma unroll
-        for (int j = 0; j < ORD_UNROLL; ++j)
-            if (pos[j] != 0xffffffffu) order[pos[j]] = (int)(i0 + j * stride);
-    }
+// blocks of the counting passes: whole chunks, so that the count layout is regular
+static long long ord_blocks(long long n) {
+    const long long chunks = (n + (1LL << ORD_CHUNK_BITS) - 1) >> ORD_CHUNK_BITS;
+    return chunks * ORD_TILES_PER_CHUNK;
 }
 
+static long long ord_round(long long bytes) { return (bytes + 255) / 256 * 256; }
+
 long long order_scratch_bytes(long long n) {
-    const long long nbins = ((n - 1) >> ORD_CHUNK_BITS) * (long long)(ORD_G * ORD_G) + ORD_G * ORD_G;
+    const long long nbins = ord_blocks(n) * ORD_CELLS;
     const long long ntiles = (nbins + ORD_TILE - 1) / ORD_TILE;
-    return 16 + nbins * 4 + n * 4 + ntiles * 4 + 1024;
+    return 256 + ord_round(nbins * 4) + ord_round(n * 4) + ntiles * 4 + 1024;
 }
 
 template <typename T>
 static cudaError_t build_order_t(const T* o, long long n, void* scratch, int** order_out, int sms, cudaStream_t s) {
-    const long long nbins = ((n - 1) >> ORD_CHUNK_BITS) * (long long)(ORD_G * ORD_G) + ORD_G * ORD_G;
+    const long long nblk = ord_blocks(n);
+    const long long nbins = nblk * ORD_CELLS;
+    const long long ntiles = (nbins + ORD_TILE - 1) / ORD_TILE;
     unsigned char* b = static_cast<unsigned char*>(scratch);
     int* box = reinterpret_cast<int*>(b);
-    unsigned* hist = reinterpret_cast<unsigned*>(b + 16);
-    int* order = reinterpret_cast<int*>(b + 16 + ((nbins * 4 + 255) / 256) * 256);
-    const long long ntiles = (nbins + ORD_TILE - 1) / ORD_TILE;
-    unsigned* tiles = reinterpret_cast<unsigned*>(b + 16 + ((nbins * 4 + 255) / 256) * 256 + ((n * 4 + 255) / 256) * 256);
-    ord_init<<<1, 32, 0, s>>>(box);
-    cudaError_t e = cudaMemsetAsync(hist, 0, nbins * 4, s);
+    unsigned* counts = reinterpret_cast<unsigned*>(b + 256);
+    int* order = reinterpret_cast<int*>(b + 256 + ord_round(nbins * 4));
+    unsigned* tiles = reinterpret_cast<unsigned*>(b + 256 + ord_round(nbins * 4) + ord_round(n * 4));
+    const int smem = ORD_CELLS * (int)sizeof(unsigned);
+    cudaError_t e = cudaFuncSetAttribute(ord_count<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ord_place<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int grid = sms * 8;
-    ord_bounds<T><<<grid, 256, 0, s>>>(o, n, box);
-    ord_hist<T><<<grid, 256, 0, s>>>(o, n, box, hist);
-    ord_tile_sums<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(hist, nbins, tiles);
+    ord_init<<<1, 32, 0, s>>>(box);
+    ord_bounds<T><<<sms * 4, 256, 0, s>>>(o, n, box);
+    ord_count<T><<<(unsigned)nblk, ORD_BLOCK, smem, s>>>(o, n, box, counts);
+    ord_tile_sums<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(counts, nbins, tiles);
     ord_scan_tiles<<<1, ORD_TILE, 0, s>>>(tiles, (int)ntiles);
-    ord_tile_scan<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(hist, nbins, tiles);
-    ord_scatter<T><<<grid, 256, 0, s>>>(o, n, box, hist, order);
+    ord_tile_scan<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(counts, nbins, tiles);
+    ord_place<T><<<(unsigned)nblk, ORD_BLOCK, smem, s>>>(o, n, box, counts, order);
     *order_out = order;
     return cudaGetLastError();
 }

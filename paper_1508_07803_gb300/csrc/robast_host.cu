@@ -879,7 +879,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     // coherent processing order (stream-ordered scratch, so concurrent launches do not share it)
     void* ord_scratch = nullptr;
     const bool want_order =
-        !src && n < (1LL << 31) && (o.coherent_order > 0 || (o.coherent_order == 0 && n >= 65536));
+        !src && n > 0 && n < (1LL << 31) && (o.coherent_order > 0 || (o.coherent_order == 0 && n >= 65536));
     if (want_order) {
         CU(cudaMallocAsync(&ord_scratch, (size_t)order_scratch_bytes(n), s), "robast_trace: order scratch");
         int* order = nullptr;
