@@ -333,16 +333,25 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
                        "timing": "host wall clock around the synchronous call (value returned to the host)"}}
 
 
+TRAFFIC_SOURCES = ("trace.cuh", "order.cu")  # the kernel and the processing order that shapes its DRAM traffic
+
+
+def traffic_source_hash():
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1508_07803_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_from_profile(n_photons):
     """DRAM bytes of the trace kernel from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    taken on the current kernel and ordering sources; else None."""
     path = os.path.join(ROOT, "profiles", "trace_kernel_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         meta = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_1508_07803_gb300", "csrc", "trace.cuh"), "rb").read()
-        if meta.get("trace_cuh_sha256") != hashlib.sha256(src).hexdigest():
+        if meta.get("sources_sha256") != traffic_source_hash():
             return None
         return meta["dram_bytes_per_photon"] * n_photons
     except Exception:
@@ -472,7 +481,7 @@ def main():
     achieved = flops / (kern_avg_ms * 1e-3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak32, "traffic": traffic_from_profile(N),
-            "kernel": "robast::trace_kernel<float,128>", "kernel_ms": kern_avg_ms,
+            "kernel": "robast::trace_kernel<float,256> (with the coherent-order sort)", "kernel_ms": kern_avg_ms,
             "flops_per_launch": flops, "work_units_per_launch": fp32["units"],
             "peak_source": "FFMA throughput probe robast_measure_alu_peak on this GPU (measured)"}
 
