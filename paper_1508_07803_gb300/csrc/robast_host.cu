@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "../../include/robast.h"
 #include "launch.h"
 
@@ -1245,6 +1247,9 @@ constexpr int kSel = 2048;         // values the device selects among
 constexpr int kScanBlock = 1024;
 constexpr int kRes = 8;            // per window: N, cx, cy, bins / range^2, fast, delta, -, -
 constexpr int kUnroll = 4;         // photons in flight per thread
+constexpr long long kCandPerWindow = 1LL << 20;  // candidate list capacity per window
+constexpr long long kCandTotal = 1LL << 23;      // ... and over all windows of a call
+namespace cg = cooperative_groups;
 
 // blocks per window of the per-photon passes (robast_psf and robast_psf_noalloc alike)
 int psf_blocks_per_window(int nw, long long maxcount) {
@@ -1253,6 +1258,7 @@ int psf_blocks_per_window(int nw, long long maxcount) {
 
 struct Win {
     long long start, count;
+    long long cand_off, cand_slice;  // this window's part of the candidate list: one slice per block (robast_psf)
 };
 
 // unevaluated float pair hi + lo; two-sum (Knuth) keeps every addition exact
@@ -1421,7 +1427,8 @@ __device__ __forceinline__ double psf_r2(T x, T y, const double* R) {
 }
 
 // Bin of each photon of one window, kUnroll photons in flight per thread;
-// body(bin, x, y) runs for the detected ones.  FAST: FP32 bins (psf_fbin).
+// body(bin, x, y, i) runs for the detected ones (i: photon index).  FAST:
+// FP32 bins (psf_fbin).
 template <bool FAST, typename T, typename F>
 __device__ __forceinline__ void psf_loop(const uint8_t* st, const T* fxy, long long ld, const Win& w, const double* R,
                                          F body) {
@@ -1449,7 +1456,7 @@ __device__ __forceinline__ void psf_loop(const uint8_t* st, const T* fxy, long l
                     b = psf_fbin((float)x[j], (float)y[j], cxf, cyf, sf);
                 else
                     b = psf_bin(psf_r2(x[j], y[j], R), R[3]);
-                body(b, x[j], y[j]);
+                body(b, x[j], y[j], w.start + k0 + j * stride);
             }
     }
 }
@@ -1475,19 +1482,6 @@ __device__ __forceinline__ int psf_sub(double r2, double a, double s2) {
     return f >= (double)kSub ? kSub - 1 : (int)f;
 }
 
-// Exact r^2 and its sub-bin, for the few photons of the kept bins: out of
-// line, so that the compiler cannot turn the rare branch into predicated
-// FP64 work on every photon.
-struct Cand {
-    double r2;
-    int sub;
-};
-template <typename T>
-__device__ __noinline__ Cand psf_cand(T x, T y, const double* R, double a, double s2) {
-    const double r2 = psf_r2(x, y, R);
-    return Cand{r2, psf_sub(r2, a, s2)};
-}
-
 template <typename T>
 __global__ void psf_hist(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
                          unsigned long long* hist) {
@@ -1495,7 +1489,7 @@ __global__ void psf_hist(const uint8_t* st, const T* fxy, long long ld, const Wi
     for (int k = threadIdx.x; k <= kBins; k += blockDim.x) h[k] = 0;
     __syncthreads();
     const Win w = win[blockIdx.y];
-    psf_for_bins(st, fxy, ld, w, res + kRes * blockIdx.y, [&](int b, T, T) { atomicAdd(&h[b], 1u); });
+    psf_for_bins(st, fxy, ld, w, res + kRes * blockIdx.y, [&](int b, T, T, long long) { atomicAdd(&h[b], 1u); });
     __syncthreads();
     unsigned long long* H = hist + (size_t)blockIdx.y * (kBins + 1);
     for (int k = threadIdx.x; k <= kBins; k += blockDim.x)
@@ -1514,7 +1508,7 @@ __global__ void psf_collect(const uint8_t* st, const T* fxy, long long ld, const
     double* out = vals + sel[4 * blockIdx.y + 2];
     const long long c = cap[blockIdx.y];
     unsigned long long* cw = cnt + blockIdx.y;
-    psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y) {
+    psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y, long long) {
         if (b >= lo && b <= hi) {
             const unsigned long long j = atomicAdd(cw, 1ull);
             if ((long long)j < c) out[j] = psf_r2(x, y, R);
@@ -1578,7 +1572,7 @@ __device__ void block_find_rank(const unsigned long long* H, int nb, long long k
 }
 
 // Round 1 decision: rank k, bin b, bins lo..hi kept, the sub-bin interval.
-__global__ void psf_pick1(const unsigned long long* hist, const double* res, Sel* sel) {
+__global__ void psf_pick1(const unsigned long long* hist, const double* res, const Win* win, int nslice, Sel* sel) {
     const int w = blockIdx.x;
     const double* R = res + kRes * w;
     const long long N = (long long)R[0];
@@ -1615,6 +1609,11 @@ __global__ void psf_pick1(const unsigned long long* hist, const double* res, Sel
     z.hi = hi;
     z.rank1 = k - below1;
     z.cap1 = cap1;
+    if (cap1 > win[w].cand_slice * nslice) {  // more kept photons than the candidate list holds: host fallback
+        z.status = 1;
+        sel[w] = z;
+        return;
+    }
     // exact r^2 of the kept photons lies in [(lo - delta) / scale, (hi + 1 + delta) / scale]
     const double scale = R[3];
     z.a = fmax(0.0, ((double)lo - 0.5) / scale);
@@ -1623,20 +1622,87 @@ __global__ void psf_pick1(const unsigned long long* hist, const double* res, Sel
     sel[w] = z;
 }
 
-// Round 2: sub-bin histogram of the exact r^2 of the kept photons.
+// Compaction: the index of every kept photon (bins lo..hi) appended to the
+// block's slice of the window's candidate list (a counter per block, one
+// atomic per group of lanes that keep one).  Only FP32 work per photon; the
+// kept photons' FP64 r^2 follows over the short list, where every lane of a
+// warp has one.
 template <typename T>
-__global__ void psf_hist2(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
-                          const Sel* sel, unsigned long long* hist2) {
+__global__ void psf_compact(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
+                            const Sel* sel, long long* cand, unsigned long long* cand_n) {
+    const Win w = win[blockIdx.y];
+    const Sel S = sel[blockIdx.y];
+    if (S.status != 0) return;
+    long long* out = cand + w.cand_off + blockIdx.x * w.cand_slice;
+    unsigned long long* cn = cand_n + (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    psf_for_bins(st, fxy, ld, w, res + kRes * blockIdx.y, [&](int b, T, T, long long i) {
+        if (b >= S.lo && b <= S.hi) {
+            cg::coalesced_group g = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (g.thread_rank() == 0) base = atomicAdd(cn, (unsigned long long)g.size());
+            base = g.shfl(base, 0);
+            const unsigned long long j = base + g.thread_rank();
+            if ((long long)j < w.cand_slice) out[j] = i;
+        }
+    });
+}
+
+// One warp per window: a slice that overflowed sends the window to the host
+// fallback; otherwise the slices must hold exactly the cap1 kept photons.
+__global__ void psf_cand_check(const Win* win, const unsigned long long* cand_n, int nslice, Sel* sel) {
+    const int w = blockIdx.x;
+    if (sel[w].status != 0) return;
+    unsigned long long tot = 0;
+    int over = 0;
+    for (int b = threadIdx.x; b < nslice; b += 32) {
+        const unsigned long long c = cand_n[(size_t)w * nslice + b];
+        tot += c;
+        over |= c > (unsigned long long)win[w].cand_slice;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, off);
+        over |= __shfl_xor_sync(0xffffffffu, over, off);
+    }
+    if (threadIdx.x == 0) sel[w].status = over ? 1 : ((long long)tot != sel[w].cap1 ? 3 : 0);
+}
+
+// Entry t of the window's candidate list (slice t / cand_slice), if filled.
+__device__ __forceinline__ bool psf_cand_at(const Win& w, const unsigned long long* cn, long long t) {
+    const long long b = t / w.cand_slice, j = t - b * w.cand_slice;
+    return j < (long long)cn[b];
+}
+
+// The kept photons' exact FP64 r^2, over the candidate list.
+template <typename T>
+__global__ void psf_cand_r2(const T* fxy, long long ld, const Win* win, const double* res, const Sel* sel,
+                            const long long* cand, const unsigned long long* cand_n, int nslice, double* r2) {
+    const Sel S = sel[blockIdx.y];
+    if (S.status != 0) return;
+    const Win w = win[blockIdx.y];
+    const double* R = res + kRes * blockIdx.y;
+    const unsigned long long* cn = cand_n + (size_t)blockIdx.y * nslice;
+    const long long n = w.cand_slice * nslice;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        if (psf_cand_at(w, cn, t)) {
+            const long long i = cand[w.cand_off + t];
+            r2[w.cand_off + t] = psf_r2(fxy[i], fxy[ld + i], R);
+        }
+}
+
+// Round 2: sub-bin histogram of the kept photons' exact r^2.
+__global__ void psf_hist2(const Win* win, const Sel* sel, const double* r2, const unsigned long long* cand_n,
+                          int nslice, unsigned long long* hist2) {
     __shared__ unsigned int h[kSub];
     for (int k = threadIdx.x; k < kSub; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    const Win w = win[blockIdx.y];
     const Sel S = sel[blockIdx.y];
-    const double* R = res + kRes * blockIdx.y;
-    if (S.status == 0)
-        psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y) {
-            if (b >= S.lo && b <= S.hi) atomicAdd(&h[psf_cand(x, y, R, S.a, S.s2).sub], 1u);
-        });
+    const Win w = win[blockIdx.y];
+    if (S.status == 0) {
+        const unsigned long long* cn = cand_n + (size_t)blockIdx.y * nslice;
+        const long long n = w.cand_slice * nslice;
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+            if (psf_cand_at(w, cn, t)) atomicAdd(&h[psf_sub(r2[w.cand_off + t], S.a, S.s2)], 1u);
+    }
     __syncthreads();
     unsigned long long* H = hist2 + (size_t)blockIdx.y * kSub;
     for (int k = threadIdx.x; k < kSub; k += blockDim.x)
@@ -1664,29 +1730,27 @@ __global__ void psf_pick2(const unsigned long long* hist2, Sel* sel) {
 
 // The exact r^2 of the sub-bin's photons (at most kSel kept), their count
 // and the bit patterns of their minimum (stored complemented) and maximum.
-template <typename T>
-__global__ void psf_collect2(const uint8_t* st, const T* fxy, long long ld, const Win* win, const double* res,
-                             const Sel* sel, double* vals2, unsigned long long* cnt2, unsigned long long* mm) {
-    const Win w = win[blockIdx.y];
+__global__ void psf_collect2(const Win* win, const Sel* sel, const double* r2, const unsigned long long* cand_n,
+                             int nslice, double* vals2, unsigned long long* cnt2, unsigned long long* mm) {
     const Sel S = sel[blockIdx.y];
     if (S.status != 0) return;
-    const double* R = res + kRes * blockIdx.y;
+    const Win w = win[blockIdx.y];
     double* out = vals2 + (size_t)blockIdx.y * kSel;
     unsigned long long* cw = cnt2 + blockIdx.y;
     unsigned long long* m = mm + 2 * blockIdx.y;
-    psf_for_bins(st, fxy, ld, w, R, [&](int b, T x, T y) {
-        if (b >= S.lo && b <= S.hi) {
-            const Cand c = psf_cand(x, y, R, S.a, S.s2);
-            const double r2 = c.r2;
-            if (c.sub == S.sub) {
-                const unsigned long long j = atomicAdd(cw, 1ull);
-                if (j < (unsigned long long)kSel) out[j] = r2;
-                const unsigned long long bits = (unsigned long long)__double_as_longlong(r2);  // r2 >= +0
-                atomicMax(m, ~bits);
-                atomicMax(m + 1, bits);
-            }
+    const unsigned long long* cn = cand_n + (size_t)blockIdx.y * nslice;
+    const long long n = w.cand_slice * nslice;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        if (!psf_cand_at(w, cn, t)) continue;
+        const double v = r2[w.cand_off + t];
+        if (psf_sub(v, S.a, S.s2) == S.sub) {
+            const unsigned long long k = atomicAdd(cw, 1ull);
+            if (k < (unsigned long long)kSel) out[k] = v;
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(v);  // r2 >= +0
+            atomicMax(m, ~bits);
+            atomicMax(m + 1, bits);
         }
-    });
+    }
 }
 
 // Final selection by counting: the value v with #(< v) <= rank2 < #(<= v).
@@ -1741,8 +1805,20 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
     long long maxcount = 0;
     for (int w = 0; w < nw; ++w) maxcount = std::max(maxcount, counts[w]);
     const int bx = psf_blocks_per_window(nw, maxcount);
+    // candidate list: per window about min(count, kCandPerWindow, kCandTotal / nw) entries, in bx
+    // slices (one per block of the compaction pass)
+    std::vector<Win> hw(nw);
+    long long ncand = 0, maxcap = 0;
+    for (int w = 0; w < nw; ++w) {
+        const long long cap = std::min({counts[w], kCandPerWindow, std::max(1LL, kCandTotal / nw)});
+        const long long slice = std::max(1LL, (cap + bx - 1) / bx);
+        hw[w] = Win{starts[w], counts[w], ncand, slice};
+        ncand += slice * bx;
+        maxcap = std::max(maxcap, slice * bx);
+    }
     // scratch: win | part | {res, out, stat, sel} (read back together) |
-    //          {hist, hist2, cnt2, mm} (cleared together) | vals2 | fallback: sel4, cnt, cap, vals
+    //          {hist, hist2, cnt2, mm, cand_n} (cleared together) | vals2 | cand | cand_r2 |
+    //          fallback: sel4, cnt, cap, vals
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         const size_t at = off;
@@ -1754,17 +1830,16 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
                  o_stat = carve((size_t)nw * 4), o_sel = carve((size_t)nw * sizeof(Sel));
     const size_t back_bytes = off - o_back;
     const size_t o_zero = off, o_hist = carve((size_t)nw * (kBins + 1) * 8), o_hist2 = carve((size_t)nw * kSub * 8),
-                 o_cnt2 = carve((size_t)nw * 8), o_mm = carve((size_t)nw * 16);
+                 o_cnt2 = carve((size_t)nw * 8), o_mm = carve((size_t)nw * 16), o_candn = carve((size_t)nw * bx * 8);
     const size_t zero_bytes = off - o_zero;
     const size_t o_vals2 = carve((size_t)nw * kSel * 8);
+    const size_t o_cand = carve((size_t)ncand * 8), o_r2 = carve((size_t)ncand * 8);
     const size_t o_sel4 = carve((size_t)nw * 32), o_cnt = carve((size_t)nw * 8), o_cap = carve((size_t)nw * 8);
     const size_t o_vals = off;
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = grow(&g->scratch, &g->scratch_bytes, o_vals + 4096 * 8, "robast_psf");
     if (rc) return rc;
     unsigned char* b = static_cast<unsigned char*>(g->scratch);
-    std::vector<Win> hw(nw);
-    for (int w = 0; w < nw; ++w) hw[w] = Win{starts[w], counts[w]};
     CU(cudaMemcpyAsync(b + o_win, hw.data(), nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
     CU(cudaMemsetAsync(b + o_zero, 0, zero_bytes, s), "robast_psf: clear");
     const Win* dwin = reinterpret_cast<const Win*>(b + o_win);
@@ -1772,15 +1847,21 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
     double* res = reinterpret_cast<double*>(b + o_res);
     Sel* sel = reinterpret_cast<Sel*>(b + o_sel);
     auto u64 = [&](size_t o) { return reinterpret_cast<unsigned long long*>(b + o); };
+    long long* cand = reinterpret_cast<long long*>(b + o_cand);
+    double* cand_r2 = reinterpret_cast<double*>(b + o_r2);
     const dim3 grid(bx, nw);
+    const dim3 cgrid((unsigned)std::max(1LL, std::min<long long>(std::max(1, kPartBlocks / nw), (maxcap + 1023) / 1024)), nw);
     psf_sums<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, part);
     psf_finish<<<nw, 32, 0, s>>>(part, bx, sizeof(T) == 4 ? 1 : 0, res);
     psf_hist<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, u64(o_hist));
-    psf_pick1<<<nw, kScanBlock, 0, s>>>(u64(o_hist), res, sel);
-    psf_hist2<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, sel, u64(o_hist2));
+    psf_pick1<<<nw, kScanBlock, 0, s>>>(u64(o_hist), res, dwin, bx, sel);
+    psf_compact<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, sel, cand, u64(o_candn));
+    psf_cand_check<<<nw, 32, 0, s>>>(dwin, u64(o_candn), bx, sel);
+    psf_cand_r2<T><<<cgrid, kRedBlock, 0, s>>>(fxy, ld, dwin, res, sel, cand, u64(o_candn), bx, cand_r2);
+    psf_hist2<<<cgrid, kRedBlock, 0, s>>>(dwin, sel, cand_r2, u64(o_candn), bx, u64(o_hist2));
     psf_pick2<<<nw, kScanBlock, 0, s>>>(u64(o_hist2), sel);
-    psf_collect2<T><<<grid, kRedBlock, 0, s>>>(st, fxy, ld, dwin, res, sel, reinterpret_cast<double*>(b + o_vals2),
-                                               u64(o_cnt2), u64(o_mm));
+    psf_collect2<<<cgrid, kRedBlock, 0, s>>>(dwin, sel, cand_r2, u64(o_candn), bx,
+                                            reinterpret_cast<double*>(b + o_vals2), u64(o_cnt2), u64(o_mm));
     psf_select<<<nw, kScanBlock, 0, s>>>(res, sel, reinterpret_cast<const double*>(b + o_vals2), u64(o_cnt2), u64(o_mm),
                                          reinterpret_cast<double*>(b + o_out), reinterpret_cast<int*>(b + o_stat));
     CU(cudaGetLastError(), "robast_psf: launch");

@@ -939,11 +939,12 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         } else {
             ph.p = ph.p + bst.t * ph.d;
             ph.last = bst.sid;
+            // the interaction's four random words (counter: photon id, bounce index); drawn
+            // only where they are used (mirrors, refracting faces), the same words either way
             const long long pid = A.first_id + ph.i;
-            const uint4 w = philox4x32_10(
-                make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)ph.bounces, 0u), key);
+            const uint4 ctr = make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)ph.bounces, 0u);
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
             ph.bounces += 1;
-            CNT(U_PHILOX);
             const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)bst.sid * REC;
             const int4 si = tb.surf_i[bst.sid];
             const int role = (si.x >> 4) & 15;
@@ -962,6 +963,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                 if (!front) {
                     status = ST_OBSCURED;
                 } else {
+                    w = philox4x32_10(ctr, key);
+                    CNT(U_PHILOX);
                     const double* M = tb.mats + (size_t)si.y * MAT_REC;
                     bool survive;
                     if constexpr (sizeof(T) == 4) {
@@ -1007,6 +1010,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     }
                 }
             } else {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
+                w = philox4x32_10(ctr, key);
+                CNT(U_PHILOX);
                 const T len = abs_length<T>(tb.meds + (size_t)(front ? si.z : si.w) * MED_REC, ph.lam);
                 if (len > T(0)) {
                     const T surv = (sizeof(T) == 4) ? (T)expf(-(float)(bst.t / len)) : (T)exp(-(double)(bst.t / len));

@@ -364,3 +364,22 @@ def test_photon_tracks_match_oracle():
     assert int(tr2["n_records"].item()) == len(rinfo)
     assert np.all(tr2["info"][10:].cpu().numpy() == 0) if tr2["info"].shape[0] > 10 else True
     geom.close()
+
+
+def test_psf_candidate_list_overflow_takes_the_host_fallback():
+    """A window whose kept bins hold more photons than the device candidate
+    list (2^20) is selected on the host; the result is the same exact rank."""
+    scene, _ = W.lst_workload(10, seed=0, angles_deg=(0.0,))
+    geom = robast.build_geometry(scene)
+    rng = np.random.default_rng(5)
+    n = 2_500_001
+    phi = rng.uniform(0, 2 * np.pi, n)
+    r = 0.05 + rng.normal(0, 1e-9, n)
+    xy = np.ascontiguousarray(np.stack([r * np.cos(phi), r * np.sin(phi)]).astype(np.float32))
+    st = np.full(n, W.DETECTED, np.uint8)
+    got = robast.psf(geom, torch.from_numpy(st).cuda(), torch.from_numpy(xy).cuda())
+    exact = metrics.psf(st, xy)
+    assert got[0] == exact["n_detected"]
+    assert abs(got[1] - exact["cx"]) < 1e-12 and abs(got[2] - exact["cy"]) < 1e-12
+    assert got[3] == pytest.approx(exact["r80"], rel=1e-12)
+    geom.close()
