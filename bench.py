@@ -425,7 +425,10 @@ def main():
         # per-photon outputs the spot diagram and the metric need: status, bounce count, focal (x, y)
         out = robast.alloc_outputs(N, precision, dev, fields=("status", "bounces", "focal_xy", "counters"))
         counters = out["counters"]
-        psf_launches = 8  # sums, finish, histogram, pick, sub-histogram, pick, collect, select (all angles at once)
+        # per step: the coherent-order sort (init, bounds, count, three scan launches, place), the
+        # trace, and the reduction (sums, finish, histogram, pick, compact, check, candidate r^2,
+        # sub-histogram, pick, collect, select; all angles at once)
+        order_launches, psf_launches = 7, 11
 
         def step(ev=None):
             if ev is not None:
@@ -467,7 +470,7 @@ def main():
         c = counters.cpu().tolist()
         bounces = c[0]
         return {"ms": ms, "kernel_ms": kern_ms, "bounces": bounces, "counters": c, "units": units, "psf": last,
-                "clocks": clk, "launches": steps * (1 + psf_launches)}
+                "clocks": clk, "launches": steps * (order_launches + 1 + psf_launches)}
 
     fp32 = measure(32, args.steps, args.warmup, want_clocks=True)
     ms = max_over_ranks(fp32["ms"])
