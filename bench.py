@@ -484,7 +484,7 @@ def main():
     achieved = flops / (kern_avg_ms * 1e-3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak32, "traffic": traffic_from_profile(N),
-            "kernel": "robast::trace_kernel<float,256> (with the coherent-order sort)", "kernel_ms": kern_avg_ms,
+            "kernel": "robast::trace_kernel<float,512> (with the coherent-order sort)", "kernel_ms": kern_avg_ms,
             "flops_per_launch": flops, "work_units_per_launch": fp32["units"],
             "peak_source": "FFMA throughput probe robast_measure_alu_peak on this GPU (measured)"}
 

@@ -223,8 +223,9 @@ typedef struct robast_trace_opts {
     const int32_t* variant_of_photon; /* device [n] or NULL (all variant 0) */
     int64_t first_photon_id;  /* photon i uses random stream id first_photon_id + i */
     double eps;               /* self-intersection epsilon; 0 = 1e-6 L_sys (FP32) / 1e-9 L_sys (FP64) */
-    int32_t block_size;       /* 64, 128 or 256; 0 = library choice (FP32: 256, FP64, source
-                                 mode and counting build: 128) */
+    int32_t block_size;       /* 64, 128 or 256 (512 too for the FP32 trace without sources);
+                                 0 = library choice (FP32: 512, FP64, source mode and counting
+                                 build: 128) */
     int32_t blocks_per_sm;    /* 0 = as many as fit */
     unsigned long long* work_units; /* device [ROBAST_N_UNITS] or NULL; non-NULL runs the
                                        counting build of the kernel (block 128, slower) and

@@ -650,13 +650,16 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
     int stack[STACK];  // packed (ref | n << 24)
     float stack_t[STACK];
     int sp = 0;
-    // float bound of the current best t, rounded up so that no candidate is lost
-    auto tcap = [&]() -> float { return bst.t == t_inf<T>() ? 3.0e38f : (float)bst.t * 1.0001f + 1e-30f; };
+    // float bound of the current best t, rounded up so that no candidate is lost; updated
+    // only when a leaf may have changed the best hit
+    float tc;
+    auto update_tc = [&]() { tc = bst.t == t_inf<T>() ? 3.0e38f : (float)bst.t * 1.0001f + 1e-30f; };
+    update_tc();
     auto pop = [&](int& ref, int& n) {
         ref = -1;
         while (sp > 0) {
             --sp;
-            if (stack_t[sp] <= tcap()) {
+            if (stack_t[sp] <= tc) {
                 ref = stack[sp] & 0xffffff;
                 n = stack[sp] >> 24;
                 return;
@@ -666,36 +669,32 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
     int ref = vr.x, n = 0;  // the root is an internal node
     while (true) {
         while (n == 0 && ref >= 0) {
-            const Node nd = tb.nodes[ref];
-            const float tc = tcap();
+            const Node nd = tb.nodes[ref];  // both children are real (a one-leaf tree repeats its leaf)
             if constexpr (C) cnt[U_AABB] += 2u;
-            const float e0 = nd.n0 < 0 ? 3.4e38f : box_entry(nd.lo0, nd.hi0, ox, oy, oz, ix, iy, iz, tc);
-            const float e1 = nd.n1 < 0 ? 3.4e38f : box_entry(nd.lo1, nd.hi1, ox, oy, oz, ix, iy, iz, tc);
+            const float e0 = box_entry(nd.lo0, nd.hi0, ox, oy, oz, ix, iy, iz, tc);
+            const float e1 = box_entry(nd.lo1, nd.hi1, ox, oy, oz, ix, iy, iz, tc);
             const bool h0 = e0 < 3.4e38f, h1 = e1 < 3.4e38f;
-            if (h0 && h1) {
-                if (sp >= STACK) {
-                    overflow = true;
-                    return;
+            if (h0 || h1) {
+                // nearer child next; with both hit, the farther one waits with its entry distance
+                const bool first0 = h0 && (!h1 || e0 <= e1);
+                if (h0 && h1) {
+                    if (sp >= STACK) {
+                        overflow = true;
+                        return;
+                    }
+                    stack[sp] = first0 ? (nd.ref1 | (nd.n1 << 24)) : (nd.ref0 | (nd.n0 << 24));
+                    stack_t[sp] = first0 ? e1 : e0;
+                    ++sp;
                 }
-                // nearer child first; the farther one waits with its entry distance
-                const bool first0 = e0 <= e1;
-                stack[sp] = first0 ? (nd.ref1 | (nd.n1 << 24)) : (nd.ref0 | (nd.n0 << 24));
-                stack_t[sp] = first0 ? e1 : e0;
-                ++sp;
                 ref = first0 ? nd.ref0 : nd.ref1;
                 n = first0 ? nd.n0 : nd.n1;
-            } else if (h0) {
-                ref = nd.ref0;
-                n = nd.n0;
-            } else if (h1) {
-                ref = nd.ref1;
-                n = nd.n1;
             } else {
                 pop(ref, n);
             }
         }
         if (ref < 0) break;
         for (int k = 0; k < n; ++k) test_surface<C>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
+        update_tc();
         pop(ref, n);
     }
 }
