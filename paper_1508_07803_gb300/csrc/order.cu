@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "launch.h"
 
 namespace robast {
@@ -205,9 +207,18 @@ static cudaError_t build_order_t(const T* o, long long n, void* scratch, int** o
     int* order = reinterpret_cast<int*>(b + 256 + ord_round(nbins * 4));
     unsigned* tiles = reinterpret_cast<unsigned*>(b + 256 + ord_round(nbins * 4) + ord_round(n * 4));
     const int smem = ORD_CELLS * (int)sizeof(unsigned);
-    cudaError_t e = cudaFuncSetAttribute(ord_count<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ord_place<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the 64 KB shared-memory opt-in, once per device and precision
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 32 ? 1ull << (dev * 2 + (sizeof(T) == 4 ? 0 : 1)) : 0ull;
+    if (!bit || !(opted.load(std::memory_order_relaxed) & bit)) {
+        e = cudaFuncSetAttribute(ord_count<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(ord_place<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(bit, std::memory_order_relaxed);
+    }
     ord_init<<<1, 32, 0, s>>>(box);
     ord_bounds<T><<<sms * 4, 256, 0, s>>>(o, n, box);
     ord_count<T><<<(unsigned)nblk, ORD_BLOCK, smem, s>>>(o, n, box, counts);

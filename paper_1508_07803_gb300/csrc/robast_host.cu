@@ -68,6 +68,15 @@ struct robast_geom {
     size_t stage_bytes = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // stream-ordered scratch (the coherent-order sort) comes from this pool, which keeps its
+    // memory between calls (the device's default pool would hand it back at every
+    // synchronisation and re-map it on the next call)
+    cudaMemPool_t pool = nullptr;
+    void* pinned = nullptr;  // pinned host staging for the reductions' small copies
+    size_t pinned_bytes = 0;
+    // resident blocks per SM of each trace kernel with this geometry's staged tables, looked
+    // up once: [precision 32/64][block 64/128/256/512][source mode]; 0 = not yet known
+    std::atomic<int> bps_cache[2][4][2] = {};
 };
 
 static const int kWorkSlots = 256;
@@ -693,6 +702,23 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = cudaMalloc(&g->dmem, total);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = g->device;
+        e = cudaMemPoolCreate(&g->pool, &props);
+        if (e == cudaSuccess) {
+            unsigned long long keep = ~0ull;  // keep whatever was used until the geometry is freed
+            e = cudaMemPoolSetAttribute(g->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        if (e != cudaSuccess) {
+            if (g->pool) cudaMemPoolDestroy(g->pool);
+            g->pool = nullptr;
+            cudaFree(g->dmem);
+            g->dmem = nullptr;
+        }
+    }
     if (e != cudaSuccess) {
         delete g;
         return e == cudaErrorMemoryAllocation ? fail(ROBAST_E_OOM, "robast_build_geometry: cudaMalloc of %zu bytes failed", total)
@@ -724,6 +750,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     e = cudaMemcpy(g->dmem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->dmem);
+        cudaMemPoolDestroy(g->pool);
         delete g;
         return cuda_fail(e, "robast_build_geometry: upload");
     }
@@ -778,6 +805,8 @@ extern "C" void robast_free_geometry(robast_geom* g) {
     cudaFree(g->dmem);
     if (g->stage) cudaFree(g->stage);
     if (g->scratch) cudaFree(g->scratch);
+    if (g->pinned) cudaFreeHost(g->pinned);
+    if (g->pool) cudaMemPoolDestroy(g->pool);
     cudaSetDevice(prev);
     delete g;
 }
@@ -872,8 +901,14 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     if (a.units && block != 128)
         return fail(ROBAST_E_INVALID, "robast_trace: the counting build (work_units) runs with block_size 128 only");
     if (a.units && src) return fail(ROBAST_E_INVALID, "robast_trace_sources: no counting build for source mode");
-    int bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem, src != nullptr)
+    const int bi = block == 64 ? 0 : block == 128 ? 1 : block == 256 ? 2 : 3;
+    std::atomic<int>& bps_slot = gm->bps_cache[sizeof(T) == 4 ? 0 : 1][bi][src ? 1 : 0];
+    int bps = bps_slot.load(std::memory_order_relaxed);
+    if (bps <= 0) {
+        bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem, src != nullptr)
                              : trace_blocks_per_sm_f64(block, smem, src != nullptr);
+        if (bps > 0) bps_slot.store(bps, std::memory_order_relaxed);
+    }
     if (bps <= 0) return fail(ROBAST_E_CUDA, "robast_trace: kernel cannot launch with %zu bytes of shared memory", smem);
     if (o.blocks_per_sm > 0) bps = std::min(bps, (int)o.blocks_per_sm);
     long long grid = (long long)g->num_sms * bps;
@@ -884,7 +919,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     const bool want_order =
         !src && n > 0 && n < (1LL << 31) && (o.coherent_order > 0 || (o.coherent_order == 0 && n >= 65536));
     if (want_order) {
-        CU(cudaMallocAsync(&ord_scratch, (size_t)order_scratch_bytes(n), s), "robast_trace: order scratch");
+        CU(cudaMallocFromPoolAsync(&ord_scratch, (size_t)order_scratch_bytes(n), gm->pool, s), "robast_trace: order scratch");
         int* order = nullptr;
         cudaError_t eo;
         if constexpr (sizeof(T) == 4)
@@ -1031,6 +1066,19 @@ static int grow(void** p, size_t* have, size_t need, const char* what) {
     cudaError_t e = cudaMalloc(p, need);
     if (e != cudaSuccess) return fail(ROBAST_E_OOM, "%s: cudaMalloc of %zu bytes failed", what, need);
     *have = need;
+    return 0;
+}
+
+// pinned host staging: copies from and to it are asynchronous, so a reduction queued
+// behind a running trace does not block the host until the trace ends
+static int grow_pinned(robast_geom* g, size_t need, const char* what) {
+    if (g->pinned_bytes >= need) return 0;
+    if (g->pinned) cudaFreeHost(g->pinned);
+    g->pinned = nullptr;
+    g->pinned_bytes = 0;
+    cudaError_t e = cudaMallocHost(&g->pinned, need);
+    if (e != cudaSuccess) return fail(ROBAST_E_OOM, "%s: cudaMallocHost of %zu bytes failed", what, need);
+    g->pinned_bytes = need;
     return 0;
 }
 
@@ -1840,8 +1888,13 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = grow(&g->scratch, &g->scratch_bytes, o_vals + 4096 * 8, "robast_psf");
     if (rc) return rc;
+    const size_t win_bytes = align16(nw * sizeof(Win));
+    rc = grow_pinned(g, win_bytes + back_bytes, "robast_psf");
+    if (rc) return rc;
+    unsigned char* hp = static_cast<unsigned char*>(g->pinned);  // [windows | read-back region]
+    std::memcpy(hp, hw.data(), nw * sizeof(Win));
     unsigned char* b = static_cast<unsigned char*>(g->scratch);
-    CU(cudaMemcpyAsync(b + o_win, hw.data(), nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(b + o_win, hp, nw * sizeof(Win), cudaMemcpyHostToDevice, s), "robast_psf: copy");
     CU(cudaMemsetAsync(b + o_zero, 0, zero_bytes, s), "robast_psf: clear");
     const Win* dwin = reinterpret_cast<const Win*>(b + o_win);
     double* part = reinterpret_cast<double*>(b + o_part);
@@ -1866,9 +1919,9 @@ int psf_impl(robast_geom* g, const uint8_t* st, const T* fxy, long long ld, int 
     psf_select<<<nw, kScanBlock, 0, s>>>(res, sel, reinterpret_cast<const double*>(b + o_vals2), u64(o_cnt2), u64(o_mm),
                                          reinterpret_cast<double*>(b + o_out), reinterpret_cast<int*>(b + o_stat));
     CU(cudaGetLastError(), "robast_psf: launch");
-    std::vector<unsigned char> back(back_bytes);
-    CU(cudaMemcpyAsync(back.data(), b + o_back, back_bytes, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
+    CU(cudaMemcpyAsync(hp + win_bytes, b + o_back, back_bytes, cudaMemcpyDeviceToHost, s), "robast_psf: copy");
     CU(cudaStreamSynchronize(s), "robast_psf: synchronize");
+    std::vector<unsigned char> back(hp + win_bytes, hp + win_bytes + back_bytes);
     const double* hout = reinterpret_cast<const double*>(back.data() + (o_out - o_back));
     const int* hstat = reinterpret_cast<const int*>(back.data() + (o_stat - o_back));
     const Sel* hsel = reinterpret_cast<const Sel*>(back.data() + (o_sel - o_back));
