@@ -495,7 +495,24 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
     T best = tmax;
     int bj = 0;
     T bu = T(0);
+    // Wall j can only be hit where the ray is in its 60-degree wedge, which is bounded by
+    // the two half-planes x.(u_j - u_{j+-1}) >= 0 shared with the neighbouring walls.  A wall
+    // whose wedge the ray cannot reach on [0, tmax] (with a margin far above rounding) is
+    // skipped; the in-wedge test at the hit point below is unchanged, so the result is too.
+    // margin: 1e-5 of the scale of any point p + t d, t <= best, far above the in-wedge test's rounding
+    const T mg = T(1e-5) * (t_abs(p.x) + t_abs(p.y) + t_abs(d.x) + t_abs(d.y) + T(1e-30));
     for (int j = 0; j < 6; ++j) {
+        bool reach = true;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int m = side ? (j + 1) % 6 : (j + 5) % 6;
+            const T ex = cj[j] - cj[m], ey = sj[j] - sj[m];
+            const T a = p.x * ex + p.y * ey, b = d.x * ex + d.y * ey;
+            // largest a + b t over t in [0, best]: at t = best if b > 0 (best may be +inf)
+            const T top = b > T(0) ? a + b * best : a;
+            if (top < -mg * (T(1) + t_min(best, T(1e30)))) reach = false;
+        }
+        if (!reach) continue;
         const T q0 = p.x * cj[j] + p.y * sj[j], dq = d.x * cj[j] + d.y * sj[j];
         const T den = dq * dq + d.z * d.z;
         if (den == T(0)) continue;
