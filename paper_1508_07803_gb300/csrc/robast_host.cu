@@ -685,7 +685,10 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t b64 = align16(rec64.size() * 8), b32 = align16(rec32.size() * 4), bi = align16(reci.size() * 16);
     const size_t bn = align16(nodes.size() * sizeof(Node)), bp = align16(prims.size() * 4);
     const size_t bv = align16(vars.size() * 16), bg = align16(glob.size() * 4);
+    std::vector<float> meds32(meds.size());
+    for (size_t k = 0; k < meds.size(); ++k) meds32[k] = (float)meds[k];
     const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8), bm32 = align16(mats32.size() * 4);
+    const size_t bd32 = align16(meds32.size() * 4);
     const size_t bw = kWorkSlots * 8;
     const size_t bg64 = align16(grec64.size() * 8), bg32 = align16(grec32.size() * 4);
     std::vector<int> surf_var(ns, 0);
@@ -695,7 +698,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         for (int s = s0; s < s1; ++s) surf_var[s] = v;
     }
     const size_t bsv = align16(surf_var.size() * 4);
-    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bw + bg64 + bg32 + bsv;
+    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bd32 + bw + bg64 + bg32 + bsv;
 
     robast_geom* g = new (std::nothrow) robast_geom();
     if (!g) return fail(ROBAST_E_OOM, "robast_build_geometry: host allocation failed");
@@ -742,6 +745,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t om = put(mats.data(), mats.size() * 8, bm);
     const size_t od = put(meds.data(), meds.size() * 8, bd);
     const size_t om32 = put(mats32.data(), mats32.size() * 4, bm32);
+    put(meds32.data(), meds32.size() * 4, bd32);  // right after the FP32 material records (meds32 in trace.cuh)
     const size_t ow = off;
     off += bw;
     const size_t og64 = put(grec64.data(), grec64.size() * 8, bg64);
@@ -780,7 +784,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->grec32 = reinterpret_cast<const float*>(base + og32);
     g->surf_var = reinterpret_cast<const int*>(base + osv);
     g->smem64 = b64 + bi + bn + bp + bv + bg + bm + bd;
-    g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd + bm32;
+    g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bd32;
     g->n_surf = ns;
     g->n_var = nv;
     g->h_var = surf_var;

@@ -93,7 +93,8 @@ struct Tables {
     const int* glob;       // surfaces without a bounding box, per variant
     const double* mats;
     const double* meds;
-    const float* mats32;  // the material records rounded to FP32 (the FP32 kernel's reads)
+    const float* mats32;  // the material records rounded to FP32 (the FP32 kernel's reads), followed
+                          // (16-byte aligned) by the medium records rounded to FP32: meds32(tb)
     int n_surf, n_nodes, n_prims, n_var, n_glob, n_mat, n_med, pad;
 };
 
@@ -484,13 +485,60 @@ __device__ __forceinline__ bool hit_box(const T* S, V3<T> p, V3<T> d, T eps, T t
 // cone is the case whose control points lie on a parabola).  Wall j faces
 // u_j = (cos j pi/3, sin j pi/3); in its (q, z) half-plane the ray crosses
 // the profile where dz (r(u) - q0) - dq (z(u) - z0) = 0, a quadratic in u.
+// Unevaluated float pairs h + l for the compensated FP32 polish of cone roots: products of
+// two floats are exact (fma gives the rounding error), sums keep their rounding error in l.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_of(float a) { return FF{a, 0.0f}; }
+__device__ __forceinline__ FF ff_mul(float a, float b) {
+    const float h = __fmul_rn(a, b);
+    return FF{h, __fmaf_rn(a, b, -h)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bp = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bp)), __fsub_rn(b.h, bp));
+    return FF{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+__device__ __forceinline__ FF ff_mulf(FF a, float b) {
+    FF p = ff_mul(a.h, b);
+    p.l = __fmaf_rn(a.l, b, p.l);
+    return p;
+}
+__device__ __forceinline__ FF ff_mul2(FF a, FF b) {
+    FF p = ff_mul(a.h, b.h);
+    p.l = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+    return p;
+}
+
+// cos and sin of j x 60 degrees, j = 0..5 (a hexagon's face directions)
+static __constant__ float k_hex_c32[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
+static __constant__ float k_hex_s32[6] = {0.0f, 0.86602540378443864676f, 0.86602540378443864676f, 0.0f,
+                                          -0.86602540378443864676f, -0.86602540378443864676f};
+static __constant__ double k_hex_c64[6] = {1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
+static __constant__ double k_hex_s64[6] = {0.0, 0.86602540378443864676, 0.86602540378443864676, 0.0,
+                                           -0.86602540378443864676, -0.86602540378443864676};
+
+template <typename T>
+__device__ __forceinline__ void hex_dir(int j, T& c, T& s) {
+    if constexpr (sizeof(T) == 4) {
+        c = k_hex_c32[j];
+        s = k_hex_s32[j];
+    } else {
+        c = T(k_hex_c64[j]);
+        s = T(k_hex_s64[j]);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
     const T ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
     const T za0 = S[F_C + 3], za1 = S[F_C + 4], za2 = S[F_C + 5];
-    const T s60 = T(0.86602540378443864676);
-    const T cj[6] = {T(1), T(0.5), T(-0.5), T(-1), T(-0.5), T(0.5)};
-    const T sj[6] = {T(0), s60, s60, T(0), -s60, -s60};
+    // wall j's outward direction (cos, sin of j x 60 degrees) from constant memory: no
+    // local-memory array for a loop-dependent j, no registers held
+    auto dir = [&](int j, T& c, T& s) { hex_dir(j, c, s); };
     bool found = false;
     T best = tmax;
     int bj = 0;
@@ -502,18 +550,21 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
     // margin: 1e-5 of the scale of any point p + t d, t <= best, far above the in-wedge test's rounding
     const T mg = T(1e-5) * (t_abs(p.x) + t_abs(p.y) + t_abs(d.x) + t_abs(d.y) + T(1e-30));
     for (int j = 0; j < 6; ++j) {
+        T cjj, sjj;
+        dir(j, cjj, sjj);
         bool reach = true;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const int m = side ? (j + 1) % 6 : (j + 5) % 6;
-            const T ex = cj[j] - cj[m], ey = sj[j] - sj[m];
+            T cm, sm;
+            dir(side ? (j + 1) % 6 : (j + 5) % 6, cm, sm);
+            const T ex = cjj - cm, ey = sjj - sm;
             const T a = p.x * ex + p.y * ey, b = d.x * ex + d.y * ey;
             // largest a + b t over t in [0, best]: at t = best if b > 0 (best may be +inf)
             const T top = b > T(0) ? a + b * best : a;
             if (top < -mg * (T(1) + t_min(best, T(1e30)))) reach = false;
         }
         if (!reach) continue;
-        const T q0 = p.x * cj[j] + p.y * sj[j], dq = d.x * cj[j] + d.y * sj[j];
+        const T q0 = p.x * cjj + p.y * sjj, dq = d.x * cjj + d.y * sjj;
         const T den = dq * dq + d.z * d.z;
         if (den == T(0)) continue;
         const T A = d.z * ra2 - dq * za2;
@@ -539,18 +590,22 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
         for (int i = 0; i < nu; ++i) {
             T u = us[i];
             const T gp = T(2) * A * u + B;
-            // one Newton polish of the root; in FP32 at grazing (|g'| small) it runs in FP64
+            // one Newton polish of the root; in FP32 at grazing (|g'| small) the coefficients
+            // and g(u) are evaluated in unevaluated float pairs (exact products by fma, two-sum
+            // additions; about 46 bits), which removes the cancellation in C at FP32 issue rate
             bool polished = false;
             if constexpr (sizeof(T) == 4) {
-                if (t_abs(gp) < T(0.05) * (t_abs(B) + t_abs(A) + t_abs(C) + T(1e-30))) {
-                    const double pj_c = (double)cj[j], pj_s = (double)sj[j];
-                    const double q0d = (double)p.x * pj_c + (double)p.y * pj_s,
-                                 dqd = (double)d.x * pj_c + (double)d.y * pj_s;
-                    const double Ad = (double)d.z * (double)ra2 - dqd * (double)za2;
-                    const double Bd = (double)d.z * (double)ra1 - dqd * (double)za1;
-                    const double Cd = (double)d.z * ((double)ra0 - q0d) - dqd * ((double)za0 - (double)p.z);
-                    const double ud = (double)u, gpd = 2.0 * Ad * ud + Bd;
-                    if (gpd != 0.0) u = (T)(ud - ((Ad * ud + Bd) * ud + Cd) / gpd);
+                // only roots that can still land in [0, 1]: the polish moves a root by far less
+                // than 0.01 (FP32 root error at a near-double root is ~1e-4 of the scale)
+                if (u > T(-0.01) && u < T(1.01) && t_abs(gp) < T(0.05) * (t_abs(B) + t_abs(A) + t_abs(C) + T(1e-30))) {
+                    const FF q0f = ff_add(ff_mul(p.x, cjj), ff_mul(p.y, sjj));
+                    const FF dqf = ff_add(ff_mul(d.x, cjj), ff_mul(d.y, sjj));
+                    const FF Af = ff_sub(ff_mul(d.z, ra2), ff_mulf(dqf, za2));
+                    const FF Bf = ff_sub(ff_mul(d.z, ra1), ff_mulf(dqf, za1));
+                    const FF Cf = ff_sub(ff_mulf(ff_sub(ff_of(ra0), q0f), d.z), ff_mul2(dqf, ff_sub(ff_of(za0), ff_of(p.z))));
+                    const FF gf = ff_add(ff_mulf(ff_add(ff_mulf(Af, u), Bf), u), Cf);
+                    const float gpf = 2.0f * Af.h * u + Bf.h;
+                    if (gpf != 0.0f) u = u - (gf.h + gf.l) / gpf;
                     polished = true;
                 }
             }
@@ -562,11 +617,14 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
             if (t <= eps || t > best) continue;
             if (found && !(t < best)) continue;
             const V3<T> x = p + t * d;
-            const T qj = x.x * cj[j] + x.y * sj[j];
+            const T qj = x.x * cjj + x.y * sjj;
             bool inwedge = true;
 #pragma unroll
-            for (int m = 0; m < 6; ++m)
-                if (m != j && x.x * cj[m] + x.y * sj[m] > qj) inwedge = false;
+            for (int m = 0; m < 6; ++m) {
+                T cm, sm;
+                hex_dir(m, cm, sm);
+                if (m != j && x.x * cm + x.y * sm > qj) inwedge = false;
+            }
             if (!inwedge) continue;
             found = true;
             best = t;
@@ -577,9 +635,11 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
     }
     if (!found) return false;
     const T Rp = ra1 + T(2) * ra2 * bu, Zp = za1 + T(2) * za2 * bu;
+    T cb, sb;
+    dir(bj, cb, sb);
     h.u = bu;
     h.t = best;
-    h.nl = unit(mk(-Zp * cj[bj], -Zp * sj[bj], Rp));
+    h.nl = unit(mk(-Zp * cb, -Zp * sb, Rp));
     return true;
 }
 
@@ -592,7 +652,15 @@ struct Best {
     bool err;
 };
 
-template <bool C, typename T>
+// The cone intersection out of line: the plain trace kernel sits at its register cap, and
+// inlining this rarely-taken path there costs spills on every other path; the source-mode
+// kernel (uncapped, the cone studies' hot path) keeps it inline.
+template <typename T>
+__device__ __noinline__ bool hit_hexcone_call(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>* h) {
+    return hit_hexcone(S, p, d, eps, tmax, *h);
+}
+
+template <bool C, bool CONE_INLINE = true, typename T>
 __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
                                              unsigned* cnt) {
     CNT(U_REBASE);
@@ -616,7 +684,10 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
             break;
         case SHAPE_HEXCONE:
             if constexpr (C) cnt[U_HEXWALL] += 6u;
-            ok = hit_hexcone(S, pl, dl, eps, bst.t, h);
+            if constexpr (CONE_INLINE)
+                ok = hit_hexcone(S, pl, dl, eps, bst.t, h);
+            else
+                ok = hit_hexcone_call(S, pl, dl, eps, bst.t, &h);
             break;
     }
     if (err) bst.err = true;
@@ -646,14 +717,14 @@ __device__ __forceinline__ float box_entry(const float* lo, const float* hi, flo
 
 constexpr int STACK = 32;
 
-template <bool C, typename T>
+template <bool C, bool CONE_INLINE = true, typename T>
 __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
                                             bool& overflow, unsigned* cnt) {
     bst.t = t_inf<T>();
     bst.sid = 0x7fffffff;
     bst.err = false;
     const int4 vr = tb.variants[var];
-    for (int k = 0; k < vr.z; ++k) test_surface<C>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
+    for (int k = 0; k < vr.z; ++k) test_surface<C, CONE_INLINE>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
     if (vr.x < 0) return;
     // Inverse direction with zero components replaced by +-1e-30, so that the
     // FMA slab form never meets inf - inf (the boxes are padded, so a ray grazing
@@ -710,7 +781,7 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
             }
         }
         if (ref < 0) break;
-        for (int k = 0; k < n; ++k) test_surface<C>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
+        for (int k = 0; k < n; ++k) test_surface<C, CONE_INLINE>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
         update_tc();
         pop(ref, n);
     }
@@ -757,9 +828,9 @@ __device__ __forceinline__ float refl_estimate32(const float* M, float lam) {
     return R[i] + (R[i + 1] - R[i]) * frac;
 }
 
-template <typename T>
-__device__ __forceinline__ T refr_index(const double* Md, T lam_nm) {
-    if (Md[0] > 0.0) return (T)Md[0];
+template <typename T, typename R>
+__device__ __forceinline__ T refr_index(const R* Md, T lam_nm) {
+    if (Md[0] > R(0)) return (T)Md[0];
     const T l = lam_nm * T(1e-3);
     const T l2 = l * l;
     T n2 = T(1);
@@ -768,13 +839,18 @@ __device__ __forceinline__ T refr_index(const double* Md, T lam_nm) {
     return t_sqrt(n2);
 }
 
+// the FP32 medium records, which follow the FP32 material records (16-byte aligned)
+__device__ __forceinline__ const float* meds32(const Tables& tb) {
+    return tb.mats32 + ((size_t)tb.n_mat * MAT_REC + 3) / 4 * 4;
+}
+
 // Absorption length at lambda (piecewise linear, clamped); <= 0: no absorption.
-template <typename T>
-__device__ __forceinline__ T abs_length(const double* Md, T lam) {
+template <typename T, typename R>
+__device__ __forceinline__ T abs_length(const R* Md, T lam) {
     const int n = (int)Md[7];
     if (n <= 0) return T(-1);
-    const double* L = Md + 8;
-    const double* A = Md + 24;
+    const R* L = Md + 8;
+    const R* A = Md + 24;
     if (n == 1 || lam <= (T)L[0]) return (T)A[0];
     if (lam >= (T)L[n - 1]) return (T)A[n - 1];
     int i = 0;
@@ -861,8 +937,10 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         tb.glob = reinterpret_cast<const int*>(stage(tb.glob, (size_t)tb.n_glob * sizeof(int)));
         tb.mats = reinterpret_cast<const double*>(stage(tb.mats, (size_t)tb.n_mat * MAT_REC * sizeof(double)));
         tb.meds = reinterpret_cast<const double*>(stage(tb.meds, (size_t)tb.n_med * MED_REC * sizeof(double)));
-        if constexpr (sizeof(T) == 4)
-            tb.mats32 = reinterpret_cast<const float*>(stage(tb.mats32, (size_t)tb.n_mat * MAT_REC * sizeof(float)));
+        if constexpr (sizeof(T) == 4) {  // the two FP32 copies, adjacent as in global memory
+            const size_t b32 = ((size_t)tb.n_mat * MAT_REC * sizeof(float) + 15) / 16 * 16;
+            tb.mats32 = reinterpret_cast<const float*>(stage(tb.mats32, b32 + (size_t)tb.n_med * MED_REC * sizeof(float)));
+        }
         __syncthreads();
     }
     const unsigned FULL = 0xffffffffu;
@@ -947,7 +1025,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         bool overflow = false;
         V3<T> fpos = mk(T(0), T(0), T(0));
         const bool bad_var = ph.bad || ph.var < 0 || ph.var >= tb.n_var;  // never index past the variant table
-        if (!bad_var) nearest_hit<C>(tb, ph.var, ph.p, ph.d, A.eps, A.newton_tol, bst, overflow, cnt);
+        if (!bad_var)
+            nearest_hit<C, SRC || sizeof(T) == 8>(tb, ph.var, ph.p, ph.d, A.eps, A.newton_tol, bst, overflow, cnt);
         if (bad_var || overflow || bst.err) {
             status = ST_ERROR;
         } else if (bst.sid == 0x7fffffff) {
@@ -1028,15 +1107,23 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             } else {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
                 w = philox4x32_10(ctr, key);
                 CNT(U_PHILOX);
-                const T len = abs_length<T>(tb.meds + (size_t)(front ? si.z : si.w) * MED_REC, ph.lam);
+                const int med = front ? si.z : si.w;
+                const T len = sizeof(T) == 4 ? abs_length<T>(meds32(tb) + (size_t)med * MED_REC, ph.lam)
+                                             : abs_length<T>(tb.meds + (size_t)med * MED_REC, ph.lam);
                 if (len > T(0)) {
                     const T surv = (sizeof(T) == 4) ? (T)expf(-(float)(bst.t / len)) : (T)exp(-(double)(bst.t / len));
                     if (!(unit_open<T>(w.w) < surv)) status = ST_ABSORBED;
                 }
             }
             if (status == 0 && role == ROLE_REFRACT) {
-                const T na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, ph.lam);
-                const T nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, ph.lam);
+                T na, nb;
+                if constexpr (sizeof(T) == 4) {  // FP32 copy of the medium records: no FP64 instruction
+                    na = refr_index<T>(meds32(tb) + (size_t)si.z * MED_REC, ph.lam);
+                    nb = refr_index<T>(meds32(tb) + (size_t)si.w * MED_REC, ph.lam);
+                } else {
+                    na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, ph.lam);
+                    nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, ph.lam);
+                }
                 const T n1 = front ? na : nb, n2 = front ? nb : na;
                 const V3<T> nf = front ? n : T(-1) * n;
                 const T ci = -dot(ph.d, nf);
