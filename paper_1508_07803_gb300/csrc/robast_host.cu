@@ -1005,6 +1005,8 @@ extern "C" int robast_sources_create(const robast_geom* g, const robast_source_g
         }
         G.a = q.apothem;
         G.R = q.apothem * 2.0 / std::sqrt(3.0);
+        G.a32 = (float)G.a;
+        G.R32 = (float)G.R;
         G.lam0 = q.lam_min;
         G.lam1 = q.lam_max;
         G.first = first;

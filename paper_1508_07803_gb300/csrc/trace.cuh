@@ -108,7 +108,10 @@ struct SrcGroup {
     double dir[3];
     double lam0, lam1;
     long long first, n;
-    int variant, pad;
+    int variant;
+    float a32;  // a rounded to FP32 (the rejection screen)
+    float R32;  // R rounded to FP32
+    int pad;
 };
 
 template <typename T>
@@ -206,17 +209,52 @@ __device__ __forceinline__ T unit_open(uint32_t w) {
 // (id_lo, id_hi, k, 1).  FP64 with every operation rounded separately, so the
 // generated inputs are bit-identical to the CPU reference's.  Returns false if
 // 64 candidates were all rejected (probability 0.25^64).
-__device__ __forceinline__ bool gen_source(const SrcGroup& G, long long pid, uint2 key, double o[3], double* lam) {
+// The candidate (x, y) of draw w in FP64 with every rounding explicit (the definition).
+__device__ __forceinline__ void src_xy(const SrcGroup& G, uint4 w, double* x, double* y) {
+    const double u0 = __dmul_rn(__dadd_rn((double)w.x, 0.5), 2.3283064365386963e-10);
+    const double u1 = __dmul_rn(__dadd_rn((double)w.y, 0.5), 2.3283064365386963e-10);
+    *x = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u0), 1.0), G.a);
+    *y = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u1), 1.0), G.R);
+}
+
+// Inside-hexagon test of the candidate in FP64 (the definition).
+__device__ __forceinline__ bool src_inside64(const SrcGroup& G, double x, double y) {
     const double s60 = 0.86602540378443864676;
+    const double hx = __dmul_rn(0.5, x), sy = __dmul_rn(s60, y);
+    const double m = fmax(fabs(x), fmax(fabs(__dadd_rn(hx, sy)), fabs(__dadd_rn(-hx, sy))));
+    return m <= G.a;
+}
+
+// Photon pid of group G: the first of up to 64 candidates (Philox stream 1, counter
+// (pid, k)) inside the hexagon.  Each candidate is screened in FP32: its hexagon measure m is
+// within 2e-6 a of the FP64 value (u to 3 FP32 roundings, x and y to 5e-7 a, the sums to
+// 1e-6 a), so a screen outside a band of 1e-5 a around a decides as FP64 would; inside the
+// band (about one candidate in 10^5) the FP64 test decides.  The accepted candidate's
+// coordinates and wavelength are then formed in FP64 exactly as defined, so the photons are
+// the same bits as an all-FP64 generator's (FP64 issues at 1/64 of the FP32 rate here, and a
+// rejection loop repeats for the whole warp until its last lane accepts).
+__device__ __forceinline__ bool gen_source(const SrcGroup& G, long long pid, uint2 key, double o[3], double* lam) {
+    const float s60f = 0.86602540378443864676f;
     for (uint32_t k = 0; k < 64; ++k) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), k, 1u), key);
-        const double u0 = __dmul_rn(__dadd_rn((double)w.x, 0.5), 2.3283064365386963e-10);
-        const double u1 = __dmul_rn(__dadd_rn((double)w.y, 0.5), 2.3283064365386963e-10);
-        const double x = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u0), 1.0), G.a);
-        const double y = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u1), 1.0), G.R);
-        const double hx = __dmul_rn(0.5, x), sy = __dmul_rn(s60, y);
-        const double m = fmax(fabs(x), fmax(fabs(__dadd_rn(hx, sy)), fabs(__dadd_rn(-hx, sy))));
-        if (m <= G.a) {
+        const float u0f = ((float)w.x + 0.5f) * 2.3283064365386963e-10f;
+        const float u1f = ((float)w.y + 0.5f) * 2.3283064365386963e-10f;
+        const float xf = (2.0f * u0f - 1.0f) * G.a32, yf = (2.0f * u1f - 1.0f) * G.R32;
+        const float hxf = 0.5f * xf, syf = s60f * yf;
+        const float mf = fmaxf(fabsf(xf), fmaxf(fabsf(hxf + syf), fabsf(syf - hxf)));
+        bool inside;
+        if (mf < G.a32 * (1.0f - 1e-5f))
+            inside = true;
+        else if (mf > G.a32 * (1.0f + 1e-5f))
+            inside = false;
+        else {
+            double x, y;
+            src_xy(G, w, &x, &y);
+            inside = src_inside64(G, x, y);
+        }
+        if (inside) {
+            double x, y;
+            src_xy(G, w, &x, &y);
             const double u2 = __dmul_rn(__dadd_rn((double)w.z, 0.5), 2.3283064365386963e-10);
             o[0] = __dadd_rn(G.c[0], x);
             o[1] = __dadd_rn(G.c[1], y);
