@@ -271,8 +271,12 @@ int robast_trace_ex(const robast_geom* g, const void* origins, const void* dirs,
 /*
  * The same trace with HOST inputs and outputs: the library copies the inputs
  * to a device staging area owned by g (grown on demand), traces, copies the
- * outputs back and synchronises the stream before returning.  Output
- * pointers in `out` are host pointers here (counters too, added to).
+ * outputs back and synchronises before returning.  Output pointers in `out`
+ * are host pointers here (counters too, added to).  The photons go in chunks
+ * (at least 2^20 photons, at most 8) over two streams owned by g, after the
+ * work already queued on opts->stream, so that copies overlap tracing; the
+ * results equal one robast_trace_ex over all photons.  Pinned host buffers
+ * (cudaHostAlloc) let the copies run asynchronously.
  */
 int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
                       uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts);

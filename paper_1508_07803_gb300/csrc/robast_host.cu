@@ -72,6 +72,8 @@ struct robast_geom {
     // memory between calls (the device's default pool would hand it back at every
     // synchronisation and re-map it on the next call)
     cudaMemPool_t pool = nullptr;
+    cudaStream_t hstream[2] = {nullptr, nullptr};  // robast_trace_host's pipeline
+    cudaEvent_t hevent = nullptr;
     void* pinned = nullptr;  // pinned host staging for the reductions' small copies
     size_t pinned_bytes = 0;
     // resident blocks per SM of each trace kernel with this geometry's staged tables, looked
@@ -811,6 +813,9 @@ extern "C" void robast_free_geometry(robast_geom* g) {
     if (g->scratch) cudaFree(g->scratch);
     if (g->pinned) cudaFreeHost(g->pinned);
     if (g->pool) cudaMemPoolDestroy(g->pool);
+    for (int k = 0; k < 2; ++k)
+        if (g->hstream[k]) cudaStreamDestroy(g->hstream[k]);
+    if (g->hevent) cudaEventDestroy(g->hevent);
     cudaSetDevice(prev);
     delete g;
 }
@@ -1088,6 +1093,10 @@ static int grow_pinned(robast_geom* g, size_t need, const char* what) {
     return 0;
 }
 
+// Host buffers in and out, copies inside.  The photons go in chunks (at least 2^20
+// photons, at most 8 chunks) over two internal streams with double-buffered device slices,
+// so the upload of chunk c+1 and the download of chunk c-1 overlap the trace of chunk c.
+// Photon i keeps id first_photon_id + i, so the results equal one launch over all photons.
 extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths,
                                  int64_t n, uint64_t seed, const robast_trace_out* out, const robast_trace_opts* opts) {
     robast_trace_opts o;
@@ -1100,52 +1109,82 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
     if (n == 0) return 0;
     std::lock_guard<std::mutex> lk(g->mu);
     const size_t es = o.precision == 32 ? 4 : 8;
-    const size_t N = (size_t)n;
-    // device layout: in o[3n] d[3n] lam[n] vop[n] | out st[n] nb[n] hit[3n] dir[3n] last[n] fxy[2n] counters[8]
+    const long long CH = std::max<long long>(1LL << 20, ((long long)n + 7) / 8);  // photons per chunk
+    const int nch = (int)((n + CH - 1) / CH);
+    const size_t C = (size_t)std::min<long long>(CH, n);
+    // one device slice per buffer set (two sets): in o[3C] d[3C] lam[C] vop[C] |
+    // out st[C] nb[C] hit[3C] dir[3C] last[C] fxy[2C]; then the counters
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         const size_t at = off;
         off += align16(bytes);
         return at;
     };
-    const size_t xo = carve(3 * N * es), xd = carve(3 * N * es), xl = carve(N * es);
-    const size_t xv = o.variant_of_photon ? carve(N * 4) : 0;
-    const size_t xs = carve(N), xb = carve(N), xh = carve(3 * N * es), xr = carve(3 * N * es), xla = carve(N * 4);
-    const size_t xf = carve(2 * N * es), xc = carve(ROBAST_N_COUNTERS * 8);
-    rc = grow(&g->stage, &g->stage_bytes, off, "robast_trace_host");
+    const size_t xo = carve(3 * C * es), xd = carve(3 * C * es), xl = carve(C * es);
+    const size_t xv = o.variant_of_photon ? carve(C * 4) : 0;
+    const size_t xs = carve(C), xb = carve(C), xh = carve(3 * C * es), xr = carve(3 * C * es), xla = carve(C * 4);
+    const size_t xf = carve(2 * C * es);
+    const size_t set_bytes = off;
+    const size_t xc = 2 * set_bytes;
+    rc = grow(&g->stage, &g->stage_bytes, xc + ROBAST_N_COUNTERS * 8, "robast_trace_host");
     if (rc) return rc;
-    unsigned char* b = static_cast<unsigned char*>(g->stage);
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
-    CU(cudaMemcpyAsync(b + xo, origins, 3 * N * es, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
-    CU(cudaMemcpyAsync(b + xd, dirs, 3 * N * es, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
-    CU(cudaMemcpyAsync(b + xl, wavelengths, N * es, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
-    robast_trace_opts od = o;
-    if (o.variant_of_photon) {
-        CU(cudaMemcpyAsync(b + xv, o.variant_of_photon, N * 4, cudaMemcpyHostToDevice, s), "robast_trace_host: copy in");
-        od.variant_of_photon = reinterpret_cast<const int32_t*>(b + xv);
-    }
-    robast_trace_out dout{};
-    dout.status = out->status ? b + xs : nullptr;
-    dout.bounces = out->bounces ? b + xb : nullptr;
-    dout.hit = out->hit ? b + xh : nullptr;
-    dout.dir = out->dir ? b + xr : nullptr;
-    dout.last_surface = out->last_surface ? reinterpret_cast<int32_t*>(b + xla) : nullptr;
-    dout.focal_xy = out->focal_xy ? b + xf : nullptr;
-    unsigned long long* dc = reinterpret_cast<unsigned long long*>(b + xc);
-    dout.counters = dc;
+    for (int k = 0; k < 2; ++k)
+        if (!g->hstream[k]) CU(cudaStreamCreateWithFlags(&g->hstream[k], cudaStreamNonBlocking), "robast_trace_host: stream");
+    if (!g->hevent) CU(cudaEventCreateWithFlags(&g->hevent, cudaEventDisableTiming), "robast_trace_host: event");
+    unsigned char* base = static_cast<unsigned char*>(g->stage);
+    unsigned long long* dc = reinterpret_cast<unsigned long long*>(base + xc);
     CU(cudaMemsetAsync(dc, 0, ROBAST_N_COUNTERS * 8, s), "robast_trace_host: counters");
-    rc = robast_trace_ex(g, b + xo, b + xd, b + xl, n, seed, &dout, &od);
-    if (rc) return rc;
-    if (out->status) CU(cudaMemcpyAsync(out->status, dout.status, N, cudaMemcpyDeviceToHost, s), "copy out");
-    if (out->bounces) CU(cudaMemcpyAsync(out->bounces, dout.bounces, N, cudaMemcpyDeviceToHost, s), "copy out");
-    if (out->hit) CU(cudaMemcpyAsync(out->hit, dout.hit, 3 * N * es, cudaMemcpyDeviceToHost, s), "copy out");
-    if (out->dir) CU(cudaMemcpyAsync(out->dir, dout.dir, 3 * N * es, cudaMemcpyDeviceToHost, s), "copy out");
-    if (out->last_surface)
-        CU(cudaMemcpyAsync(out->last_surface, dout.last_surface, N * 4, cudaMemcpyDeviceToHost, s), "copy out");
-    if (out->focal_xy) CU(cudaMemcpyAsync(out->focal_xy, dout.focal_xy, 2 * N * es, cudaMemcpyDeviceToHost, s), "copy out");
+    CU(cudaEventRecord(g->hevent, s), "robast_trace_host: event");  // after the caller's earlier work
+    for (int k = 0; k < 2; ++k) CU(cudaStreamWaitEvent(g->hstream[k], g->hevent, 0), "robast_trace_host: wait");
+    const unsigned char* ho = static_cast<const unsigned char*>(origins);
+    const unsigned char* hd = static_cast<const unsigned char*>(dirs);
+    const unsigned char* hl = static_cast<const unsigned char*>(wavelengths);
+    const size_t pitch = (size_t)n * es;  // host distance between the x, y, z rows
+    for (int c = 0; c < nch; ++c) {
+        cudaStream_t st = g->hstream[c & 1];
+        unsigned char* b = base + (size_t)(c & 1) * set_bytes;
+        const size_t s0 = (size_t)c * CH, nc = (size_t)std::min<long long>(CH, n - (long long)s0);
+        // rows of the chunk: x, y, z of photons s0 .. s0 + nc - 1
+        CU(cudaMemcpy2DAsync(b + xo, nc * es, ho + s0 * es, pitch, nc * es, 3, cudaMemcpyHostToDevice, st),
+           "robast_trace_host: copy in");
+        CU(cudaMemcpy2DAsync(b + xd, nc * es, hd + s0 * es, pitch, nc * es, 3, cudaMemcpyHostToDevice, st),
+           "robast_trace_host: copy in");
+        CU(cudaMemcpyAsync(b + xl, hl + s0 * es, nc * es, cudaMemcpyHostToDevice, st), "robast_trace_host: copy in");
+        robast_trace_opts od = o;
+        od.stream = st;
+        od.first_photon_id = o.first_photon_id + (long long)s0;
+        if (o.variant_of_photon) {
+            CU(cudaMemcpyAsync(b + xv, o.variant_of_photon + s0, nc * 4, cudaMemcpyHostToDevice, st),
+               "robast_trace_host: copy in");
+            od.variant_of_photon = reinterpret_cast<const int32_t*>(b + xv);
+        }
+        robast_trace_out dout{};
+        dout.status = out->status ? b + xs : nullptr;
+        dout.bounces = out->bounces ? b + xb : nullptr;
+        dout.hit = out->hit ? b + xh : nullptr;
+        dout.dir = out->dir ? b + xr : nullptr;
+        dout.last_surface = out->last_surface ? reinterpret_cast<int32_t*>(b + xla) : nullptr;
+        dout.focal_xy = out->focal_xy ? b + xf : nullptr;
+        dout.counters = dc;
+        rc = robast_trace_ex(g, b + xo, b + xd, b + xl, (int64_t)nc, seed, &dout, &od);
+        if (rc) return rc;
+        unsigned char* os = static_cast<unsigned char*>(out->status);
+        unsigned char* ob = static_cast<unsigned char*>(out->bounces);
+        unsigned char* oh = static_cast<unsigned char*>(out->hit);
+        unsigned char* orr = static_cast<unsigned char*>(out->dir);
+        unsigned char* ol = reinterpret_cast<unsigned char*>(out->last_surface);
+        unsigned char* of = static_cast<unsigned char*>(out->focal_xy);
+        if (os) CU(cudaMemcpyAsync(os + s0, dout.status, nc, cudaMemcpyDeviceToHost, st), "copy out");
+        if (ob) CU(cudaMemcpyAsync(ob + s0, dout.bounces, nc, cudaMemcpyDeviceToHost, st), "copy out");
+        if (oh) CU(cudaMemcpy2DAsync(oh + s0 * es, pitch, dout.hit, nc * es, nc * es, 3, cudaMemcpyDeviceToHost, st), "copy out");
+        if (orr) CU(cudaMemcpy2DAsync(orr + s0 * es, pitch, dout.dir, nc * es, nc * es, 3, cudaMemcpyDeviceToHost, st), "copy out");
+        if (ol) CU(cudaMemcpyAsync(ol + s0 * 4, dout.last_surface, nc * 4, cudaMemcpyDeviceToHost, st), "copy out");
+        if (of) CU(cudaMemcpy2DAsync(of + s0 * es, pitch, dout.focal_xy, nc * es, nc * es, 2, cudaMemcpyDeviceToHost, st), "copy out");
+    }
     unsigned long long hc[ROBAST_N_COUNTERS];
-    CU(cudaMemcpyAsync(hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s), "copy out");
-    CU(cudaStreamSynchronize(s), "robast_trace_host: synchronize");
+    for (int k = 0; k < 2; ++k) CU(cudaStreamSynchronize(g->hstream[k]), "robast_trace_host: synchronize");
+    CU(cudaMemcpy(hc, dc, sizeof hc, cudaMemcpyDeviceToHost), "copy out");
     if (out->counters)
         for (int k = 0; k < ROBAST_N_COUNTERS; ++k) out->counters[k] += hc[k];
     return 0;

@@ -213,6 +213,22 @@ def test_host_buffer_entry_point_equals_device_entry_point():
     geom.close()
 
 
+def test_host_entry_point_pipelines_chunks_with_identical_results():
+    """More than 2^20 photons go through the host entry point in several chunks on two
+    streams; every output (and the counters) equals one device launch over all photons,
+    from pinned and from pageable host buffers alike."""
+    scene, b = W.lst_workload(460_001, seed=7)  # 2.3e6 photons: 3 chunks
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 32)
+    dev = to_numpy(robast.trace(geom, o, d, w, seed=4, first_photon_id=11))
+    for pin in (True, False):
+        ho, hd, hw = (t.cpu().pin_memory() if pin else t.cpu() for t in (o, d, w))
+        host = robast.trace_host(geom, ho, hd, hw, seed=4, first_photon_id=11)
+        for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters"):
+            assert np.array_equal(dev[k], host[k].numpy()), (pin, k)
+    geom.close()
+
+
 def test_bad_arguments_raise():
     scene, b = W.sphere_workload(100, seed=0)
     geom = robast.build_geometry(scene)
