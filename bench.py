@@ -425,10 +425,10 @@ def main():
         # per-photon outputs the spot diagram and the metric need: status, bounce count, focal (x, y)
         out = robast.alloc_outputs(N, precision, dev, fields=("status", "bounces", "focal_xy", "counters"))
         counters = out["counters"]
-        # per step: the coherent-order sort (init, bounds, count, three scan launches, place), the
+        # per step: the coherent-order sort (init, bounds, count, columns, three scan launches, place), the
         # trace, and the reduction (sums, finish, histogram, pick, compact, check, candidate r^2,
         # sub-histogram, pick, collect, select; all angles at once)
-        order_launches, psf_launches = 7, 11
+        order_launches, psf_launches = 8, 11
 
         def step(ev=None):
             if ev is not None:

@@ -15,9 +15,11 @@
 //
 // The sort is one pass of a block-local counting sort: every block of
 // 2^ORD_TILE_BITS photons (one tile of a chunk) counts its photons per cell
-// in shared memory; the counts, laid out [chunk][cell][tile of the chunk],
-// are scanned once; a second pass places each photon at its block's offset
-// for its cell (shared-memory atomics only).
+// in shared memory and writes them contiguously, [chunk][tile][cell]; one
+// thread per (chunk, cell) turns its column into running offsets over the
+// tiles (in place) and its total; the totals are scanned; a second pass places
+// each photon at base(chunk, cell) + offset(tile, cell) + its rank in the
+// block (shared-memory atomics only).  Every pass reads and writes coalesced.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -92,8 +94,8 @@ __device__ __forceinline__ int ord_cell(const T* o, long long n, long long i, co
     return cy * ORD_G + ((cy & 1) ? ORD_G - 1 - cx : cx);
 }
 
-// Pass 1: per-block cell counts, to counts[(chunk * CELLS + cell) * TILES + tile].
-// Blocks past n (in the last chunk) write zeros.
+// Pass 1: per-block cell counts, to counts[(chunk * TILES + tile) * CELLS + cell] (the
+// block's tile index is blockIdx.x).  Blocks past n (in the last chunk) write zeros.
 template <typename T>
 __global__ void __launch_bounds__(ORD_BLOCK) ord_count(const T* o, long long n, const int* box, unsigned* counts) {
     extern __shared__ unsigned h[];
@@ -104,19 +106,35 @@ __global__ void __launch_bounds__(ORD_BLOCK) ord_count(const T* o, long long n, 
     const long long b1 = min(n, b0 + (1LL << ORD_TILE_BITS));
     for (long long i = b0 + threadIdx.x; i < b1; i += ORD_BLOCK) atomicAdd(&h[ord_cell(o, n, i, m)], 1u);
     __syncthreads();
-    const long long chunk = blockIdx.x / ORD_TILES_PER_CHUNK, tile = blockIdx.x % ORD_TILES_PER_CHUNK;
-    unsigned* dst = counts + chunk * (long long)ORD_CELLS * ORD_TILES_PER_CHUNK + tile;
-    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) dst[(long long)c * ORD_TILES_PER_CHUNK] = h[c];
+    unsigned* dst = counts + (long long)blockIdx.x * ORD_CELLS;
+    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) dst[c] = h[c];
 }
 
-// Pass 2: each photon at its block's running offset for its cell.
+// Per (chunk, cell): the column of tile counts becomes running offsets (exclusive, in
+// place) and the column total goes to totals[chunk * CELLS + cell].
+__global__ void ord_columns(unsigned* counts, long long nchunks, unsigned* totals) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // chunk * CELLS + cell
+    if (k >= nchunks * ORD_CELLS) return;
+    const long long chunk = k / ORD_CELLS, cell = k % ORD_CELLS;
+    unsigned* col = counts + chunk * ORD_TILES_PER_CHUNK * (long long)ORD_CELLS + cell;
+    unsigned run = 0;
+    for (int t = 0; t < ORD_TILES_PER_CHUNK; ++t) {
+        const unsigned v = col[(long long)t * ORD_CELLS];
+        col[(long long)t * ORD_CELLS] = run;
+        run += v;
+    }
+    totals[k] = run;
+}
+
+// Pass 2: each photon at base(chunk, cell) + offset(tile, cell) + its rank in the block.
 template <typename T>
 __global__ void __launch_bounds__(ORD_BLOCK) ord_place(const T* o, long long n, const int* box, const unsigned* offs,
-                                                      int* order) {
+                                                      const unsigned* base, int* order) {
     extern __shared__ unsigned h[];
-    const long long chunk = blockIdx.x / ORD_TILES_PER_CHUNK, tile = blockIdx.x % ORD_TILES_PER_CHUNK;
-    const unsigned* src = offs + chunk * (long long)ORD_CELLS * ORD_TILES_PER_CHUNK + tile;
-    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) h[c] = src[(long long)c * ORD_TILES_PER_CHUNK];
+    const long long chunk = blockIdx.x / ORD_TILES_PER_CHUNK;
+    const unsigned* src = offs + (long long)blockIdx.x * ORD_CELLS;
+    const unsigned* bc = base + chunk * ORD_CELLS;
+    for (int c = threadIdx.x; c < ORD_CELLS; c += ORD_BLOCK) h[c] = bc[c] + src[c];
     __syncthreads();
     const OrdMap m = ord_map(box);
     const long long b0 = (long long)blockIdx.x << ORD_TILE_BITS;
@@ -192,20 +210,24 @@ static long long ord_round(long long bytes) { return (bytes + 255) / 256 * 256; 
 
 long long order_scratch_bytes(long long n) {
     const long long nbins = ord_blocks(n) * ORD_CELLS;
-    const long long ntiles = (nbins + ORD_TILE - 1) / ORD_TILE;
-    return 256 + ord_round(nbins * 4) + ord_round(n * 4) + ntiles * 4 + 1024;
+    const long long ncells = ord_blocks(n) / ORD_TILES_PER_CHUNK * ORD_CELLS;  // (chunk, cell) totals
+    const long long ntiles = (ncells + ORD_TILE - 1) / ORD_TILE;
+    return 256 + ord_round(nbins * 4) + ord_round(ncells * 4) + ord_round(n * 4) + ntiles * 4 + 1024;
 }
 
 template <typename T>
 static cudaError_t build_order_t(const T* o, long long n, void* scratch, int** order_out, int sms, cudaStream_t s) {
     const long long nblk = ord_blocks(n);
-    const long long nbins = nblk * ORD_CELLS;
-    const long long ntiles = (nbins + ORD_TILE - 1) / ORD_TILE;
+    const long long nchunks = nblk / ORD_TILES_PER_CHUNK;
+    const long long nbins = nblk * ORD_CELLS, ncells = nchunks * ORD_CELLS;
+    const long long ntiles = (ncells + ORD_TILE - 1) / ORD_TILE;
     unsigned char* b = static_cast<unsigned char*>(scratch);
     int* box = reinterpret_cast<int*>(b);
     unsigned* counts = reinterpret_cast<unsigned*>(b + 256);
-    int* order = reinterpret_cast<int*>(b + 256 + ord_round(nbins * 4));
-    unsigned* tiles = reinterpret_cast<unsigned*>(b + 256 + ord_round(nbins * 4) + ord_round(n * 4));
+    unsigned* totals = reinterpret_cast<unsigned*>(b + 256 + ord_round(nbins * 4));
+    int* order = reinterpret_cast<int*>(b + 256 + ord_round(nbins * 4) + ord_round(ncells * 4));
+    unsigned* tiles =
+        reinterpret_cast<unsigned*>(b + 256 + ord_round(nbins * 4) + ord_round(ncells * 4) + ord_round(n * 4));
     const int smem = ORD_CELLS * (int)sizeof(unsigned);
     // the 64 KB shared-memory opt-in, once per device and precision
     static std::atomic<unsigned long long> opted{0};
@@ -222,10 +244,11 @@ static cudaError_t build_order_t(const T* o, long long n, void* scratch, int** o
     ord_init<<<1, 32, 0, s>>>(box);
     ord_bounds<T><<<sms * 4, 256, 0, s>>>(o, n, box);
     ord_count<T><<<(unsigned)nblk, ORD_BLOCK, smem, s>>>(o, n, box, counts);
-    ord_tile_sums<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(counts, nbins, tiles);
+    ord_columns<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(counts, nchunks, totals);
+    ord_tile_sums<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(totals, ncells, tiles);
     ord_scan_tiles<<<1, ORD_TILE, 0, s>>>(tiles, (int)ntiles);
-    ord_tile_scan<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(counts, nbins, tiles);
-    ord_place<T><<<(unsigned)nblk, ORD_BLOCK, smem, s>>>(o, n, box, counts, order);
+    ord_tile_scan<<<(unsigned)ntiles, ORD_TILE, 0, s>>>(totals, ncells, tiles);
+    ord_place<T><<<(unsigned)nblk, ORD_BLOCK, smem, s>>>(o, n, box, counts, totals, order);
     *order_out = order;
     return cudaGetLastError();
 }

@@ -53,8 +53,7 @@ struct robast_geom {
     double length_scale = 1.0;
     void* dmem = nullptr;  // one allocation holding every table
     Tables tab32{}, tab64{};
-    const float* grec32 = nullptr;    // per surface: d rows / d tilt_x, d rows / d tilt_y
-    const double* grec64 = nullptr;
+    const double* grec64 = nullptr;    // per surface: d rows / d tilt_x, d rows / d tilt_y
     const int* surf_var = nullptr;    // variant of each surface
     std::vector<int> h_var, h_flags;  // host copies: variant, shape | role << 4 of each surface
     size_t smem32 = 0, smem64 = 0;  // bytes to stage each precision's tables
@@ -539,7 +538,6 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     std::vector<int4> reci(ns);
     std::vector<std::vector<Ref>> refs_of(ns);  // BVH references per surface; empty = unbounded
     std::vector<double> grec64((size_t)ns * 18, 0.0);
-    std::vector<float> grec32((size_t)ns * 18, 0.0f);
     for (int i = 0; i < ns; ++i) {
         const robast_surface_desc& s = d->surfaces[i];
         double* R = &rec64[(size_t)i * REC];
@@ -610,7 +608,6 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
             mat3_mul(rxT, s.rot, t1);
             mat3_mul(dryT, t1, t2);  // d/db
             for (int k = 0; k < 9; ++k) grec64[(size_t)i * 18 + 9 + k] = t2[k];
-            for (int k = 0; k < 18; ++k) grec32[(size_t)i * 18 + k] = (float)grec64[(size_t)i * 18 + k];
         }
         reci[i] = make_int4(s.shape | (s.role << 4) | (s.aperture << 8) | ((asph ? 1 : 0) << 12), s.material,
                             s.medium_front, s.medium_back);
@@ -692,7 +689,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t bm = align16(mats.size() * 8), bd = align16(meds.size() * 8), bm32 = align16(mats32.size() * 4);
     const size_t bd32 = align16(meds32.size() * 4);
     const size_t bw = kWorkSlots * 8;
-    const size_t bg64 = align16(grec64.size() * 8), bg32 = align16(grec32.size() * 4);
+    const size_t bg64 = align16(grec64.size() * 8);
     std::vector<int> surf_var(ns, 0);
     for (int v = 0; v < nv; ++v) {
         const int s0 = d->variant_offsets ? d->variant_offsets[v] : 0;
@@ -700,7 +697,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         for (int s = s0; s < s1; ++s) surf_var[s] = v;
     }
     const size_t bsv = align16(surf_var.size() * 4);
-    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bd32 + bw + bg64 + bg32 + bsv;
+    const size_t total = b64 + b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bd32 + bw + bg64 + bsv;
 
     robast_geom* g = new (std::nothrow) robast_geom();
     if (!g) return fail(ROBAST_E_OOM, "robast_build_geometry: host allocation failed");
@@ -751,7 +748,6 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     const size_t ow = off;
     off += bw;
     const size_t og64 = put(grec64.data(), grec64.size() * 8, bg64);
-    const size_t og32 = put(grec32.data(), grec32.size() * 4, bg32);
     const size_t osv = put(surf_var.data(), surf_var.size() * 4, bsv);
     e = cudaMemcpy(g->dmem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -783,7 +779,6 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->tab32.surf = base + o32;
     g->work = reinterpret_cast<unsigned long long*>(base + ow);
     g->grec64 = reinterpret_cast<const double*>(base + og64);
-    g->grec32 = reinterpret_cast<const float*>(base + og32);
     g->surf_var = reinterpret_cast<const int*>(base + osv);
     g->smem64 = b64 + bi + bn + bp + bv + bg + bm + bd;
     g->smem32 = b32 + bi + bn + bp + bv + bg + bm + bd + bm32 + bd32;
