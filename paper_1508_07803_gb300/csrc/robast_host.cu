@@ -1564,7 +1564,7 @@ __device__ __forceinline__ void psf_for_bins(const uint8_t* st, const T* fxy, lo
     psf_loop<false>(st, fxy, ld, w, R, body);
 }
 
-// sub-bin of r^2 in round 2 (non-decreasing in r^2 for any a and s2 >= 0)
+// sub-bin of r^2 in the second histogram (non-decreasing in r^2 for any a and s2 >= 0)
 __device__ __forceinline__ int psf_sub(double r2, double a, double s2) {
     const double f = (r2 - a) * s2;
     if (!(f > 0.0)) return 0;  // also NaN
@@ -1660,7 +1660,7 @@ __device__ void block_find_rank(const unsigned long long* H, int nb, long long k
     *total = (long long)csum[kScanBlock - 1];
 }
 
-// Round 1 decision: rank k, bin b, bins lo..hi kept, the sub-bin interval.
+// First-histogram decision: rank k, bin b, bins lo..hi kept, the sub-bin interval.
 __global__ void psf_pick1(const unsigned long long* hist, const double* res, const Win* win, int nslice, Sel* sel) {
     const int w = blockIdx.x;
     const double* R = res + kRes * w;
@@ -1778,7 +1778,7 @@ __global__ void psf_cand_r2(const T* fxy, long long ld, const Win* win, const do
         }
 }
 
-// Round 2: sub-bin histogram of the kept photons' exact r^2.
+// Second histogram: sub-bins of the kept photons' exact r^2.
 __global__ void psf_hist2(const Win* win, const Sel* sel, const double* r2, const unsigned long long* cand_n,
                           int nslice, unsigned long long* hist2) {
     __shared__ unsigned int h[kSub];
@@ -1798,7 +1798,7 @@ __global__ void psf_hist2(const Win* win, const Sel* sel, const double* r2, cons
         if (h[k]) atomicAdd(H + k, (unsigned long long)h[k]);
 }
 
-// Round 2 decision: the sub-bin that holds rank1.
+// Second-histogram decision: the sub-bin that holds rank1.
 __global__ void psf_pick2(const unsigned long long* hist2, Sel* sel) {
     const int w = blockIdx.x;
     const Sel S = sel[w];
