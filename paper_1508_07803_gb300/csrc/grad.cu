@@ -84,8 +84,14 @@ __device__ __forceinline__ T sigmoid_t(T x) {
     return T(1) / (T(1) + (sizeof(T) == 4 ? (T)expf(-(float)x) : (T)exp(-(double)x)));
 }
 
+// Resident blocks of 128 threads per SM the register allocation must allow.  The dual state
+// spills at any cap; more warps hide the local-memory latency better.  Dish batch, 3.2e7
+// photons (FP32 form): 1 (255 registers) 720 ms, 2 721, 3 973, 4 637, 5 640, 6 642, 8 658.
+#ifndef ROBAST_GRAD_MIN_BLOCKS
+#define ROBAST_GRAD_MIN_BLOCKS 4
+#endif
 template <typename T, int BLOCK, bool STAGED>
-__global__ void __launch_bounds__(BLOCK) grad_kernel(GradArgs<T> A) {
+__global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(GradArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     Tables tb = A.tab;
     if constexpr (STAGED) {
