@@ -231,9 +231,10 @@ typedef struct robast_trace_opts {
                                        counting build of the kernel (block 128, slower) and
                                        adds the work units below to it */
     int32_t coherent_order;   /* 0: library default (on for n >= 65536), 1: on, -1: off.  On, the
-                                 photons are first sorted by origin cell (stream-ordered scratch
-                                 of ~4n bytes) so that each warp traces neighbouring rays; the
-                                 results are identical either way */
+                                 photons are first sorted by origin cell so that each warp traces
+                                 neighbouring rays; the results are identical either way.  The
+                                 sort's scratch (~5n bytes) is stream-ordered, from a memory pool
+                                 owned by g that keeps its largest use until robast_free_geometry */
     const robast_track_opts* track; /* host pointer or NULL: record photon tracks */
     int32_t refill_min;       /* 0..32; 0 = library default (24).  A warp takes new photons for its
                                  idle lanes once at least refill_min of its 32 lanes are idle, or all
