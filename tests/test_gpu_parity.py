@@ -229,6 +229,32 @@ def test_host_entry_point_pipelines_chunks_with_identical_results():
     geom.close()
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+def test_host_entry_point_chunks_with_variants(precision):
+    """The chunked host path with a variant index per photon, in both precisions: the
+    chunks' variant slices and FP64 row pitches land where one device launch puts them."""
+    nv = 4
+    scene = W.cone_scene(n_variants=nv, seed=2)
+    Hs = W.cone_heights(nv, seed=2)
+    bs, vop = [], []
+    for v in range(nv):
+        b = W.hexagon_bundle(330_001, W.CONE_A_IN, Hs[v] + W.CONE_WINDOW + 1e-4, math.radians(4 * v), seed=v,
+                             stream=600 + v)
+        bs.append(b)
+        vop.append(np.full(b.n, v, np.int32))
+    b = W.concat(bs)  # 1.32e6 photons: two chunks
+    vop = np.concatenate(vop)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, precision)
+    dev = to_numpy(robast.trace(geom, o, d, w, seed=8, precision=precision, max_bounces=30,
+                                variant_of_photon=torch.from_numpy(vop).cuda()))
+    host = robast.trace_host(geom, o.cpu().pin_memory(), d.cpu().pin_memory(), w.cpu().pin_memory(), seed=8,
+                             precision=precision, max_bounces=30, variant_of_photon=torch.from_numpy(vop))
+    for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters"):
+        assert np.array_equal(dev[k], host[k].numpy()), k
+    geom.close()
+
+
 def test_bad_arguments_raise():
     scene, b = W.sphere_workload(100, seed=0)
     geom = robast.build_geometry(scene)
