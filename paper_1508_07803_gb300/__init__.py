@@ -268,6 +268,9 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
 
     work_units: optional CUDA int64 tensor [N_UNITS]; when given, the counting
     build of the kernel runs and adds its work units (UNIT_NAMES) to it.
+    block_size (64, 128, 256, or 512 for FP32), blocks_per_sm, coherent_order
+    and refill_min (0..32: idle lanes a warp waits for before it takes new
+    photons) shape the launch only: the results do not depend on them.
     """
     import torch
     lib = load()
@@ -303,7 +306,11 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
 def trace_host(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32,
                max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
                eps: Optional[float] = None, variant_of_photon=None):
-    """robast_trace_host: host (CPU, ideally pinned) tensors in and out; synchronous."""
+    """robast_trace_host: host (CPU, ideally pinned) tensors in and out; synchronous.
+
+    The photons go to the GPU in chunks over two streams, so copies overlap the
+    trace; the results equal one robast.trace over all photons.
+    """
     import torch
     lib = load()
     dt = torch.float32 if precision == 32 else torch.float64
