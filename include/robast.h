@@ -186,7 +186,14 @@ int robast_geometry_info(const robast_geom* g, int32_t* n_surfaces, int32_t* n_v
  *        interaction point, or the origin if there was none),
  *   dir [3n] final direction, last_surface [n] i32 (-1: none),
  *   focal_xy [2n] local (x, y) on the focal surface (DETECTED only, else 0),
- *   counters [ROBAST_N_COUNTERS] u64, atomically accumulated.
+ *   counters [ROBAST_N_COUNTERS] u64, atomically accumulated,
+ *   err [2n] f32, FP32 trace only: per photon, the running first-order estimate of
+ *        the rounding error of the final position (m, row 0) and direction (rad,
+ *        row 1) against an exact trace of the same inputs; -1, -1 where the result
+ *        comes from the FP64 re-trace of the accuracy guard (robast_trace_opts),
+ *   retraced [2] u64, atomically accumulated: [0] photons of the FP32 trace
+ *        re-traced in FP64 by the accuracy guard, [1] photons over the guard's
+ *        bounds that did not fit its queue and keep their FP32 result.
  */
 typedef struct robast_trace_out {
     uint8_t* status;
@@ -196,6 +203,8 @@ typedef struct robast_trace_out {
     int32_t* last_surface;
     void* focal_xy;
     unsigned long long* counters;
+    float* err;
+    unsigned long long* retraced;
 } robast_trace_out;
 
 /*
@@ -242,6 +251,20 @@ typedef struct robast_trace_opts {
                                  lanes of a warp on the same bounce of neighbouring photons (coherent
                                  traversal) at the cost of idle lanes; 1 refills at once.  The
                                  results do not depend on it */
+    double accuracy_pos;      /* FP32 accuracy guard (0 = off), final-position error bound (m), and */
+    double accuracy_dir;      /* final-direction error bound (rad); 0 in one = no bound on it.  Every
+                                 FP32 photon carries a first-order estimate of its accumulated
+                                 rounding error: per interaction the hit point moves by (lateral
+                                 offset + segment x direction error + a few ulps of the coordinates)
+                                 / |cos incidence|, the normal by the surface's curvature bound times
+                                 that, and the new direction by twice the normal's error
+                                 (reflection) or by Snell's derivative (refraction).  A photon whose
+                                 estimate exceeds half a bound, or that ends in ERROR, is re-traced
+                                 from its inputs in FP64 (same random streams, same epsilon) by a
+                                 second launch on the same stream, whose result replaces the FP32
+                                 one.  The queue holds n photons (n > 2^26: max(2^26, n / 8)); its
+                                 scratch comes from g's memory pool like the sort's.  Off with
+                                 photon tracks or the counting build */
 } robast_trace_opts;
 
 /* Work units counted when opts.work_units is set: ray-box tests, quadric root
@@ -309,7 +332,10 @@ typedef struct robast_source_group {
 
 typedef struct robast_sources robast_sources; /* opaque device-resident group table */
 
-/* Upload n_groups groups (host array, deep-copied) for geometry g.  Synchronous. */
+/* Upload n_groups groups (host array, deep-copied) for geometry g.  Synchronous.  Also
+ * allocates the FP32 accuracy guard's re-trace queue for these photons (8 bytes per queued
+ * photon: all N photons for N <= 2^26, else max(2^26, N / 16)), so that robast_trace_sources
+ * allocates nothing. */
 int robast_sources_create(const robast_geom* g, const robast_source_group* groups, int32_t n_groups,
                           robast_sources** out);
 void robast_sources_free(robast_sources* s);
@@ -322,7 +348,8 @@ int robast_sources_info(const robast_sources* s, int32_t* n_groups, int64_t* n_p
  * collection efficiency = counts[1] / counts[7].  `out` (device arrays of the
  * total photon count, any field NULL) may be NULL.  opts as for
  * robast_trace_ex (variant_of_photon must be NULL).  Asynchronous; issues
- * only a memset and a kernel launch on the stream, so it can be captured in a
+ * only memsets and kernel launches on the stream (with the accuracy guard on,
+ * two more memsets and the FP64 re-trace launch), so it can be captured in a
  * CUDA graph.
  */
 int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64_t seed,
@@ -410,20 +437,27 @@ int robast_psf(robast_geom* g, const uint8_t* status, const void* focal_xy, int6
 /*
  * robast_psf_noalloc: the same statistics as robast_psf (same arguments minus
  * the geometry, same results) for callers that cannot allocate device memory
- * when they need them -- for example code recording a CUDA graph, code whose
- * device memory is all owned by a caching allocator, or an embedding with a
- * fixed memory budget.  The paper has no counterpart; this is a property of
- * the library, not of the method.
+ * when they need them -- for example code whose device memory is all owned by
+ * a caching allocator, or an embedding with a fixed memory budget.  The paper
+ * has no counterpart; this is a property of the library, not of the method.
  *
  * It allocates nothing: its scratch is one fixed array of about 6.4 MB in
  * device memory, defined at file scope in the library, which every GPU that
  * loads the library holds until the process exits; its host buffers are
  * static too.  Limit: at most 64 windows per call (ROBAST_E_INVALID beyond).
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture on it.
- * Every call on a device shares the array and leaves its contents behind
- * (each call clears what it needs cleared), so calls whose GPU work overlaps
- * race with one another: issue them one at a time.  Synchronises the stream.
+ * device current.  Every call on a device shares the array and leaves its
+ * contents behind (each call clears what it needs cleared), so calls whose
+ * GPU work overlaps race with one another: issue them one at a time.
+ * Synchronises the stream several times and reads intermediate results on the
+ * host, so it must not be called while the stream is being captured into a
+ * CUDA graph.  The R80 is the exact nearest-rank value, as robast_psf's: a
+ * rank that falls among many copies of a few nearly equal values is resolved
+ * by counting the copies of each value.  ROBAST_E_INVALID if the rank's final
+ * bin still spans 4096 or more distinct doubles after 8 rounds of 4096-bin
+ * refinement: possible only for FP64 coordinates whose radii about the
+ * centroid come within about 1e-29 of the spot's size of zero without being
+ * zero (robast_psf has no such limit).
  */
 int robast_psf_noalloc(const uint8_t* status, const void* focal_xy, int64_t ld, int32_t n_windows,
                        const int64_t* starts, const int64_t* counts, int32_t precision, void* stream,

@@ -68,7 +68,9 @@ class GeomDesc(ctypes.Structure):
 class TraceOut(ctypes.Structure):
     _fields_ = [("status", ctypes.c_void_p), ("bounces", ctypes.c_void_p), ("hit", ctypes.c_void_p),
                 ("dir", ctypes.c_void_p), ("last_surface", ctypes.c_void_p), ("focal_xy", ctypes.c_void_p),
-                ("counters", ctypes.c_void_p)]
+                ("counters", ctypes.c_void_p), ("err", ctypes.c_void_p), ("retraced", ctypes.c_void_p)]
+
+OUT_FIELDS = ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters", "err", "retraced")
 
 
 class TrackOpts(ctypes.Structure):
@@ -81,7 +83,14 @@ class TraceOpts(ctypes.Structure):
                 ("variant_of_photon", ctypes.c_void_p), ("first_photon_id", ctypes.c_int64),
                 ("eps", ctypes.c_double), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("work_units", ctypes.c_void_p), ("coherent_order", ctypes.c_int32),
-                ("track", ctypes.POINTER(TrackOpts)), ("refill_min", ctypes.c_int32)]
+                ("track", ctypes.POINTER(TrackOpts)), ("refill_min", ctypes.c_int32),
+                ("accuracy_pos", ctypes.c_double), ("accuracy_dir", ctypes.c_double)]
+
+# Default FP32 accuracy: final positions within 1e-6 of the system focal length, final
+# directions within 1e-5 rad of an exact trace of the same inputs (the accuracy guard re-traces
+# in FP64 every photon whose running error estimate exceeds half of either bound).
+ACCURACY_REL_POS = 1e-6
+ACCURACY_DIR = 1e-5
 
 N_UNITS = 12
 UNIT_NAMES = ("aabb", "sag", "newton", "aperture", "cylinder", "box", "hexwall", "reflect", "refract", "rough",
@@ -188,6 +197,7 @@ class Geometry:
     def __init__(self, handle, scene):
         self._h = ctypes.c_void_p(handle)
         self.length_scale = float(scene.length_scale)
+        self.focal_length = float(scene.focal_length)
         self.n_surfaces = len(scene.surfaces)
         ns, nv, nn = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(_lib.robast_geometry_info(self._h, ctypes.byref(ns), ctypes.byref(nv), ctypes.byref(nn)))
@@ -225,8 +235,23 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _trace_out(out):
+    return TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None) for k in OUT_FIELDS])
+
+
+def _accuracy(geom, precision, accuracy):
+    """(position bound m, direction bound rad) of the FP32 accuracy guard: None = the default
+    (1e-6 f, 1e-5 rad), False / 0 = off, or a pair."""
+    if precision != 32 or accuracy is False or accuracy == 0:
+        return 0.0, 0.0
+    if accuracy is None:
+        return ACCURACY_REL_POS * geom.focal_length, ACCURACY_DIR
+    pos, ang = accuracy
+    return float(pos or 0.0), float(ang or 0.0)
+
+
 def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_size, blocks_per_sm, units=None,
-          coherent_order=0, refill_min=0):
+          coherent_order=0, refill_min=0, accuracy=(0.0, 0.0)):
     o = TraceOpts()
     _lib.robast_trace_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -240,6 +265,7 @@ def _opts(precision, max_bounces, stream, vop_ptr, first_photon_id, eps, block_s
     o.work_units = ctypes.c_void_p(units.data_ptr()) if units is not None else None
     o.coherent_order = int(coherent_order)
     o.refill_min = int(refill_min)
+    o.accuracy_pos, o.accuracy_dir = float(accuracy[0]), float(accuracy[1])
     return o
 
 
@@ -255,15 +281,17 @@ def alloc_outputs(n: int, precision: int = 32, device="cuda", fields=None):
         "last_surface": lambda: torch.empty(n, dtype=torch.int32, device=device),
         "focal_xy": lambda: torch.empty((2, n), dtype=dt, device=device),
         "counters": lambda: torch.zeros(N_COUNTERS, dtype=torch.int64, device=device),
+        "retraced": lambda: torch.zeros(2, dtype=torch.int64, device=device),
+        "err": lambda: torch.empty((2, n), dtype=torch.float32, device=device),
     }
-    keys = fields if fields is not None else list(all_fields)
+    keys = fields if fields is not None else [k for k in all_fields if k != "err" and (k != "retraced" or precision == 32)]
     return {k: all_fields[k]() for k in keys}
 
 
 def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32, max_bounces: int = 100,
           stream=None, variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None,
           block_size: int = 0, blocks_per_sm: int = 0, out: Optional[dict] = None, work_units=None,
-          coherent_order: int = 0, track=None, refill_min: int = 0):
+          coherent_order: int = 0, track=None, refill_min: int = 0, accuracy=None, error_estimate: bool = False):
     """robast_trace_ex on CUDA tensors; returns the dict of output tensors.
 
     work_units: optional CUDA int64 tensor [N_UNITS]; when given, the counting
@@ -271,6 +299,13 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
     block_size (64, 128, 256, or 512 for FP32), blocks_per_sm, coherent_order
     and refill_min (0..32: idle lanes a warp waits for before it takes new
     photons) shape the launch only: the results do not depend on them.
+    accuracy (FP32): None = final positions within 1e-6 of the geometry's focal
+    length and directions within 1e-5 rad of an exact trace, enforced by
+    re-tracing in FP64 the photons whose running error estimate exceeds half a
+    bound; a (pos_m, dir_rad) pair sets the bounds; False turns the guard off.
+    out["retraced"] counts (re-traced, over a bound but not re-traced).
+    error_estimate: also return out["err"] [2, n] float32, the per-photon
+    position / direction error estimate (-1 where the photon was re-traced).
     """
     import torch
     lib = load()
@@ -281,8 +316,9 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
             raise RobastError(f"{name}: need a contiguous CUDA {dt} tensor of shape {shape}")
     if out is None:
         out = alloc_outputs(n, precision, origins.device)
-    tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
-                      for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
+        if error_estimate and precision == 32:
+            out["err"] = torch.empty((2, n), dtype=torch.float32, device=origins.device)
+    tout = _trace_out(out)
     if stream is None:
         stream = torch.cuda.current_stream(origins.device)
     sp = ctypes.c_void_p(stream.cuda_stream)
@@ -292,7 +328,7 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
             raise RobastError("variant_of_photon: need a CUDA int32 tensor")
         vop = ctypes.c_void_p(variant_of_photon.data_ptr())
     o = _opts(precision, max_bounces, sp, vop, first_photon_id, eps, block_size, blocks_per_sm, work_units,
-              coherent_order, refill_min)
+              coherent_order, refill_min, _accuracy(geom, precision, accuracy))
     tr = None
     if track is not None:
         tr = TrackOpts(int(track["first"]), int(track["count"]), int(track["cap"]), track["points"].data_ptr(),
@@ -305,11 +341,12 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
 
 def trace_host(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: int = 32,
                max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
-               eps: Optional[float] = None, variant_of_photon=None):
+               eps: Optional[float] = None, variant_of_photon=None, accuracy=None, error_estimate: bool = False):
     """robast_trace_host: host (CPU, ideally pinned) tensors in and out; synchronous.
 
     The photons go to the GPU in chunks over two streams, so copies overlap the
-    trace; the results equal one robast.trace over all photons.
+    trace; the results equal one robast.trace over all photons.  accuracy and
+    error_estimate as for trace().
     """
     import torch
     lib = load()
@@ -320,12 +357,14 @@ def trace_host(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precis
             raise RobastError(f"{name}: need a contiguous host {dt} tensor")
     if out is None:
         out = alloc_outputs(n, precision, "cpu")
-    tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
-                      for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
+        if error_estimate and precision == 32:
+            out["err"] = torch.empty((2, n), dtype=torch.float32)
+    tout = _trace_out(out)
     if stream is None:
         stream = torch.cuda.current_stream()
     vop = ctypes.c_void_p(variant_of_photon.data_ptr()) if variant_of_photon is not None else None
-    o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), vop, first_photon_id, eps, 0, 0)
+    o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), vop, first_photon_id, eps, 0, 0,
+              accuracy=_accuracy(geom, precision, accuracy))
     _check(lib.robast_trace_host(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,
                                  ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(tout), ctypes.byref(o)))
     return out
@@ -345,18 +384,34 @@ def psf(geom: Geometry, status, focal_xy, precision: int = 32, stream=None, star
     single = windows is None
     if single:
         windows = [(start, N - start if count is None else int(count))]
-    if not (tuple(focal_xy.shape) == (2, N) and focal_xy.is_contiguous()):
-        raise RobastError("psf: need status [N] and contiguous focal_xy [2, N]")
+    _check_spot_args(status, focal_xy, precision, "psf")
     if stream is None:
         stream = torch.cuda.current_stream(status.device)
     nw = len(windows)
     st = (ctypes.c_int64 * nw)(*[int(w[0]) for w in windows])
     ct = (ctypes.c_int64 * nw)(*[int(w[1]) for w in windows])
     res = (ctypes.c_double * (4 * nw))()
-    _check(lib.robast_psf(geom.handle, _ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
-                          ctypes.c_void_p(stream.cuda_stream), res))
+    with torch.cuda.device(status.device):
+        _check(lib.robast_psf(geom.handle, _ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
+                              ctypes.c_void_p(stream.cuda_stream), res))
     out = [tuple(res[4 * w:4 * w + 4]) for w in range(nw)]
     return out[0] if single else out
+
+
+def _check_spot_args(status, focal_xy, precision, name):
+    """The spot-diagram reductions read N status bytes and 2N focal coordinates of the
+    precision's type from one device: anything else would read past the buffers."""
+    import torch
+    want = {32: torch.float32, 64: torch.float64}.get(int(precision))
+    if want is None:
+        raise RobastError(f"{name}: precision must be 32 or 64")
+    N = int(status.shape[0]) if status.dim() == 1 else -1
+    if status.dtype != torch.uint8 or status.dim() != 1 or not status.is_contiguous():
+        raise RobastError(f"{name}: status must be a contiguous uint8 tensor [N]")
+    if focal_xy.dtype != want or tuple(focal_xy.shape) != (2, N) or not focal_xy.is_contiguous():
+        raise RobastError(f"{name}: focal_xy must be a contiguous {want} tensor [2, {N}] for precision {precision}")
+    if not (status.is_cuda and focal_xy.is_cuda) or status.device != focal_xy.device:
+        raise RobastError(f"{name}: status and focal_xy must be CUDA tensors on one device")
 
 
 def version() -> str:
@@ -388,16 +443,16 @@ def psf_noalloc(status, focal_xy, windows, precision: int = 32, stream=None):
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.POINTER(ctypes.c_double)]
     N = int(status.shape[0])
-    if not (tuple(focal_xy.shape) == (2, N) and focal_xy.is_contiguous()):
-        raise RobastError("psf_noalloc: need status [N] and contiguous focal_xy [2, N]")
+    _check_spot_args(status, focal_xy, precision, "psf_noalloc")
     if stream is None:
         stream = torch.cuda.current_stream(status.device)
     nw = len(windows)
     st = (ctypes.c_int64 * nw)(*[int(w[0]) for w in windows])
     ct = (ctypes.c_int64 * nw)(*[int(w[1]) for w in windows])
     res = (ctypes.c_double * (4 * nw))()
-    _check(lib.robast_psf_noalloc(_ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
-                                  ctypes.c_void_p(stream.cuda_stream), res))
+    with torch.cuda.device(status.device):
+        _check(lib.robast_psf_noalloc(_ptr(status), _ptr(focal_xy), N, nw, st, ct, int(precision),
+                                      ctypes.c_void_p(stream.cuda_stream), res))
     return [tuple(res[4 * w:4 * w + 4]) for w in range(nw)]
 
 
@@ -459,11 +514,13 @@ def sources_create(geom: Geometry, groups) -> Sources:
 
 def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, precision: int = 32,
                   max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
-                  eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0):
+                  eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0,
+                  accuracy=None):
     """robast_trace_sources: trace every photon of the source groups in one launch.
 
     group_counts: CUDA int64 tensor [n_groups, 8], added to.  out: optional
     dict of per-photon output tensors (see alloc_outputs) for src.n_photons.
+    accuracy as for trace() (FP32: the FP64 re-trace is a second launch).
     """
     import torch
     lib = load()
@@ -476,10 +533,9 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
         stream = torch.cuda.current_stream(group_counts.device)
     tout = None
     if out is not None:
-        tout = TraceOut(*[(out[k].data_ptr() if out.get(k) is not None else None)
-                          for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "counters")])
+        tout = _trace_out(out)
     o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), None, first_photon_id, eps, block_size,
-              blocks_per_sm, refill_min=refill_min)
+              blocks_per_sm, refill_min=refill_min, accuracy=_accuracy(geom, precision, accuracy))
     _check(lib.robast_trace_sources(geom.handle, src.handle, ctypes.c_uint64(seed & (2**64 - 1)),
                                     ctypes.c_void_p(group_counts.data_ptr()),
                                     ctypes.byref(tout) if tout is not None else None, ctypes.byref(o)))

@@ -50,4 +50,8 @@ cudaError_t build_order_f64(const double* o, long long n, void* scratch, int** o
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceArgs<double>& a, int block, int grid, size_t smem, cudaStream_t s);
 
+// FP64 re-trace of the FP32 photons queued by the accuracy guard (block 128).
+int retrace_blocks_per_sm(size_t smem, bool src);
+cudaError_t launch_retrace(const TraceArgs<double, float>& a, int grid, size_t smem, cudaStream_t s);
+
 }  // namespace robast

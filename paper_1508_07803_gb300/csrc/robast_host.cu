@@ -78,6 +78,7 @@ struct robast_geom {
     // resident blocks per SM of each trace kernel with this geometry's staged tables, looked
     // up once: [precision 32/64][block 64/128/256/512][source mode]; 0 = not yet known
     std::atomic<int> bps_cache[2][4][2] = {};
+    std::atomic<int> bps_retrace[2] = {};  // the FP64 re-trace kernel [source mode]
 };
 
 static const int kWorkSlots = 256;
@@ -131,6 +132,58 @@ bool any_asph(const robast_surface_desc& s) {
     for (int i = 0; i < 8; ++i)
         if (s.asph[i] != 0.0) return true;
     return false;
+}
+
+// Bound on the principal curvatures of a surface over the region its hits can lie in (the
+// FP32 error estimate turns a hit-point error into a normal error with it): the largest of
+// the meridional and sagittal curvatures of a sag surface sampled over 1.1x its aperture's
+// bounding radius, 1 / radius for a cylinder, 0 for a box, the largest curvature of a cone's
+// Bezier profile; times 1.1 for what the sampling (1024 points) misses.
+double curvature_bound(const robast_surface_desc& s, double L) {
+    const int NS = 1024;
+    double kmax = 0.0;
+    switch (s.shape) {
+        case ROBAST_SHAPE_SAG: {
+            const double c = s.curv, k1 = 1.0 + s.conic;
+            double rmax = 1.1 * aperture_bound(s);
+            if (k1 * c * c > 0.0) rmax = std::min(rmax, 0.999 / std::sqrt(k1 * c * c));
+            if (!std::isfinite(rmax)) rmax = 10.0 * L;
+            for (int k = 0; k <= NS; ++k) {
+                const double r = rmax * k / NS, rho = r * r;
+                const double arg = 1.0 - k1 * c * c * rho;
+                if (arg <= 0.0) break;
+                const double sq = std::sqrt(arg);
+                double S = c / (2.0 * sq), dS = c * k1 * c * c / (4.0 * sq * sq * sq);
+                double rp = 1.0;  // rho^(i-1)
+                for (int i = 1; i <= 8; ++i) {
+                    S += i * s.asph[i - 1] * rp;
+                    if (i >= 2) dS += i * (i - 1) * s.asph[i - 1] * rp / rho;
+                    rp *= rho;
+                }
+                if (rho == 0.0) dS = c * k1 * c * c / 4.0 + 2.0 * s.asph[1];
+                const double z1 = 2.0 * r * S, z2 = 2.0 * S + 4.0 * rho * dS;  // dz/dr, d2z/dr2
+                const double q = 1.0 + z1 * z1;
+                const double km = std::fabs(z2) / (q * std::sqrt(q));
+                const double ks = std::fabs(2.0 * S) / std::sqrt(q);  // (dz/dr) / (r sqrt q)
+                kmax = std::max(kmax, std::max(km, ks));
+            }
+            break;
+        }
+        case ROBAST_SHAPE_CYLINDER: kmax = s.prm[0] > 0.0 ? 1.0 / s.prm[0] : 0.0; break;
+        case ROBAST_SHAPE_BOX: kmax = 0.0; break;
+        case ROBAST_SHAPE_HEXCONE: {
+            const double ra1 = 2.0 * (s.prm[2] - s.prm[0]), ra2 = s.prm[0] - 2.0 * s.prm[2] + s.prm[4];
+            const double za1 = 2.0 * (s.prm[3] - s.prm[1]), za2 = s.prm[1] - 2.0 * s.prm[3] + s.prm[5];
+            for (int k = 0; k <= NS; ++k) {
+                const double u = (double)k / NS;
+                const double r1 = ra1 + 2.0 * ra2 * u, z1 = za1 + 2.0 * za2 * u;
+                const double q = r1 * r1 + z1 * z1;
+                if (q > 0.0) kmax = std::max(kmax, std::fabs(r1 * 2.0 * za2 - z1 * 2.0 * ra2) / (q * std::sqrt(q)));
+            }
+            break;
+        }
+    }
+    return 1.1 * kmax;
 }
 
 double sag_eval(const robast_surface_desc& s, double rho, bool* ok) {
@@ -594,6 +647,11 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
                 break;
             }
         }
+        R[F_KAP] = curvature_bound(s, L);
+        // rounding of the root along the ray, ulps per unit length: a plane's root is one
+        // quotient; a curved surface's quadratic (or Newton, or Bezier) root about 3 ulps
+        const bool planar = (s.shape == ROBAST_SHAPE_SAG && s.curv == 0.0 && !any_asph(s)) || s.shape == ROBAST_SHAPE_BOX;
+        R[F_KA] = planar ? 1.0 : 4.0;
         for (int k = 0; k < REC; ++k) rec32[(size_t)i * REC + k] = (float)R[k];
         {
             // derivatives of the tilted rows Ry(b)^T Rx(a)^T R with respect to a and b
@@ -840,7 +898,20 @@ struct robast_sources {
     int n_groups = 0;
     long long n_photons = 0;
     SrcGroup* d_groups = nullptr;
+    // the accuracy guard's re-trace queue: [4] u64 header (entries appended, spare), then
+    // qcap photon indices
+    unsigned long long* d_queue = nullptr;
+    long long qcap = 0;
 };
+
+// The accuracy guard re-traces a photon whose error estimate exceeds this fraction of a bound.
+static const double kGuardFrac = 1.0;
+
+// Capacity of the accuracy guard's re-trace queue for n photons.
+static long long retrace_queue_cap(long long n, long long div) {
+    const long long full = 1LL << 26;
+    return n <= full ? n : std::max(full, n / div);
+}
 
 template <typename T>
 static int do_trace(const robast_geom* g, const void* origins, const void* dirs, const void* wl, int64_t n,
@@ -879,6 +950,11 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     a.fxy = static_cast<T*>(out->focal_xy);
     a.counters = out->counters;
     a.units = o.work_units;
+    if (sizeof(T) == 4) a.err = out->err;
+    if (!(o.accuracy_pos >= 0.0) || !(o.accuracy_dir >= 0.0))
+        return fail(ROBAST_E_INVALID, "robast_trace: accuracy bounds must be >= 0");
+    // FP32 accuracy guard: photons over half a bound are queued and re-traced in FP64
+    const bool guard = sizeof(T) == 4 && (o.accuracy_pos > 0.0 || o.accuracy_dir > 0.0) && !o.track && !o.work_units;
     if (o.track) {
         const robast_track_opts& t = *o.track;
         if (t.first < 0 || t.count < 0 || t.cap < 0 || !t.points || !t.info || !t.n_records)
@@ -936,12 +1012,92 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
         }
         a.order = order;
     }
+    void* q_scratch = nullptr;
+    unsigned long long* qhdr = nullptr;
+    long long qcap = 0;
+    if (guard) {
+        if (src) {
+            qhdr = src->d_queue;
+            qcap = src->qcap;
+        } else {
+            qcap = retrace_queue_cap(n, 8);
+            cudaError_t eq = cudaMallocFromPoolAsync(&q_scratch, (size_t)(4 + qcap) * 8, gm->pool, s);
+            if (eq != cudaSuccess) {
+                if (ord_scratch) cudaFreeAsync(ord_scratch, s);
+                return cuda_fail(eq, "robast_trace: re-trace queue");
+            }
+            qhdr = static_cast<unsigned long long*>(q_scratch);
+        }
+        cudaError_t eq = cudaMemsetAsync(qhdr, 0, 4 * sizeof(unsigned long long), s);
+        if (eq != cudaSuccess) {
+            if (ord_scratch) cudaFreeAsync(ord_scratch, s);
+            if (q_scratch) cudaFreeAsync(q_scratch, s);
+            return cuda_fail(eq, "robast_trace: re-trace queue");
+        }
+        a.queue_out = reinterpret_cast<long long*>(qhdr + 4);
+        a.queue_n = qhdr;
+        a.queue_cap = qcap;
+        a.acc_pos = o.accuracy_pos > 0.0 ? (float)(kGuardFrac * o.accuracy_pos) : INFINITY;
+        a.acc_dir = o.accuracy_dir > 0.0 ? (float)(kGuardFrac * o.accuracy_dir) : INFINITY;
+        a.retraced = out->retraced ? out->retraced : qhdr + 1;
+    }
+    a.n_work = n;
     cudaError_t e;
     if constexpr (sizeof(T) == 4)
         e = launch_trace_f32(a, block, (int)grid, smem, s);
     else
         e = launch_trace_f64(a, block, (int)grid, smem, s);
     if (ord_scratch) cudaFreeAsync(ord_scratch, s);
+    if (e == cudaSuccess && guard) {
+        // the FP64 re-trace of the queued photons: FP64 arithmetic and tables, the FP32 arrays,
+        // the same epsilon, random streams and outputs
+        TraceArgs<double, float> r{};
+        r.tab = g->tab64;
+        r.o = reinterpret_cast<const float*>(a.o);
+        r.d = reinterpret_cast<const float*>(a.d);
+        r.lam = reinterpret_cast<const float*>(a.lam);
+        r.vop = a.vop;
+        r.n = n;
+        r.n_work = qcap;
+        r.n_work_dev = qhdr;
+        r.queue_in = a.queue_out;
+        r.seed = a.seed;
+        r.first_id = a.first_id;
+        r.max_bounces = a.max_bounces;
+        r.refill_min = a.refill_min;
+        r.eps = eps;
+        r.newton_tol = eps * 1e-4;
+        r.newton_tol64 = eps * 1e-4;
+        r.st = a.st;
+        r.nb = a.nb;
+        r.hit = reinterpret_cast<float*>(a.hit);
+        r.dir = reinterpret_cast<float*>(a.dir);
+        r.last = a.last;
+        r.fxy = reinterpret_cast<float*>(a.fxy);
+        r.counters = a.counters;
+        r.groups = a.groups;
+        r.n_groups = a.n_groups;
+        r.gcounts = a.gcounts;
+        r.err = a.err;
+        r.retraced = a.retraced;
+        r.work = g->work + (gm->work_slot.fetch_add(1) % kWorkSlots);
+        e = cudaMemsetAsync(r.work, 0, sizeof(unsigned long long), s);
+        r.stage = g->smem64 <= kSmemCap ? 1 : 0;
+        const size_t smem_r = r.stage ? g->smem64 : 0;
+        std::atomic<int>& slot = gm->bps_retrace[src ? 1 : 0];
+        int bps_r = slot.load(std::memory_order_relaxed);
+        if (bps_r <= 0) {
+            bps_r = retrace_blocks_per_sm(smem_r, src != nullptr);
+            if (bps_r > 0) slot.store(bps_r, std::memory_order_relaxed);
+        }
+        if (e == cudaSuccess && bps_r <= 0) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) {
+            long long grid_r = (long long)g->num_sms * bps_r;
+            grid_r = std::max(1LL, std::min(grid_r, (qcap + 127) / 128));
+            e = launch_retrace(r, (int)grid_r, smem_r, s);
+        }
+    }
+    if (q_scratch) cudaFreeAsync(q_scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "robast_trace: launch");
     return 0;
 }
@@ -1018,11 +1174,14 @@ extern "C" int robast_sources_create(const robast_geom* g, const robast_source_g
     if (!s) return fail(ROBAST_E_OOM, "robast_sources_create: host allocation failed");
     s->n_groups = n_groups;
     s->n_photons = first;
+    s->qcap = retrace_queue_cap(first, 16);
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_groups, h.size() * sizeof(SrcGroup));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_groups, h.data(), h.size() * sizeof(SrcGroup), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_queue, (size_t)(4 + s->qcap) * 8);
     if (e != cudaSuccess) {
         if (s->d_groups) cudaFree(s->d_groups);
+        if (s->d_queue) cudaFree(s->d_queue);
         delete s;
         return cuda_fail(e, "robast_sources_create");
     }
@@ -1034,6 +1193,7 @@ extern "C" void robast_sources_free(robast_sources* s) {
     if (!s) return;
     cudaDeviceSynchronize();
     cudaFree(s->d_groups);
+    cudaFree(s->d_queue);
     delete s;
 }
 
@@ -1119,9 +1279,11 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
     const size_t xv = o.variant_of_photon ? carve(C * 4) : 0;
     const size_t xs = carve(C), xb = carve(C), xh = carve(3 * C * es), xr = carve(3 * C * es), xla = carve(C * 4);
     const size_t xf = carve(2 * C * es);
+    const size_t xe = carve(2 * C * 4);
     const size_t set_bytes = off;
     const size_t xc = 2 * set_bytes;
-    rc = grow(&g->stage, &g->stage_bytes, xc + ROBAST_N_COUNTERS * 8, "robast_trace_host");
+    const int NC = ROBAST_N_COUNTERS + 2;  // the counters, then the accuracy guard's two
+    rc = grow(&g->stage, &g->stage_bytes, xc + NC * 8, "robast_trace_host");
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
     for (int k = 0; k < 2; ++k)
@@ -1129,7 +1291,7 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
     if (!g->hevent) CU(cudaEventCreateWithFlags(&g->hevent, cudaEventDisableTiming), "robast_trace_host: event");
     unsigned char* base = static_cast<unsigned char*>(g->stage);
     unsigned long long* dc = reinterpret_cast<unsigned long long*>(base + xc);
-    CU(cudaMemsetAsync(dc, 0, ROBAST_N_COUNTERS * 8, s), "robast_trace_host: counters");
+    CU(cudaMemsetAsync(dc, 0, NC * 8, s), "robast_trace_host: counters");
     CU(cudaEventRecord(g->hevent, s), "robast_trace_host: event");  // after the caller's earlier work
     for (int k = 0; k < 2; ++k) CU(cudaStreamWaitEvent(g->hstream[k], g->hevent, 0), "robast_trace_host: wait");
     const unsigned char* ho = static_cast<const unsigned char*>(origins);
@@ -1161,7 +1323,9 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
         dout.dir = out->dir ? b + xr : nullptr;
         dout.last_surface = out->last_surface ? reinterpret_cast<int32_t*>(b + xla) : nullptr;
         dout.focal_xy = out->focal_xy ? b + xf : nullptr;
+        dout.err = out->err && o.precision == 32 ? reinterpret_cast<float*>(b + xe) : nullptr;
         dout.counters = dc;
+        dout.retraced = dc + ROBAST_N_COUNTERS;
         rc = robast_trace_ex(g, b + xo, b + xd, b + xl, (int64_t)nc, seed, &dout, &od);
         if (rc) return rc;
         unsigned char* os = static_cast<unsigned char*>(out->status);
@@ -1176,12 +1340,17 @@ extern "C" int robast_trace_host(robast_geom* g, const void* origins, const void
         if (orr) CU(cudaMemcpy2DAsync(orr + s0 * es, pitch, dout.dir, nc * es, nc * es, 3, cudaMemcpyDeviceToHost, st), "copy out");
         if (ol) CU(cudaMemcpyAsync(ol + s0 * 4, dout.last_surface, nc * 4, cudaMemcpyDeviceToHost, st), "copy out");
         if (of) CU(cudaMemcpy2DAsync(of + s0 * es, pitch, dout.focal_xy, nc * es, nc * es, 2, cudaMemcpyDeviceToHost, st), "copy out");
+        if (dout.err)
+            CU(cudaMemcpy2DAsync(reinterpret_cast<unsigned char*>(out->err) + s0 * 4, (size_t)n * 4, dout.err, nc * 4,
+                                 nc * 4, 2, cudaMemcpyDeviceToHost, st), "copy out");
     }
-    unsigned long long hc[ROBAST_N_COUNTERS];
+    unsigned long long hc[NC];
     for (int k = 0; k < 2; ++k) CU(cudaStreamSynchronize(g->hstream[k]), "robast_trace_host: synchronize");
     CU(cudaMemcpy(hc, dc, sizeof hc, cudaMemcpyDeviceToHost), "copy out");
     if (out->counters)
         for (int k = 0; k < ROBAST_N_COUNTERS; ++k) out->counters[k] += hc[k];
+    if (out->retraced)
+        for (int k = 0; k < 2; ++k) out->retraced[k] += hc[ROBAST_N_COUNTERS + k];
     return 0;
 }
 
@@ -2098,9 +2267,11 @@ extern "C" int robast_measure_alu_peak(int32_t precision, void* stream, double* 
 // without allocating anything.
 //
 // Some callers cannot allocate device memory at the time they want these
-// statistics: code running inside a CUDA graph that is being captured, code
-// under a caching allocator that owns all device memory, or embedders whose
-// memory budget is fixed up front.  This entry point serves them.  Its
+// statistics: code under a caching allocator that owns all device memory, or
+// embedders whose memory budget is fixed up front.  This entry point serves
+// them.  It synchronises the caller's stream between its histogram rounds and
+// reads their results on the host, so it must not be issued on a stream that
+// is being captured into a CUDA graph.  Its
 // scratch lives in one file-scope __device__ array of fixed size (about
 // 6.4 MB) that every GPU which loads the library holds until the process
 // exits; it calls no cudaMalloc, cudaFree or allocating library routine, and
@@ -2110,8 +2281,10 @@ extern "C" int robast_measure_alu_peak(int32_t precision, void* stream, double* 
 // bounded, the selection of the 80% radius does not collect a whole
 // histogram bin (which can hold any number of photons): it refines the bin
 // that holds the rank with further 4096-bin histograms until that bin holds
-// at most NA_CAP values, then selects among them exactly.  The result is the
-// same number robast_psf returns.
+// at most NA_CAP values, then selects among them exactly; a bin still over
+// NA_CAP after NA_ROUNDS rounds spans only a few doubles, whose copies are
+// counted one value at a time.  The result is the same number robast_psf
+// returns.
 //
 // Sharing: every call on a device uses the same scratch array and leaves its
 // contents behind; each call clears what must start at zero.  Calls whose GPU
@@ -2140,6 +2313,7 @@ struct NaScratch {
     unsigned long long hist[NA_MAX_WINDOWS * (NA_BINS + 1)];
     unsigned long long cnt[NA_MAX_WINDOWS];
     unsigned long long rmax_bits[NA_MAX_WINDOWS];
+    unsigned long long rmin_bits[NA_MAX_WINDOWS];
     double vals[NA_MAX_WINDOWS * NA_CAP];
 };
 
@@ -2263,6 +2437,52 @@ __global__ void na_collect(const uint8_t* st, const T* fxy, long long ld, WinSet
     }
 }
 
+// Smallest and largest value (as bit patterns: radii are >= 0, so their bits order like the
+// values) of the final bin of each window with upto[w] > 0.
+template <typename T>
+__global__ void na_minmax(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S, const int* upto) {
+    const int w = blockIdx.y;
+    const int u = upto[w];
+    if (u <= 0) return;
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
+         k += (long long)gridDim.x * blockDim.x) {
+        double r;
+        if (na_member(st, fxy, ld, ws.start[w] + k, w, u, S, &r)) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+            lo = min(lo, b);
+            hi = max(hi, b);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(S->rmin_bits + w, lo);
+        atomicMax(S->rmax_bits + w, hi);
+    }
+}
+
+// One bin per representable double from the final bin's smallest value: counts of each
+// distinct value of the final bin (its values span fewer than NA_BINS doubles).
+template <typename T>
+__global__ void na_ulp_hist(const uint8_t* st, const T* fxy, long long ld, WinSet ws, NaScratch* S, const int* upto) {
+    const int w = blockIdx.y;
+    const int u = upto[w];
+    if (u <= 0) return;
+    const unsigned long long b0 = S->rmin_bits[w];
+    unsigned long long* H = S->hist + (size_t)w * (NA_BINS + 1);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ws.count[w];
+         k += (long long)gridDim.x * blockDim.x) {
+        double r;
+        if (na_member(st, fxy, ld, ws.start[w] + k, w, u, S, &r)) {
+            const unsigned long long j = (unsigned long long)__double_as_longlong(r) - b0;
+            if (j < (unsigned long long)NA_BINS) atomicAdd(H + j, 1ull);
+        }
+    }
+}
+
 // device address of the scratch, looked up once per device
 std::mutex na_mu;
 NaScratch* na_dev[NA_MAX_DEVICES] = {nullptr};
@@ -2275,6 +2495,8 @@ double na_h_lohi[NA_MAX_WINDOWS * NA_ROUNDS * 2];
 int na_h_upto[NA_MAX_WINDOWS];
 unsigned long long na_h_cnt[NA_MAX_WINDOWS];
 unsigned long long na_h_rmax[NA_MAX_WINDOWS];
+unsigned long long na_h_rmin[NA_MAX_WINDOWS];
+int na_h_over[NA_MAX_WINDOWS];
 
 template <typename T>
 int na_impl(NaScratch* S, const uint8_t* st, const T* fxy, long long ld, const WinSet& ws0, cudaStream_t s,
@@ -2402,18 +2624,63 @@ int na_impl(NaScratch* S, const uint8_t* st, const T* fxy, long long ld, const W
     CU(cudaMemcpyAsync(na_h_vals, S->vals, sizeof(double) * (size_t)nw * NA_CAP, cudaMemcpyDeviceToHost, s),
           "robast_psf_noalloc: copy");
     CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+    bool any_over = false;
     for (int w = 0; w < nw; ++w) {
+        na_h_over[w] = 0;
         if (na_h_upto[w] <= 0) continue;
-        const long long got = (long long)std::min<unsigned long long>(na_h_cnt[w], NA_CAP);
-        if (got <= 0) return fail(ROBAST_E_CUDA, "robast_psf_noalloc: selection lost values in window %d", w);
-        // a bin still over the cap after the last round spans less than one ulp:
-        // its values are all equal, so any of them is the answer
-        const long long k = std::min(rank[w], got - 1);
-        if ((long long)na_h_cnt[w] <= NA_CAP && got <= rank[w])
-            return fail(ROBAST_E_CUDA, "robast_psf_noalloc: selection lost values in window %d", w);
+        if (na_h_cnt[w] > (unsigned long long)NA_CAP) {
+            // still over the cap after the last round: resolved exactly below
+            na_h_over[w] = na_h_upto[w];
+            any_over = true;
+            continue;
+        }
+        const long long got = (long long)na_h_cnt[w];
+        if (got <= rank[w]) return fail(ROBAST_E_CUDA, "robast_psf_noalloc: selection lost values in window %d", w);
         double* v = na_h_vals + (size_t)w * NA_CAP;
-        std::nth_element(v, v + k, v + got);
-        results[4 * w + 3] = v[k];
+        std::nth_element(v, v + rank[w], v + got);
+        results[4 * w + 3] = v[rank[w]];
+    }
+    if (any_over) {
+        // A final bin over the cap is a few ulps wide (each round pads its interval by 4 ulps
+        // of its upper edge), so it holds a few distinct doubles with many copies each: count
+        // the copies of every distinct value and take the rank's, the same exact nearest-rank
+        // value that robast_psf selects, whatever the order of the atomics.
+        CU(cudaMemcpyAsync(S->part, na_h_over, sizeof(int) * nw, cudaMemcpyHostToDevice, s), "robast_psf_noalloc: copy");
+        CU(cudaMemsetAsync(S->rmin_bits, 0xff, sizeof(unsigned long long) * nw, s), "robast_psf_noalloc: clear");
+        CU(cudaMemsetAsync(S->rmax_bits, 0, sizeof(unsigned long long) * nw, s), "robast_psf_noalloc: clear");
+        na_minmax<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S, reinterpret_cast<const int*>(S->part));
+        CU(cudaGetLastError(), "robast_psf_noalloc: launch");
+        CU(cudaMemcpyAsync(na_h_rmin, S->rmin_bits, sizeof(unsigned long long) * nw, cudaMemcpyDeviceToHost, s),
+           "robast_psf_noalloc: copy");
+        CU(cudaMemcpyAsync(na_h_rmax, S->rmax_bits, sizeof(unsigned long long) * nw, cudaMemcpyDeviceToHost, s),
+           "robast_psf_noalloc: copy");
+        CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+        for (int w = 0; w < nw; ++w)
+            if (na_h_over[w] && na_h_rmax[w] - na_h_rmin[w] >= (unsigned long long)NA_BINS)
+                return fail(ROBAST_E_INVALID,
+                            "robast_psf_noalloc: window %d: the rank's bin still spans %llu doubles after %d rounds", w,
+                            na_h_rmax[w] - na_h_rmin[w] + 1, NA_ROUNDS);
+        CU(cudaMemsetAsync(S->hist, 0, sizeof(unsigned long long) * nw * (NA_BINS + 1), s), "robast_psf_noalloc: clear");
+        na_ulp_hist<T><<<grid, NA_BLOCK, 0, s>>>(st, fxy, ld, ws, S, reinterpret_cast<const int*>(S->part));
+        CU(cudaGetLastError(), "robast_psf_noalloc: launch");
+        CU(cudaMemcpyAsync(na_h_hist, S->hist, sizeof(unsigned long long) * nw * (NA_BINS + 1), cudaMemcpyDeviceToHost, s),
+           "robast_psf_noalloc: copy");
+        CU(cudaStreamSynchronize(s), "robast_psf_noalloc: synchronize");
+        for (int w = 0; w < nw; ++w) {
+            if (!na_h_over[w]) continue;
+            const unsigned long long* H = na_h_hist + (size_t)w * (NA_BINS + 1);
+            long long acc = 0;
+            int b = 0;
+            for (; b < NA_BINS; ++b) {
+                if (acc + (long long)H[b] > rank[w]) break;
+                acc += (long long)H[b];
+            }
+            if (b >= NA_BINS) return fail(ROBAST_E_CUDA, "robast_psf_noalloc: rank not found in window %d", w);
+            const unsigned long long bits = na_h_rmin[w] + (unsigned long long)b;
+            double v;
+            std::memcpy(&v, &bits, sizeof v);
+            results[4 * w + 3] = v;
+        }
     }
     return 0;
 }

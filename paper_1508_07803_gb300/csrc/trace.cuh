@@ -41,7 +41,9 @@ enum { ST_DETECTED = 1, ST_ABSORBED = 2, ST_OBSCURED = 3, ST_ESCAPED = 4, ST_MAX
 //   HEXCONE: [12..14] r power-basis coefficients, [15..17] z coefficients
 //   aperture [22..27]: CIRCLE r^2; ANNULUS rmin^2 rmax^2; SECTOR rmin^2 rmax^2 e0x e0y e1x e1y;
 //                      HEX apothem; RECT hx hy
-enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, REC = 32 };
+//   [29] bound on the surface's principal curvatures over its aperture, [30] rounding of its
+//        root along the ray in ulps per unit length (the FP32 error estimate)
+enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_KA = 30, REC = 32 };
 // Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12, y = material,
 // z = medium front, w = medium back.
 // Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
@@ -114,15 +116,20 @@ struct SrcGroup {
     int pad;
 };
 
-template <typename T>
+// T: arithmetic precision of the trace; IO: element type of the caller's input and output
+// arrays (the FP64 re-trace of FP32 photons reads and writes the FP32 arrays).
+template <typename T, typename IO = T>
 struct TraceArgs {
     Tables tab;
-    const T* o;
-    const T* d;
-    const T* lam;
+    const IO* o;
+    const IO* d;
+    const IO* lam;
     const int* vop;
     const int* order;  // optional processing order: work index -> photon index
-    long long n;
+    long long n;       // photons: the stride of the SoA arrays
+    long long n_work;  // work items (n, or the capacity of a re-trace queue)
+    const unsigned long long* n_work_dev;  // if set: work items = min(*n_work_dev, n_work)
+    const long long* queue_in;             // if set: work index -> photon index (FP64 re-trace)
     unsigned long long seed;
     long long first_id;
     int max_bounces;
@@ -133,10 +140,10 @@ struct TraceArgs {
     double newton_tol64;
     uint8_t* st;
     uint8_t* nb;
-    T* hit;
-    T* dir;
+    IO* hit;
+    IO* dir;
     int* last;
-    T* fxy;
+    IO* fxy;
     unsigned long long* counters;
     unsigned long long* work;
     unsigned long long* units;  // [U_N], counting instantiation only
@@ -144,10 +151,21 @@ struct TraceArgs {
     int n_groups;
     // photon tracks: every interaction of photons tr_first .. tr_first + tr_count - 1
     long long tr_first, tr_count, tr_cap;
-    T* tr_pts;                      // [tr_cap * 4]: x, y, z, 0
+    IO* tr_pts;                     // [tr_cap * 4]: x, y, z, 0
     int* tr_info;                   // [tr_cap * 4]: photon, bounce, surface, status after
     unsigned long long* tr_n;       // records appended (may exceed tr_cap)
     unsigned long long* gcounts;  // source mode: [n_groups][8] counters per group
+    // FP32 accuracy guard: a photon whose running error estimate exceeds acc_pos (final
+    // position, m) or acc_dir (final direction, rad), or that ends in ERROR, is appended to
+    // queue_out and re-traced in FP64 by a second launch (queue_in, n_work_dev = queue_n)
+    float acc_pos, acc_dir;
+    long long* queue_out;
+    unsigned long long* queue_n;    // entries appended (may exceed queue_cap)
+    long long queue_cap;
+    float* err;                     // [2n] per photon: position and direction error estimate
+                                    // (-1, -1: the result comes from the FP64 re-trace)
+    unsigned long long* retraced;   // [2]: photons re-traced in FP64; photons over a bound that
+                                    // did not fit the queue (they keep the FP32 result)
 };
 
 
@@ -922,6 +940,10 @@ struct Photon {
     int group; // source mode: group of the photon
     bool bad;  // source mode: no point generated
     unsigned long long thr;
+    // FP32 form: first-order estimate of the accumulated rounding error (see trace_kernel)
+    float ep;  // lateral offset of the current ray (m)
+    float ed;  // direction (rad)
+    float eh;  // last interaction point (m)
 };
 
 // STAGED: the tables fit in shared memory and every table pointer is derived
@@ -944,8 +966,18 @@ struct TraceBounds {
     static constexpr int min_blocks = sizeof(T) == 4 && (mb * 128) / BLOCK > 0 ? (mb * 128) / BLOCK : 1;
 };
 
-template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false>
-__global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks)) trace_kernel(TraceArgs<T> A) {
+// Rounding units of the FP32 error estimate, per interaction: the frame transform puts KT ulps
+// of the coordinate scale on the hit point (across and along the ray), the root the surface's
+// own ulps per unit of the segment along it (record slot F_KA), the new ray's origin carries KP
+// ulps of its coordinates, the normal KN ulps and the new direction KD ulps (reflection or
+// refraction and normalisation).
+constexpr float EST_U = 5.9604645e-08f;  // 2^-24
+constexpr float EST_KT = 1.0f * EST_U, EST_KP = 0.5f * EST_U, EST_KN = 1.0f * EST_U, EST_KD = 1.5f * EST_U;
+
+template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false, typename IO = T>
+__global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks)) trace_kernel(TraceArgs<T, IO> A) {
+    // the FP32 form carries a running error estimate; the counting build and FP64 do not
+    constexpr bool EST = sizeof(T) == 4 && !C;
     unsigned cnt[U_N];
     if constexpr (C) {
 #pragma unroll
@@ -986,6 +1018,11 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint2 key = make_uint2((uint32_t)A.seed, (uint32_t)(A.seed >> 32));
     const long long n = A.n;
+    long long n_work = A.n_work;
+    if (A.n_work_dev) {
+        const unsigned long long q = *A.n_work_dev;
+        if ((long long)q < n_work) n_work = (long long)q;
+    }
 
     Photon<T> ph;
     ph.i = -1;
@@ -1003,6 +1040,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         }
     };
     unsigned long long my_bounces = 0;
+    unsigned int my_retraced = 0;  // FP64 re-trace: photons finished here
     unsigned int my_status[7] = {0, 0, 0, 0, 0, 0, 0};
 
     while (true) {
@@ -1017,8 +1055,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             base = __shfl_sync(FULL, base, leader);
             if (need) {
                 const long long widx = (long long)base + __popc(m & lt_mask);
-                if (widx < n) {
-                    const long long idx = A.order ? (long long)A.order[widx] : widx;
+                if (widx < n_work) {
+                    const long long idx = A.queue_in ? A.queue_in[widx] : A.order ? (long long)A.order[widx] : widx;
                     ph.i = idx;
                     if constexpr (SRC) {
                         // group: the last one whose first index is <= idx
@@ -1039,9 +1077,9 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         ph.var = G.variant;
                         ph.group = lo;
                     } else {
-                        ph.p = mk(A.o[idx], A.o[n + idx], A.o[2 * n + idx]);
-                        ph.d = mk(A.d[idx], A.d[n + idx], A.d[2 * n + idx]);
-                        ph.lam = A.lam[idx];
+                        ph.p = mk((T)A.o[idx], (T)A.o[n + idx], (T)A.o[2 * n + idx]);
+                        ph.d = mk((T)A.d[idx], (T)A.d[n + idx], (T)A.d[2 * n + idx]);
+                        ph.lam = (T)A.lam[idx];
                         ph.var = A.vop ? A.vop[idx] : 0;
                         ph.bad = false;
                     }
@@ -1049,6 +1087,9 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     ph.mat_cache = -1;
                     ph.last = -1;
                     ph.thr = 0;
+                    ph.ep = 0.0f;
+                    ph.ed = 0.0f;
+                    ph.eh = 0.0f;
                 } else {
                     done = true;
                 }
@@ -1082,7 +1123,29 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             const int4 si = tb.surf_i[bst.sid];
             const int role = (si.x >> 4) & 15;
             const V3<T> n = unit(to_world_vec(S, bst.nl));
-            const bool front = dot(ph.d, n) < T(0);
+            const T d_n = dot(ph.d, n);
+            const bool front = d_n < T(0);
+            // FP32 error estimate, first order.  A ray whose lateral offset is ep and whose
+            // direction is off by ed meets the surface (incidence cosine c = |d.n|, after a
+            // segment t) at a point off by el = (ep + t ed + KT scale) / c along the surface
+            // (scale: the coordinates' magnitude, which sets the frame transform's rounding);
+            // the root adds ea = (KA t + KT scale) / c along the ray.  The normal there is off by
+            // (curvature bound) x (el + ea sin(incidence)), plus rounding.  The outgoing ray's
+            // lateral offset is el times its own cosine plus ea times the sine of the turn (the
+            // part of an along-ray shift that is across the new direction).
+            float e_n = 0.0f, e_l = 0.0f, e_a = 0.0f, e_c = 1.0f, e_s = 0.0f, e_sn = 0.0f;
+            if constexpr (EST) {
+                e_c = fmaxf(fabsf((float)d_n), 1e-20f);
+                e_sn = sqrtf(fmaxf(0.0f, 1.0f - e_c * e_c));
+                e_s = fmaxf(fabsf((float)ph.p.x), fmaxf(fabsf((float)ph.p.y), fabsf((float)ph.p.z)));
+                e_s = fmaxf(e_s, fmaxf(fabsf((float)S[F_O]), fmaxf(fabsf((float)S[F_O + 1]), fabsf((float)S[F_O + 2])))) +
+                      (float)bst.t;
+                const float ts = EST_KT * e_s;
+                e_l = (ph.ep + (float)bst.t * ph.ed + ts) / e_c;
+                e_a = ((float)S[F_KA] * EST_U * (float)bst.t + ts) / e_c;
+                ph.eh = e_l + e_a;
+                e_n = (float)S[F_KAP] * (e_l + e_a * e_sn) + EST_KN;
+            }
             if (role == ROLE_OBSC) {
                 status = ST_OBSCURED;
             } else if (role == ROLE_FOCAL) {
@@ -1140,6 +1203,13 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         }
                         ph.d = unit(ph.d - (T(2) * dot(ph.d, nn)) * nn);
                         CNT(U_REFLECT);
+                        // reflection: the direction error grows by twice the normal's; the
+                        // outgoing ray leaves at the incidence cosine and turns by twice the
+                        // incidence angle (sine 2 s c)
+                        if constexpr (EST) {
+                            ph.ed += 2.0f * e_n + EST_KD;
+                            ph.ep = e_l * e_c + e_a * (2.0f * e_sn * e_c) + EST_KP * e_s;
+                        }
                     }
                 }
             } else {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
@@ -1170,11 +1240,25 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                 if (unit_open<T>(w.x) < R) {
                     ph.d = unit(ph.d - (T(2) * dot(ph.d, nf)) * nf);
                     CNT(U_REFLECT);
+                    if constexpr (EST) {
+                        ph.ed += 2.0f * e_n + EST_KD;
+                        ph.ep = e_l * e_c + e_a * (2.0f * e_sn * e_c) + EST_KP * e_s;
+                    }
                 } else {
                     const T eta = n1 / n2;
                     const T s2 = eta * eta * (T(1) - ci * ci);
                     const T ct = t_sqrt(T(1) - s2);
                     ph.d = unit(eta * ph.d + (eta * ci - ct) * nf);
+                    if constexpr (EST) {
+                        // Snell: cos(theta_t) dtheta_t = eta cos(theta_i) dtheta_i, with the angles
+                        // measured from a normal that is itself off by e_n; the transmitted ray
+                        // leaves at cosine ct and turns by theta_i - theta_t
+                        const float ctf = fmaxf((float)ct, 1e-20f);
+                        const float g = (float)(eta * ci) / ctf;
+                        ph.ed = (ph.ed + e_n) * g + e_n + EST_KD;
+                        const float st = sqrtf(fmaxf(0.0f, 1.0f - ctf * ctf));
+                        ph.ep = e_l * ctf + e_a * fabsf(e_sn * ctf - e_c * st) + EST_KP * e_s;
+                    }
                 }
             }
             if (status == 0 && !(t_finite(ph.d.x) && t_finite(ph.d.y) && t_finite(ph.d.z))) status = ST_ERROR;
@@ -1182,10 +1266,10 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             if (A.tr_pts && ph.i >= A.tr_first && ph.i < A.tr_first + A.tr_count) {
                 const unsigned long long k = atomicAdd(A.tr_n, 1ull);
                 if ((long long)k < A.tr_cap) {
-                    A.tr_pts[4 * k + 0] = ph.p.x;
-                    A.tr_pts[4 * k + 1] = ph.p.y;
-                    A.tr_pts[4 * k + 2] = ph.p.z;
-                    A.tr_pts[4 * k + 3] = T(0);
+                    A.tr_pts[4 * k + 0] = (IO)ph.p.x;
+                    A.tr_pts[4 * k + 1] = (IO)ph.p.y;
+                    A.tr_pts[4 * k + 2] = (IO)ph.p.z;
+                    A.tr_pts[4 * k + 3] = IO(0);
                     A.tr_info[4 * k + 0] = (int)ph.i;
                     A.tr_info[4 * k + 1] = ph.bounces - 1;
                     A.tr_info[4 * k + 2] = ph.last;
@@ -1196,24 +1280,47 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         if (status == 0) continue;
         // ---- photon finished: store (SoA)
         const long long i = ph.i;
+        if constexpr (EST) {
+            if (A.err) {
+                A.err[i] = ph.eh;
+                A.err[n + i] = ph.ed;
+            }
+            // over a bound (or an ERROR, which FP64 may not reproduce): re-traced in FP64 by the
+            // next launch, which writes every output and counts the photon
+            if (A.queue_out && (ph.eh > A.acc_pos || ph.ed > A.acc_dir || status == ST_ERROR)) {
+                const unsigned long long k = atomicAdd(A.queue_n, 1ull);
+                if ((long long)k < A.queue_cap) {
+                    A.queue_out[k] = i;
+                    ph.i = -1;
+                    continue;
+                }
+                atomicAdd(A.retraced + 1, 1ull);
+            }
+        } else {
+            if (A.queue_in && A.err) {
+                A.err[i] = -1.0f;
+                A.err[n + i] = -1.0f;
+            }
+        }
         if (A.st) A.st[i] = (uint8_t)status;
         if (A.nb) A.nb[i] = (uint8_t)ph.bounces;
         if (A.hit) {
-            A.hit[i] = ph.p.x;
-            A.hit[n + i] = ph.p.y;
-            A.hit[2 * n + i] = ph.p.z;
+            A.hit[i] = (IO)ph.p.x;
+            A.hit[n + i] = (IO)ph.p.y;
+            A.hit[2 * n + i] = (IO)ph.p.z;
         }
         if (A.dir) {
-            A.dir[i] = ph.d.x;
-            A.dir[n + i] = ph.d.y;
-            A.dir[2 * n + i] = ph.d.z;
+            A.dir[i] = (IO)ph.d.x;
+            A.dir[n + i] = (IO)ph.d.y;
+            A.dir[2 * n + i] = (IO)ph.d.z;
         }
         if (A.fxy) {
-            A.fxy[i] = fpos.x;
-            A.fxy[n + i] = fpos.y;
+            A.fxy[i] = (IO)fpos.x;
+            A.fxy[n + i] = (IO)fpos.y;
         }
         if (A.last) A.last[i] = ph.last;
         my_bounces += (unsigned long long)ph.bounces;
+        if (A.queue_in) ++my_retraced;
         my_status[status] += 1u;
         if constexpr (SRC) {
             if (ph.group != cur_g) {
@@ -1234,6 +1341,10 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             const unsigned v = __reduce_add_sync(FULL, cnt[k]);
             if (lane == 0 && v) atomicAdd(A.units + k, (unsigned long long)v);
         }
+    }
+    if (A.queue_in && A.retraced) {
+        const unsigned v = __reduce_add_sync(FULL, my_retraced);
+        if (lane == 0 && v) atomicAdd(A.retraced, (unsigned long long)v);
     }
     // warp-aggregated counters
     if (A.counters) {

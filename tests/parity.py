@@ -1,29 +1,29 @@
 """Element-by-element comparison of a GPU trace with the oracle's.
 
 Tolerances (per photon, on the same seeded inputs):
-  FP64 trace: status and bounce count identical for every photon; final
-      position within 1e-10 x the system focal length; final direction and
-      focal-plane coordinates within 1e-10 (direction) / 1e-10 f.
+  FP64 trace: status, bounce count and last surface identical for every
+      photon; final position within 1e-10 x the system focal length f; final
+      direction within 1e-10; focal-plane coordinates within 1e-10 f.
   FP32 trace (the oracle traces the FP32-rounded inputs, with the FP32
-      self-intersection epsilon): status identical for >= 99.999% of photons;
+      self-intersection epsilon): status identical for at least 99.999% of
+      photons (at most floor(1e-5 n) mismatches, so none below 1e5 photons);
       every photon whose status, bounce count or last surface differs must
       have met an aperture / wedge / range edge within 1e-5 (relative) on its
-      oracle path; photons whose path is the same have directions within
-      max(1e-5, 1e-6 (K - 1)) rad and positions within 1e-6 f x max(1, K - 1), where K is the
-      path's conditioning, the sum over its interactions of 1 / |cos(theta)|
-      (theta = angle of incidence).  First-order error propagation: every
-      interaction rounds the new direction to FP32, that error grows with the
-      distance travelled, and a hit at incidence theta stretches it by
-      1 / |cos(theta)|; a position error on a curved wall turns the next
-      normal, so direction errors accumulate per redirection too.  Telescope
-      paths (two or three near-normal interactions, K ~ 2-3) stay at 1e-5 rad
-      and 1e-6 to 2e-6 f; concentrator paths with tens of wall reflections, or
-      a grazing last hit, get the allowance their geometry implies.
+      oracle path; every photon whose path is the same has its final position
+      within 1e-6 f, its focal-plane coordinates within 1e-6 f and its final
+      direction within 1e-5 rad.  These are fixed bounds; the path's
+      conditioning K = sum over its interactions of 1 / |cos(incidence)| is
+      reported next to the worst photons, never used to widen them.
 """
 import numpy as np
 
 import oracle
 import workloads as W
+
+POS_REL_FP32 = 1e-6   # x focal length
+DIR_FP32 = 1e-5       # rad
+STATUS_FRAC_FP32 = 1e-5
+EDGE_FP32 = 1e-5
 
 
 def to_numpy(out):
@@ -61,32 +61,33 @@ def compare(gpu, ref, precision, focal_length, label=""):
         return report
     same_status = g["status"] == ref["status"]
     same_path = same_status & (g["bounces"] == ref["bounces"]) & (g["last_surface"] == ref["last_surface"])
-    frac = 1.0 - same_status.mean()
-    report["status_mismatch_frac"] = float(frac)
+    n_status = int((~same_status).sum())
+    report["status_mismatches"] = n_status
     report["path_mismatches"] = int((~same_path).sum())
-    assert frac <= 1e-5 or (~same_status).sum() <= 1, f"{label}: FP32 status mismatch fraction {frac}"
+    if "retraced" in g:
+        report["retraced_fp64"] = [int(x) for x in np.asarray(g["retraced"]).ravel()]
+    assert n_status <= int(STATUS_FRAC_FP32 * n), \
+        f"{label}: {n_status} FP32 status mismatches in {n} photons (at most {int(STATUS_FRAC_FP32 * n)})"
     bad = np.where(~same_path)[0]
     if bad.size:
         m = ref["edge_margin"][bad]
-        assert np.all(m <= 1e-5), f"{label}: FP32 path mismatch away from any edge: ids {bad[m > 1e-5][:10]}, " \
-                                  f"margins {m[m > 1e-5][:10]}"
+        assert np.all(m <= EDGE_FP32), f"{label}: FP32 path mismatch away from any edge: ids {bad[m > EDGE_FP32][:10]}, " \
+                                       f"margins {m[m > EDGE_FP32][:10]}"
     ok = same_path
-    allow = 1e-6 * f * np.maximum(1.0, ref["cond"] - 1.0)
+    det = ok & (ref["status"] == W.DETECTED)
     eh = np.abs(g["hit"].astype(np.float64) - ref["hit"]).max(axis=0)
     ed = np.abs(g["dir"].astype(np.float64) - ref["dir"]).max(axis=0)
     ef = np.abs(g["focal_xy"].astype(np.float64) - ref["focal_xy"]).max(axis=0)
-    det = ok & (ref["status"] == W.DETECTED)
-    report.update(max_dhit=float(eh[ok].max(initial=0.0)), max_ddir=float(ed[ok].max(initial=0.0)),
-                  max_dfocal=float(ef[det].max(initial=0.0)),
-                  max_dhit_over_allowance=float((eh[ok] / allow[ok]).max(initial=0.0)))
-    worst = np.argmax(np.where(ok, eh / allow, 0.0))
-    assert np.all(eh[ok] <= allow[ok]), \
-        f"{label}: FP32 hit error {eh[worst]} > {allow[worst]} (photon {worst}, {ref['bounces'][worst]} bounces)"
-    dallow = np.maximum(1e-5, 1e-6 * (ref["cond"] - 1.0))
-    worst_d = np.argmax(np.where(ok, ed / dallow, 0.0))
-    report["max_ddir_over_allowance"] = float((ed[ok] / dallow[ok]).max(initial=0.0))
-    assert np.all(ed[ok] <= dallow[ok]), \
-        f"{label}: FP32 direction error {ed[worst_d]} > {dallow[worst_d]} (photon {worst_d}, " \
-        f"{ref['bounces'][worst_d]} bounces, K = {ref['cond'][worst_d]:.1f})"
-    assert np.all(ef[det] <= allow[det]), f"{label}: FP32 focal error {ef[det].max()}"
+    tol_p, tol_d = POS_REL_FP32 * f, DIR_FP32
+    report.update(max_dhit_over_f=float(eh[ok].max(initial=0.0) / f), max_ddir=float(ed[ok].max(initial=0.0)),
+                  max_dfocal_over_f=float(ef[det].max(initial=0.0) / f))
+    worst = int(np.argmax(np.where(ok, eh, -1.0)))
+    assert not np.any(eh[ok] > tol_p), \
+        f"{label}: FP32 hit error {eh[worst]:.3e} m > {tol_p:.3e} m = 1e-6 f (photon {worst}, " \
+        f"{ref['bounces'][worst]} bounces, K = {ref['cond'][worst]:.1f}); {int((eh[ok] > tol_p).sum())} photons over"
+    worst_d = int(np.argmax(np.where(ok, ed, -1.0)))
+    assert not np.any(ed[ok] > tol_d), \
+        f"{label}: FP32 direction error {ed[worst_d]:.3e} rad > 1e-5 rad (photon {worst_d}, " \
+        f"{ref['bounces'][worst_d]} bounces, K = {ref['cond'][worst_d]:.1f}); {int((ed[ok] > tol_d).sum())} photons over"
+    assert not np.any(ef[det] > tol_p), f"{label}: FP32 focal error {ef[det].max():.3e} m > 1e-6 f"
     return report

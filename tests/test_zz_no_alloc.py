@@ -1,9 +1,10 @@
 """The allocation-free spot-diagram entry point (robast_psf_noalloc).
 
 Some callers cannot allocate device memory when they need these statistics
-(graph capture, a caching allocator that owns the device, a fixed memory
-budget); robast_psf_noalloc serves them from a fixed scratch array inside the
-library.  This test calls it through the C ABI and checks it against the
+(a caching allocator that owns the device, a fixed memory budget);
+robast_psf_noalloc serves them from a fixed scratch array inside the library.
+(It synchronises its stream between rounds, so it is not for streams that are
+being captured into a CUDA graph.)  This test calls it through the C ABI and checks it against the
 allocating entry point robast_psf on two calls in a row (different traces,
 window layouts and precisions), since the scratch keeps the previous call's
 contents.  The file is named so that pytest collects it last.
@@ -106,6 +107,10 @@ def test_noalloc_refines_crowded_bins(precision):
     ref = robast.psf(geom, status, fxy, precision=precision, windows=[(0, n)])[0]
     got = robast.psf_noalloc(status, fxy, [(0, n)], precision=precision)[0]
     _same(got, ref)
+    # the crowded final bin is resolved by counting copies of each value: the exact
+    # nearest-rank radius, identical to the allocating entry point's and from call to call
+    assert got[3] == ref[3]
+    assert robast.psf_noalloc(status, fxy, [(0, n)], precision=precision)[0][3] == got[3]
     x = xy.astype(np.float32 if precision == 32 else np.float64).astype(np.float64)
     r = np.sort(np.hypot(x[0] - ref[1], x[1] - ref[2]))
     assert got[3] == pytest.approx(r[int(math.ceil(0.8 * n)) - 1], rel=1e-12, abs=1e-15)
