@@ -746,9 +746,12 @@ int check_scene(const o_scene* sc) {
 
 /* ==================================================== frozen-path gradients
  * Forward-mode dual numbers: every quantity carries its value and its
- * derivatives with respect to up to NT parameters (the parameters of the one
- * differentiable surface a photon's path meets, see oracle.h). */
-constexpr int NT = 10;
+ * derivatives with respect to up to NT parameters: the parameters of up to
+ * NSURF differentiable surfaces of a photon's path (10 slots each, see
+ * oracle.h).  A path that meets more of them is replayed once per group of
+ * NSURF surfaces. */
+constexpr int NSURF = 4;
+constexpr int NT = 10 * NSURF;
 
 struct Dual {
     double v;
@@ -1104,8 +1107,20 @@ bool differentiable(const o_surface& s) {
     return s.role == O_ROLE_MIRROR && (s.shape == O_SHAPE_SAG || s.shape == O_SHAPE_HEXCONE);
 }
 
-/* Replay one recorded path with parameters as numbers of type N.  `tracked`
- * is the surface whose parameters carry the derivative slots (Dual only). */
+/* The differentiable surfaces whose parameters carry derivative slots in one
+ * replay: surface sid[j] owns slots 10 j .. 10 j + 9. */
+struct Tracked {
+    int sid[NSURF];
+    int n = 0;
+    int index(int s) const {
+        for (int j = 0; j < n; ++j)
+            if (sid[j] == s) return j;
+        return -1;
+    }
+};
+
+/* Replay one recorded path with parameters as numbers of type N; the
+ * parameters of the `tracked` surfaces carry derivative slots (Dual only). */
 template <class N>
 struct Replay {
     bool ok;
@@ -1125,7 +1140,7 @@ Dual param_number<Dual>(double v, int slot) {
 }
 
 template <class N>
-PSurf<N> psurf_for(const o_surface& s, int sid, int tracked, const double* delta) {
+PSurf<N> psurf_for(const o_surface& s, int sid, const Tracked& tracked, const double* delta) {
     N prm[O_N_PARAM];
     double nom[O_N_PARAM];
     nom[0] = s.tilt[0];
@@ -1135,7 +1150,11 @@ PSurf<N> psurf_for(const o_surface& s, int sid, int tracked, const double* delta
     for (int k = 0; k < O_N_PARAM; ++k) {
         const double v = nom[k] + (delta ? delta[(size_t)sid * O_N_PARAM + k] : 0.0);
         int slot = -1;
-        if (sid == tracked) slot = s.shape == O_SHAPE_SAG ? (k < 10 ? k : -1) : (k >= 10 ? k - 10 : -1);
+        const int j = tracked.index(sid);
+        if (j >= 0) {
+            const int local = s.shape == O_SHAPE_SAG ? (k < 10 ? k : -1) : (k >= 10 ? k - 10 : -1);
+            if (local >= 0) slot = 10 * j + local;
+        }
         prm[k] = param_number<N>(v, slot);
     }
     return make_psurf<N>(s, prm);
@@ -1143,7 +1162,7 @@ PSurf<N> psurf_for(const o_surface& s, int sid, int tracked, const double* delta
 
 template <class N>
 Replay<N> replay(const Ctx& cx, const std::vector<Step>& path, V3 p0, V3 d0, double lam, int64_t pid,
-                 const uint32_t key[2], int tracked, const double* delta) {
+                 const uint32_t key[2], const Tracked& tracked, const double* delta) {
     const o_scene* sc = cx.sc;
     Replay<N> R;
     R.ok = true;
@@ -1248,13 +1267,6 @@ bool exit_margin(const o_scene* sc, int v, const NV3<N>& p, const NV3<N>& d, N* 
     return false;
 }
 
-struct PhotonRec {
-    int status;
-    double w;
-    int tracked;
-    std::vector<Step> path;
-};
-
 double sigmoid(double x) { return 1.0 / (1.0 + std::exp(-x)); }
 }  // namespace
 
@@ -1329,8 +1341,9 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* O, const dou
     if (n_threads <= 0) n_threads = 1;
     if ((int64_t)n_threads > n) n_threads = (int32_t)n;
     const size_t NP = (size_t)scene->n_surfaces * O_N_PARAM;
-    // per photon: value-pass results
-    std::vector<int> status(n), tracked(n, -1);
+    // per photon: value-pass results; has_diff: the path meets a differentiable surface
+    std::vector<int> status(n);
+    std::vector<char> has_diff(n, 0);
     std::vector<double> w(n, 0.0), qx(n, 0.0), qy(n, 0.0), mval(n, 0.0);
     std::vector<char> valid(n, 0);
     auto photon = [&](int64_t i, std::vector<Step>& path) {
@@ -1339,10 +1352,7 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* O, const dou
         const int64_t pid = first_photon_id + i;
         status[i] = record_path(cx, v, p, d, L[i], pid, key, max_bounces, &path, &w[i]);
         for (const Step& st : path)
-            if (differentiable(scene->surfaces[st.sid])) {
-                tracked[i] = st.sid;
-                break;
-            }
+            if (differentiable(scene->surfaces[st.sid])) has_diff[i] = 1;
     };
     // pass 1: values with the perturbed parameters
     {
@@ -1353,7 +1363,7 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* O, const dou
                 for (int64_t i = n * k / n_threads; i < n * (k + 1) / n_threads; ++i) {
                     photon(i, path);
                     V3 p = v3(O[i], O[n + i], O[2 * n + i]), d = v3(D[i], D[n + i], D[2 * n + i]);
-                    Replay<double> R = replay<double>(cx, path, p, d, L[i], first_photon_id + i, key, -1, delta);
+                    Replay<double> R = replay<double>(cx, path, p, d, L[i], first_photon_id + i, key, Tracked(), delta);
                     if (!R.ok) continue;
                     valid[i] = 1;
                     qx[i] = R.qx;
@@ -1419,29 +1429,43 @@ int oracle_objective(const o_scene* scene, int64_t n, const double* O, const dou
                 std::vector<double>& g = part[k];
                 double dummy_w;
                 for (int64_t i = n * k / n_threads; i < n * (k + 1) / n_threads; ++i) {
-                    if (valid[i] != 1 || tracked[i] < 0) continue;
+                    if (valid[i] != 1 || !has_diff[i]) continue;
                     if (objective != 1 && status[i] != O_ST_DETECTED) continue;
                     V3 p = v3(O[i], O[n + i], O[2 * n + i]), d = v3(D[i], D[n + i], D[2 * n + i]);
                     const int v = vop ? vop[i] : 0;
                     record_path(cx, v, p, d, L[i], first_photon_id + i, key, max_bounces, &path, &dummy_w);
-                    Replay<Dual> R = replay<Dual>(cx, path, p, d, L[i], first_photon_id + i, key, tracked[i], delta);
-                    if (!R.ok) continue;
-                    const o_surface& ts = scene->surfaces[tracked[i]];
-                    const int base = ts.shape == O_SHAPE_SAG ? 0 : 10;
-                    const int nslots = ts.shape == O_SHAPE_SAG ? 10 : 6;
-                    Dual m;
-                    if (objective == 1 && !exit_margin<Dual>(scene, v, R.p, R.d, &m)) continue;
-                    for (int k2 = 0; k2 < nslots; ++k2) {
-                        double c;
-                        if (centroid) {
-                            c = w[i] / Wv[v] * (cax == 0 ? R.qx.d[k2] : R.qy.d[k2]);
-                        } else if (objective == 0) {
-                            c = 2.0 * w[i] / Wv[v] * ((qx[i] - cxv[v]) * R.qx.d[k2] + (qy[i] - cyv[v]) * R.qy.d[k2]);
-                        } else {
-                            const double sg = sigmoid(m.v / tau);
-                            c = w[i] * sg * (1.0 - sg) / tau * m.d[k2] / nv[v];
+                    // every differentiable surface of the path, in order of first meeting
+                    std::vector<int> sids;
+                    for (const Step& st : path)
+                        if (differentiable(scene->surfaces[st.sid]) &&
+                            std::find(sids.begin(), sids.end(), st.sid) == sids.end())
+                            sids.push_back(st.sid);
+                    for (size_t g0 = 0; g0 < sids.size(); g0 += NSURF) {
+                        Tracked tr;
+                        for (size_t j = g0; j < sids.size() && tr.n < NSURF; ++j) tr.sid[tr.n++] = sids[j];
+                        Replay<Dual> R = replay<Dual>(cx, path, p, d, L[i], first_photon_id + i, key, tr, delta);
+                        if (!R.ok) break;
+                        Dual m;
+                        if (objective == 1 && !exit_margin<Dual>(scene, v, R.p, R.d, &m)) break;
+                        for (int j = 0; j < tr.n; ++j) {
+                            const o_surface& ts = scene->surfaces[tr.sid[j]];
+                            const int base = ts.shape == O_SHAPE_SAG ? 0 : 10;
+                            const int nslots = ts.shape == O_SHAPE_SAG ? 10 : 6;
+                            for (int k2 = 0; k2 < nslots; ++k2) {
+                                const int sl = 10 * j + k2;
+                                double c;
+                                if (centroid) {
+                                    c = w[i] / Wv[v] * (cax == 0 ? R.qx.d[sl] : R.qy.d[sl]);
+                                } else if (objective == 0) {
+                                    c = 2.0 * w[i] / Wv[v] *
+                                        ((qx[i] - cxv[v]) * R.qx.d[sl] + (qy[i] - cyv[v]) * R.qy.d[sl]);
+                                } else {
+                                    const double sg = sigmoid(m.v / tau);
+                                    c = w[i] * sg * (1.0 - sg) / tau * m.d[sl] / nv[v];
+                                }
+                                g[(size_t)tr.sid[j] * O_N_PARAM + base + k2] += c;
+                            }
                         }
-                        g[(size_t)tracked[i] * O_N_PARAM + base + k2] += c;
                     }
                 }
             });

@@ -123,7 +123,9 @@ int64_t oracle_generate_sources(const o_source_group* groups, int32_t n_groups, 
  * Parameters: 16 per surface -- [0..1] tilt about local x, y; [2..9] A1..A8
  * (SAG mirrors); [10..15] Bezier control points P0r, P0z, P1r, P1z, P2r, P2z
  * (HEXCONE mirrors).  grad (may be NULL): d objective / d parameter by
- * forward-mode dual numbers along the frozen paths. */
+ * forward-mode dual numbers along the frozen paths, for every differentiable
+ * surface a path meets (a path meeting several is replayed with the slots of
+ * four of them at a time). */
 #define O_N_PARAM 16
 int oracle_objective(const o_scene* scene, int64_t n, const double* origins, const double* dirs,
                      const double* wavelengths, const int32_t* variant_of_photon, uint64_t seed,
