@@ -11,10 +11,18 @@ field angle.  Metric: photon-bounces/s (sum of per-photon interaction counts
 divided by the device time of the step).  Inputs are resident in HBM and
 larger than L2 (1.4 GB for FP32).
 
-Reported beside it: the FP64 form of the same step, the end-to-end rate
-through the host-buffer entry point (inputs copied in and results copied out
-inside the timed region), the ALU roofline of the trace kernel and, at one
-GPU, the CPU oracle timed on the host cores.
+The FP32 step runs with the accuracy guard: every photon whose running error
+estimate exceeds 1e-6 f (position) or 1e-5 rad (direction) is re-traced in
+FP64 by a second launch inside the step.
+
+Reported beside it: the FP64 form of the same step; the two-mirror aspheric
+(Schwarzschild-Couder-like) system, 1e7 photons at each of 8 field angles, in
+FP32 and FP64; the GCT-like dual-mirror system (1e7 photons at each of 5
+field angles, FP32); the batched concentrator study; the misalignment sweep; the
+gradient batch; the end-to-end rate through the host-buffer entry point
+(inputs copied in and results copied out inside the timed region); the ALU
+roofline of each trace form and, at one GPU, the CPU oracle timed on the host
+cores together with each form's error against it on fixed photon windows.
 
 Multi-GPU (torchrun): photons are independent, so every rank traces its own
 full workload with its own photon-id range (weak scaling, no collective in
@@ -53,7 +61,7 @@ ANGLES = W.LST_ANGLES_DEG
 # reflection 8, Fresnel + Snell 35, plus the frame transform (33) and the
 # roughness perturbation (36).  Philox is integer work and counts 0 here.
 UNIT_FLOPS = {"aabb": 12, "sag": 21, "newton": 35, "aperture": 15, "cylinder": 25, "box": 20, "hexwall": 30,
-              "reflect": 8, "refract": 35, "rough": 36, "philox": 0, "rebase": 33}
+              "reflect": 8, "refract": 35, "rough": 36, "philox": 0, "rebase": 33, "refine": 120}
 
 
 class ClockSampler:
@@ -124,6 +132,7 @@ def workload_config(n_per_angle):
             "photons_per_angle": n_per_angle, "field_angles_deg": list(ANGLES), "wavelength_nm": [300, 600],
             "facet_tilt_sigma_mrad": 0.1, "roughness_sigma_mrad": 0.3, "max_bounces": 100,
             "outputs": "status, bounce count, focal-plane (x, y) per photon; per-angle centroid and R80",
+            "accuracy_bound": "FP32: final positions 1e-6 f, directions 1e-5 rad (FP64 re-trace of photons over it)",
             "l2": "inputs larger than L2 (no flush)"}
 
 
@@ -147,6 +156,52 @@ def cpu_oracle_rate(n_target_s=15.0, cap=2_000_000, seed=0):
     return {"value": bounces / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_per_angle} photons per field angle x {len(ANGLES)} angles of the same workload "
                       f"(FP32-rounded inputs, brute-force FP64 oracle, {cores} threads), {dt:.1f} s"}
+
+
+def _compare(g, r, precision, f, windows, status_det=1):
+    """Per-photon error of a GPU trace against the oracle's on the same photons, and the relative
+    error of each window's R80, effective area (detected count) and collection efficiency."""
+    from oracle import metrics
+    same_st = g["status"] == r["status"]
+    same = same_st & (g["bounces"] == r["bounces"]) & (g["last_surface"] == r["last_surface"])
+    eh = np.abs(g["hit"].astype(np.float64) - r["hit"]).max(axis=0)
+    ed = np.abs(g["dir"].astype(np.float64) - r["dir"]).max(axis=0)
+    bad = np.where(~same)[0]
+    rep = {"photons": int(g["status"].shape[0]), "max_pos_err_over_f": float(eh[same].max(initial=0.0) / f),
+           "max_dir_err_rad": float(ed[same].max(initial=0.0)),
+           "status_mismatch_frac": float(1.0 - same_st.mean()), "path_mismatches": int(bad.size),
+           "path_mismatch_max_edge_margin": float(r["edge_margin"][bad].max()) if bad.size else None}
+    r80e, ne, cee = [], [], []
+    for s0, c in windows:
+        sl = slice(s0, s0 + c)
+        mg = metrics.psf(g["status"][sl], g["focal_xy"][:, sl])
+        mr = metrics.psf(r["status"][sl], r["focal_xy"][:, sl])
+        if mr["n_detected"] > 0:
+            r80e.append(abs(mg["r80"] - mr["r80"]) / max(mr["r80"], 1e-300))
+            ne.append(abs(mg["n_detected"] - mr["n_detected"]) / mr["n_detected"])
+            cee.append(abs((g["status"][sl] == status_det).mean() - (r["status"][sl] == status_det).mean()) /
+                       max((r["status"][sl] == status_det).mean(), 1e-300))
+    rep.update(r80_rel_err_max=float(max(r80e)) if r80e else None,
+               a_eff_rel_err_max=float(max(ne)) if ne else None, ce_rel_err_max=float(max(cee)) if cee else None)
+    if "retraced" in g:
+        rep["fp64_retraced"] = int(np.asarray(g["retraced"]).ravel()[0])
+    return rep
+
+
+def accuracy_leg(checks):
+    """Each form's error against the FP64 oracle on a fixed window of its photon ids (outside
+    every timed region; part of the CPU-baseline leg, the one place the bench runs the oracle).
+    checks: name -> callable returning (gpu outputs, oracle outputs, precision, f, windows)."""
+    out = {}
+    for name, fn in checks.items():
+        try:
+            g, r, precision, f, wins = fn()
+            rep = _compare(g, r, precision, f, wins)
+            rep["window"] = f"{len(wins)} windows of {wins[0][1]} photons"
+            out[name] = rep
+        except Exception as e:  # a failed check is reported, not fatal to the bench line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_reference(args):
@@ -181,12 +236,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_ranks, barrier):
+def roofline_of(units, kernel_ms, peak, label, peak_source):
+    """ALU roofline of a trace launch: algorithmic FLOPs (work units x per-unit figure) over the
+    launch's CUDA-event time, against the measured FMA peak."""
+    flops = sum(units.get(k, 0) * UNIT_FLOPS[k] for k in UNIT_FLOPS)
+    achieved = flops / (kernel_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "kernel": label, "kernel_ms": kernel_ms, "flops_per_launch": flops,
+            "work_units_per_launch": units, "peak_source": peak_source}
+
+
+def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_ranks, barrier, peak32):
     """Batched concentrator study: 64 Bezier-cone variants x 41 incidence angles
     (0-40 deg) x photons per group generated on the device, all in ONE
-    persistent launch, replayed from a captured CUDA graph; launch shape from
-    the autotuner.  Metric: photon-bounces/s; result: collection efficiency per
-    (variant, angle)."""
+    persistent launch (plus the FP32 accuracy guard's FP64 re-trace launch),
+    replayed from a captured CUDA graph; launch shape from the autotuner.
+    Metric: photon-bounces/s; result: collection efficiency per (variant, angle)."""
     import torch
     import paper_1508_07803_gb300 as robast
     from paper_1508_07803_gb300 import autotune
@@ -194,9 +259,10 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
     scene, groups = W.cone_batch(n_variants=64, angles_deg=W.CONE_ANGLES_DEG,
                                  n_per_group=args.batch_photons_per_group, seed=0)
     geom = robast.build_geometry(scene)
-    (block, bps), table = autotune.tune_sources(geom, groups, precision=32, max_bounces=30, stream=stream)
+    (block, bps, rfm), table = autotune.tune_sources(geom, groups, precision=32, max_bounces=30, stream=stream)
     src = robast.sources_create(geom, groups)
     counts = torch.zeros((src.n_groups, 8), dtype=torch.int64, device=geom_dev)
+    retraced = torch.zeros(2, dtype=torch.int64, device=geom_dev)
     first_id = rank * src.n_photons
 
     # capture on a side stream (graphs cannot be captured on the default stream)
@@ -204,15 +270,18 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
     cap.wait_stream(stream)
     with torch.cuda.stream(cap):
         robast.trace_sources(geom, src, counts, seed=0, precision=32, max_bounces=30, stream=cap,
-                             first_photon_id=first_id, block_size=block, blocks_per_sm=bps)  # warm-up
+                             first_photon_id=first_id, block_size=block, blocks_per_sm=bps, refill_min=rfm,
+                             out={"retraced": retraced})  # warm-up
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=cap):
             robast.trace_sources(geom, src, counts, seed=0, precision=32, max_bounces=30, stream=cap,
-                                 first_photon_id=first_id, block_size=block, blocks_per_sm=bps)
+                                 first_photon_id=first_id, block_size=block, blocks_per_sm=bps, refill_min=rfm,
+                                 out={"retraced": retraced})
     graph.replay()  # warm-up replay
     torch.cuda.synchronize()
     counts.zero_()
+    retraced.zero_()
     barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -229,21 +298,73 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
     summary = {f"{int(a)}deg": {"mean": float(ce[:, i].mean()), "min": float(ce[:, i].min()),
                                 "max": float(ce[:, i].max())}
                for i, a in enumerate(angles) if int(a) in (0, 10, 20, 25, 30, 35, 40)}
+    # work units of the launch, counted on a 1/20 sample of every group (outside the timed region)
+    frac = 20
+    sample = [dict(g, n=max(1, g["n"] // frac)) for g in groups]
+    ssrc = robast.sources_create(geom, sample)
+    units_t = torch.zeros(robast.N_UNITS, dtype=torch.int64, device=geom_dev)
+    scounts = torch.zeros((ssrc.n_groups, 8), dtype=torch.int64, device=geom_dev)
+    robast.trace_sources(geom, ssrc, scounts, seed=0, precision=32, max_bounces=30, stream=stream,
+                         block_size=128, work_units=units_t, accuracy=False)
+    torch.cuda.synchronize()
+    units = {k: v * frac for k, v in zip(robast.UNIT_NAMES, units_t.cpu().tolist())}
+    ssrc.close()
+    kern_ms = ms / args.batch_steps
+    roof = roofline_of(units, kern_ms, peak32, "robast::trace_kernel<float,SRC> (+ FP64 re-trace)",
+                       "FFMA throughput probe robast_measure_alu_peak on this GPU (measured); work units counted "
+                       "on a 1/20 sample of every group, times 20")
+    rt = retraced.cpu().tolist()
     src.close()
     geom.close()
-    return {"value": bounces / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.batch_steps,
+    return {"value": bounces / (ms * 1e-3), "unit": UNIT, "ms_per_step": kern_ms,
             "steps": args.batch_steps, "photons_per_step": src.n_photons,
             "bounces_per_step": bounces / args.batch_steps / ws,
+            "fp64_retraced_per_step": rt[0] // args.batch_steps, "over_bound_not_retraced": rt[1],
+            "roofline": roof,
             "config": {"workload": "hex_bezier_cone_64_variants_x_41_angles", "variants": 64,
                        "angles_deg": [0, 40, 1], "photons_per_group": args.batch_photons_per_group,
                        "max_bounces": 30, "sources": "generated on the device (Philox stream 1)",
-                       "launch": "one persistent launch per step, replayed from a CUDA graph"},
-            "autotune": {"block": block, "blocks_per_sm": bps,
-                         "candidates_ms": {f"{b}x{p}": round(t, 3) for (b, p), t in table.items()}},
+                       "launch": "one persistent launch per step (+ the accuracy guard's FP64 re-trace), "
+                                 "replayed from a CUDA graph"},
+            "autotune": {"block": block, "blocks_per_sm": bps, "refill_min": rfm,
+                         "candidates_ms": {f"{b}x{p}/r{r}": round(t, 3) for (b, p, r), t in table.items()}},
             "collection_efficiency": summary}
 
 
-def measure_tolerance(args, dev, stream, ws, rank, max_over_ranks, sum_over_ranks, barrier):
+def batched_accuracy_check(dev, n_window=12_500, n_groups=8):
+    """Windows of single groups of the batched study, re-traced on the GPU at their original
+    photon ids (source mode, FP32 with the accuracy guard) and by the oracle."""
+    import torch
+    import oracle
+    import paper_1508_07803_gb300 as robast
+    scene, groups = W.cone_batch(n_variants=64, angles_deg=W.CONE_ANGLES_DEG, n_per_group=2_000_000, seed=0)
+    geom = robast.build_geometry(scene)
+    first = np.cumsum([0] + [g["n"] for g in groups])
+    rng = np.random.default_rng(11)
+    gs, rs = [], []
+    for gi in sorted(rng.choice(len(groups), size=n_groups, replace=False).tolist()):
+        pid0 = int(first[gi]) + int(rng.integers(0, groups[gi]["n"] - n_window))
+        one = [dict(groups[gi], n=n_window)]
+        s1 = robast.sources_create(geom, one)
+        cnt = torch.zeros((1, 8), dtype=torch.int64, device=dev)
+        out = robast.alloc_outputs(n_window, 32, dev)
+        robast.trace_sources(geom, s1, cnt, seed=0, precision=32, max_bounces=30, out=out, first_photon_id=pid0)
+        torch.cuda.synchronize()
+        s1.close()
+        bb, var, _ = oracle.generate_sources(one, seed=0, first_photon_id=pid0)
+        bundle = W.Bundle(bb["origins"], bb["dirs"], bb["wavelengths"]).rounded_to(np.float32)
+        rs.append(oracle.trace(scene, bundle, seed=0, first_photon_id=pid0, max_bounces=30, variant_of_photon=var,
+                               eps=oracle.default_eps(scene, 32)))
+        gs.append({k: v.cpu().numpy() for k, v in out.items()})
+    geom.close()
+    cat = lambda ds, k: np.concatenate([d[k] for d in ds], axis=-1)
+    g = {k: cat(gs, k) for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy")}
+    g["retraced"] = np.array([sum(int(d["retraced"][0]) for d in gs)])
+    r = {k: cat(rs, k) for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "edge_margin")}
+    return g, r, 32, scene.focal_length, [(k * n_window, n_window) for k in range(n_groups)]
+
+
+def measure_tolerance(args, dev, stream, ws, rank, max_over_ranks, sum_over_ranks, barrier, peak32):
     """Misalignment study: 64 realisations of the dish with Gaussian facet-tilt
     errors (0.5 mrad per axis), 1e6 photons each at a 1 deg field, all
     realisations in one launch (variants); the step includes the R80 of every
@@ -258,36 +379,99 @@ def measure_tolerance(args, dev, stream, ws, rank, max_over_ranks, sum_over_rank
     d = torch.from_numpy(b.dirs).to(dev, torch.float32)
     w = torch.from_numpy(b.wavelengths).to(dev, torch.float32)
     v = torch.from_numpy(vop).to(dev)
-    out = robast.alloc_outputs(b.n, 32, dev, fields=("status", "bounces", "focal_xy", "counters"))
+    out = robast.alloc_outputs(b.n, 32, dev, fields=("status", "bounces", "focal_xy", "counters", "retraced"))
     wins = [(k * m, m) for k in range(nr)]
 
-    def step():
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
         robast.trace(geom, o, d, w, seed=0, variant_of_photon=v, out=out, stream=stream,
                      first_photon_id=rank * b.n)
+        if ev is not None:
+            ev[1].record(stream)
         return robast.psf(geom, out["status"], out["focal_xy"], windows=wins, stream=stream)
 
     for _ in range(3):
         step()
+    units_t = torch.zeros(robast.N_UNITS, dtype=torch.int64, device=dev)
+    robast.trace(geom, o, d, w, seed=0, variant_of_photon=v, stream=stream, first_photon_id=rank * b.n,
+                 work_units=units_t, block_size=128, accuracy=False,
+                 out=robast.alloc_outputs(b.n, 32, dev, fields=("status",)))
+    torch.cuda.synchronize()
+    units = dict(zip(robast.UNIT_NAMES, units_t.cpu().tolist()))
     out["counters"].zero_()
+    out["retraced"].zero_()
     barrier()
+    steps = 5
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    steps = 5
     t0.record(stream)
-    for _ in range(steps):
-        res = step()
+    for k in range(steps):
+        res = step(evs[k])
     t1.record(stream)
     barrier()
     ms = max_over_ranks(t0.elapsed_time(t1))
+    kern_ms = statistics.mean(a.elapsed_time(z) for a, z in evs)
     bounces = sum_over_ranks(float(out["counters"][0].item()))
     r80 = np.array([r[3] for r in res])
+    rt = out["retraced"].cpu().tolist()
     geom.close()
     return {"value": bounces / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-            "photons_per_step": int(b.n),
+            "photons_per_step": int(b.n), "fp64_retraced_per_step": rt[0] // steps,
+            "roofline": roofline_of(units, kern_ms, peak32, "robast::trace_kernel<float,512> (+ sort, FP64 re-trace)",
+                                    "FFMA throughput probe robast_measure_alu_peak on this GPU (measured)"),
             "r80_m": {"mean": float(r80.mean()), "std": float(r80.std()), "min": float(r80.min()),
                       "max": float(r80.max())},
             "config": {"workload": "lst_tolerance_64_realisations_tilt_0.5mrad", "realisations": nr,
                        "photons_per_realisation": m, "field_deg": 1.0}}
+
+
+def tolerance_accuracy_check(dev, n_window=25_000):
+    import torch
+    import oracle
+    import paper_1508_07803_gb300 as robast
+    nr, m = 64, 1_000_000
+    scene, b, vop = W.tolerance_sweep(n_realizations=nr, tilt_sigma=0.5e-3, photons_per_realization=m, seed=0)
+    wins = [(k * m + 4321, n_window) for k in (0, 21, 42, 63)]
+    idx = np.concatenate([np.arange(s0, s0 + c) for s0, c in wins])
+    return _plain_window_check(dev, scene, b, idx, 32, vop=vop, n_window=n_window)
+
+
+def _plain_window_check(dev, scene, b, idx, precision, vop=None, n_window=None, max_bounces=100):
+    """GPU re-trace (at the original photon ids) and oracle trace of windows of a plain workload;
+    idx: the photon indices of the windows, contiguous runs of n_window."""
+    import torch
+    import oracle
+    import paper_1508_07803_gb300 as robast
+    geom = robast.build_geometry(scene)
+    dt = torch.float32 if precision == 32 else torch.float64
+    gs, rs = [], []
+    for s0 in idx[::n_window]:
+        s0 = int(s0)
+        sl = slice(s0, s0 + n_window)
+        part = W.Bundle(np.ascontiguousarray(b.origins[:, sl]), np.ascontiguousarray(b.dirs[:, sl]),
+                        b.wavelengths[sl].copy())
+        if precision == 32:
+            part = part.rounded_to(np.float32)
+        v = None if vop is None else np.ascontiguousarray(vop[sl])
+        o = torch.from_numpy(part.origins).to(dev, dt)
+        d = torch.from_numpy(part.dirs).to(dev, dt)
+        w = torch.from_numpy(part.wavelengths).to(dev, dt)
+        out = robast.trace(geom, o, d, w, seed=0, precision=precision, first_photon_id=s0, max_bounces=max_bounces,
+                           variant_of_photon=None if v is None else torch.from_numpy(v).to(dev))
+        torch.cuda.synchronize()
+        gs.append({k: x.cpu().numpy() for k, x in out.items()})
+        rs.append(oracle.trace(scene, part, seed=0, first_photon_id=s0, max_bounces=max_bounces,
+                               eps=oracle.default_eps(scene, precision), variant_of_photon=v))
+    geom.close()
+    cat = lambda ds, k: np.concatenate([x[k] for x in ds], axis=-1)
+    g = {k: cat(gs, k) for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy")}
+    if precision == 32:
+        g["retraced"] = np.array([sum(int(x["retraced"][0]) for x in gs)])
+    r = {k: cat(rs, k) for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy", "edge_margin")}
+    nw = len(gs)
+    return g, r, precision, scene.focal_length, [(k * n_window, n_window) for k in range(nw)]
 
 
 def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
@@ -322,11 +506,14 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
     barrier()
     dt = max_over_ranks(time.perf_counter() - t0)
     gn = float(torch.linalg.vector_norm(g).item())
+    layout = robast.param_layout(geom)
+    active = sum(1 for p in layout if p[3])
     geom.close()
     return {"value": ws * args.grad_steps / dt, "unit": "grad evals/s", "ms_per_eval": 1e3 * dt / args.grad_steps,
             "photons_per_eval": int(b.n), "photons_per_s": ws * args.grad_steps * b.n / dt,
             "objective": "sum over 32 dishes of the mean-squared spot radius (frozen path, expected weights)",
             "objective_value_m2": value, "gradient_norm": gn, "n_params": int(geom.n_surfaces * robast.N_PARAM),
+            "n_params_active": active,
             "n_detected": int(info["n_detected"]), "untracked_photons": int(info["n_untracked"]),
             "config": {"workload": "dish_batch_32_dishes_60_to_198_facets", "facets": [counts[0], counts[-1]],
                        "photons_per_dish": args.grad_photons_per_dish, "field_angle_deg": "2 v / 31 for dish v",
@@ -367,9 +554,14 @@ def main():
     ap.add_argument("--photons-per-angle", type=int, default=10_000_000)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--ref-photons-per-angle", type=int, default=20_000)
+    ap.add_argument("--sct-photons-per-angle", type=int, default=10_000_000)
+    ap.add_argument("--sct-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-sct", action="store_true")
+    ap.add_argument("--no-gct", action="store_true")
+    ap.add_argument("--gct-photons-per-angle", type=int, default=10_000_000)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-tolerance", action="store_true")
@@ -396,18 +588,7 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     robast.load()
-
-    npa = args.photons_per_angle
-    N = npa * len(ANGLES)
-    scene, bundle = W.lst_workload(npa, seed=rank)
-    geom = robast.build_geometry(scene)
-    first_id = shard.replica_first_id(rank, N)
     stream = torch.cuda.current_stream(dev)
-
-    def inputs(precision):
-        dt = torch.float32 if precision == 32 else torch.float64
-        return (torch.from_numpy(bundle.origins).to(dev, dt), torch.from_numpy(bundle.dirs).to(dev, dt),
-                torch.from_numpy(bundle.wavelengths).to(dev, dt))
 
     def barrier():
         if ws > 1:
@@ -420,35 +601,51 @@ def main():
     def sum_over_ranks(x):
         return shard.all_reduce_scalar(x, "sum", device=dev)
 
-    def measure(precision, steps, warmup, want_clocks):
-        o, d, w = inputs(precision)
+    def measure(scene, bundle, npa, n_angles, precision, steps, warmup, want_clocks):
+        """One step: coherent-order sort, one trace launch (+ the accuracy guard's FP64 re-trace in
+        FP32), spot-diagram reduction of every field angle."""
+        geom = robast.build_geometry(scene)
+        N = bundle.n
+        first_id = shard.replica_first_id(rank, N)
+        dt = torch.float32 if precision == 32 else torch.float64
+        o = torch.from_numpy(bundle.origins).to(dev, dt)
+        d = torch.from_numpy(bundle.dirs).to(dev, dt)
+        w = torch.from_numpy(bundle.wavelengths).to(dev, dt)
         # per-photon outputs the spot diagram and the metric need: status, bounce count, focal (x, y)
-        out = robast.alloc_outputs(N, precision, dev, fields=("status", "bounces", "focal_xy", "counters"))
+        fields = ("status", "bounces", "focal_xy", "counters") + (("retraced",) if precision == 32 else ())
+        out = robast.alloc_outputs(N, precision, dev, fields=fields)
         counters = out["counters"]
         # per step: the coherent-order sort (init, bounds, count, columns, three scan launches, place), the
-        # trace, and the reduction (sums, finish, histogram, pick, compact, check, candidate r^2,
-        # sub-histogram, pick, collect, select; all angles at once)
+        # trace (+ the FP64 re-trace in FP32), and the reduction (sums, finish, histogram, pick, compact,
+        # check, candidate r^2, sub-histogram, pick, collect, select; all angles at once)
         order_launches, psf_launches = 8, 11
+        trace_launches = 2 if precision == 32 else 1
+        wins = [(k * npa, npa) for k in range(n_angles)]
+        # launch shape and refill threshold from the autotuner (on the first 2e6 photons, untimed)
+        from paper_1508_07803_gb300 import autotune
+        (blk, bps, rfm), table = autotune.tune_trace(geom, o, d, w, precision=precision, stream=stream)
 
         def step(ev=None):
             if ev is not None:
                 ev[0].record(stream)
             robast.trace(geom, o, d, w, seed=0, precision=precision, first_photon_id=first_id, out=out,
-                         stream=stream)
+                         stream=stream, block_size=blk, blocks_per_sm=bps, refill_min=rfm)
             if ev is not None:
                 ev[1].record(stream)
-            return robast.psf(geom, out["status"], out["focal_xy"], precision=precision, stream=stream,
-                              windows=[(k * npa, npa) for k in range(len(ANGLES))])
+            return robast.psf(geom, out["status"], out["focal_xy"], precision=precision, stream=stream, windows=wins)
 
         for _ in range(warmup):
             step()
         # work units of one launch (counting build, outside the timed region)
         units = torch.zeros(robast.N_UNITS, dtype=torch.int64, device=dev)
-        robast.trace(geom, o, d, w, seed=0, precision=precision, first_photon_id=first_id, out=out,
-                     stream=stream, work_units=units, block_size=128)
+        robast.trace(geom, o, d, w, seed=0, precision=precision, first_photon_id=first_id, stream=stream,
+                     work_units=units, block_size=128, accuracy=False,
+                     out=robast.alloc_outputs(N, precision, dev, fields=("status",)))
         torch.cuda.synchronize()
         units = dict(zip(robast.UNIT_NAMES, units.cpu().tolist()))
         counters.zero_()
+        if "retraced" in out:
+            out["retraced"].zero_()
         barrier()
         clocks = ClockSampler(dev.index) if want_clocks else None
         if clocks:
@@ -468,49 +665,79 @@ def main():
         kern_ms = [a.elapsed_time(b) for a, b in evs]
         clk = clocks.stop() if clocks else None
         c = counters.cpu().tolist()
-        bounces = c[0]
-        return {"ms": ms, "kernel_ms": kern_ms, "bounces": bounces, "counters": c, "units": units, "psf": last,
-                "clocks": clk, "launches": steps * (order_launches + 1 + psf_launches)}
+        rt = out["retraced"].cpu().tolist() if "retraced" in out else [0, 0]
+        geom.close()
+        return {"ms": ms, "kernel_ms": kern_ms, "bounces": c[0], "counters": c, "units": units, "psf": last,
+                "clocks": clk, "launches": steps * (order_launches + trace_launches + psf_launches),
+                "retraced_per_step": rt[0] // steps, "over_bound_not_retraced": rt[1],
+                "autotune": {"block": blk, "blocks_per_sm": bps, "refill_min": rfm,
+                             "candidates_ms": {f"{b}x{p}/r{r}": round(t, 3) for (b, p, r), t in table.items()}}}
 
-    fp32 = measure(32, args.steps, args.warmup, want_clocks=True)
-    ms = max_over_ranks(fp32["ms"])
-    bounces_all = sum_over_ranks(fp32["bounces"])
-    value = bounces_all / (ms * 1e-3)
-    kern_avg_ms = statistics.mean(fp32["kernel_ms"])
+    def form_of(m, steps, precision, peak, label):
+        msx = max_over_ranks(m["ms"])
+        v = sum_over_ranks(m["bounces"]) / (msx * 1e-3)
+        k = statistics.mean(m["kernel_ms"])
+        f = {"value": v, "ms_per_step": msx / steps, "kernel_ms": k, "bounces_per_step": m["bounces"] / steps,
+             "roofline": roofline_of(m["units"], k, peak, label,
+                                     ("FFMA" if precision == 32 else "DFMA") +
+                                     " throughput probe robast_measure_alu_peak on this GPU (measured)")}
+        if precision == 32:
+            f["fp64_retraced_per_step"] = m["retraced_per_step"]
+            f["over_bound_not_retraced"] = m["over_bound_not_retraced"]
+        f["autotune"] = m["autotune"]
+        return f
 
-    # ALU roofline of the trace kernel (FP32 FMA peak measured on this device)
     peak32 = robast.measure_alu_peak(32)
-    flops = sum(fp32["units"][k] * UNIT_FLOPS[k] for k in UNIT_FLOPS)
-    achieved = flops / (kern_avg_ms * 1e-3)
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak32, "traffic": traffic_from_profile(N),
-            "kernel": "robast::trace_kernel<float,512> (with the coherent-order sort)", "kernel_ms": kern_avg_ms,
-            "flops_per_launch": flops, "work_units_per_launch": fp32["units"],
-            "peak_source": "FFMA throughput probe robast_measure_alu_peak on this GPU (measured)"}
-
-    forms = {"fp32": {"value": value, "ms_per_step": ms / args.steps, "kernel_ms": kern_avg_ms,
-                      "bounces_per_step": bounces_all / args.steps / ws}}
+    peak64 = robast.measure_alu_peak(64)
+    npa = args.photons_per_angle
+    scene, bundle = W.lst_workload(npa, seed=rank)
+    N = bundle.n
+    fp32 = measure(scene, bundle, npa, len(ANGLES), 32, args.steps, args.warmup, want_clocks=True)
+    forms = {"fp32": form_of(fp32, args.steps, 32, peak32, "robast::trace_kernel<float,512> (+ sort, FP64 re-trace)")}
+    ms = max_over_ranks(fp32["ms"])
+    value = forms["fp32"]["value"]
+    roof = dict(forms["fp32"]["roofline"])
+    roof["traffic"] = traffic_from_profile(N)
     if not args.no_fp64:
-        fp64 = measure(64, args.fp64_steps, 3, want_clocks=False)
-        ms64 = max_over_ranks(fp64["ms"])
-        v64 = sum_over_ranks(fp64["bounces"]) / (ms64 * 1e-3)
-        k64 = statistics.mean(fp64["kernel_ms"])
-        peak64 = robast.measure_alu_peak(64)
-        fl64 = sum(fp64["units"][k] * UNIT_FLOPS[k] for k in UNIT_FLOPS)
-        forms["fp64"] = {"value": v64, "ms_per_step": ms64 / args.fp64_steps, "kernel_ms": k64,
-                         "roofline": {"bound": "alu", "achieved": fl64 / (k64 * 1e-3) / 1e12, "peak": peak64 / 1e12,
-                                      "unit": "TFLOP/s", "frac": fl64 / (k64 * 1e-3) / peak64,
-                                      "peak_source": "DFMA throughput probe (measured)"}}
+        fp64 = measure(scene, bundle, npa, len(ANGLES), 64, args.fp64_steps, 3, want_clocks=False)
+        forms["fp64"] = form_of(fp64, args.fp64_steps, 64, peak64, "robast::trace_kernel<double,128> (+ sort)")
+
+    if not args.no_sct:
+        snpa = args.sct_photons_per_angle
+        sscene, sbundle = W.sct_workload(snpa, seed=rank)
+        nang = len(W.SCT_ANGLES_DEG)
+        s32 = measure(sscene, sbundle, snpa, nang, 32, args.sct_steps, 3, want_clocks=False)
+        forms["sct_fp32"] = form_of(s32, args.sct_steps, 32, peak32, "robast::trace_kernel<float,512> (+ sort, FP64 re-trace)")
+        s64 = measure(sscene, sbundle, snpa, nang, 64, max(2, args.sct_steps // 2), 3, want_clocks=False)
+        forms["sct_fp64"] = form_of(s64, max(2, args.sct_steps // 2), 64, peak64, "robast::trace_kernel<double,128> (+ sort)")
+        for k, m in (("sct_fp32", s32), ("sct_fp64", s64)):
+            forms[k]["config"] = {"workload": "sct_two_mirror_aspheric_8_field_angles", "photons_per_angle": snpa,
+                                  "field_angles_deg": [round(a, 4) for a in W.SCT_ANGLES_DEG],
+                                  "newton": "FP32 bulk, FP64 last Newton step at grazing incidence"}
+            forms[k]["psf"] = [{"field_deg": round(a, 4), "n_detected": int(p[0]), "r80_m": p[3]}
+                               for a, p in zip(W.SCT_ANGLES_DEG, m["psf"])]
+        del sbundle
+
+    if not args.no_gct:
+        gnpa = args.gct_photons_per_angle
+        gscene, gbundle = W.gct_workload(gnpa, seed=rank)
+        g32 = measure(gscene, gbundle, gnpa, len(W.GCT_ANGLES_DEG), 32, args.sct_steps, 3, want_clocks=False)
+        forms["gct_fp32"] = form_of(g32, args.sct_steps, 32, peak32, "robast::trace_kernel<float,512> (+ sort, FP64 re-trace)")
+        forms["gct_fp32"]["config"] = {"workload": "gct_like_dual_mirror_6_petals_5_field_angles",
+                                       "photons_per_angle": gnpa, "field_angles_deg": list(W.GCT_ANGLES_DEG)}
+        forms["gct_fp32"]["psf"] = [{"field_deg": a, "n_detected": int(p[0]), "r80_m": p[3]}
+                                    for a, p in zip(W.GCT_ANGLES_DEG, g32["psf"])]
+        del gbundle
 
     if not args.no_batched:
         forms["batched_fp32"] = measure_batched(args, geom_dev=dev, stream=stream, ws=ws, rank=rank,
                                                 max_over_ranks=max_over_ranks, sum_over_ranks=sum_over_ranks,
-                                                barrier=barrier)
+                                                barrier=barrier, peak32=peak32)
 
     if not args.no_tolerance:
         forms["tolerance_fp32"] = measure_tolerance(args, dev=dev, stream=stream, ws=ws, rank=rank,
                                                     max_over_ranks=max_over_ranks, sum_over_ranks=sum_over_ranks,
-                                                    barrier=barrier)
+                                                    barrier=barrier, peak32=peak32)
 
     if not args.no_grad:
         forms["grad_fp32"] = measure_grad(args, dev=dev, stream=stream, ws=ws, rank=rank,
@@ -518,6 +745,8 @@ def main():
 
     e2e = None
     if not args.no_e2e:
+        geom = robast.build_geometry(scene)
+        first_id = shard.replica_first_id(rank, N)
         dt = torch.float32
         ho = torch.from_numpy(bundle.origins).to(dt).pin_memory()
         hd = torch.from_numpy(bundle.dirs).to(dt).pin_memory()
@@ -525,7 +754,8 @@ def main():
         hout = {"status": torch.empty(N, dtype=torch.uint8).pin_memory(),
                 "bounces": torch.empty(N, dtype=torch.uint8).pin_memory(),
                 "focal_xy": torch.empty((2, N), dtype=dt).pin_memory(),
-                "counters": torch.zeros(robast.N_COUNTERS, dtype=torch.int64)}
+                "counters": torch.zeros(robast.N_COUNTERS, dtype=torch.int64),
+                "retraced": torch.zeros(2, dtype=torch.int64)}
         for _ in range(2):
             robast.trace_host(geom, ho, hd, hw, seed=0, out=hout, first_photon_id=first_id)
         hout["counters"].zero_()
@@ -537,26 +767,59 @@ def main():
         barrier()
         et = max_over_ranks(time.perf_counter() - t0)
         eb = sum_over_ranks(float(hout["counters"][0].item()))
+        geom.close()
         e2e = {"value": eb / et, "unit": UNIT, "h2d_bytes_per_step": int(N * 7 * 4),
                "d2h_bytes_per_step": int(N * (1 + 1 + 2 * 4)), "steps": e2e_steps,
-               "api": "robast_trace_host (pinned host buffers in and out)"}
+               "api": "robast_trace_host (pinned host buffers in and out, FP32 with the accuracy guard)"}
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
     cpu = None
+    accuracy = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()
+        # each form's error against the oracle, on fixed windows of its photon ids
+        m = 20_000
+        dish_idx = np.concatenate([np.arange(k * npa + 7777, k * npa + 7777 + m) for k in range(len(ANGLES))])
+        checks = {"fp32": lambda: _plain_window_check(dev, scene, bundle, dish_idx, 32, n_window=m)}
+        if not args.no_fp64:
+            checks["fp64"] = lambda: _plain_window_check(dev, scene, bundle, dish_idx, 64, n_window=m)
+        if not args.no_sct:
+            sm = 12_500
+            sscene, sbundle = W.sct_workload(args.sct_photons_per_angle, seed=0)
+            sidx = np.concatenate([np.arange(k * args.sct_photons_per_angle + 555,
+                                             k * args.sct_photons_per_angle + 555 + sm)
+                                   for k in range(len(W.SCT_ANGLES_DEG))])
+            checks["sct_fp32"] = lambda: _plain_window_check(dev, sscene, sbundle, sidx, 32, n_window=sm)
+            checks["sct_fp64"] = lambda: _plain_window_check(dev, sscene, sbundle, sidx, 64, n_window=sm)
+        if not args.no_gct:
+            gm = 20_000
+            gscene, gbundle = W.gct_workload(args.gct_photons_per_angle, seed=0)
+            gidx = np.concatenate([np.arange(k * args.gct_photons_per_angle + 999,
+                                             k * args.gct_photons_per_angle + 999 + gm)
+                                   for k in range(len(W.GCT_ANGLES_DEG))])
+            checks["gct_fp32"] = lambda: _plain_window_check(dev, gscene, gbundle, gidx, 32, n_window=gm)
+        if not args.no_batched:
+            checks["batched_fp32"] = lambda: batched_accuracy_check(dev)
+        if not args.no_tolerance:
+            checks["tolerance_fp32"] = lambda: tolerance_accuracy_check(dev)
+        accuracy = accuracy_leg(checks)
+        for k, a in accuracy.items():
+            if k in forms:
+                forms[k]["accuracy"] = a
     psf = [{"field_deg": a, "n_detected": int(p[0]), "cx_m": p[1], "cy_m": p[2], "r80_m": p[3],
             "a_eff_m2": p[0] / npa * math.pi * 12.0 ** 2} for a, p in zip(ANGLES, fp32["psf"])]
     cfg = workload_config(npa)
     cfg["parallelism"] = f"replicas{ws}" if ws > 1 else "single"
+    launches = fp32["launches"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "forms": forms,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": fp32["launches"],
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": fp32["clocks"], "psf": psf,
+            "accuracy": (accuracy or {}).get("fp32"),
             "status_counts_per_step": [c // args.steps for c in fp32["counters"][1:7]]}
     print(json.dumps(line), flush=True)
     if ws > 1:

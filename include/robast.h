@@ -237,8 +237,9 @@ typedef struct robast_trace_opts {
                                  build: 128) */
     int32_t blocks_per_sm;    /* 0 = as many as fit */
     unsigned long long* work_units; /* device [ROBAST_N_UNITS] or NULL; non-NULL runs the
-                                       counting build of the kernel (block 128, slower) and
-                                       adds the work units below to it */
+                                       counting build of the kernel (block 128, slower; FP32
+                                       only in source mode) and adds the work units below to
+                                       it */
     int32_t coherent_order;   /* 0: library default (on for n >= 65536), 1: on, -1: off.  On, the
                                  photons are first sorted by origin cell so that each warp traces
                                  neighbouring rays; the results are identical either way.  The
@@ -252,26 +253,31 @@ typedef struct robast_trace_opts {
                                  traversal) at the cost of idle lanes; 1 refills at once.  The
                                  results do not depend on it */
     double accuracy_pos;      /* FP32 accuracy guard (0 = off), final-position error bound (m), and */
-    double accuracy_dir;      /* final-direction error bound (rad); 0 in one = no bound on it.  Every
-                                 FP32 photon carries a first-order estimate of its accumulated
-                                 rounding error: per interaction the hit point moves by (lateral
-                                 offset + segment x direction error + a few ulps of the coordinates)
-                                 / |cos incidence|, the normal by the surface's curvature bound times
-                                 that, and the new direction by twice the normal's error
-                                 (reflection) or by Snell's derivative (refraction).  A photon whose
-                                 estimate exceeds half a bound, or that ends in ERROR, is re-traced
-                                 from its inputs in FP64 (same random streams, same epsilon) by a
-                                 second launch on the same stream, whose result replaces the FP32
-                                 one.  The queue holds n photons (n > 2^26: max(2^26, n / 8)); its
-                                 scratch comes from g's memory pool like the sort's.  Off with
-                                 photon tracks or the counting build */
+    double accuracy_dir;      /* final-direction error bound (rad); 0 in one = no bound on it.  The FP32
+                                 trace keeps each position as a float pair and re-solves every hit
+                                 from the approximate hit point (a few ulps of the local scale instead
+                                 of the distance travelled), and every photon carries a first-order
+                                 estimate of its accumulated rounding error: per interaction the hit
+                                 point moves by (lateral offset + segment x direction error) / |cos
+                                 incidence| plus local rounding, the normal by the surface's
+                                 curvature (a cone wall's local profile curvature) times that, and
+                                 the new direction by twice the normal's error (reflection) or by
+                                 Snell's derivative (refraction); errors carried along add
+                                 linearly, fresh roundings in quadrature.  A photon whose estimate
+                                 exceeds 0.8 of a bound, or that ends in ERROR, is re-traced from its
+                                 inputs in FP64 (same random streams, same epsilon) by a second
+                                 launch on the same stream, whose result replaces the FP32 one.  The
+                                 queue holds n photons (n > 2^26: max(2^26, n / 8)); its scratch
+                                 comes from g's memory pool like the sort's.  Off with photon tracks
+                                 or the counting build */
 } robast_trace_opts;
 
 /* Work units counted when opts.work_units is set: ray-box tests, quadric root
  * solves, aspheric Newton iterations, aperture tests, cylinder tests, box
  * tests, Bezier wall tests, reflections, Fresnel/Snell evaluations, roughness
- * perturbations, Philox calls, frame transforms. */
-#define ROBAST_N_UNITS 12
+ * perturbations, Philox calls, frame transforms, compensated re-solves of a
+ * hit (FP32 trace). */
+#define ROBAST_N_UNITS 13
 
 /* Fill opts with the defaults. */
 void robast_trace_opts_default(robast_trace_opts* opts);
@@ -374,8 +380,8 @@ int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64
  *   ROBAST_OBJ_CENTROID_X / _Y: sum w q_x / W (resp. q_y) over DETECTED.
  * Parameters: ROBAST_N_PARAM per surface, [0..1] tilt about local x, y
  * (as robast_surface_desc.tilt), [2..9] A1..A8 (SAG mirrors), [10..15]
- * Bezier control points P0r, P0z, P1r, P1z, P2r, P2z (HEXCONE mirrors); a
- * path carries derivatives for the first such mirror it meets.  With several
+ * Bezier control points P0r, P0z, P1r, P1z, P2r, P2z (HEXCONE mirrors);
+ * every such mirror a path meets gets its derivatives.  With several
  * variants the objective is the sum of the variants' objectives, each over
  * its own photons (a batch of designs evaluated in one launch).
  */
@@ -405,13 +411,19 @@ int robast_param_layout(const robast_geom* g, robast_param_info* out);
  * Objective value (HOST *value) and, if d_params (device, FP64,
  * [robast_param_count]) is not NULL, d_params += d_obj * d value / d param.
  * Inputs as robast_trace_ex (device, the precision's element type).  One
- * pass: each photon's path is re-traced (nothing per bounce is stored) and
- * every surface it meets is re-intersected in forward-mode dual numbers;
- * sums over photons are FP64.  info (HOST, 8 doubles, may be NULL; totals
- * over variants): W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid,
- * N_detected, photons meeting a second differentiable mirror (untracked), N
- * (photons with an invalid variant index are skipped).  Synchronises the
- * stream; uses device scratch owned by g.
+ * launch, an adjoint trace: each photon's path is found (nearest hits in
+ * the trace precision, interactions re-solved in FP64), then the derivative
+ * of its objective terms with respect to the ray state is carried backwards
+ * through its interactions; the state before each interaction is
+ * recomputed from the photon's inputs (nothing per bounce is stored) and the
+ * interaction is evaluated in FP64 dual numbers seeded on that state and on
+ * the surface's parameters.  Sums over photons are 128-bit fixed point with
+ * integer atomics: repeated calls give identical bits.  info (HOST, 8
+ * doubles, may be NULL; totals over variants): W, sum w q_x, sum w q_y,
+ * sum w |q|^2, sum w sigmoid, N_detected, photons whose path had more than
+ * 64 interactions (untracked: no gradient), N (photons with an invalid
+ * variant index are skipped).  Synchronises the stream; uses device scratch
+ * owned by g.
  */
 int robast_trace_grad(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
                       uint64_t seed, int32_t objective, double tau, double d_obj, double* value, double* d_params,

@@ -92,9 +92,9 @@ class TraceOpts(ctypes.Structure):
 ACCURACY_REL_POS = 1e-6
 ACCURACY_DIR = 1e-5
 
-N_UNITS = 12
+N_UNITS = 13
 UNIT_NAMES = ("aabb", "sag", "newton", "aperture", "cylinder", "box", "hexwall", "reflect", "refract", "rough",
-              "philox", "rebase")
+              "philox", "rebase", "refine")
 
 
 _lib = None
@@ -515,12 +515,14 @@ def sources_create(geom: Geometry, groups) -> Sources:
 def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, precision: int = 32,
                   max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
                   eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0,
-                  accuracy=None):
+                  accuracy=None, work_units=None):
     """robast_trace_sources: trace every photon of the source groups in one launch.
 
     group_counts: CUDA int64 tensor [n_groups, 8], added to.  out: optional
     dict of per-photon output tensors (see alloc_outputs) for src.n_photons.
     accuracy as for trace() (FP32: the FP64 re-trace is a second launch).
+    work_units: optional CUDA int64 tensor [N_UNITS] (FP32 only): run the
+    counting build (block 128) and add its work units to it.
     """
     import torch
     lib = load()
@@ -535,7 +537,7 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
     if out is not None:
         tout = _trace_out(out)
     o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), None, first_photon_id, eps, block_size,
-              blocks_per_sm, refill_min=refill_min, accuracy=_accuracy(geom, precision, accuracy))
+              blocks_per_sm, units=work_units, refill_min=refill_min, accuracy=_accuracy(geom, precision, accuracy))
     _check(lib.robast_trace_sources(geom.handle, src.handle, ctypes.c_uint64(seed & (2**64 - 1)),
                                     ctypes.c_void_p(group_counts.data_ptr()),
                                     ctypes.byref(tout) if tout is not None else None, ctypes.byref(o)))
@@ -600,7 +602,12 @@ def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed
                                  ctypes.byref(val), ctypes.c_void_p(g.data_ptr()) if g is not None else None,
                                  ctypes.byref(o), info))
     keys = ("W", "sum_wqx", "sum_wqy", "sum_wq2", "sum_soft", "n_detected", "n_untracked", "n")
-    return val.value, g, dict(zip(keys, list(info)))
+    res = dict(zip(keys, list(info)))
+    if res["n_untracked"] > 0:
+        import warnings
+        warnings.warn(f"trace_grad: {int(res['n_untracked'])} photons had paths longer than the adjoint's "
+                      f"64-interaction record and contribute no gradient", RuntimeWarning)
+    return val.value, g, res
 
 
 def apply_params(scene, params):

@@ -10,31 +10,52 @@
 //    local x, y, W = sum w, qbar = sum w q / W); soft CE = (1/N) sum w
 //    sigmoid(m / tau), m = the exit-hexagon margin of the crossing of the
 //    photon's last segment with its variant's focal plane.
-// Per photon the kernel re-traces the path (nearest hits in the trace's
-// precision; per-bounce state recomputed, nothing stored) and re-intersects
-// each surface it meets in FP64 forward-mode dual numbers carrying the
-// derivatives with respect to the (at most 10) parameters of the one
-// differentiable surface the path meets.  The duals are FP64 in both forms:
-// derivatives of roots near tangency and the sums that combine them lose too
-// much in FP32 (a few 1e-3 relative on the concentrator), and there is one
-// dual intersection per bounce, so FP64 costs little here.  FP64 sums over photons give the value and the
-// gradient in one pass (MSR: sum w q.dq and sum w dq, combined with qbar
-// after the pass).
+//
+// Adjoint method, per photon:
+//  1. forward pass: the path's surfaces come from the trace's nearest-hit
+//     search (in the trace precision); each interaction is re-solved in FP64,
+//     which gives the state, the weight and the objective terms.  Only the
+//     surface ids and the refracting faces' reflect/refract decisions are
+//     kept, not the states;
+//  2. reverse sweep: the derivative of the photon's objective terms with
+//     respect to the ray state (point, direction) is carried backwards
+//     through the interactions.  For interaction k the state before it is
+//     recomputed by replaying interactions 0 .. k-1 from the photon's inputs
+//     (known surfaces, no search), and interaction k is evaluated once in
+//     forward-mode dual numbers seeded on that state (6 slots) and on the
+//     surface's parameters (up to 10 slots): the state Jacobian carries the
+//     adjoint one interaction back, the parameter Jacobian contracted with the
+//     adjoint is the photon's gradient for that surface.  Every
+//     differentiable surface the path meets gets its share, however many.
+// Sums over photons are 128-bit fixed point (two's complement, 64 fraction
+// bits) accumulated with integer atomics, so they do not depend on the order
+// in which photons finish: repeated runs give identical bits.
 #include "dual.cuh"
 #include "launch.h"
 
 namespace robast {
 
-constexpr int GNT = 10;
+constexpr int GW = 16;        // dual slots: 6 ray-state components, then 10 surface parameters
+constexpr int GMAXB = 64;     // interactions a path may have and still be differentiated
+using DX = Dn<double, GW>;
 
-template <typename T>
-using D = Dn<T, GNT>;
-using DD = Dn<double, GNT>;
-
-__device__ __forceinline__ V3<DD> lift(V3<double> a) { return mk(DD(a.x), DD(a.y), DD(a.z)); }
-template <typename T>
-__device__ __forceinline__ V3<T> value_of(const V3<DD>& a) {
-    return mk((T)a.x.v, (T)a.y.v, (T)a.z.v);
+// ------------------------------------------------------------ fixed point
+// a[0] = low word (fraction, 2^-64 units), a[1] = high word (integer part, two's complement).
+__device__ __forceinline__ void fx_add(unsigned long long* a, double c) {
+    if (!(c != 0.0) || !(fabs(c) < 9.0e18)) return;  // zero, NaN or beyond the format
+    const double m = fabs(c);
+    const double ip = floor(m);
+    unsigned long long hi = (unsigned long long)ip;
+    unsigned long long lo = (unsigned long long)((m - ip) * 18446744073709551616.0);  // exact fraction x 2^64
+    if (c < 0.0) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const unsigned long long old = atomicAdd(a, lo);
+    atomicAdd(a + 1, hi + (old + lo < old ? 1ull : 0ull));
+}
+__host__ __device__ __forceinline__ double fx_value(const unsigned long long* a) {
+    return (double)(long long)a[1] + (double)a[0] * 5.421010862427522e-20;  // 2^-64
 }
 
 // R(lambda), piecewise linear in the material's table (clamped)
@@ -49,34 +70,155 @@ __device__ __forceinline__ double refl_value(const double* M, double lam) {
     return R[i] + (R[i + 1] - R[i]) * ((lam - L[i]) / (L[i + 1] - L[i]));
 }
 
-// The dual-number record of surface sid: derivative slots only when it is the
-// tracked surface (SAG mirror: tilt x, y, A1..A8; HEXCONE mirror: P0r, P0z,
-// P1r, P1z, P2r, P2z).
-template <typename T>
-__device__ __forceinline__ void dual_record(const T* S, const T* G, int shape, bool tracked, D<T>* Sd) {
-    for (int k = 0; k < REC; ++k) Sd[k] = D<T>(S[k]);
-    if (!tracked) return;
-    if (shape == SHAPE_SAG) {
-        for (int j = 0; j < 9; ++j) {
-            Sd[F_R + j].d[0] = G[j];
-            Sd[F_R + j].d[1] = G[9 + j];
+// Record accessor of the gradient pass: FP64 record values, with derivative slots 6.. for the
+// parameters of a differentiable surface (mode 1, SAG mirror: tilt x, y -> slots 6, 7 through the
+// frame rows, A1..A8 -> slots 8..15; mode 2, HEXCONE mirror: control points P0r, P0z, P1r, P1z,
+// P2r, P2z -> slots 6..11 through the power-basis coefficients of the profile).
+struct GRec {
+    const double* S;
+    const double* G;  // d rows / d tilt_x (9), d rows / d tilt_y (9)
+    int mode;
+    __device__ __forceinline__ DX operator[](int k) const {
+        DX r(S[k]);
+        if (mode == 1) {
+            if (k >= F_R && k < F_R + 9) {
+                r.d[6] = G[k - F_R];
+                r.d[7] = G[9 + k - F_R];
+            } else if (k >= F_A && k < F_A + 8) {
+                r.d[8 + (k - F_A)] = 1.0;
+            }
+        } else if (mode == 2) {
+            switch (k) {  // r(u) = ra0 + ra1 u + ra2 u^2 with ra0 = P0r, ra1 = 2 (P1r - P0r), ra2 = P0r - 2 P1r + P2r
+                case F_C + 0: r.d[6] = 1.0; break;
+                case F_C + 1: r.d[6] = -2.0; r.d[8] = 2.0; break;
+                case F_C + 2: r.d[6] = 1.0; r.d[8] = -2.0; r.d[10] = 1.0; break;
+                case F_C + 3: r.d[7] = 1.0; break;
+                case F_C + 4: r.d[7] = -2.0; r.d[9] = 2.0; break;
+                case F_C + 5: r.d[7] = 1.0; r.d[9] = -2.0; r.d[11] = 1.0; break;
+                default: break;
+            }
         }
-        for (int i = 0; i < 8; ++i) Sd[F_A + i].d[2 + i] = T(1);
-    } else {
-        // power-basis coefficients of the Bezier profile in the control points
-        Sd[F_C + 0].d[0] = T(1);
-        Sd[F_C + 1].d[0] = T(-2);
-        Sd[F_C + 1].d[2] = T(2);
-        Sd[F_C + 2].d[0] = T(1);
-        Sd[F_C + 2].d[2] = T(-2);
-        Sd[F_C + 2].d[4] = T(1);
-        Sd[F_C + 3].d[1] = T(1);
-        Sd[F_C + 4].d[1] = T(-2);
-        Sd[F_C + 4].d[3] = T(2);
-        Sd[F_C + 5].d[1] = T(1);
-        Sd[F_C + 5].d[3] = T(-2);
-        Sd[F_C + 5].d[5] = T(1);
+        return r;
     }
+};
+
+template <typename N>
+__device__ __forceinline__ double val_of(const N& x);
+template <>
+__device__ __forceinline__ double val_of<double>(const double& x) { return x; }
+template <>
+__device__ __forceinline__ double val_of<DX>(const DX& x) { return x.v; }
+
+enum { GI_LOST = 0, GI_ON = 1, GI_DETECTED = 2, GI_OBSCURED = 3 };
+
+// One interaction of the frozen path on the known surface S (FP64 values; N = double, or DX to
+// carry derivatives): re-intersect, move the point, apply the surface's role.  At a refracting
+// face refl_in = 0 refracts, 1 reflects, 2 decides with the trace's Fresnel draw (the forward
+// pass), and *refl_out reports the choice.  Returns GI_LOST if the surface is not met any more,
+// GI_DETECTED (q = local x, y) or GI_OBSCURED at the end of the path, GI_ON otherwise; *seg is
+// the segment length and *front whether the ray met the front side.  The roughness tilt and the
+// Fresnel decision use the trace's draws in the trace precision T.
+template <typename T, typename N, typename SR>
+__device__ __forceinline__ int g_interact(const Tables& tb, SR S, int4 si, double lam, uint4 wd, int refl_in,
+                                          bool* refl_out, double eps, double ntol, V3<N>& p, V3<N>& d, N& qx, N& qy,
+                                          double* seg, bool* front_out) {
+    const int shape = si.x & 15, role = (si.x >> 4) & 15;
+    const V3<N> pl = to_local_pt<N>(S, p), dl = to_local_vec<N>(S, d);
+    LHit<N> h;
+    bool ok = false, err = false;
+    const N big = N(1.0e300);
+    if (shape == SHAPE_SAG) {
+        ok = hit_sag<false, N>(S, (si.x >> 8) & 15, (si.x >> 12) & 1, pl, dl, N(eps), big, N(ntol), h, err, nullptr);
+        if (ok) {
+            // one Newton step on the full sag: exact derivatives of the root in every parameter
+            V3<N> x = pl + h.t * dl;
+            N z, sl;
+            if (sag_slope<N>(S, x.x * x.x + x.y * x.y, &z, &sl)) {
+                const N fp = dl.z - sl * N(2) * (x.x * dl.x + x.y * dl.y);
+                h.t = h.t - (x.z - z) / fp;
+                x = pl + h.t * dl;
+                if (sag_slope<N>(S, x.x * x.x + x.y * x.y, &z, &sl)) {
+                    h.pl = x;
+                    h.nl = unit(mk(N(-2) * x.x * sl, N(-2) * x.y * sl, N(1)));
+                }
+            }
+        }
+    } else if (shape == SHAPE_HEXCONE) {
+        ok = hit_hexcone<N>(S, pl, dl, N(eps), big, h);
+    }
+    if (!ok || err) return GI_LOST;
+    *seg = val_of<N>(h.t);
+    p = p + h.t * d;
+    const V3<N> nw = unit(to_world_vec<N>(S, h.nl));
+    const bool front = val_of<N>(dot(d, nw)) < 0.0;
+    *front_out = front;
+    *refl_out = false;
+    if (role == ROLE_FOCAL) {
+        if (!front) return GI_OBSCURED;
+        qx = h.pl.x;
+        qy = h.pl.y;
+        return GI_DETECTED;
+    }
+    if (role == ROLE_MIRROR) {
+        if (!front) return GI_OBSCURED;
+        const double* M = tb.mats + (size_t)si.y * MAT_REC;
+        V3<N> nn = nw;
+        const T sigma = (T)M[33];
+        if (sigma > T(0)) {
+            const T u1 = unit_open<T>(wd.y), u2 = unit_open<T>(wd.z);
+            const T rad = t_sqrt(T(-2) * t_log(u1));
+            T sn, cs;
+            t_sincospi(T(2) * u2, &sn, &cs);
+            const N g1 = N((double)(sigma * rad * cs)), g2 = N((double)(sigma * rad * sn));
+            const N sgn = N(val_of<N>(nw.z) >= 0.0 ? 1.0 : -1.0);
+            const N aa = N(-1) / (sgn + nw.z);
+            const N bb = nw.x * nw.y * aa;
+            const V3<N> tt = mk(N(1) + sgn * nw.x * nw.x * aa, sgn * bb, N(0) - sgn * nw.x);
+            const V3<N> bv = mk(bb, sgn + nw.y * nw.y * aa, N(0) - nw.y);
+            nn = unit(nw + g1 * tt + g2 * bv);
+        }
+        d = unit(d - (N(2) * dot(d, nn)) * nn);
+        return GI_ON;
+    }
+    // refracting face: the recorded choice, reflect or Snell
+    const T na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, (T)lam);
+    const T nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, (T)lam);
+    const T n1 = front ? na : nb, n2 = front ? nb : na;
+    const V3<N> nf = front ? nw : N(-1) * nw;
+    const N ci = N(0) - dot(d, nf);
+    bool rv = refl_in == 1;
+    if (refl_in == 2) rv = unit_open<T>(wd.x) < fresnel(n1, n2, (T)val_of<N>(ci));
+    *refl_out = rv;
+    if (rv) {
+        d = unit(d - (N(2) * dot(d, nf)) * nf);
+    } else {
+        const N eta = N((double)n1 / (double)n2);
+        const N s2 = eta * eta * (N(1) - ci * ci);
+        d = unit(eta * d + (eta * ci - t_sqrt(N(1) - s2)) * nf);
+    }
+    return GI_ON;
+}
+
+// Signed margin of the exit hexagon (apothem - max_k |x . u_k|) where the ray crosses the plane
+// of the variant's exit surface; false if the ray does not head into it.
+template <typename N>
+__device__ __forceinline__ bool g_exit_margin(const double* S, V3<N> p, V3<N> d, N* m) {
+    const V3<N> pl = to_local_pt<N>(S, p), dl = to_local_vec<N>(S, d);
+    if (!(val_of<N>(dl.z) < 0.0)) return false;
+    const N t = N(0) - pl.z / dl.z;
+    const V3<N> x = pl + t * dl;
+    const N s60 = N(0.86602540378443864676);
+    const N c0 = x.x, c1 = N(0.5) * x.x + s60 * x.y, c2 = N(-0.5) * x.x + s60 * x.y;
+    N mx = t_abs(c0);
+    if (val_of<N>(t_abs(c1)) > val_of<N>(mx)) mx = t_abs(c1);
+    if (val_of<N>(t_abs(c2)) > val_of<N>(mx)) mx = t_abs(c2);
+    *m = N(S[F_AP]) - mx;
+    return true;
+}
+
+__device__ __forceinline__ bool g_differentiable(int4 si) {
+    const int shape = si.x & 15, role = (si.x >> 4) & 15;
+    return role == ROLE_MIRROR && (shape == SHAPE_SAG || shape == SHAPE_HEXCONE);
 }
 
 template <typename T>
@@ -84,9 +226,7 @@ __device__ __forceinline__ T sigmoid_t(T x) {
     return T(1) / (T(1) + (sizeof(T) == 4 ? (T)expf(-(float)x) : (T)exp(-(double)x)));
 }
 
-// Resident blocks of 128 threads per SM the register allocation must allow.  The dual state
-// spills at any cap; more warps hide the local-memory latency better.  Dish batch, 3.2e7
-// photons (FP32 form): 1 (255 registers) 720 ms, 2 721, 3 973, 4 637, 5 640, 6 642, 8 658.
+// Resident blocks of 128 threads per SM the register allocation must allow.
 #ifndef ROBAST_GRAD_MIN_BLOCKS
 #define ROBAST_GRAD_MIN_BLOCKS 4
 #endif
@@ -117,38 +257,27 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
     }
     const uint2 key = make_uint2((uint32_t)A.seed, (uint32_t)(A.seed >> 32));
     const long long n = A.n;
-    // per-variant sums held for the variant of this thread's current photons (photons of a
-    // variant are contiguous, so a thread changes variant rarely): W, sum w qx, sum w qy,
-    // sum w |q|^2, sum soft CE, n_det, untracked, n
-    double vs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int cur_var = -1;
-    auto flush = [&]() {
-        if (cur_var < 0) return;
-        for (int k = 0; k < 8; ++k)
-            if (vs[k] != 0.0) {
-                atomicAdd(A.vals + (size_t)cur_var * 8 + k, vs[k]);
-                vs[k] = 0.0;
-            }
-    };
-    DD Sd[REC];
+    const int nq = A.objective == 1 ? 1 : 2;  // objective terms per photon: (qx, qy) or the margin m
+    int ids[GMAXB];
     for (long long i = blockIdx.x * (long long)BLOCK + threadIdx.x; i < n; i += (long long)gridDim.x * BLOCK) {
-        V3<DD> p = lift(mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]));
-        V3<DD> d = lift(mk((double)A.d[i], (double)A.d[n + i], (double)A.d[2 * n + i]));
+        const V3<double> p0 = mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]);
+        const V3<double> d0 = mk((double)A.d[i], (double)A.d[n + i], (double)A.d[2 * n + i]);
         const T lam = A.lam[i];
         const int var = A.vop ? A.vop[i] : 0;
         const long long pid = A.first_id + i;
-        double w = 1.0;
-        int tracked = -1, status = 0, extra = 0;
-        DD qx(0), qy(0);
         if (var < 0 || var >= tb.n_var) continue;  // no variant to account it to
-        if (var != cur_var) {
-            flush();
-            cur_var = var;
-        }
+        unsigned long long* V = A.vals + (size_t)var * 16;
+        // ---- 1. forward pass
+        V3<double> p = p0, d = d0;
+        double w = 1.0, qx = 0.0, qy = 0.0;
+        unsigned long long refl = 0ull;  // refracting faces: bit k set = reflected at interaction k
+        int K = 0, status = 0, first_diff = -1;
+        bool untracked = false;
         for (int b = 0; status == 0; ++b) {
             Best<T> bst;
             bool overflow = false;
-            nearest_hit<false>(tb, var, value_of<T>(p), value_of<T>(d), A.eps, A.newton_tol, bst, overflow, nullptr);
+            nearest_hit<false>(tb, var, mk((T)p.x, (T)p.y, (T)p.z), mk((T)d.x, (T)d.y, (T)d.z), A.eps, A.newton_tol,
+                               bst, overflow, nullptr);
             if (overflow || bst.err) {
                 status = ST_ERROR;
                 break;
@@ -160,165 +289,216 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
             const int sid = bst.sid;
             const int4 si = tb.surf_i[sid];
             const int shape = si.x & 15, role = (si.x >> 4) & 15;
-            const bool diff = role == ROLE_MIRROR && (shape == SHAPE_SAG || shape == SHAPE_HEXCONE);
-            if (diff && tracked < 0) tracked = sid;
-            if (diff && sid != tracked) extra = 1;
             if (role == ROLE_OBSC || shape == SHAPE_CYL || shape == SHAPE_BOX) {
                 status = ST_OBSCURED;
                 break;
             }
-            const double* S = A.surf64 + (size_t)sid * REC;
-            dual_record<double>(S, A.grec + (size_t)sid * 18, shape, sid == tracked, Sd);
-            const V3<DD> pl = to_local_pt<DD>(Sd, p), dl = to_local_vec<DD>(Sd, d);
-            LHit<DD> h;
-            bool ok = false, err = false;
-            const DD big = DD(1.0e300);
-            if (shape == SHAPE_SAG) {
-                ok = hit_sag<false, DD>(Sd, (si.x >> 8) & 15, (si.x >> 12) & 1, pl, dl, DD((double)A.eps), big,
-                                        DD(A.newton_tol64), h, err, nullptr);
-                if (ok) {
-                    // one Newton step on the full sag: exact derivatives of the root in every parameter
-                    V3<DD> x = pl + h.t * dl;
-                    DD z, sl;
-                    if (sag_slope<DD>(Sd, x.x * x.x + x.y * x.y, &z, &sl)) {
-                        const DD fp = dl.z - sl * DD(2) * (x.x * dl.x + x.y * dl.y);
-                        h.t = h.t - (x.z - z) / fp;
-                        x = pl + h.t * dl;
-                        if (sag_slope<DD>(Sd, x.x * x.x + x.y * x.y, &z, &sl)) {
-                            h.pl = x;
-                            h.nl = unit(mk(DD(-2) * x.x * sl, DD(-2) * x.y * sl, DD(1)));
-                        }
-                    }
-                }
-            } else {
-                ok = hit_hexcone<DD>(Sd, pl, dl, DD((double)A.eps), big, h);
+            if (K >= GMAXB) {  // longer than the path record: not differentiated
+                untracked = true;
+                status = ST_ERROR;
+                break;
             }
-            if (!ok || err) {
+            const uint4 wd = philox4x32_10(
+                make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)b, 0u), key);
+            const double* S = A.surf64 + (size_t)sid * REC;
+            double seg = 0.0;
+            bool rev = false, front = true;
+            const int gi = g_interact<T, double>(tb, S, si, (double)lam, wd, 2, &rev, (double)A.eps, A.newton_tol64, p,
+                                                 d, qx, qy, &seg, &front);
+            if (gi == GI_LOST) {
                 status = ST_ERROR;  // the frozen path was lost
                 break;
             }
-            p = p + h.t * d;
-            const uint4 wd = philox4x32_10(
-                make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)b, 0u), key);
-            const V3<DD> nw = unit(to_world_vec<DD>(Sd, h.nl));
-            const bool front = dot(value_of<double>(d), value_of<double>(nw)) < 0.0;
-            if (role == ROLE_FOCAL) {
-                if (front) {
-                    status = ST_DETECTED;
-                    qx = h.pl.x;
-                    qy = h.pl.y;
-                } else {
-                    status = ST_OBSCURED;
-                }
+            if (role == ROLE_REFRACT) {
+                // bulk absorption of the segment through the medium the photon arrived in
+                const T len = abs_length<T>(tb.meds + (size_t)(front ? si.z : si.w) * MED_REC, lam);
+                if (len > T(0)) w *= exp(-seg / (double)len);
+            }
+            ids[K] = sid;
+            if (rev) refl |= 1ull << K;
+            if (first_diff < 0 && g_differentiable(si)) first_diff = K;
+            ++K;
+            if (gi == GI_DETECTED) {
+                status = ST_DETECTED;
                 break;
             }
-            if (role == ROLE_MIRROR) {
-                if (!front) {
-                    status = ST_OBSCURED;
-                    break;
-                }
-                const double* M = tb.mats + (size_t)si.y * MAT_REC;
-                w *= refl_value(M, (double)lam);
-                V3<DD> nn = nw;
-                const T sigma = (T)M[33];
-                if (sigma > T(0)) {
-                    // the trace's roughness draw, in its precision
-                    const T u1 = unit_open<T>(wd.y), u2 = unit_open<T>(wd.z);
-                    const T rad = t_sqrt(T(-2) * t_log(u1));
-                    T sn, cs;
-                    t_sincospi(T(2) * u2, &sn, &cs);
-                    const DD g1 = DD((double)(sigma * rad * cs)), g2 = DD((double)(sigma * rad * sn));
-                    const DD sgn = DD(nw.z.v >= 0.0 ? 1 : -1);
-                    const DD aa = DD(-1) / (sgn + nw.z);
-                    const DD bb = nw.x * nw.y * aa;
-                    const V3<DD> tt = mk(DD(1) + sgn * nw.x * nw.x * aa, sgn * bb, -sgn * nw.x);
-                    const V3<DD> bv = mk(bb, sgn + nw.y * nw.y * aa, -nw.y);
-                    nn = unit(nw + g1 * tt + g2 * bv);
-                }
-                d = unit(d - (DD(2) * dot(d, nn)) * nn);
-            } else {  // refracting face: bulk absorption weight, the trace's Fresnel decision, reflect or Snell
-                const T len = abs_length<T>(tb.meds + (size_t)(front ? si.z : si.w) * MED_REC, lam);
-                if (len > T(0)) w *= exp(-h.t.v / (double)len);
-                const T na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, lam);
-                const T nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, lam);
-                const T n1 = front ? na : nb, n2 = front ? nb : na;
-                const V3<DD> nf = front ? nw : DD(-1) * nw;
-                const DD ci = -dot(d, nf);
-                if (unit_open<T>(wd.x) < fresnel(n1, n2, (T)ci.v)) {
-                    d = unit(d - (DD(2) * dot(d, nf)) * nf);
-                } else {
-                    const DD eta = DD((double)n1 / (double)n2);
-                    const DD s2 = eta * eta * (DD(1) - ci * ci);
-                    d = unit(eta * d + (eta * ci - t_sqrt(DD(1) - s2)) * nf);
-                }
+            if (gi == GI_OBSCURED) {
+                status = ST_OBSCURED;
+                break;
             }
+            if (role == ROLE_MIRROR) w *= refl_value(tb.mats + (size_t)si.y * MAT_REC, (double)lam);
             if (b + 1 >= A.max_bounces) status = ST_MAXB;
         }
-        vs[7] += 1.0;
-        if (extra) vs[6] += 1.0;
-        const int base = tracked >= 0 ? (((tb.surf_i[tracked].x & 15) == SHAPE_SAG) ? 0 : 10) : 0;
-        const int nslot = tracked >= 0 ? (base == 0 ? 10 : 6) : 0;
-        double* acc = A.acc + (size_t)tracked * 16 * 3;
+        fx_add(V + 2 * 7, 1.0);
+        if (untracked) fx_add(V + 2 * 6, 1.0);
+        // ---- objective terms of this photon
+        bool contributes = false;
+        double coef = 0.0, m_val = 0.0;
+        const int ex = tb.variants[var].w;
         if (A.objective != 1) {
             if (status == ST_DETECTED) {
-                const double x = (double)qx.v, y = (double)qy.v;
-                vs[0] += w;
-                vs[1] += w * x;
-                vs[2] += w * y;
-                vs[3] += w * (x * x + y * y);
-                vs[5] += 1.0;
-                for (int k = 0; k < nslot; ++k) {
-                    const double gx = (double)qx.d[k], gy = (double)qy.d[k];
-                    atomicAdd(acc + (base + k) * 3 + 0, w * (x * gx + y * gy));
-                    atomicAdd(acc + (base + k) * 3 + 1, w * gx);
-                    atomicAdd(acc + (base + k) * 3 + 2, w * gy);
-                }
+                contributes = true;
+                fx_add(V + 2 * 0, w);
+                fx_add(V + 2 * 1, w * qx);
+                fx_add(V + 2 * 2, w * qy);
+                fx_add(V + 2 * 3, w * (qx * qx + qy * qy));
+                fx_add(V + 2 * 5, 1.0);
             }
-        } else if (status != ST_OBSCURED && status != ST_ERROR && status != ST_MAXB) {
-            const int ex = tb.variants[var].w;
-            if (ex >= 0) {
-                const double* S = A.surf64 + (size_t)ex * REC;
-                dual_record<double>(S, A.grec + (size_t)ex * 18, SHAPE_SAG, false, Sd);
-                const V3<DD> pl = to_local_pt<DD>(Sd, p), dl = to_local_vec<DD>(Sd, d);
-                if (dl.z.v < T(0)) {
-                    const DD t = -pl.z / dl.z;
-                    const V3<DD> x = pl + t * dl;
-                    const DD s60 = DD(0.86602540378443864676);
-                    const DD c0 = x.x, c1 = DD(0.5) * x.x + s60 * x.y, c2 = DD(-0.5) * x.x + s60 * x.y;
-                    DD mx = t_abs(c0);
-                    if (t_abs(c1).v > mx.v) mx = t_abs(c1);
-                    if (t_abs(c2).v > mx.v) mx = t_abs(c2);
-                    const DD m = DD(S[F_AP]) - mx;
-                    const double sg = 1.0 / (1.0 + exp(-m.v / A.tau));
-                    vs[4] += w * sg;
-                    const double coef = w * sg * (1.0 - sg) / A.tau;
-                    for (int k = 0; k < nslot; ++k) atomicAdd(acc + (base + k) * 3, coef * (double)m.d[k]);
-                }
+        } else if (status != ST_OBSCURED && status != ST_ERROR && status != ST_MAXB && ex >= 0) {
+            double m;
+            if (g_exit_margin<double>(A.surf64 + (size_t)ex * REC, p, d, &m)) {
+                const double sg = 1.0 / (1.0 + exp(-m / A.tau));
+                fx_add(V + 2 * 4, w * sg);
+                coef = w * sg * (1.0 - sg) / A.tau;
+                m_val = m;
+                contributes = true;
             }
         }
+        (void)m_val;
+        if (!contributes || first_diff < 0) continue;
+        // ---- 2. reverse sweep
+        double a[2][6];
+        int k;  // the adjoint is with respect to the state before interaction k + 1 (after k)
+        auto replay = [&](int upto, V3<double>& pr, V3<double>& dr) {
+            // the state before interaction `upto`, from the photon's inputs
+            pr = p0;
+            dr = d0;
+            for (int j = 0; j < upto; ++j) {
+                const uint4 wd = philox4x32_10(
+                    make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)j, 0u), key);
+                double qa, qb, sg;
+                bool rv, fr;
+                g_interact<T, double>(tb, A.surf64 + (size_t)ids[j] * REC, tb.surf_i[ids[j]], (double)lam, wd,
+                                      (int)((refl >> j) & 1ull), &rv, (double)A.eps, A.newton_tol64, pr, dr, qa, qb, &sg,
+                                      &fr);
+            }
+        };
+        auto seed_state = [](V3<double> pv, V3<double> dv, V3<DX>& ps, V3<DX>& ds) {
+            ps = mk(DX(pv.x), DX(pv.y), DX(pv.z));
+            ds = mk(DX(dv.x), DX(dv.y), DX(dv.z));
+            ps.x.d[0] = 1.0;
+            ps.y.d[1] = 1.0;
+            ps.z.d[2] = 1.0;
+            ds.x.d[3] = 1.0;
+            ds.y.d[4] = 1.0;
+            ds.z.d[5] = 1.0;
+        };
+        if (A.objective != 1) {
+            // terminal adjoint: d(qx, qy) / d(state before the detecting interaction K - 1)
+            V3<double> pr, dr;
+            replay(K - 1, pr, dr);
+            V3<DX> ps, ds;
+            seed_state(pr, dr, ps, ds);
+            const uint4 wd = philox4x32_10(
+                make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)(K - 1), 0u), key);
+            DX qa(0.0), qb(0.0);
+            double sg;
+            bool rv, fr;
+            const GRec R{A.surf64 + (size_t)ids[K - 1] * REC, A.grec + (size_t)ids[K - 1] * 18, 0};
+            g_interact<T, DX>(tb, R, tb.surf_i[ids[K - 1]], (double)lam, wd, 0, &rv, (double)A.eps, A.newton_tol64, ps,
+                              ds, qa, qb, &sg, &fr);
+            for (int j = 0; j < 6; ++j) {
+                a[0][j] = qa.d[j];
+                a[1][j] = qb.d[j];
+            }
+            k = K - 2;
+        } else {
+            // terminal adjoint: d m / d(state after the last interaction)
+            V3<DX> ps, ds;
+            seed_state(p, d, ps, ds);
+            DX m(0.0);
+            g_exit_margin<DX>(A.surf64 + (size_t)ex * REC, ps, ds, &m);
+            for (int j = 0; j < 6; ++j) a[0][j] = m.d[j];
+            k = K - 1;
+        }
+        // per-surface gradient of this photon's terms, flushed when the surface changes
+        int cur = -1;
+        double gs[2][10];
+        auto flush = [&]() {
+            if (cur < 0) return;
+            const bool sag = (tb.surf_i[cur].x & 15) == SHAPE_SAG;
+            const int base = sag ? 0 : 10, np = sag ? 10 : 6;
+            unsigned long long* acc = A.acc + (size_t)cur * GRAD_SLOTS;
+            for (int m = 0; m < np; ++m) {
+                unsigned long long* c = acc + (size_t)(base + m) * 6;
+                if (A.objective != 1) {
+                    fx_add(c + 0, w * (qx * gs[0][m] + qy * gs[1][m]));
+                    fx_add(c + 2, w * gs[0][m]);
+                    fx_add(c + 4, w * gs[1][m]);
+                } else {
+                    fx_add(c + 0, coef * gs[0][m]);
+                }
+            }
+        };
+        for (; k >= first_diff; --k) {
+            V3<double> pr, dr;
+            replay(k, pr, dr);
+            V3<DX> ps, ds;
+            seed_state(pr, dr, ps, ds);
+            const int sid = ids[k];
+            const int4 si = tb.surf_i[sid];
+            const int mode = g_differentiable(si) ? ((si.x & 15) == SHAPE_SAG ? 1 : 2) : 0;
+            const GRec R{A.surf64 + (size_t)sid * REC, A.grec + (size_t)sid * 18, mode};
+            const uint4 wd = philox4x32_10(
+                make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)k, 0u), key);
+            DX qa(0.0), qb(0.0);
+            double sg;
+            bool rv, fr;
+            g_interact<T, DX>(tb, R, si, (double)lam, wd, (int)((refl >> k) & 1ull), &rv, (double)A.eps,
+                              A.newton_tol64, ps, ds, qa, qb, &sg, &fr);
+            const DX* out[6] = {&ps.x, &ps.y, &ps.z, &ds.x, &ds.y, &ds.z};
+            if (mode) {
+                if (sid != cur) {
+                    flush();
+                    cur = sid;
+                    for (int c = 0; c < 2; ++c)
+                        for (int m = 0; m < 10; ++m) gs[c][m] = 0.0;
+                }
+                const int np = mode == 1 ? 10 : 6;
+                for (int c = 0; c < nq; ++c)
+                    for (int m = 0; m < np; ++m) {
+                        double acc = 0.0;
+                        for (int j = 0; j < 6; ++j) acc += a[c][j] * out[j]->d[6 + m];
+                        gs[c][m] += acc;
+                    }
+            }
+            double na[2][6];
+            for (int c = 0; c < nq; ++c)
+                for (int j = 0; j < 6; ++j) {
+                    double acc = 0.0;
+                    for (int i2 = 0; i2 < 6; ++i2) acc += a[c][i2] * out[i2]->d[j];
+                    na[c][j] = acc;
+                }
+            for (int c = 0; c < nq; ++c)
+                for (int j = 0; j < 6; ++j) a[c][j] = na[c][j];
+        }
+        flush();
     }
-    flush();
 }
 
-// d_params[p] += d_obj * gradient, from the sums of the pass (the sums of the
+// d_params[p] += d_obj * gradient, from the fixed-point sums of the pass (the sums of the
 // variant the parameter's surface belongs to)
-__global__ void grad_finish(const double* acc, const double* vals_all, const int* surf_var, int n_params,
-                            int objective, double d_obj, double* out) {
+__global__ void grad_finish(const unsigned long long* acc, const unsigned long long* vals_all, const int* surf_var,
+                            int n_params, int objective, double d_obj, double* out) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_params) return;
-    const double* vals = vals_all + (size_t)surf_var[p / 16] * 8;
-    const double W = vals[0];
+    const unsigned long long* V = vals_all + (size_t)surf_var[p / 16] * 16;
+    const unsigned long long* c = acc + (size_t)p * 6;
+    const double W = fx_value(V + 0);
     double g = 0.0;
     if (objective == 1) {
-        g = vals[7] > 0 ? acc[3 * p] / vals[7] : 0.0;
+        const double N = fx_value(V + 14);
+        g = N > 0 ? fx_value(c) / N : 0.0;
     } else if (W > 0) {
-        const double qx = vals[1] / W, qy = vals[2] / W;
-        if (objective == 0) g = 2.0 / W * (acc[3 * p] - qx * acc[3 * p + 1] - qy * acc[3 * p + 2]);
-        if (objective == 2) g = acc[3 * p + 1] / W;
-        if (objective == 3) g = acc[3 * p + 2] / W;
+        const double qx = fx_value(V + 2) / W, qy = fx_value(V + 4) / W;
+        if (objective == 0) g = 2.0 / W * (fx_value(c) - qx * fx_value(c + 2) - qy * fx_value(c + 4));
+        if (objective == 2) g = fx_value(c + 2) / W;
+        if (objective == 3) g = fx_value(c + 4) / W;
     }
     out[p] += d_obj * g;
 }
+
+double grad_fx_value(const unsigned long long* a) { return fx_value(a); }
 
 template <typename T, int BLOCK, bool STAGED>
 static cudaError_t launch_grad_one(const GradArgs<T>& a, int grid, size_t smem, cudaStream_t s) {
@@ -338,8 +518,8 @@ cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cu
     return a.stage ? launch_grad_one<double, 128, true>(a, grid, smem, s)
                    : launch_grad_one<double, 128, false>(a, grid, 0, s);
 }
-cudaError_t launch_grad_finish(const double* acc, const double* vals, const int* surf_var, int n_params, int objective,
-                               double d_obj, double* out, cudaStream_t s) {
+cudaError_t launch_grad_finish(const unsigned long long* acc, const unsigned long long* vals, const int* surf_var,
+                               int n_params, int objective, double d_obj, double* out, cudaStream_t s) {
     grad_finish<<<(n_params + 255) / 256, 256, 0, s>>>(acc, vals, surf_var, n_params, objective, d_obj, out);
     return cudaGetLastError();
 }

@@ -12,7 +12,9 @@ namespace robast {
 int trace_blocks_per_sm_f32(int block, size_t smem, bool src);
 int trace_blocks_per_sm_f64(int block, size_t smem, bool src);
 
-// Gradient pass (grad.cu): frozen-path objective sums and per-parameter sums.
+// Gradient pass (grad.cu): frozen-path objective sums and per-parameter sums, 128-bit fixed
+// point (two u64 words each: fraction, integer part).
+constexpr int GRAD_SLOTS = 16 * 3 * 2;  // u64 words per surface: 16 parameters x 3 sums x 2
 template <typename T>
 struct GradArgs {
     Tables tab;              // precision T: the nearest-hit search
@@ -32,13 +34,15 @@ struct GradArgs {
     double newton_tol64;  // Newton tolerance of the FP64 dual re-intersection
     int objective;
     double tau;
-    double* acc;   // [n_surf * 16 * 3]
-    double* vals;  // [n_variants * 8]
+    unsigned long long* acc;   // [n_surf * GRAD_SLOTS]
+    unsigned long long* vals;  // [n_variants * 8 * 2]
 };
 cudaError_t launch_grad_f32(const GradArgs<float>& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_grad_finish(const double* acc, const double* vals, const int* surf_var, int n_params, int objective,
-                               double d_obj, double* out, cudaStream_t s);
+cudaError_t launch_grad_finish(const unsigned long long* acc, const unsigned long long* vals, const int* surf_var,
+                               int n_params, int objective, double d_obj, double* out, cudaStream_t s);
+// value of a 128-bit fixed-point sum
+double grad_fx_value(const unsigned long long* a);
 
 // Coherent processing order (order.cu): scratch bytes for n photons, and the
 // permutation (work index -> photon index) built in `scratch` on stream s.

@@ -41,9 +41,10 @@ enum { ST_DETECTED = 1, ST_ABSORBED = 2, ST_OBSCURED = 3, ST_ESCAPED = 4, ST_MAX
 //   HEXCONE: [12..14] r power-basis coefficients, [15..17] z coefficients
 //   aperture [22..27]: CIRCLE r^2; ANNULUS rmin^2 rmax^2; SECTOR rmin^2 rmax^2 e0x e0y e1x e1y;
 //                      HEX apothem; RECT hx hy
-//   [29] bound on the surface's principal curvatures over its aperture, [30] rounding of its
-//        root along the ray in ulps per unit length (the FP32 error estimate)
-enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_KA = 30, REC = 32 };
+//   [29] bound on the surface's principal curvatures over its aperture (the FP32 error estimate)
+//   [30..32] FP32 record: the origin's rounding error (origin - float(origin)), so that the
+//        origin is the pair [0..2] + [30..32]; FP64 record: 0
+enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_OL = 30, REC = 36 };
 // Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12, y = material,
 // z = medium front, w = medium back.
 // Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
@@ -68,7 +69,8 @@ enum {
     U_ROUGH = 9,     // roughness perturbations (Box-Muller + basis)
     U_PHILOX = 10,   // Philox4x32-10 calls (integer pipe)
     U_REBASE = 11,   // world -> local frame transforms
-    U_N = 12
+    U_REFINE = 12,   // compensated re-solves of the hit (FP32 form)
+    U_N = 13
 };
 #define CNT(k)                         \
     do {                               \
@@ -285,39 +287,42 @@ __device__ __forceinline__ bool gen_source(const SrcGroup& G, long long pid, uin
 }
 
 // ------------------------------------------------------ frame transforms
-template <typename T>
-__device__ __forceinline__ V3<T> to_local_pt(const T* S, V3<T> p) {
+// The record S is any indexable source of record values: a pointer into the surface table, or
+// (gradient pass) an accessor whose values carry derivatives.
+template <typename T, typename SR>
+__device__ __forceinline__ V3<T> to_local_pt(SR S, V3<T> p) {
     const T qx = p.x - S[F_O], qy = p.y - S[F_O + 1], qz = p.z - S[F_O + 2];
     return mk(S[F_R + 0] * qx + S[F_R + 1] * qy + S[F_R + 2] * qz, S[F_R + 3] * qx + S[F_R + 4] * qy + S[F_R + 5] * qz,
               S[F_R + 6] * qx + S[F_R + 7] * qy + S[F_R + 8] * qz);
 }
-template <typename T>
-__device__ __forceinline__ V3<T> to_local_vec(const T* S, V3<T> q) {
+template <typename T, typename SR>
+__device__ __forceinline__ V3<T> to_local_vec(SR S, V3<T> q) {
     return mk(S[F_R + 0] * q.x + S[F_R + 1] * q.y + S[F_R + 2] * q.z, S[F_R + 3] * q.x + S[F_R + 4] * q.y + S[F_R + 5] * q.z,
               S[F_R + 6] * q.x + S[F_R + 7] * q.y + S[F_R + 8] * q.z);
 }
-template <typename T>
-__device__ __forceinline__ V3<T> to_world_vec(const T* S, V3<T> q) {
+template <typename T, typename SR>
+__device__ __forceinline__ V3<T> to_world_vec(SR S, V3<T> q) {
     return mk(S[F_R + 0] * q.x + S[F_R + 3] * q.y + S[F_R + 6] * q.z, S[F_R + 1] * q.x + S[F_R + 4] * q.y + S[F_R + 7] * q.z,
               S[F_R + 2] * q.x + S[F_R + 5] * q.y + S[F_R + 8] * q.z);
 }
 
 // ------------------------------------------------------------- apertures
-template <typename T>
-__device__ __forceinline__ bool aperture_inside(const T* S, int ap, T x, T y) {
-    const T* A = S + F_AP;
+template <typename T, typename SR>
+__device__ __forceinline__ bool aperture_inside(SR S, int ap, T x, T y) {
     const T r2 = x * x + y * y;
     switch (ap) {
         case AP_NONE: return true;
-        case AP_CIRCLE: return r2 <= A[0];
-        case AP_ANNULUS: return r2 >= A[0] && r2 <= A[1];
-        case AP_SECTOR: return r2 >= A[0] && r2 <= A[1] && (A[2] * y - A[3] * x) >= T(0) && (x * A[5] - y * A[4]) >= T(0);
+        case AP_CIRCLE: return r2 <= T(S[F_AP]);
+        case AP_ANNULUS: return r2 >= T(S[F_AP]) && r2 <= T(S[F_AP + 1]);
+        case AP_SECTOR:
+            return r2 >= T(S[F_AP]) && r2 <= T(S[F_AP + 1]) && (T(S[F_AP + 2]) * y - T(S[F_AP + 3]) * x) >= T(0) &&
+                   (x * T(S[F_AP + 5]) - y * T(S[F_AP + 4])) >= T(0);
         case AP_HEX: {
             const T s60 = T(0.86602540378443864676);
             const T m = t_max(t_abs(x), t_max(t_abs(T(0.5) * x + s60 * y), t_abs(-T(0.5) * x + s60 * y)));
-            return m <= A[0];
+            return m <= T(S[F_AP]);
         }
-        case AP_RECT: return t_abs(x) <= A[0] && t_abs(y) <= A[1];
+        case AP_RECT: return t_abs(x) <= T(S[F_AP]) && t_abs(y) <= T(S[F_AP + 1]);
     }
     return false;
 }
@@ -331,17 +336,17 @@ struct LHit {
 };
 
 // sag z(rho) and dz/drho of the even asphere; false outside the conic's domain
-template <typename T>
-__device__ __forceinline__ bool sag_slope(const T* S, T rho, T* z, T* slope) {
+template <typename T, typename SR>
+__device__ __forceinline__ bool sag_slope(SR S, T rho, T* z, T* slope) {
     const T c = S[F_C];
-    const T arg = T(1) - S[F_K1] * c * c * rho;
+    const T arg = T(1) - T(S[F_K1]) * c * c * rho;
     if (arg < T(0)) return false;
     const T sq = t_sqrt(arg);
     T poly = T(0), dpoly = T(0);
 #pragma unroll
     for (int i = 8; i >= 1; --i) {  // Horner in rho
-        poly = poly * rho + S[F_A + i - 1];
-        dpoly = dpoly * rho + T(i) * S[F_A + i - 1];
+        poly = poly * rho + T(S[F_A + i - 1]);
+        dpoly = dpoly * rho + T(i) * T(S[F_A + i - 1]);
     }
     *z = c * rho / (T(1) + sq) + poly * rho;
     *slope = c / (T(2) * sq) + dpoly;
@@ -376,8 +381,8 @@ __device__ __forceinline__ bool newton_step_fp64(const T* S, V3<T> p, V3<T> d, T
 // Ray vs SAG surface (local frame).  Quadric F = c (x^2 + y^2 + (1+k) z^2) - 2z,
 // sag branch (1+k) c z <= 1; both roots in ascending order, first valid one.
 // Aspheres: Newton from the first on-branch root beyond eps.
-template <bool C, typename T>
-__device__ __forceinline__ bool hit_sag(const T* S, int ap, bool asph, V3<T> p, V3<T> d, T eps, T tmax, T tol, LHit<T>& h,
+template <bool C, typename T, typename SR>
+__device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> d, T eps, T tmax, T tol, LHit<T>& h,
                                         bool& err, unsigned* cnt) {
     CNT(U_SAG);
     const T c = S[F_C], k1 = S[F_K1];
@@ -409,7 +414,7 @@ __device__ __forceinline__ bool hit_sag(const T* S, int ap, bool asph, V3<T> p, 
         if (k1 * c * q.z > T(1)) continue;
         if (asph) {
             if (t <= eps) continue;
-            if (q.x * q.x + q.y * q.y > S[F_RB2]) return false;
+            if (q.x * q.x + q.y * q.y > T(S[F_RB2])) return false;
             bool conv = false;
             T slope = T(0);
             for (int it = 0; it < 32; ++it) {
@@ -588,8 +593,8 @@ __device__ __forceinline__ void hex_dir(int j, T& c, T& s) {
     }
 }
 
-template <typename T>
-__device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
+template <typename T, typename SR>
+__device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
     const T ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
     const T za0 = S[F_C + 3], za1 = S[F_C + 4], za2 = S[F_C + 5];
     // wall j's outward direction (cos, sin of j x 60 degrees) from constant memory: no
@@ -696,6 +701,165 @@ __device__ __forceinline__ bool hit_hexcone(const T* S, V3<T> p, V3<T> d, T eps,
     h.u = bu;
     h.t = best;
     h.nl = unit(mk(-Zp * cb, -Zp * sb, Rp));
+    return true;
+}
+
+// ------------------------------------------------ compensated FP32 hit refinement
+// The FP32 trace keeps each photon's position as an unevaluated pair hi + lo (per component,
+// |lo| <= ulp(hi) / 2).  The nearest-hit search runs on hi alone; the surface it picks is then
+// re-solved from the approximate hit point itself, whose local coordinates are small, so the
+// hit is found to a few ulps of the local scale instead of a few ulps of the distance the
+// photon travelled.
+__device__ __forceinline__ void pair_advance(float& hi, float& lo, float t, float d) {
+    const float pr = __fmul_rn(t, d);
+    const float pe = __fmaf_rn(t, d, -pr);  // exact product = pr + pe
+    const float s = __fadd_rn(hi, pr);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(pr, bp));
+    const float l = __fadd_rn(lo, __fadd_rn(e, pe));
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
+// Hit of the ray (P + t d), P = the pair (ph, pl) at (or very near) surface S, re-solved in
+// S's local frame for the small parameter dt.  Returns false where no root is found near the
+// point (a grazing ray the FP32 search only just met); the caller then keeps the search's hit.
+// kap: the curvature bound to use at this hit (the profile's local curvature for a cone wall,
+// else the surface's bound).
+__device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph, V3<float> ph, V3<float> plo,
+                                           V3<float> d, float& dt, V3<float>& xl, V3<float>& nl, float& kap) {
+    kap = S[F_KAP];
+    // local origin of the ray: (ph - O_hi) + (plo - O_lo), exact to the rounding of small numbers
+    const float qx = __fadd_rn(__fsub_rn(ph.x, S[F_O]), __fsub_rn(plo.x, S[F_OL]));
+    const float qy = __fadd_rn(__fsub_rn(ph.y, S[F_O + 1]), __fsub_rn(plo.y, S[F_OL + 1]));
+    const float qz = __fadd_rn(__fsub_rn(ph.z, S[F_O + 2]), __fsub_rn(plo.z, S[F_OL + 2]));
+    const V3<float> p = to_local_vec(S, mk(qx, qy, qz)), dl = to_local_vec(S, d);
+    float t = 0.0f;
+    switch (shape) {
+        case SHAPE_SAG: {
+            const float c = S[F_C], k1 = S[F_K1];
+            if (!asph) {
+                // the quadric's root nearest 0: g / q in the stable form
+                const float a = c * (dl.x * dl.x + dl.y * dl.y + k1 * dl.z * dl.z);
+                const float b = c * (p.x * dl.x + p.y * dl.y + k1 * p.z * dl.z) - dl.z;
+                const float g = c * (p.x * p.x + p.y * p.y + k1 * p.z * p.z) - 2.0f * p.z;
+                const float disc = b * b - a * g;
+                if (disc < 0.0f) return false;
+                const float q = -(b + copysignf(sqrtf(disc), b));
+                if (q == 0.0f) return false;
+                t = g / q;
+                const V3<float> x = p + t * dl;
+                xl = x;
+                nl = unit(mk(-c * x.x, -c * x.y, 1.0f - c * k1 * x.z));
+            } else {
+                float slope = 0.0f;
+                for (int it = 0; it < 2; ++it) {  // Newton from the point: quadratic convergence
+                    const V3<float> x = p + t * dl;
+                    float z;
+                    if (!sag_slope(S, x.x * x.x + x.y * x.y, &z, &slope)) return false;
+                    const float fp = dl.z - slope * 2.0f * (x.x * dl.x + x.y * dl.y);
+                    if (fp == 0.0f) return false;
+                    t -= (x.z - z) / fp;
+                }
+                const V3<float> x = p + t * dl;
+                float z;
+                if (!sag_slope(S, x.x * x.x + x.y * x.y, &z, &slope)) return false;
+                xl = x;
+                nl = unit(mk(-2.0f * x.x * slope, -2.0f * x.y * slope, 1.0f));
+            }
+            break;
+        }
+        case SHAPE_CYL: {
+            const float rad = S[F_C];
+            const float a = dl.x * dl.x + dl.y * dl.y;
+            const float b = p.x * dl.x + p.y * dl.y;
+            const float g = (p.x - rad) * (p.x + rad) + p.y * p.y;  // |p_xy|^2 - r^2
+            const float disc = b * b - a * g;
+            if (disc < 0.0f) return false;
+            const float q = -(b + copysignf(sqrtf(disc), b));
+            if (q == 0.0f) return false;
+            t = g / q;
+            const V3<float> x = p + t * dl;
+            xl = x;
+            nl = unit(mk(x.x, x.y, 0.0f));
+            break;
+        }
+        case SHAPE_BOX: {
+            // the face the point lies on: the axis where it is furthest out relative to the half extent
+            const float r0 = fabsf(p.x) / S[F_C], r1 = fabsf(p.y) / S[F_C + 1], r2 = fabsf(p.z) / S[F_C + 2];
+            const int ax = r0 >= r1 ? (r0 >= r2 ? 0 : 2) : (r1 >= r2 ? 1 : 2);
+            const float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z), dc = ax == 0 ? dl.x : (ax == 1 ? dl.y : dl.z);
+            if (dc == 0.0f) return false;
+            const float sg = pc >= 0.0f ? 1.0f : -1.0f;
+            t = (sg * S[F_C + ax] - pc) / dc;
+            xl = p + t * dl;
+            nl = mk(ax == 0 ? sg : 0.0f, ax == 1 ? sg : 0.0f, ax == 2 ? sg : 0.0f);
+            break;
+        }
+        case SHAPE_HEXCONE: {
+            // the wall whose wedge holds the point, then the profile root nearest the point
+            int j = 0;
+            float best = -3.0e38f;
+            for (int m = 0; m < 6; ++m) {
+                float cm, sm;
+                hex_dir(m, cm, sm);
+                const float v = p.x * cm + p.y * sm;
+                if (v > best) {
+                    best = v;
+                    j = m;
+                }
+            }
+            float cj, sj;
+            hex_dir(j, cj, sj);
+            const float ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
+            const float za0 = S[F_C + 3], za1 = S[F_C + 4], za2 = S[F_C + 5];
+            const float q0 = best, dq = dl.x * cj + dl.y * sj;
+            const float den = dq * dq + dl.z * dl.z;
+            if (den == 0.0f) return false;
+            const float A = dl.z * ra2 - dq * za2, B = dl.z * ra1 - dq * za1;
+            const float C = dl.z * (ra0 - q0) - dq * (za0 - p.z);
+            // candidate roots in u; keep the one whose ray parameter is nearest 0
+            float us[2];
+            int nu = 0;
+            if (A == 0.0f) {
+                if (B != 0.0f) us[nu++] = -C / B;
+            } else {
+                const float disc = B * B - 4.0f * A * C;
+                if (disc < 0.0f) return false;
+                const float q = -0.5f * (B + copysignf(sqrtf(disc), B));
+                if (q != 0.0f) {
+                    us[nu++] = q / A;
+                    us[nu++] = C / q;
+                }
+            }
+            bool got = false;
+            float bu = 0.0f;
+            for (int i = 0; i < nu; ++i) {
+                float u = us[i];
+                const float gp = 2.0f * A * u + B;
+                if (gp != 0.0f) u -= ((A * u + B) * u + C) / gp;
+                const float R = ra0 + u * (ra1 + u * ra2), Z = za0 + u * (za1 + u * za2);
+                const float tt = ((R - q0) * dq + (Z - p.z) * dl.z) / den;
+                if (!got || fabsf(tt) < fabsf(t)) {
+                    got = true;
+                    t = tt;
+                    bu = u;
+                }
+            }
+            if (!got) return false;
+            xl = p + t * dl;
+            const float Rp = ra1 + 2.0f * ra2 * bu, Zp = za1 + 2.0f * za2 * bu;
+            nl = unit(mk(-Zp * cj, -Zp * sj, Rp));
+            // the wall is straight across the profile plane: its one curvature is the profile's,
+            // |r' z'' - z' r''| / (r'^2 + z'^2)^(3/2) at the hit, with a margin for the hit's error
+            const float q2 = Rp * Rp + Zp * Zp;
+            kap = 1.2f * fabsf(Rp * 2.0f * za2 - Zp * 2.0f * ra2) / (q2 * sqrtf(q2));
+            break;
+        }
+        default: return false;
+    }
+    if (!(fabsf(t) < 3.0e38f)) return false;
+    dt = t;
     return true;
 }
 
@@ -941,6 +1105,7 @@ struct Photon {
     bool bad;  // source mode: no point generated
     unsigned long long thr;
     // FP32 form: first-order estimate of the accumulated rounding error (see trace_kernel)
+    V3<T> plo; // FP32 form: low parts of the position pair (p, plo)
     float ep;  // lateral offset of the current ray (m)
     float ed;  // direction (rad)
     float eh;  // last interaction point (m)
@@ -966,13 +1131,14 @@ struct TraceBounds {
     static constexpr int min_blocks = sizeof(T) == 4 && (mb * 128) / BLOCK > 0 ? (mb * 128) / BLOCK : 1;
 };
 
-// Rounding units of the FP32 error estimate, per interaction: the frame transform puts KT ulps
-// of the coordinate scale on the hit point (across and along the ray), the root the surface's
-// own ulps per unit of the segment along it (record slot F_KA), the new ray's origin carries KP
-// ulps of its coordinates, the normal KN ulps and the new direction KD ulps (reflection or
-// refraction and normalisation).
+// Rounding units of the FP32 error estimate, per interaction, in ulps of the hit's coordinate
+// scale (the local scale of a refined hit, else the world coordinates plus the segment): KT
+// for the frame transform (across and along the ray), KA for the root along the ray (KW for an
+// unrefined hit, whose root was solved from far away), KP for the new ray's origin; KN ulps on
+// the normal and KD on the new direction (reflection or refraction and normalisation).
 constexpr float EST_U = 5.9604645e-08f;  // 2^-24
-constexpr float EST_KT = 1.0f * EST_U, EST_KP = 0.5f * EST_U, EST_KN = 1.0f * EST_U, EST_KD = 1.5f * EST_U;
+constexpr float EST_KT = 1.0f * EST_U, EST_KA = 2.0f * EST_U, EST_KW = 5.0f * EST_U, EST_KP = 0.5f * EST_U,
+                EST_KN = 1.0f * EST_U, EST_KD = 1.5f * EST_U;
 
 template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false, typename IO = T>
 __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks)) trace_kernel(TraceArgs<T, IO> A) {
@@ -1071,9 +1237,11 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         const SrcGroup& G = A.groups[lo];
                         double o[3], lam;
                         ph.bad = !gen_source(G, A.first_id + idx, key, o, &lam);
-                        ph.p = mk((T)o[0], (T)o[1], (T)o[2]);
-                        ph.d = mk((T)G.dir[0], (T)G.dir[1], (T)G.dir[2]);
-                        ph.lam = (T)lam;
+                        // rounded to the precision of the caller's arrays first: the FP64 re-trace of
+                        // an FP32 photon starts from the same FP32 inputs as the FP32 trace
+                        ph.p = mk((T)(IO)o[0], (T)(IO)o[1], (T)(IO)o[2]);
+                        ph.d = mk((T)(IO)G.dir[0], (T)(IO)G.dir[1], (T)(IO)G.dir[2]);
+                        ph.lam = (T)(IO)lam;
                         ph.var = G.variant;
                         ph.group = lo;
                     } else {
@@ -1087,6 +1255,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     ph.mat_cache = -1;
                     ph.last = -1;
                     ph.thr = 0;
+                    ph.plo = mk(T(0), T(0), T(0));
                     ph.ep = 0.0f;
                     ph.ed = 0.0f;
                     ph.eh = 0.0f;
@@ -1111,7 +1280,37 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         } else if (bst.sid == 0x7fffffff) {
             status = ST_ESCAPED;
         } else {
-            ph.p = ph.p + bst.t * ph.d;
+            const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)bst.sid * REC;
+            const int4 si = tb.surf_i[bst.sid];
+            float e_s = 0.0f;     // FP32: coordinate scale of this hit's rounding
+            float e_kap = 0.0f;   // FP32: curvature bound at this hit
+            bool refined = false;  // FP32: hit re-solved from the compensated position
+            if constexpr (sizeof(T) == 4) {
+                e_s = fmaxf(fabsf(ph.p.x), fmaxf(fabsf(ph.p.y), fabsf(ph.p.z))) +
+                      fmaxf(fabsf(S[F_O]), fmaxf(fabsf(S[F_O + 1]), fabsf(S[F_O + 2]))) + bst.t;
+                e_kap = S[F_KAP];
+                pair_advance(ph.p.x, ph.plo.x, bst.t, ph.d.x);
+                pair_advance(ph.p.y, ph.plo.y, bst.t, ph.d.y);
+                pair_advance(ph.p.z, ph.plo.z, bst.t, ph.d.z);
+                float dt, kap;
+                V3<float> xl, nl;
+                CNT(U_REFINE);
+                // accepted only as a correction of the search's own rounding (a grazing ray
+                // whose re-solve lands on the other root keeps the search's hit)
+                if (refine_hit(S, si.x & 15, (si.x >> 12) & 1, ph.p, ph.plo, ph.d, dt, xl, nl, kap) &&
+                    fabsf(dt) <= 1e-4f * e_s) {
+                    e_kap = kap;
+                    pair_advance(ph.p.x, ph.plo.x, dt, ph.d.x);
+                    pair_advance(ph.p.y, ph.plo.y, dt, ph.d.y);
+                    pair_advance(ph.p.z, ph.plo.z, dt, ph.d.z);
+                    bst.pl = xl;
+                    bst.nl = nl;
+                    refined = true;
+                    e_s = fmaxf(fabsf(xl.x), fmaxf(fabsf(xl.y), fabsf(xl.z))) + fabsf(dt);
+                }
+            } else {
+                ph.p = ph.p + bst.t * ph.d;
+            }
             ph.last = bst.sid;
             // the interaction's four random words (counter: photon id, bounce index); drawn
             // only where they are used (mirrors, refracting faces), the same words either way
@@ -1119,32 +1318,30 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             const uint4 ctr = make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)ph.bounces, 0u);
             uint4 w = make_uint4(0u, 0u, 0u, 0u);
             ph.bounces += 1;
-            const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)bst.sid * REC;
-            const int4 si = tb.surf_i[bst.sid];
             const int role = (si.x >> 4) & 15;
             const V3<T> n = unit(to_world_vec(S, bst.nl));
             const T d_n = dot(ph.d, n);
             const bool front = d_n < T(0);
             // FP32 error estimate, first order.  A ray whose lateral offset is ep and whose
             // direction is off by ed meets the surface (incidence cosine c = |d.n|, after a
-            // segment t) at a point off by el = (ep + t ed + KT scale) / c along the surface
-            // (scale: the coordinates' magnitude, which sets the frame transform's rounding);
-            // the root adds ea = (KA t + KT scale) / c along the ray.  The normal there is off by
-            // (curvature bound) x (el + ea sin(incidence)), plus rounding.  The outgoing ray's
-            // lateral offset is el times its own cosine plus ea times the sine of the turn (the
-            // part of an along-ray shift that is across the new direction).
-            float e_n = 0.0f, e_l = 0.0f, e_a = 0.0f, e_c = 1.0f, e_s = 0.0f, e_sn = 0.0f;
+            // segment t) at a point off by el = (ep + t ed) / c along the surface, plus the frame
+            // transform's rounding KT s / c (s: the coordinate scale of the hit's rounding); the
+            // root adds ea = KA s / c along the ray.  The normal there is off by (curvature
+            // bound) x (el + ea sin(incidence)), plus rounding.  The outgoing ray's lateral offset
+            // is el times its own cosine plus ea times the sine of the turn (the part of an
+            // along-ray shift that is across the new direction) plus the rounding of its origin.
+            // Errors carried along the path add linearly (they may be correlated); the fresh
+            // roundings of one interaction are independent of them and of each other and add in
+            // quadrature.
+            float e_n = 0.0f, e_l = 0.0f, e_a = 0.0f, e_c = 1.0f, e_sn = 0.0f;
             if constexpr (EST) {
                 e_c = fmaxf(fabsf((float)d_n), 1e-20f);
                 e_sn = sqrtf(fmaxf(0.0f, 1.0f - e_c * e_c));
-                e_s = fmaxf(fabsf((float)ph.p.x), fmaxf(fabsf((float)ph.p.y), fabsf((float)ph.p.z)));
-                e_s = fmaxf(e_s, fmaxf(fabsf((float)S[F_O]), fmaxf(fabsf((float)S[F_O + 1]), fabsf((float)S[F_O + 2])))) +
-                      (float)bst.t;
-                const float ts = EST_KT * e_s;
-                e_l = (ph.ep + (float)bst.t * ph.ed + ts) / e_c;
-                e_a = ((float)S[F_KA] * EST_U * (float)bst.t + ts) / e_c;
-                ph.eh = e_l + e_a;
-                e_n = (float)S[F_KAP] * (e_l + e_a * e_sn) + EST_KN;
+                const float ic = 1.0f / e_c;
+                e_l = hypotf((ph.ep + (float)bst.t * ph.ed) * ic, EST_KT * e_s * ic);
+                e_a = (refined ? EST_KA : EST_KW) * e_s * ic;
+                ph.eh = hypotf(e_l, e_a);
+                e_n = hypotf(e_kap * (e_l + e_a * e_sn), EST_KN);
             }
             if (role == ROLE_OBSC) {
                 status = ST_OBSCURED;
@@ -1207,8 +1404,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         // outgoing ray leaves at the incidence cosine and turns by twice the
                         // incidence angle (sine 2 s c)
                         if constexpr (EST) {
-                            ph.ed += 2.0f * e_n + EST_KD;
-                            ph.ep = e_l * e_c + e_a * (2.0f * e_sn * e_c) + EST_KP * e_s;
+                            ph.ed = hypotf(ph.ed + 2.0f * (e_n - EST_KN), hypotf(2.0f * EST_KN, EST_KD));
+                            ph.ep = hypotf(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
                         }
                     }
                 }
@@ -1241,8 +1438,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     ph.d = unit(ph.d - (T(2) * dot(ph.d, nf)) * nf);
                     CNT(U_REFLECT);
                     if constexpr (EST) {
-                        ph.ed += 2.0f * e_n + EST_KD;
-                        ph.ep = e_l * e_c + e_a * (2.0f * e_sn * e_c) + EST_KP * e_s;
+                        ph.ed = hypotf(ph.ed + 2.0f * (e_n - EST_KN), hypotf(2.0f * EST_KN, EST_KD));
+                        ph.ep = hypotf(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
                     }
                 } else {
                     const T eta = n1 / n2;
@@ -1255,9 +1452,9 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         // leaves at cosine ct and turns by theta_i - theta_t
                         const float ctf = fmaxf((float)ct, 1e-20f);
                         const float g = (float)(eta * ci) / ctf;
-                        ph.ed = (ph.ed + e_n) * g + e_n + EST_KD;
+                        ph.ed = hypotf((ph.ed + e_n) * g + e_n, EST_KD);
                         const float st = sqrtf(fmaxf(0.0f, 1.0f - ctf * ctf));
-                        ph.ep = e_l * ctf + e_a * fabsf(e_sn * ctf - e_c * st) + EST_KP * e_s;
+                        ph.ep = hypotf(e_l * ctf + e_a * fabsf(e_sn * ctf - e_c * st), EST_KP * e_s);
                     }
                 }
             }
@@ -1266,9 +1463,9 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             if (A.tr_pts && ph.i >= A.tr_first && ph.i < A.tr_first + A.tr_count) {
                 const unsigned long long k = atomicAdd(A.tr_n, 1ull);
                 if ((long long)k < A.tr_cap) {
-                    A.tr_pts[4 * k + 0] = (IO)ph.p.x;
-                    A.tr_pts[4 * k + 1] = (IO)ph.p.y;
-                    A.tr_pts[4 * k + 2] = (IO)ph.p.z;
+                    A.tr_pts[4 * k + 0] = (IO)(ph.p.x + ph.plo.x);
+                    A.tr_pts[4 * k + 1] = (IO)(ph.p.y + ph.plo.y);
+                    A.tr_pts[4 * k + 2] = (IO)(ph.p.z + ph.plo.z);
                     A.tr_pts[4 * k + 3] = IO(0);
                     A.tr_info[4 * k + 0] = (int)ph.i;
                     A.tr_info[4 * k + 1] = ph.bounces - 1;
@@ -1280,14 +1477,17 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         if (status == 0) continue;
         // ---- photon finished: store (SoA)
         const long long i = ph.i;
+        if constexpr (sizeof(T) == 4) ph.p = ph.p + ph.plo;  // the position pair, rounded
         if constexpr (EST) {
+            // the stored position adds its own rounding
+            const float e_pos = hypotf(ph.eh, 0.5f * EST_U * fmaxf(fabsf(ph.p.x), fmaxf(fabsf(ph.p.y), fabsf(ph.p.z))));
             if (A.err) {
-                A.err[i] = ph.eh;
+                A.err[i] = e_pos;
                 A.err[n + i] = ph.ed;
             }
             // over a bound (or an ERROR, which FP64 may not reproduce): re-traced in FP64 by the
             // next launch, which writes every output and counts the photon
-            if (A.queue_out && (ph.eh > A.acc_pos || ph.ed > A.acc_dir || status == ST_ERROR)) {
+            if (A.queue_out && (e_pos > A.acc_pos || ph.ed > A.acc_dir || status == ST_ERROR)) {
                 const unsigned long long k = atomicAdd(A.queue_n, 1ull);
                 if ((long long)k < A.queue_cap) {
                     A.queue_out[k] = i;

@@ -50,7 +50,10 @@ int trace_blocks_per_sm_f32(int block, size_t smem, bool src) {
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s) {
     const bool st = a.stage != 0;
     if (a.groups) {
-        if (a.units) return cudaErrorInvalidConfiguration;
+        if (a.units) {  // counting build of the source-mode kernel (block 128)
+            if (block != 128) return cudaErrorInvalidConfiguration;
+            return st ? launch_one<128, true, true, true>(a, grid, smem, s) : launch_one<128, true, false, true>(a, grid, smem, s);
+        }
         switch (block) {
             case 64: return st ? launch_one<64, false, true, true>(a, grid, smem, s) : launch_one<64, false, false, true>(a, grid, smem, s);
             case 128: return st ? launch_one<128, false, true, true>(a, grid, smem, s) : launch_one<128, false, false, true>(a, grid, smem, s);

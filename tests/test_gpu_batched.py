@@ -140,3 +140,37 @@ def test_tolerance_sweep_r80_distribution_matches_oracle():
     r0 = robast.psf(g0, out0["status"], out0["focal_xy"], windows=[(0, m)])[0][3]
     assert r0 < np.mean(r80)
     g0.close()
+
+
+def test_autotuners_pick_a_candidate_and_results_do_not_depend_on_it():
+    """The launch-shape tuners time every (block, blocks per SM, refill threshold)
+    candidate and return the fastest; tracing with it gives the same results as the
+    default launch (photon-id random streams)."""
+    from paper_1508_07803_gb300 import autotune
+    scene, groups = _setup(nv=2, angles=(0.0, 30.0), n=20_000)
+    geom = robast.build_geometry(scene)
+    best, table = autotune.tune_sources(geom, groups, max_bounces=30, fraction=0.05,
+                                        shapes=((128, 0), (64, 2)), refill=(8, 24))
+    assert best in table and len(table) == 4 and all(t > 0 for t in table.values())
+    src = robast.sources_create(geom, groups)
+    a = torch.zeros((src.n_groups, 8), dtype=torch.int64, device="cuda")
+    b = torch.zeros_like(a)
+    robast.trace_sources(geom, src, a, seed=3, max_bounces=30)
+    robast.trace_sources(geom, src, b, seed=3, max_bounces=30, block_size=best[0], blocks_per_sm=best[1],
+                         refill_min=best[2])
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    src.close()
+    geom.close()
+    scene, bun = W.lst_workload(40_000, seed=4, angles_deg=(1.0,))
+    geom = robast.build_geometry(scene)
+    o = torch.from_numpy(bun.rounded_to(np.float32).origins).cuda()
+    d = torch.from_numpy(bun.rounded_to(np.float32).dirs).cuda()
+    w = torch.from_numpy(bun.rounded_to(np.float32).wavelengths).cuda()
+    best, table = autotune.tune_trace(geom, o, d, w, n_sample=20_000, shapes=((512, 0), (128, 0)), refill=(16, 24))
+    assert best in table and len(table) == 4
+    ref = to_numpy(robast.trace(geom, o, d, w, seed=2))
+    got = to_numpy(robast.trace(geom, o, d, w, seed=2, block_size=best[0], blocks_per_sm=best[1], refill_min=best[2]))
+    for k in ("status", "bounces", "hit", "dir", "last_surface", "focal_xy"):
+        assert np.array_equal(ref[k], got[k]), k
+    geom.close()

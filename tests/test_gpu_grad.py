@@ -2,6 +2,7 @@
 the oracle's dual-number gradients and central finite differences.
 
 Tolerances: GPU vs oracle duals 1e-3 relative (FP32 trace) and 1e-8 (FP64);
+repeated runs bit-identical;
 GPU (FP64) vs oracle central differences (h = 1e-6) 1e-4.  Relative error is
 |g - g_ref| / max(|g_ref|, 1e-3 max|g_ref|).
 """
@@ -147,3 +148,47 @@ def test_param_layout_marks_the_differentiated_slots():
     act = [(sid, slot) for sid, _, slot, a in lay if a]
     assert act and all(cone.surfaces[sid].shape == "hexcone" and slot.startswith("P") for sid, slot in act)
     geom.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-8), (32, 1e-3)])
+def test_two_mirror_gradient_covers_primary_and_secondary(precision, tol):
+    """Schwarzschild-Couder-like optics: every detected photon meets a primary and a secondary
+    panel; the adjoint sweep gives both their gradients, matching the oracle's duals (which
+    carry every differentiable surface of a path) and central differences."""
+    scene, b = W.sct_workload(1_500, seed=4, angles_deg=(0.0, 2.0))
+    v, g, info = _gpu(scene, b, "msr", precision, seed=5)
+    ref_b = b if precision == 64 else b.rounded_to(np.float32)
+    rv, rg = oracle.objective(scene, ref_b, "msr", seed=5, eps=oracle.default_eps(scene, precision))
+    assert v == pytest.approx(rv, rel=1e-9 if precision == 64 else 1e-5)
+    assert info["n_untracked"] == 0
+    prim = [i for i, s in enumerate(scene.surfaces) if s.role == "mirror" and s.origin[2] == 0.0]
+    sec = [i for i, s in enumerate(scene.surfaces) if s.role == "mirror" and s.origin[2] != 0.0]
+    assert np.abs(rg[prim]).sum() > 0 and np.abs(rg[sec]).sum() > 0
+    assert np.abs(g[sec]).sum() > 0
+    mask = np.abs(rg).sum(axis=1) > 0
+    assert np.max(_rel(g[mask], rg[mask])) < tol
+    if precision == 64:
+        ns = len(scene.surfaces)
+        for sid in (max(prim, key=lambda i: abs(g[i, 0])), max(sec, key=lambda i: abs(g[i, 0]))):
+            for k, h in ((0, 1e-6), (1, 1e-6)):
+                dp = np.zeros((ns, 16))
+                dp[sid, k] = h
+                vp, _ = oracle.objective(scene, b, "msr", seed=5, delta=dp, grad=False)
+                vm, _ = oracle.objective(scene, b, "msr", seed=5, delta=-dp, grad=False)
+                fd = (vp - vm) / (2 * h)
+                assert abs(g[sid, k] - fd) / max(abs(fd), 1e-3 * np.max(np.abs(g))) < 1e-4, (sid, k, g[sid, k], fd)
+
+
+def test_gradient_is_bit_identical_from_run_to_run():
+    """The sums over photons are fixed point with integer atomics: the order in which photons
+    finish does not change a bit of the value or the gradient."""
+    scene, b, vop, _ = W.dish_batch(n_dishes=4, n_min=60, n_max=198, photons_per_dish=50_000)
+    geom = robast.build_geometry(scene)
+    o, d, w = _dev(b, 32)
+    v = torch.from_numpy(vop).cuda()
+    runs = [robast.trace_grad(geom, o, d, w, objective="msr", precision=32, seed=1, variant_of_photon=v)
+            for _ in range(3)]
+    geom.close()
+    for val, g, _ in runs[1:]:
+        assert val == runs[0][0]
+        assert torch.equal(g, runs[0][1])

@@ -72,6 +72,16 @@ def test_sct_parity(precision):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+def test_gct_parity(precision):
+    """GCT-like dual-mirror telescope (6 primary petals, monolithic secondary, curved focal surface)."""
+    scene, b = W.gct_workload(4_003, seed=6)
+    g = _run(scene, b, precision, seed=3)
+    r = oracle_for(scene, b, precision, seed=3)
+    assert (r["status"] == W.DETECTED).sum() > 5_000
+    print(compare(g, r, precision, scene.focal_length, f"gct fp{precision}"))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 def test_cone_parity(precision):
     scene = W.cone_scene()
     H = W.cone_heights(1)[0]

@@ -424,3 +424,56 @@ def test_sct_paraxial_focus():
     s_img = 1 / (1 / (W.SC_R2 / 2) - 1 / s)
     assert abs(8.4 - s_img - 6.4) < 1e-12
     assert abs(f1 * s_img / abs(s) - 5.6) < 1e-12
+
+
+def test_gct_paraxial_focus_by_mirror_equation_and_trace():
+    """GCT-like prescription: the mirror equation puts the secondary's image of
+    the primary focus at the focal surface's vertex z = 6.4 s with effective
+    focal length 2.283 m; tracing near-axis rays through the two mirrors
+    (apertures opened, asphere terms off: the paraxial system) reproduces both:
+    a ray at height h leaves the secondary at angle atan(h / EFL) and crosses
+    the axis at the image point."""
+    s = W.GCT_S
+    R1, R2 = W.SC_R1 * s, W.SC_R2 * s
+    f1 = R1 / 2
+    z2 = 8.4 * s
+    so = -(f1 - z2)
+    si = 1 / (1 / (R2 / 2) - 1 / so)
+    assert abs(z2 - si - 6.4 * s) < 1e-12
+    assert abs(f1 * si / abs(so) - W.GCT_F) < 1e-12
+    prim = W.Surface("sag", "mirror", "circle", curv=1.0 / R1, ap=(4.85 * s, 0, 0, 0))
+    sec = W.Surface("sag", "mirror", "circle", origin=(0.0, 0.0, z2), rot=W.FACING_DOWN, curv=1.0 / R2,
+                    ap=(2.7 * s, 0, 0, 0))
+    scene = W.Scene("gct_paraxial", [prim, sec], [W.Material([400.0], [1.0])], [W.Medium()], 7.0, W.GCT_F)
+    hs = np.array([1e-4, 2e-4, 5e-4])
+    phi = np.array([0.3, 1.7, 4.0])
+    o = np.stack([hs * np.cos(phi), hs * np.sin(phi), np.full(3, z2 - 0.01)])
+    b = W.Bundle(o, np.repeat([[0.0], [0.0], [-1.0]], 3, axis=1), np.full(3, 400.0))
+    r = _trace(scene, b, max_bounces=2)  # stop after the secondary: the last point is on it
+    assert np.all(r["status"] == MAX_BOUNCES) and np.all(r["last_surface"] == 1)
+    d = r["dir"]
+    p = r["hit"]
+    rho_d = np.hypot(d[0], d[1])
+    efl = hs * (-d[2]) / rho_d
+    assert np.max(np.abs(efl / W.GCT_F - 1)) < 1e-6
+    # axis crossing of the outgoing line through the last point, along the radial direction
+    radial = (p[0] * np.cos(phi) + p[1] * np.sin(phi))
+    drad = d[0] * np.cos(phi) + d[1] * np.sin(phi)
+    zc = p[2] - radial * d[2] / drad
+    assert np.max(np.abs(zc - 6.4 * s)) < 1e-6
+
+
+def test_gct_scene_detects_through_both_mirrors():
+    scene, b = W.gct_workload(4_000, seed=2)
+    s = W.GCT_S
+    mirrors = [x for x in scene.surfaces if x.role == "mirror"]
+    assert len(mirrors) == 7  # six primary petals, one secondary
+    assert all(abs(m.curv - 1 / (W.SC_R1 * s)) < 1e-15 and m.origin[2] == 0.0 for m in mirrors[:6])
+    assert abs(mirrors[6].curv - 1 / (W.SC_R2 * s)) < 1e-15 and abs(mirrors[6].origin[2] - 8.4 * s) < 1e-15
+    assert abs(scene.surfaces[0].origin[2] - 6.4 * s) < 1e-15
+    r = _trace(scene, b)
+    det = r["status"] == DETECTED
+    assert det.mean() > 0.3
+    assert np.all(r["bounces"][det] == 3)
+    # detected photons last met the focal surface (surface 0) after a petal and the secondary
+    assert np.all(r["last_surface"][det] == 0)

@@ -225,6 +225,45 @@ def sct_scene(seed: int = 0, asph_scale: float = 1e-3) -> Scene:
     return Scene("sct", surfs, [mat], [Medium()], length_scale=17.3, focal_length=5.6)
 
 
+# GCT-like dual-mirror small telescope (the paper prints no prescription): the SC-like system
+# above scaled to an effective focal length of 2.283 m (primary 3.95 m, secondary 2.2 m across),
+# primary split into 6 petals, monolithic secondary, its own seeded asphere terms.
+GCT_F = 2.283
+GCT_S = GCT_F / 5.6
+
+
+def gct_scene(seed: int = 0, asph_scale: float = 1e-3) -> Scene:
+    """GCT-like Schwarzschild-Couder system: the SC-like prescription scaled by
+    s = 2.283 / 5.6 (concave primary R = s 392/15 m, annulus s (4.4-9.7) m in
+    6 petals; concave secondary R = 7 s m facing down at z = 8.4 s, one
+    annulus s (0.8-5.4) m); even-asphere terms r^2..r^16 at a 1e-3 relative
+    sag scale (Philox stream 2 of `seed`); spherical focal surface R = s m at
+    z = 6.4 s; an obscuring disk over the secondary hole.  Paraxial effective
+    focal length 2.283 m."""
+    s = GCT_S
+    rng = _rng(seed + 7_000_003, 2)
+    mat = Material(lam=[300.0, 600.0], refl=[0.88, 0.9], sigma=0.0)
+    surfs: List[Surface] = []
+    surfs.append(Surface("sag", "focal", "circle", origin=(0.0, 0.0, 6.4 * s), curv=1.0 / s, ap=(0.45 * s, 0, 0, 0)))
+    surfs.append(Surface("sag", "obscuration", "circle", origin=(0.0, 0.0, 8.5 * s), ap=(0.45 * s, 0, 0, 0)))
+
+    def coeffs(R, rmax):
+        eps = rng.normal(0.0, 1.0, size=8)
+        sb = _sag_base(R, rmax)
+        return tuple(float(eps[k - 1] * asph_scale * sb / rmax ** (2 * k)) for k in range(1, 9))
+
+    R1, R2 = SC_R1 * s, SC_R2 * s
+    a1 = coeffs(R1, 4.85 * s)
+    a2 = coeffs(R2, 2.7 * s)
+    for p in range(6):
+        phi0, phi1 = 2 * math.pi * p / 6, 2 * math.pi * (p + 1) / 6
+        surfs.append(Surface("sag", "mirror", "sector", material=0, curv=1.0 / R1, asph=a1,
+                             ap=(2.2 * s, 4.85 * s, phi0, phi1)))
+    surfs.append(Surface("sag", "mirror", "annulus", material=0, origin=(0.0, 0.0, 8.4 * s), rot=FACING_DOWN,
+                         curv=1.0 / R2, asph=a2, ap=(0.4 * s, 2.7 * s, 0, 0)))
+    return Scene("gct", surfs, [mat], [Medium()], length_scale=17.3 * s, focal_length=GCT_F)
+
+
 # Hexagonal light concentrator (entrance 50 mm flat-to-flat, exit 25 mm).
 CONE_A_IN = 0.025
 CONE_A_OUT = 0.0125
@@ -410,6 +449,18 @@ SCT_ANGLES_DEG = tuple(4.0 * k / 7.0 for k in range(8))
 def sct_workload(n_per_angle: int, seed: int = 0, angles_deg=SCT_ANGLES_DEG):
     scene = sct_scene(seed=seed)
     bs = [disk_bundle(n_per_angle, 5.0, 10.0, math.radians(a), (300.0, 600.0), seed, stream=200 + k)
+          for k, a in enumerate(angles_deg)]
+    return scene, concat(bs)
+
+
+GCT_ANGLES_DEG = (0.0, 1.0, 2.0, 3.0, 4.0)
+
+
+def gct_workload(n_per_angle: int, seed: int = 0, angles_deg=GCT_ANGLES_DEG):
+    """GCT-like system: n photons per field angle on a 2.1 m disk from z = 10 s,
+    wavelength uniform over 300-600 nm."""
+    scene = gct_scene(seed=seed)
+    bs = [disk_bundle(n_per_angle, 5.0 * GCT_S, 10.0 * GCT_S, math.radians(a), (300.0, 600.0), seed, stream=250 + k)
           for k, a in enumerate(angles_deg)]
     return scene, concat(bs)
 
