@@ -9,6 +9,8 @@ pressure and traversal coherence against each other, and the best choice
 depends on the optical system (surface count, bounce mix).  The tuners time
 the launch on a reduced copy of the work for every candidate and return the
 fastest; the results do not depend on the shape (photon-id random streams).
+They time the FP32 trace launch alone (accuracy guard off): the guard's FP64
+re-trace is a separate launch with its own fixed shape.
 """
 from __future__ import annotations
 
@@ -53,7 +55,8 @@ def tune_sources(geom, groups, precision: int = 32, max_bounces: int = 100, frac
             try:
                 times[(block, bps, rm)] = _time(
                     lambda: trace_sources(geom, src, counts, seed=seed, precision=precision, max_bounces=max_bounces,
-                                          block_size=block, blocks_per_sm=bps, refill_min=rm, stream=stream),
+                                          block_size=block, blocks_per_sm=bps, refill_min=rm, stream=stream,
+                                          accuracy=False),
                     reps, stream)
             except RobastError:
                 continue
@@ -85,7 +88,8 @@ def tune_trace(geom, origins, dirs, wavelengths, precision: int = 32, max_bounce
             try:
                 times[(block, bps, rm)] = _time(
                     lambda: trace(geom, o, d, w, seed=seed, precision=precision, max_bounces=max_bounces, stream=stream,
-                                  block_size=block, blocks_per_sm=bps, refill_min=rm, variant_of_photon=v),
+                                  block_size=block, blocks_per_sm=bps, refill_min=rm, variant_of_photon=v,
+                                  accuracy=False),
                     reps, stream)
             except RobastError:
                 continue
