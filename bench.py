@@ -481,6 +481,70 @@ def _plain_window_check(dev, scene, b, idx, precision, vop=None, n_window=None, 
     return g, r, precision, scene.focal_length, [(k * n_window, n_window) for k in range(nw)]
 
 
+# FP64 FLOPs of one re-solved interaction of the gradient pass (frame transform 33, quadric or
+# Bezier root and one Newton step ~56, aperture 15, normal ~10, reflection 8, roughness 36), and
+# the multiplier of its 16-slot dual form (each operation carries 16 derivative lanes: an add 16
+# more, a product 32 more; about 17x on this mix)
+GRAD_INTERACTION_FLOPS = 158
+GRAD_DUAL_FACTOR = 17
+
+
+def grad_roofline(units, ms_per_eval, peak64):
+    fwd, rep, dual = units
+    flops = (fwd + rep) * GRAD_INTERACTION_FLOPS + dual * GRAD_INTERACTION_FLOPS * GRAD_DUAL_FACTOR
+    achieved = flops / (ms_per_eval * 1e-3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak64, "kernel": "robast::grad_kernel<float> (adjoint, FP64 duals)",
+            "flops_per_eval": flops, "work_units_per_eval": {"fwd_interactions": fwd, "replayed_interactions": rep,
+                                                             "dual_interactions": dual},
+            "peak_source": "DFMA throughput probe robast_measure_alu_peak on this GPU (measured); FLOPs per "
+                           "interaction estimated from the operation counts"}
+
+
+def measure_grad_cone(args, dev, stream, ws, rank, max_over_ranks, barrier):
+    """Soft collection efficiency of a Bezier hexagonal cone behind its window and its gradient
+    with respect to the 6 control-point coordinates of the wall profile: 1e6 photons over
+    incidence angles 0-30 deg (FP32 trace, FP64 adjoint).  Metric: gradient evaluations/s."""
+    import math
+    import torch
+    import paper_1508_07803_gb300 as robast
+    scene = W.cone_scene(n_variants=1, seed=rank)
+    H = W.cone_heights(1)[0]
+    m = args.grad_cone_photons // 7
+    b = W.concat([W.hexagon_bundle(m, W.CONE_A_IN, H + W.CONE_WINDOW + 1e-4, math.radians(a), seed=rank,
+                                   stream=700 + k) for k, a in enumerate(range(0, 31, 5))])
+    geom = robast.build_geometry(scene)
+    o = torch.from_numpy(b.origins).to(dev, torch.float32)
+    d = torch.from_numpy(b.dirs).to(dev, torch.float32)
+    w = torch.from_numpy(b.wavelengths).to(dev, torch.float32)
+    g = torch.zeros((geom.n_surfaces, robast.N_PARAM), dtype=torch.float64, device=dev)
+
+    def evaluate():
+        g.zero_()
+        return robast.trace_grad(geom, o, d, w, objective="soft_ce", precision=32, seed=0, max_bounces=30,
+                                 stream=stream, out=g)
+
+    for _ in range(2):
+        evaluate()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.grad_steps):
+        value, _, info = evaluate()
+    barrier()
+    dt = max_over_ranks(time.perf_counter() - t0)
+    units = torch.zeros(3, dtype=torch.int64, device=dev)
+    robast.trace_grad(geom, o, d, w, objective="soft_ce", precision=32, seed=0, max_bounces=30, stream=stream,
+                      work_units=units, grad=False)
+    grad = g[1, 10:16].cpu().tolist()
+    geom.close()
+    return {"value": ws * args.grad_steps / dt, "unit": "grad evals/s", "ms_per_eval": 1e3 * dt / args.grad_steps,
+            "roofline": grad_roofline(units.cpu().tolist(), 1e3 * dt / args.grad_steps, args.peak64),
+            "photons_per_eval": int(b.n), "objective": "soft collection efficiency (tau = 0.5 mm), frozen path",
+            "objective_value": value, "gradient_P0r_P0z_P1r_P1z_P2r_P2z": grad,
+            "config": {"workload": "bezier_hex_cone_soft_ce_7_angles_0_to_30_deg", "photons": int(b.n),
+                       "max_bounces": 30, "timing": "host wall clock around the synchronous call"}}
+
+
 def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
     """Differentiable batch: 32 LST-like dishes with 60-198 facets, 1e6
     photons each over field angles 0-2 deg, one evaluation = the summed
@@ -515,8 +579,12 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
     gn = float(torch.linalg.vector_norm(g).item())
     layout = robast.param_layout(geom)
     active = sum(1 for p in layout if p[3])
+    units = torch.zeros(3, dtype=torch.int64, device=dev)
+    robast.trace_grad(geom, o, d, w, objective="msr", precision=32, seed=0, variant_of_photon=v, stream=stream,
+                      work_units=units, grad=False)
     geom.close()
     return {"value": ws * args.grad_steps / dt, "unit": "grad evals/s", "ms_per_eval": 1e3 * dt / args.grad_steps,
+            "roofline": grad_roofline(units.cpu().tolist(), 1e3 * dt / args.grad_steps, args.peak64),
             "photons_per_eval": int(b.n), "photons_per_s": ws * args.grad_steps * b.n / dt,
             "objective": "sum over 32 dishes of the mean-squared spot radius (frozen path, expected weights)",
             "objective_value_m2": value, "gradient_norm": gn, "n_params": int(geom.n_surfaces * robast.N_PARAM),
@@ -576,6 +644,7 @@ def main():
                     help="library launch defaults instead of the tuners (keeps profiler launch counts small)")
     ap.add_argument("--grad-photons-per-dish", type=int, default=1_000_000)
     ap.add_argument("--grad-steps", type=int, default=3)
+    ap.add_argument("--grad-cone-photons", type=int, default=1_000_000)
     ap.add_argument("--batch-photons-per-group", type=int, default=2_000_000)
     ap.add_argument("--batch-steps", type=int, default=1)
     args = ap.parse_args()
@@ -701,6 +770,7 @@ def main():
 
     peak32 = robast.measure_alu_peak(32)
     peak64 = robast.measure_alu_peak(64)
+    args.peak64 = peak64
     npa = args.photons_per_angle
     scene, bundle = W.lst_workload(npa, seed=rank)
     N = bundle.n
@@ -754,6 +824,8 @@ def main():
     if not args.no_grad:
         forms["grad_fp32"] = measure_grad(args, dev=dev, stream=stream, ws=ws, rank=rank,
                                           max_over_ranks=max_over_ranks, barrier=barrier)
+        forms["grad_cone_fp32"] = measure_grad_cone(args, dev=dev, stream=stream, ws=ws, rank=rank,
+                                                    max_over_ranks=max_over_ranks, barrier=barrier)
 
     e2e = None
     if not args.no_e2e:

@@ -239,7 +239,10 @@ typedef struct robast_trace_opts {
     unsigned long long* work_units; /* device [ROBAST_N_UNITS] or NULL; non-NULL runs the
                                        counting build of the kernel (block 128, slower; FP32
                                        only in source mode) and adds the work units below to
-                                       it */
+                                       it.  robast_trace_grad adds its own three instead:
+                                       FP64 interactions of the forward passes, interactions
+                                       replayed by the reverse sweeps, dual-number
+                                       interactions */
     int32_t coherent_order;   /* 0: library default (on for n >= 65536), 1: on, -1: off.  On, the
                                  photons are first sorted by origin cell so that each warp traces
                                  neighbouring rays; the results are identical either way.  The
@@ -267,9 +270,10 @@ typedef struct robast_trace_opts {
                                  exceeds 0.8 of a bound, or that ends in ERROR, is re-traced from its
                                  inputs in FP64 (same random streams, same epsilon) by a second
                                  launch on the same stream, whose result replaces the FP32 one.  The
-                                 queue holds n photons (n > 2^26: max(2^26, n / 8)); its scratch
-                                 comes from g's memory pool like the sort's.  Off with photon tracks
-                                 or the counting build */
+                                 queue has an entry (8 bytes) per photon, from g's memory pool like
+                                 the sort's scratch; source-mode traces run in chunks of 2^27 photons,
+                                 each followed by its re-trace, with the queue of their sources.  Off
+                                 with photon tracks or the counting build */
 } robast_trace_opts;
 
 /* Work units counted when opts.work_units is set: ray-box tests, quadric root
@@ -339,9 +343,8 @@ typedef struct robast_source_group {
 typedef struct robast_sources robast_sources; /* opaque device-resident group table */
 
 /* Upload n_groups groups (host array, deep-copied) for geometry g.  Synchronous.  Also
- * allocates the FP32 accuracy guard's re-trace queue for these photons (8 bytes per queued
- * photon: all N photons for N <= 2^26, else max(2^26, N / 16)), so that robast_trace_sources
- * allocates nothing. */
+ * allocates the FP32 accuracy guard's re-trace queue for one chunk of these photons (8 bytes per
+ * photon, at most 2^27 photons), so that robast_trace_sources allocates nothing. */
 int robast_sources_create(const robast_geom* g, const robast_source_group* groups, int32_t n_groups,
                           robast_sources** out);
 void robast_sources_free(robast_sources* s);
@@ -354,9 +357,10 @@ int robast_sources_info(const robast_sources* s, int32_t* n_groups, int64_t* n_p
  * collection efficiency = counts[1] / counts[7].  `out` (device arrays of the
  * total photon count, any field NULL) may be NULL.  opts as for
  * robast_trace_ex (variant_of_photon must be NULL).  Asynchronous; issues
- * only memsets and kernel launches on the stream (with the accuracy guard on,
- * two more memsets and the FP64 re-trace launch), so it can be captured in a
- * CUDA graph.
+ * only memsets and kernel launches on the stream (with the FP32 accuracy guard
+ * on: per chunk of 2^27 photons, the trace launch and the FP64 re-trace
+ * launch of the chunk's queued photons), so it can be captured in a CUDA
+ * graph.
  */
 int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64_t seed,
                          unsigned long long* group_counts, const robast_trace_out* out,

@@ -49,7 +49,7 @@ def tune_sources(geom, groups, precision: int = 32, max_bounces: int = 100, frac
     counts = torch.zeros((src.n_groups, 8), dtype=torch.int64, device="cuda")
     if stream is None:
         stream = torch.cuda.current_stream()
-    times = {}
+    times, last_err = {}, None
     for block, bps in shapes:
         for rm in refill:
             try:
@@ -58,11 +58,12 @@ def tune_sources(geom, groups, precision: int = 32, max_bounces: int = 100, frac
                                           block_size=block, blocks_per_sm=bps, refill_min=rm, stream=stream,
                                           accuracy=False),
                     reps, stream)
-            except RobastError:
+            except RobastError as e:
+                last_err = e
                 continue
     src.close()
     if not times:
-        raise RobastError("autotune: no candidate launch shape ran")
+        raise RobastError(f"autotune: no candidate launch shape ran ({last_err})")
     best = min(times, key=times.get)
     return best, times
 
@@ -80,7 +81,7 @@ def tune_trace(geom, origins, dirs, wavelengths, precision: int = 32, max_bounce
     v = variant_of_photon[:n].contiguous() if variant_of_photon is not None else None
     if stream is None:
         stream = torch.cuda.current_stream()
-    times = {}
+    times, last_err = {}, None
     for block, bps in shapes:
         if precision == 64 and block == 512:
             continue
@@ -91,9 +92,10 @@ def tune_trace(geom, origins, dirs, wavelengths, precision: int = 32, max_bounce
                                   block_size=block, blocks_per_sm=bps, refill_min=rm, variant_of_photon=v,
                                   accuracy=False),
                     reps, stream)
-            except RobastError:
+            except RobastError as e:
+                last_err = e
                 continue
     if not times:
-        raise RobastError("autotune: no candidate launch shape ran")
+        raise RobastError(f"autotune: no candidate launch shape ran ({last_err})")
     best = min(times, key=times.get)
     return best, times

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
     const long long n = A.n;
     const int nq = A.objective == 1 ? 1 : 2;  // objective terms per photon: (qx, qy) or the margin m
     int ids[GMAXB];
+    unsigned int u_fwd = 0, u_rep = 0, u_dual = 0;  // work units (when A.units is set)
     for (long long i = blockIdx.x * (long long)BLOCK + threadIdx.x; i < n; i += (long long)gridDim.x * BLOCK) {
         const V3<double> p0 = mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]);
         const V3<double> d0 = mk((double)A.d[i], (double)A.d[n + i], (double)A.d[2 * n + i]);
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
             bool rev = false, front = true;
             const int gi = g_interact<T, double>(tb, S, si, (double)lam, wd, 2, &rev, (double)A.eps, A.newton_tol64, p,
                                                  d, qx, qy, &seg, &front);
+            ++u_fwd;
             if (gi == GI_LOST) {
                 status = ST_ERROR;  // the frozen path was lost
                 break;
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
             // the state before interaction `upto`, from the photon's inputs
             pr = p0;
             dr = d0;
+            u_rep += (unsigned)upto;
             for (int j = 0; j < upto; ++j) {
                 const uint4 wd = philox4x32_10(
                     make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)j, 0u), key);
@@ -397,6 +400,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
             const GRec R{A.surf64 + (size_t)ids[K - 1] * REC, A.grec + (size_t)ids[K - 1] * 18, 0};
             g_interact<T, DX>(tb, R, tb.surf_i[ids[K - 1]], (double)lam, wd, 0, &rv, (double)A.eps, A.newton_tol64, ps,
                               ds, qa, qb, &sg, &fr);
+            ++u_dual;
             for (int j = 0; j < 6; ++j) {
                 a[0][j] = qa.d[j];
                 a[1][j] = qb.d[j];
@@ -446,6 +450,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
             bool rv, fr;
             g_interact<T, DX>(tb, R, si, (double)lam, wd, (int)((refl >> k) & 1ull), &rv, (double)A.eps,
                               A.newton_tol64, ps, ds, qa, qb, &sg, &fr);
+            ++u_dual;
             const DX* out[6] = {&ps.x, &ps.y, &ps.z, &ds.x, &ds.y, &ds.z};
             if (mode) {
                 if (sid != cur) {
@@ -473,6 +478,15 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
                 for (int j = 0; j < 6; ++j) a[c][j] = na[c][j];
         }
         flush();
+    }
+    if (A.units) {  // one atomic per warp and unit
+        const unsigned fw = __reduce_add_sync(0xffffffffu, u_fwd), rp = __reduce_add_sync(0xffffffffu, u_rep),
+                       du = __reduce_add_sync(0xffffffffu, u_dual);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(A.units + 0, (unsigned long long)fw);
+            atomicAdd(A.units + 1, (unsigned long long)rp);
+            atomicAdd(A.units + 2, (unsigned long long)du);
+        }
     }
 }
 

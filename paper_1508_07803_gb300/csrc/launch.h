@@ -36,6 +36,8 @@ struct GradArgs {
     double tau;
     unsigned long long* acc;   // [n_surf * GRAD_SLOTS]
     unsigned long long* vals;  // [n_variants * 8 * 2]
+    unsigned long long* units; // optional [3]: FP64 interactions of the forward passes, interactions
+                               // replayed by the reverse sweeps, dual-number interactions
 };
 cudaError_t launch_grad_f32(const GradArgs<float>& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cudaStream_t s);

@@ -907,10 +907,60 @@ struct robast_sources {
 // bound, the error stays below 0.9 of the estimate).
 static const double kGuardFrac = 0.8;
 
-// Capacity of the accuracy guard's re-trace queue for n photons.
-static long long retrace_queue_cap(long long n, long long div) {
-    const long long full = 1LL << 26;
-    return n <= full ? n : std::max(full, n / div);
+// Photons per launch of a source-mode trace with the accuracy guard on: each chunk is followed by
+// its own re-trace launch, so the queue (one entry per photon of a chunk) never overflows.
+static const long long kSrcChunk = 1LL << 27;
+
+// The FP64 re-trace of the photons the FP32 launch `a` queued: FP64 arithmetic and tables, the
+// FP32 arrays, the same epsilon, random streams and outputs; the queue's length is read on the
+// device.
+template <typename T>
+static cudaError_t launch_retrace_of(const robast_geom* g, robast_geom* gm, const TraceArgs<T>& a,
+                                     unsigned long long* qhdr, long long qcap, double eps, bool src, cudaStream_t s) {
+    TraceArgs<double, float> r{};
+    r.tab = g->tab64;
+    r.o = reinterpret_cast<const float*>(a.o);
+    r.d = reinterpret_cast<const float*>(a.d);
+    r.lam = reinterpret_cast<const float*>(a.lam);
+    r.vop = a.vop;
+    r.n = a.n;
+    r.n_work = qcap;
+    r.n_work_dev = qhdr;
+    r.queue_in = a.queue_out;
+    r.seed = a.seed;
+    r.first_id = a.first_id;
+    r.max_bounces = a.max_bounces;
+    r.refill_min = a.refill_min;
+    r.eps = eps;
+    r.newton_tol = eps * 1e-4;
+    r.newton_tol64 = eps * 1e-4;
+    r.st = a.st;
+    r.nb = a.nb;
+    r.hit = reinterpret_cast<float*>(a.hit);
+    r.dir = reinterpret_cast<float*>(a.dir);
+    r.last = a.last;
+    r.fxy = reinterpret_cast<float*>(a.fxy);
+    r.counters = a.counters;
+    r.groups = a.groups;
+    r.n_groups = a.n_groups;
+    r.gcounts = a.gcounts;
+    r.err = a.err;
+    r.retraced = a.retraced;
+    r.work = g->work + (gm->work_slot.fetch_add(1) % kWorkSlots);
+    cudaError_t e = cudaMemsetAsync(r.work, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    r.stage = g->smem64 <= kSmemCap ? 1 : 0;
+    const size_t smem_r = r.stage ? g->smem64 : 0;
+    std::atomic<int>& slot = gm->bps_retrace[src ? 1 : 0];
+    int bps_r = slot.load(std::memory_order_relaxed);
+    if (bps_r <= 0) {
+        bps_r = retrace_blocks_per_sm(smem_r, src);
+        if (bps_r > 0) slot.store(bps_r, std::memory_order_relaxed);
+    }
+    if (bps_r <= 0) return cudaErrorInvalidConfiguration;
+    long long grid_r = (long long)g->num_sms * bps_r;
+    grid_r = std::max(1LL, std::min(grid_r, (qcap + 127) / 128));
+    return launch_retrace(r, (int)grid_r, smem_r, s);
 }
 
 template <typename T>
@@ -1021,7 +1071,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
             qhdr = src->d_queue;
             qcap = src->qcap;
         } else {
-            qcap = retrace_queue_cap(n, 8);
+            qcap = n;
             cudaError_t eq = cudaMallocFromPoolAsync(&q_scratch, (size_t)(4 + qcap) * 8, gm->pool, s);
             if (eq != cudaSuccess) {
                 if (ord_scratch) cudaFreeAsync(ord_scratch, s);
@@ -1042,62 +1092,26 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
         a.acc_dir = o.accuracy_dir > 0.0 ? (float)(kGuardFrac * o.accuracy_dir) : INFINITY;
         a.retraced = out->retraced ? out->retraced : qhdr + 1;
     }
-    a.n_work = n;
-    cudaError_t e;
-    if constexpr (sizeof(T) == 4)
-        e = launch_trace_f32(a, block, (int)grid, smem, s);
-    else
-        e = launch_trace_f64(a, block, (int)grid, smem, s);
-    if (ord_scratch) cudaFreeAsync(ord_scratch, s);
-    if (e == cudaSuccess && guard) {
-        // the FP64 re-trace of the queued photons: FP64 arithmetic and tables, the FP32 arrays,
-        // the same epsilon, random streams and outputs
-        TraceArgs<double, float> r{};
-        r.tab = g->tab64;
-        r.o = reinterpret_cast<const float*>(a.o);
-        r.d = reinterpret_cast<const float*>(a.d);
-        r.lam = reinterpret_cast<const float*>(a.lam);
-        r.vop = a.vop;
-        r.n = n;
-        r.n_work = qcap;
-        r.n_work_dev = qhdr;
-        r.queue_in = a.queue_out;
-        r.seed = a.seed;
-        r.first_id = a.first_id;
-        r.max_bounces = a.max_bounces;
-        r.refill_min = a.refill_min;
-        r.eps = eps;
-        r.newton_tol = eps * 1e-4;
-        r.newton_tol64 = eps * 1e-4;
-        r.st = a.st;
-        r.nb = a.nb;
-        r.hit = reinterpret_cast<float*>(a.hit);
-        r.dir = reinterpret_cast<float*>(a.dir);
-        r.last = a.last;
-        r.fxy = reinterpret_cast<float*>(a.fxy);
-        r.counters = a.counters;
-        r.groups = a.groups;
-        r.n_groups = a.n_groups;
-        r.gcounts = a.gcounts;
-        r.err = a.err;
-        r.retraced = a.retraced;
-        r.work = g->work + (gm->work_slot.fetch_add(1) % kWorkSlots);
-        e = cudaMemsetAsync(r.work, 0, sizeof(unsigned long long), s);
-        r.stage = g->smem64 <= kSmemCap ? 1 : 0;
-        const size_t smem_r = r.stage ? g->smem64 : 0;
-        std::atomic<int>& slot = gm->bps_retrace[src ? 1 : 0];
-        int bps_r = slot.load(std::memory_order_relaxed);
-        if (bps_r <= 0) {
-            bps_r = retrace_blocks_per_sm(smem_r, src != nullptr);
-            if (bps_r > 0) slot.store(bps_r, std::memory_order_relaxed);
+    // one launch over all work, or (source mode with the guard) chunks of the queue's size, each
+    // followed by its FP64 re-trace
+    const long long chunk = guard && src ? qcap : n;
+    cudaError_t e = cudaSuccess;
+    for (long long base = 0; base < n && e == cudaSuccess; base += chunk) {
+        a.work_base = base;
+        a.n_work = std::min(chunk, n - base);
+        if (base > 0) {
+            a.work = g->work + (gm->work_slot.fetch_add(1) % kWorkSlots);
+            e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess && guard) e = cudaMemsetAsync(qhdr, 0, sizeof(unsigned long long), s);
+            if (e != cudaSuccess) break;
         }
-        if (e == cudaSuccess && bps_r <= 0) e = cudaErrorInvalidConfiguration;
-        if (e == cudaSuccess) {
-            long long grid_r = (long long)g->num_sms * bps_r;
-            grid_r = std::max(1LL, std::min(grid_r, (qcap + 127) / 128));
-            e = launch_retrace(r, (int)grid_r, smem_r, s);
-        }
+        if constexpr (sizeof(T) == 4)
+            e = launch_trace_f32(a, block, (int)grid, smem, s);
+        else
+            e = launch_trace_f64(a, block, (int)grid, smem, s);
+        if (e == cudaSuccess && guard) e = launch_retrace_of(g, gm, a, qhdr, qcap, eps, src != nullptr, s);
     }
+    if (ord_scratch) cudaFreeAsync(ord_scratch, s);
     if (q_scratch) cudaFreeAsync(q_scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "robast_trace: launch");
     return 0;
@@ -1175,7 +1189,7 @@ extern "C" int robast_sources_create(const robast_geom* g, const robast_source_g
     if (!s) return fail(ROBAST_E_OOM, "robast_sources_create: host allocation failed");
     s->n_groups = n_groups;
     s->n_photons = first;
-    s->qcap = retrace_queue_cap(first, 16);
+    s->qcap = std::min<long long>(first, kSrcChunk);
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_groups, h.size() * sizeof(SrcGroup));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_groups, h.data(), h.size() * sizeof(SrcGroup), cudaMemcpyHostToDevice);
@@ -1398,6 +1412,7 @@ static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl,
     a.newton_tol64 = 1e-13 * L;
     a.objective = objective;
     a.tau = tau;
+    a.units = op.work_units;  // the gradient pass's three work units, when asked for
     const size_t NP = (size_t)g->n_surf * ROBAST_N_PARAM;
     const size_t NV = (size_t)g->n_var;
     std::lock_guard<std::mutex> lk(g->mu);

@@ -129,7 +129,8 @@ struct TraceArgs {
     const int* vop;
     const int* order;  // optional processing order: work index -> photon index
     long long n;       // photons: the stride of the SoA arrays
-    long long n_work;  // work items (n, or the capacity of a re-trace queue)
+    long long n_work;  // work items (n, a chunk of it, or the capacity of a re-trace queue)
+    long long work_base;  // first work index of this launch (chunked source-mode launches)
     const unsigned long long* n_work_dev;  // if set: work items = min(*n_work_dev, n_work)
     const long long* queue_in;             // if set: work index -> photon index (FP64 re-trace)
     unsigned long long seed;
@@ -1137,8 +1138,12 @@ struct TraceBounds {
 // unrefined hit, whose root was solved from far away), KP for the new ray's origin; KN ulps on
 // the normal and KD on the new direction (reflection or refraction and normalisation).
 constexpr float EST_U = 5.9604645e-08f;  // 2^-24
+// The estimate needs no correct rounding: square roots and quotients in their fast forms.
+__device__ __forceinline__ float est_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ float est_hyp(float a, float b) { return est_sqrt(fmaf(a, a, b * b)); }
 constexpr float EST_KT = 1.0f * EST_U, EST_KA = 2.0f * EST_U, EST_KW = 5.0f * EST_U, EST_KP = 0.5f * EST_U,
                 EST_KN = 1.0f * EST_U, EST_KD = 1.5f * EST_U;
+constexpr float EST_KR2 = 2.5f * EST_U;  // a reflection's fresh direction rounding: hypot(2 KN, KD)
 
 template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false, typename IO = T>
 __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks)) trace_kernel(TraceArgs<T, IO> A) {
@@ -1222,7 +1227,9 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             if (need) {
                 const long long widx = (long long)base + __popc(m & lt_mask);
                 if (widx < n_work) {
-                    const long long idx = A.queue_in ? A.queue_in[widx] : A.order ? (long long)A.order[widx] : widx;
+                    const long long idx = A.queue_in ? A.queue_in[widx]
+                                          : A.order  ? (long long)A.order[widx]
+                                                     : A.work_base + widx;
                     ph.i = idx;
                     if constexpr (SRC) {
                         // group: the last one whose first index is <= idx
@@ -1336,12 +1343,12 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             float e_n = 0.0f, e_l = 0.0f, e_a = 0.0f, e_c = 1.0f, e_sn = 0.0f;
             if constexpr (EST) {
                 e_c = fmaxf(fabsf((float)d_n), 1e-20f);
-                e_sn = sqrtf(fmaxf(0.0f, 1.0f - e_c * e_c));
-                const float ic = 1.0f / e_c;
-                e_l = hypotf((ph.ep + (float)bst.t * ph.ed) * ic, EST_KT * e_s * ic);
+                e_sn = est_sqrt(1.0f - e_c * e_c);
+                const float ic = __fdividef(1.0f, e_c);
+                e_l = est_hyp((ph.ep + (float)bst.t * ph.ed) * ic, EST_KT * e_s * ic);
                 e_a = (refined ? EST_KA : EST_KW) * e_s * ic;
-                ph.eh = hypotf(e_l, e_a);
-                e_n = hypotf(e_kap * (e_l + e_a * e_sn), EST_KN);
+                ph.eh = est_hyp(e_l, e_a);
+                e_n = est_hyp(e_kap * (e_l + e_a * e_sn), EST_KN);
             }
             if (role == ROLE_OBSC) {
                 status = ST_OBSCURED;
@@ -1404,8 +1411,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         // outgoing ray leaves at the incidence cosine and turns by twice the
                         // incidence angle (sine 2 s c)
                         if constexpr (EST) {
-                            ph.ed = hypotf(ph.ed + 2.0f * (e_n - EST_KN), hypotf(2.0f * EST_KN, EST_KD));
-                            ph.ep = hypotf(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
+                            ph.ed = est_hyp(ph.ed + 2.0f * (e_n - EST_KN), EST_KR2);
+                            ph.ep = est_hyp(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
                         }
                     }
                 }
@@ -1438,8 +1445,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     ph.d = unit(ph.d - (T(2) * dot(ph.d, nf)) * nf);
                     CNT(U_REFLECT);
                     if constexpr (EST) {
-                        ph.ed = hypotf(ph.ed + 2.0f * (e_n - EST_KN), hypotf(2.0f * EST_KN, EST_KD));
-                        ph.ep = hypotf(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
+                        ph.ed = est_hyp(ph.ed + 2.0f * (e_n - EST_KN), EST_KR2);
+                        ph.ep = est_hyp(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
                     }
                 } else {
                     const T eta = n1 / n2;
@@ -1451,10 +1458,10 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         // measured from a normal that is itself off by e_n; the transmitted ray
                         // leaves at cosine ct and turns by theta_i - theta_t
                         const float ctf = fmaxf((float)ct, 1e-20f);
-                        const float g = (float)(eta * ci) / ctf;
-                        ph.ed = hypotf((ph.ed + e_n) * g + e_n, EST_KD);
-                        const float st = sqrtf(fmaxf(0.0f, 1.0f - ctf * ctf));
-                        ph.ep = hypotf(e_l * ctf + e_a * fabsf(e_sn * ctf - e_c * st), EST_KP * e_s);
+                        const float g = __fdividef((float)(eta * ci), ctf);
+                        ph.ed = est_hyp((ph.ed + e_n) * g + e_n, EST_KD);
+                        const float st = est_sqrt(1.0f - ctf * ctf);
+                        ph.ep = est_hyp(e_l * ctf + e_a * fabsf(e_sn * ctf - e_c * st), EST_KP * e_s);
                     }
                 }
             }
@@ -1480,7 +1487,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         if constexpr (sizeof(T) == 4) ph.p = ph.p + ph.plo;  // the position pair, rounded
         if constexpr (EST) {
             // the stored position adds its own rounding
-            const float e_pos = hypotf(ph.eh, 0.5f * EST_U * fmaxf(fabsf(ph.p.x), fmaxf(fabsf(ph.p.y), fabsf(ph.p.z))));
+            const float e_pos = est_hyp(ph.eh, 0.5f * EST_U * fmaxf(fabsf(ph.p.x), fmaxf(fabsf(ph.p.y), fabsf(ph.p.z))));
             if (A.err) {
                 A.err[i] = e_pos;
                 A.err[n + i] = ph.ed;

@@ -164,9 +164,9 @@ def test_autotuners_pick_a_candidate_and_results_do_not_depend_on_it():
     geom.close()
     scene, bun = W.lst_workload(40_000, seed=4, angles_deg=(1.0,))
     geom = robast.build_geometry(scene)
-    o = torch.from_numpy(bun.rounded_to(np.float32).origins).cuda()
-    d = torch.from_numpy(bun.rounded_to(np.float32).dirs).cuda()
-    w = torch.from_numpy(bun.rounded_to(np.float32).wavelengths).cuda()
+    o = torch.from_numpy(bun.origins).to("cuda", torch.float32)
+    d = torch.from_numpy(bun.dirs).to("cuda", torch.float32)
+    w = torch.from_numpy(bun.wavelengths).to("cuda", torch.float32)
     best, table = autotune.tune_trace(geom, o, d, w, n_sample=20_000, shapes=((512, 0), (128, 0)), refill=(16, 24))
     assert best in table and len(table) == 4
     ref = to_numpy(robast.trace(geom, o, d, w, seed=2))

@@ -97,8 +97,11 @@ def test_batched_full_size_counters_and_sampled_ids():
     src = robast.sources_create(geom, groups)
     assert src.n_photons == 64 * 41 * 2_000_000 > 2**32
     counts = torch.zeros((src.n_groups, 8), dtype=torch.int64, device="cuda")
-    robast.trace_sources(geom, src, counts, seed=0, precision=32, max_bounces=30)
+    retraced = torch.zeros(2, dtype=torch.int64, device="cuda")
+    robast.trace_sources(geom, src, counts, seed=0, precision=32, max_bounces=30, out={"retraced": retraced})
     torch.cuda.synchronize()
+    # launched in chunks of the re-trace queue's size: every photon over the bounds was re-traced
+    assert int(retraced[1]) == 0 and int(retraced[0]) > 0
     c = counts.cpu().numpy()
     assert np.all(c[:, 7] == 2_000_000)
     assert np.all(c[:, 1:7].sum(axis=1) == c[:, 7])
