@@ -1,6 +1,6 @@
 """Compile the CUDA library (csrc/*.cu) for sm_103a into _build/librobast.so.
 
-nvcc compiles the three translation units in parallel and links them into one
+nvcc compiles the translation units in parallel and links them into one
 shared library with the C ABI of include/robast.h.  Rebuilds only when a
 source is newer than the library.
 """

@@ -79,6 +79,7 @@ struct robast_geom {
     // up once: [precision 32/64][block 64/128/256/512][source mode]; 0 = not yet known
     std::atomic<int> bps_cache[2][4][2] = {};
     std::atomic<int> bps_retrace[2] = {};  // the FP64 re-trace kernel [source mode]
+    unsigned feat = 0;  // the surface kinds and interactions the geometry uses (FT_* bits)
 };
 
 static const int kWorkSlots = 256;
@@ -591,6 +592,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     std::vector<int4> reci(ns);
     std::vector<std::vector<Ref>> refs_of(ns);  // BVH references per surface; empty = unbounded
     std::vector<double> grec64((size_t)ns * 18, 0.0);
+    unsigned feat = 0;
     for (int i = 0; i < ns; ++i) {
         const robast_surface_desc& s = d->surfaces[i];
         double* R = &rec64[(size_t)i * REC];
@@ -667,6 +669,10 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
         }
         reci[i] = make_int4(s.shape | (s.role << 4) | (s.aperture << 8) | ((asph ? 1 : 0) << 12), s.material,
                             s.medium_front, s.medium_back);
+        feat |= (asph ? (unsigned)FT_ASPH : 0u) | (s.shape == ROBAST_SHAPE_CYLINDER ? (unsigned)FT_CYL : 0u) |
+                (s.shape == ROBAST_SHAPE_BOX ? (unsigned)FT_BOX : 0u) |
+                (s.shape == ROBAST_SHAPE_HEXCONE ? (unsigned)FT_CONE : 0u) |
+                (s.role == ROBAST_ROLE_REFRACT ? (unsigned)FT_REFR : 0u);
         double lo[3], hi[3];
         if (local_box(s, lo, hi)) refs_of[i].push_back(Ref{i, world_box(rows, s.origin, lo, hi, 1e-6 * L)});
     }
@@ -849,6 +855,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     g->n_prims = (int)prims.size();
     g->n_glob = (int)glob.size();
     g->length_scale = L;
+    g->feat = feat;
     *out = g;
     return 0;
 }
@@ -910,6 +917,14 @@ static const double kGuardFrac = 0.8;
 // Photons per launch of a source-mode trace with the accuracy guard on: each chunk is followed by
 // its own re-trace launch, so the queue (one entry per photon of a chunk) never overflows.
 static const long long kSrcChunk = 1LL << 27;
+
+// The feature profile of the FP32 kernel that traces g: the reduced ones where they cover the
+// geometry's features (telescopes in plain traces, concentrators in source mode), else all.
+static unsigned trace_profile(const robast_geom* g, bool src) {
+    if (!src && (g->feat & ~(unsigned)FT_TELESCOPE) == 0) return FT_TELESCOPE;
+    if (src && (g->feat & ~(unsigned)FT_CONCENTRATOR) == 0) return FT_CONCENTRATOR;
+    return FT_ALL;
+}
 
 // The FP64 re-trace of the photons the FP32 launch `a` queued: FP64 arithmetic and tables, the
 // FP32 arrays, the same epsilon, random streams and outputs; the queue's length is read on the
@@ -1036,7 +1051,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     std::atomic<int>& bps_slot = gm->bps_cache[sizeof(T) == 4 ? 0 : 1][bi][src ? 1 : 0];
     int bps = bps_slot.load(std::memory_order_relaxed);
     if (bps <= 0) {
-        bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem, src != nullptr)
+        bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem, src != nullptr, trace_profile(g, src != nullptr))
                              : trace_blocks_per_sm_f64(block, smem, src != nullptr);
         if (bps > 0) bps_slot.store(bps, std::memory_order_relaxed);
     }
@@ -1106,7 +1121,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
             if (e != cudaSuccess) break;
         }
         if constexpr (sizeof(T) == 4)
-            e = launch_trace_f32(a, block, (int)grid, smem, s);
+            e = launch_trace_f32(a, block, (int)grid, smem, s, trace_profile(g, src != nullptr));
         else
             e = launch_trace_f64(a, block, (int)grid, smem, s);
         if (e == cudaSuccess && guard) e = launch_retrace_of(g, gm, a, qhdr, qcap, eps, src != nullptr, s);

@@ -33,6 +33,21 @@ enum { ROLE_MIRROR = 0, ROLE_REFRACT = 1, ROLE_FOCAL = 2, ROLE_OBSC = 3 };
 enum { AP_NONE = 0, AP_CIRCLE = 1, AP_ANNULUS = 2, AP_SECTOR = 3, AP_HEX = 4, AP_RECT = 5 };
 enum { ST_DETECTED = 1, ST_ABSORBED = 2, ST_OBSCURED = 3, ST_ESCAPED = 4, ST_MAXB = 5, ST_ERROR = 6 };
 
+// Feature profile of a kernel instantiation: the surface kinds and interactions whose code it
+// carries.  A geometry is traced by a profile that covers its features; leaving the others out
+// keeps the loop's instruction footprint small (instruction fetch was the kernels' top stall).
+enum : unsigned {
+    FT_ASPH = 1,       // even-asphere terms (Newton intersections)
+    FT_CYL = 2,        // cylinders
+    FT_BOX = 4,        // boxes
+    FT_CONE = 8,       // hexagonal Bezier cones
+    FT_REFR = 16,      // refracting faces
+    FT_CONE_CALL = 32, // the cone intersection out of line (not a feature: code placement)
+    FT_ALL = 31,
+    FT_TELESCOPE = FT_ASPH | FT_CYL | FT_BOX,  // mirrors, masts, camera boxes
+    FT_CONCENTRATOR = FT_CONE | FT_REFR,       // cones behind windows
+};
+
 // Surface record: REC values of the working precision T.
 //   [0..2] origin   [3..11] rows of the (tilted) local frame
 //   SAG:     [12] c  [13] 1+k  [14..21] A1..A8  [28] (1.1 r_bound)^2 (Newton seed domain)
@@ -382,9 +397,10 @@ __device__ __forceinline__ bool newton_step_fp64(const T* S, V3<T> p, V3<T> d, T
 // Ray vs SAG surface (local frame).  Quadric F = c (x^2 + y^2 + (1+k) z^2) - 2z,
 // sag branch (1+k) c z <= 1; both roots in ascending order, first valid one.
 // Aspheres: Newton from the first on-branch root beyond eps.
-template <bool C, typename T, typename SR>
+template <bool C, bool ASPH = true, typename T, typename SR>
 __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> d, T eps, T tmax, T tol, LHit<T>& h,
                                         bool& err, unsigned* cnt) {
+    if constexpr (!ASPH) asph = false;  // a profile without aspheres carries no Newton code
     CNT(U_SAG);
     const T c = S[F_C], k1 = S[F_K1];
     const T a = c * (d.x * d.x + d.y * d.y + k1 * d.z * d.z);
@@ -727,9 +743,14 @@ __device__ __forceinline__ void pair_advance(float& hi, float& lo, float t, floa
 // point (a grazing ray the FP32 search only just met); the caller then keeps the search's hit.
 // kap: the curvature bound to use at this hit (the profile's local curvature for a cone wall,
 // else the surface's bound).
+template <unsigned FEAT>
 __device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph, V3<float> ph, V3<float> plo,
                                            V3<float> d, float& dt, V3<float>& xl, V3<float>& nl, float& kap) {
     kap = S[F_KAP];
+    if constexpr ((FEAT & FT_ASPH) == 0) asph = false;
+    if (((FEAT & FT_CYL) == 0 && shape == SHAPE_CYL) || ((FEAT & FT_BOX) == 0 && shape == SHAPE_BOX) ||
+        ((FEAT & FT_CONE) == 0 && shape == SHAPE_HEXCONE))
+        return false;
     // local origin of the ray: (ph - O_hi) + (plo - O_lo), exact to the rounding of small numbers
     const float qx = __fadd_rn(__fsub_rn(ph.x, S[F_O]), __fsub_rn(plo.x, S[F_OL]));
     const float qy = __fadd_rn(__fsub_rn(ph.y, S[F_O + 1]), __fsub_rn(plo.y, S[F_OL + 1]));
@@ -771,90 +792,99 @@ __device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph,
             break;
         }
         case SHAPE_CYL: {
-            const float rad = S[F_C];
-            const float a = dl.x * dl.x + dl.y * dl.y;
-            const float b = p.x * dl.x + p.y * dl.y;
-            const float g = (p.x - rad) * (p.x + rad) + p.y * p.y;  // |p_xy|^2 - r^2
-            const float disc = b * b - a * g;
-            if (disc < 0.0f) return false;
-            const float q = -(b + copysignf(sqrtf(disc), b));
-            if (q == 0.0f) return false;
-            t = g / q;
-            const V3<float> x = p + t * dl;
-            xl = x;
-            nl = unit(mk(x.x, x.y, 0.0f));
+            if constexpr ((FEAT & FT_CYL) != 0) {
+                const float rad = S[F_C];
+                const float a = dl.x * dl.x + dl.y * dl.y;
+                const float b = p.x * dl.x + p.y * dl.y;
+                const float g = (p.x - rad) * (p.x + rad) + p.y * p.y;  // |p_xy|^2 - r^2
+                const float disc = b * b - a * g;
+                if (disc < 0.0f) return false;
+                const float q = -(b + copysignf(sqrtf(disc), b));
+                if (q == 0.0f) return false;
+                t = g / q;
+                const V3<float> x = p + t * dl;
+                xl = x;
+                nl = unit(mk(x.x, x.y, 0.0f));
+                break;
+            }
             break;
         }
         case SHAPE_BOX: {
-            // the face the point lies on: the axis where it is furthest out relative to the half extent
-            const float r0 = fabsf(p.x) / S[F_C], r1 = fabsf(p.y) / S[F_C + 1], r2 = fabsf(p.z) / S[F_C + 2];
-            const int ax = r0 >= r1 ? (r0 >= r2 ? 0 : 2) : (r1 >= r2 ? 1 : 2);
-            const float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z), dc = ax == 0 ? dl.x : (ax == 1 ? dl.y : dl.z);
-            if (dc == 0.0f) return false;
-            const float sg = pc >= 0.0f ? 1.0f : -1.0f;
-            t = (sg * S[F_C + ax] - pc) / dc;
-            xl = p + t * dl;
-            nl = mk(ax == 0 ? sg : 0.0f, ax == 1 ? sg : 0.0f, ax == 2 ? sg : 0.0f);
+            if constexpr ((FEAT & FT_BOX) != 0) {
+                // the face the point lies on: the axis where it is furthest out relative to the half extent
+                const float r0 = fabsf(p.x) / S[F_C], r1 = fabsf(p.y) / S[F_C + 1], r2 = fabsf(p.z) / S[F_C + 2];
+                const int ax = r0 >= r1 ? (r0 >= r2 ? 0 : 2) : (r1 >= r2 ? 1 : 2);
+                const float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z), dc = ax == 0 ? dl.x : (ax == 1 ? dl.y : dl.z);
+                if (dc == 0.0f) return false;
+                const float sg = pc >= 0.0f ? 1.0f : -1.0f;
+                t = (sg * S[F_C + ax] - pc) / dc;
+                xl = p + t * dl;
+                nl = mk(ax == 0 ? sg : 0.0f, ax == 1 ? sg : 0.0f, ax == 2 ? sg : 0.0f);
+                break;
+            }
             break;
         }
         case SHAPE_HEXCONE: {
-            // the wall whose wedge holds the point, then the profile root nearest the point
-            int j = 0;
-            float best = -3.0e38f;
-            for (int m = 0; m < 6; ++m) {
-                float cm, sm;
-                hex_dir(m, cm, sm);
-                const float v = p.x * cm + p.y * sm;
-                if (v > best) {
-                    best = v;
-                    j = m;
+            if constexpr ((FEAT & FT_CONE) != 0) {
+                // the wall whose wedge holds the point, then the profile root nearest the point
+                int j = 0;
+                float best = -3.0e38f;
+                for (int m = 0; m < 6; ++m) {
+                    float cm, sm;
+                    hex_dir(m, cm, sm);
+                    const float v = p.x * cm + p.y * sm;
+                    if (v > best) {
+                        best = v;
+                        j = m;
+                    }
                 }
-            }
-            float cj, sj;
-            hex_dir(j, cj, sj);
-            const float ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
-            const float za0 = S[F_C + 3], za1 = S[F_C + 4], za2 = S[F_C + 5];
-            const float q0 = best, dq = dl.x * cj + dl.y * sj;
-            const float den = dq * dq + dl.z * dl.z;
-            if (den == 0.0f) return false;
-            const float A = dl.z * ra2 - dq * za2, B = dl.z * ra1 - dq * za1;
-            const float C = dl.z * (ra0 - q0) - dq * (za0 - p.z);
-            // candidate roots in u; keep the one whose ray parameter is nearest 0
-            float us[2];
-            int nu = 0;
-            if (A == 0.0f) {
-                if (B != 0.0f) us[nu++] = -C / B;
-            } else {
-                const float disc = B * B - 4.0f * A * C;
-                if (disc < 0.0f) return false;
-                const float q = -0.5f * (B + copysignf(sqrtf(disc), B));
-                if (q != 0.0f) {
-                    us[nu++] = q / A;
-                    us[nu++] = C / q;
+                float cj, sj;
+                hex_dir(j, cj, sj);
+                const float ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
+                const float za0 = S[F_C + 3], za1 = S[F_C + 4], za2 = S[F_C + 5];
+                const float q0 = best, dq = dl.x * cj + dl.y * sj;
+                const float den = dq * dq + dl.z * dl.z;
+                if (den == 0.0f) return false;
+                const float A = dl.z * ra2 - dq * za2, B = dl.z * ra1 - dq * za1;
+                const float C = dl.z * (ra0 - q0) - dq * (za0 - p.z);
+                // candidate roots in u; keep the one whose ray parameter is nearest 0
+                float us[2];
+                int nu = 0;
+                if (A == 0.0f) {
+                    if (B != 0.0f) us[nu++] = -C / B;
+                } else {
+                    const float disc = B * B - 4.0f * A * C;
+                    if (disc < 0.0f) return false;
+                    const float q = -0.5f * (B + copysignf(sqrtf(disc), B));
+                    if (q != 0.0f) {
+                        us[nu++] = q / A;
+                        us[nu++] = C / q;
+                    }
                 }
-            }
-            bool got = false;
-            float bu = 0.0f;
-            for (int i = 0; i < nu; ++i) {
-                float u = us[i];
-                const float gp = 2.0f * A * u + B;
-                if (gp != 0.0f) u -= ((A * u + B) * u + C) / gp;
-                const float R = ra0 + u * (ra1 + u * ra2), Z = za0 + u * (za1 + u * za2);
-                const float tt = ((R - q0) * dq + (Z - p.z) * dl.z) / den;
-                if (!got || fabsf(tt) < fabsf(t)) {
-                    got = true;
-                    t = tt;
-                    bu = u;
+                bool got = false;
+                float bu = 0.0f;
+                for (int i = 0; i < nu; ++i) {
+                    float u = us[i];
+                    const float gp = 2.0f * A * u + B;
+                    if (gp != 0.0f) u -= ((A * u + B) * u + C) / gp;
+                    const float R = ra0 + u * (ra1 + u * ra2), Z = za0 + u * (za1 + u * za2);
+                    const float tt = ((R - q0) * dq + (Z - p.z) * dl.z) / den;
+                    if (!got || fabsf(tt) < fabsf(t)) {
+                        got = true;
+                        t = tt;
+                        bu = u;
+                    }
                 }
+                if (!got) return false;
+                xl = p + t * dl;
+                const float Rp = ra1 + 2.0f * ra2 * bu, Zp = za1 + 2.0f * za2 * bu;
+                nl = unit(mk(-Zp * cj, -Zp * sj, Rp));
+                // the wall is straight across the profile plane: its one curvature is the profile's,
+                // |r' z'' - z' r''| / (r'^2 + z'^2)^(3/2) at the hit, with a margin for the hit's error
+                const float q2 = Rp * Rp + Zp * Zp;
+                kap = 1.2f * fabsf(Rp * 2.0f * za2 - Zp * 2.0f * ra2) / (q2 * sqrtf(q2));
+                break;
             }
-            if (!got) return false;
-            xl = p + t * dl;
-            const float Rp = ra1 + 2.0f * ra2 * bu, Zp = za1 + 2.0f * za2 * bu;
-            nl = unit(mk(-Zp * cj, -Zp * sj, Rp));
-            // the wall is straight across the profile plane: its one curvature is the profile's,
-            // |r' z'' - z' r''| / (r'^2 + z'^2)^(3/2) at the hit, with a margin for the hit's error
-            const float q2 = Rp * Rp + Zp * Zp;
-            kap = 1.2f * fabsf(Rp * 2.0f * za2 - Zp * 2.0f * ra2) / (q2 * sqrtf(q2));
             break;
         }
         default: return false;
@@ -881,7 +911,7 @@ __device__ __noinline__ bool hit_hexcone_call(const T* S, V3<T> p, V3<T> d, T ep
     return hit_hexcone(S, p, d, eps, tmax, *h);
 }
 
-template <bool C, bool CONE_INLINE = true, typename T>
+template <bool C, unsigned FEAT = FT_ALL, typename T>
 __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
                                              unsigned* cnt) {
     CNT(U_REBASE);
@@ -893,22 +923,29 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
     bool ok = false, err = false;
     switch (shape) {
         case SHAPE_SAG:
-            ok = hit_sag<C>(S, (flags >> 8) & 15, (flags >> 12) & 1, pl, dl, eps, bst.t, tol, h, err, cnt);
+            ok = hit_sag<C, (FEAT & FT_ASPH) != 0>(S, (flags >> 8) & 15, (flags >> 12) & 1, pl, dl, eps, bst.t, tol, h,
+                                                   err, cnt);
             break;
         case SHAPE_CYL:
-            CNT(U_CYL);
-            ok = hit_cyl(S, pl, dl, eps, bst.t, h);
+            if constexpr ((FEAT & FT_CYL) != 0) {
+                CNT(U_CYL);
+                ok = hit_cyl(S, pl, dl, eps, bst.t, h);
+            }
             break;
         case SHAPE_BOX:
-            CNT(U_BOX);
-            ok = hit_box(S, pl, dl, eps, bst.t, h);
+            if constexpr ((FEAT & FT_BOX) != 0) {
+                CNT(U_BOX);
+                ok = hit_box(S, pl, dl, eps, bst.t, h);
+            }
             break;
         case SHAPE_HEXCONE:
-            if constexpr (C) cnt[U_HEXWALL] += 6u;
-            if constexpr (CONE_INLINE)
-                ok = hit_hexcone(S, pl, dl, eps, bst.t, h);
-            else
-                ok = hit_hexcone_call(S, pl, dl, eps, bst.t, &h);
+            if constexpr ((FEAT & FT_CONE) != 0) {
+                if constexpr (C) cnt[U_HEXWALL] += 6u;
+                if constexpr ((FEAT & FT_CONE_CALL) == 0)
+                    ok = hit_hexcone(S, pl, dl, eps, bst.t, h);
+                else
+                    ok = hit_hexcone_call(S, pl, dl, eps, bst.t, &h);
+            }
             break;
     }
     if (err) bst.err = true;
@@ -938,14 +975,14 @@ __device__ __forceinline__ float box_entry(const float* lo, const float* hi, flo
 
 constexpr int STACK = 32;
 
-template <bool C, bool CONE_INLINE = true, typename T>
+template <bool C, unsigned FEAT = FT_ALL, typename T>
 __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
                                             bool& overflow, unsigned* cnt) {
     bst.t = t_inf<T>();
     bst.sid = 0x7fffffff;
     bst.err = false;
     const int4 vr = tb.variants[var];
-    for (int k = 0; k < vr.z; ++k) test_surface<C, CONE_INLINE>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
+    for (int k = 0; k < vr.z; ++k) test_surface<C, FEAT>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
     if (vr.x < 0) return;
     // Inverse direction with zero components replaced by +-1e-30, so that the
     // FMA slab form never meets inf - inf (the boxes are padded, so a ray grazing
@@ -1002,7 +1039,7 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
             }
         }
         if (ref < 0) break;
-        for (int k = 0; k < n; ++k) test_surface<C, CONE_INLINE>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
+        for (int k = 0; k < n; ++k) test_surface<C, FEAT>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
         update_tc();
         pop(ref, n);
     }
@@ -1145,10 +1182,13 @@ constexpr float EST_KT = 1.0f * EST_U, EST_KA = 2.0f * EST_U, EST_KW = 5.0f * ES
                 EST_KN = 1.0f * EST_U, EST_KD = 1.5f * EST_U;
 constexpr float EST_KR2 = 2.5f * EST_U;  // a reflection's fresh direction rounding: hypot(2 KN, KD)
 
-template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false, typename IO = T>
+template <typename T, int BLOCK, bool C = false, bool STAGED = true, bool SRC = false, typename IO = T,
+          unsigned FEAT = FT_ALL>
 __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks)) trace_kernel(TraceArgs<T, IO> A) {
     // the FP32 form carries a running error estimate; the counting build and FP64 do not
     constexpr bool EST = sizeof(T) == 4 && !C;
+    // the plain FP32 kernel keeps the cone intersection out of line (it sits at its register cap)
+    constexpr unsigned FH = FEAT | ((!SRC && sizeof(T) == 4) ? (unsigned)FT_CONE_CALL : 0u);
     unsigned cnt[U_N];
     if constexpr (C) {
 #pragma unroll
@@ -1281,7 +1321,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         V3<T> fpos = mk(T(0), T(0), T(0));
         const bool bad_var = ph.bad || ph.var < 0 || ph.var >= tb.n_var;  // never index past the variant table
         if (!bad_var)
-            nearest_hit<C, SRC || sizeof(T) == 8>(tb, ph.var, ph.p, ph.d, A.eps, A.newton_tol, bst, overflow, cnt);
+            nearest_hit<C, FH>(tb, ph.var, ph.p, ph.d, A.eps, A.newton_tol, bst, overflow, cnt);
         if (bad_var || overflow || bst.err) {
             status = ST_ERROR;
         } else if (bst.sid == 0x7fffffff) {
@@ -1304,7 +1344,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                 CNT(U_REFINE);
                 // accepted only as a correction of the search's own rounding (a grazing ray
                 // whose re-solve lands on the other root keeps the search's hit)
-                if (refine_hit(S, si.x & 15, (si.x >> 12) & 1, ph.p, ph.plo, ph.d, dt, xl, nl, kap) &&
+                if (refine_hit<FEAT>(S, si.x & 15, (si.x >> 12) & 1, ph.p, ph.plo, ph.d, dt, xl, nl, kap) &&
                     fabsf(dt) <= 1e-4f * e_s) {
                     e_kap = kap;
                     pair_advance(ph.p.x, ph.plo.x, dt, ph.d.x);
@@ -1416,7 +1456,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         }
                     }
                 }
-            } else {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
+            } else if constexpr ((FEAT & FT_REFR) != 0) {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
                 w = philox4x32_10(ctr, key);
                 CNT(U_PHILOX);
                 const int med = front ? si.z : si.w;
@@ -1427,7 +1467,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     if (!(unit_open<T>(w.w) < surv)) status = ST_ABSORBED;
                 }
             }
-            if (status == 0 && role == ROLE_REFRACT) {
+            if ((FEAT & FT_REFR) != 0 && status == 0 && role == ROLE_REFRACT) {
                 T na, nb;
                 if constexpr (sizeof(T) == 4) {  // FP32 copy of the medium records: no FP64 instruction
                     na = refr_index<T>(meds32(tb) + (size_t)si.z * MED_REC, ph.lam);
