@@ -9,9 +9,12 @@ namespace robast {
 
 // Occupancy: resident blocks of trace_kernel<T, block> per SM for `smem`
 // bytes of dynamic shared memory (0 if the configuration cannot launch); prof: the feature
-// profile (FT_ALL, FT_TELESCOPE for plain traces, FT_CONCENTRATOR for source mode).
+// profile (FT_ALL, FT_TELESCOPE for plain traces, FT_CONCENTRATOR for source mode).  The
+// source-mode halves live in their own translation units (trace_f32_src.cu, trace_f64_src.cu).
 int trace_blocks_per_sm_f32(int block, size_t smem, bool src, unsigned prof);
-int trace_blocks_per_sm_f64(int block, size_t smem, bool src);
+int trace_blocks_per_sm_f64(int block, size_t smem, bool src, unsigned prof);
+int trace_blocks_per_sm_f32_src(int block, size_t smem, unsigned prof);
+int trace_blocks_per_sm_f64_src(int block, size_t smem, unsigned prof);
 
 // Gradient pass (grad.cu): frozen-path objective sums and per-parameter sums, 128-bit fixed
 // point (two u64 words each: fraction, integer part).
@@ -56,14 +59,16 @@ cudaError_t build_order_f64(const double* o, long long n, void* scratch, int** o
 // Launch the persistent trace kernel; returns the cudaError_t of the launch.
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s,
                              unsigned prof);
-// the source-mode half of the FP32 instantiations (trace_f32_src.cu)
-int trace_blocks_per_sm_f32_src(int block, size_t smem, unsigned prof);
 cudaError_t launch_trace_f32_src(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s,
                                  unsigned prof);
-cudaError_t launch_trace_f64(const TraceArgs<double>& a, int block, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_trace_f64(const TraceArgs<double>& a, int block, int grid, size_t smem, cudaStream_t s,
+                             unsigned prof);
+cudaError_t launch_trace_f64_src(const TraceArgs<double>& a, int block, int grid, size_t smem, cudaStream_t s,
+                                 unsigned prof);
 
-// FP64 re-trace of the FP32 photons queued by the accuracy guard (block 128).
-int retrace_blocks_per_sm(size_t smem, bool src);
-cudaError_t launch_retrace(const TraceArgs<double, float>& a, int grid, size_t smem, cudaStream_t s);
+// FP64 re-trace of the FP32 photons queued by the accuracy guard (block 128; prof: the FP32
+// launch's feature profile).
+int retrace_blocks_per_sm(size_t smem, bool src, unsigned prof);
+cudaError_t launch_retrace(const TraceArgs<double, float>& a, int grid, size_t smem, cudaStream_t s, unsigned prof);
 
 }  // namespace robast

@@ -918,8 +918,9 @@ static const double kGuardFrac = 0.8;
 // its own re-trace launch, so the queue (one entry per photon of a chunk) never overflows.
 static const long long kSrcChunk = 1LL << 27;
 
-// The feature profile of the FP32 kernel that traces g: the reduced ones where they cover the
-// geometry's features (telescopes in plain traces, concentrators in source mode), else all.
+// The feature profile of the kernel that traces g (FP32 or FP64, and the FP32 trace's FP64
+// re-trace): the reduced ones where they cover the geometry's features (telescopes in plain
+// traces, concentrators in source mode), else all.
 static unsigned trace_profile(const robast_geom* g, bool src) {
     if (!src && (g->feat & ~(unsigned)FT_TELESCOPE) == 0) return FT_TELESCOPE;
     if (src && (g->feat & ~(unsigned)FT_CONCENTRATOR) == 0) return FT_CONCENTRATOR;
@@ -969,13 +970,13 @@ static cudaError_t launch_retrace_of(const robast_geom* g, robast_geom* gm, cons
     std::atomic<int>& slot = gm->bps_retrace[src ? 1 : 0];
     int bps_r = slot.load(std::memory_order_relaxed);
     if (bps_r <= 0) {
-        bps_r = retrace_blocks_per_sm(smem_r, src);
+        bps_r = retrace_blocks_per_sm(smem_r, src, trace_profile(g, src));
         if (bps_r > 0) slot.store(bps_r, std::memory_order_relaxed);
     }
     if (bps_r <= 0) return cudaErrorInvalidConfiguration;
     long long grid_r = (long long)g->num_sms * bps_r;
     grid_r = std::max(1LL, std::min(grid_r, (qcap + 127) / 128));
-    return launch_retrace(r, (int)grid_r, smem_r, s);
+    return launch_retrace(r, (int)grid_r, smem_r, s, trace_profile(g, src));
 }
 
 template <typename T>
@@ -1052,7 +1053,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     int bps = bps_slot.load(std::memory_order_relaxed);
     if (bps <= 0) {
         bps = sizeof(T) == 4 ? trace_blocks_per_sm_f32(block, smem, src != nullptr, trace_profile(g, src != nullptr))
-                             : trace_blocks_per_sm_f64(block, smem, src != nullptr);
+                             : trace_blocks_per_sm_f64(block, smem, src != nullptr, trace_profile(g, src != nullptr));
         if (bps > 0) bps_slot.store(bps, std::memory_order_relaxed);
     }
     if (bps <= 0) return fail(ROBAST_E_CUDA, "robast_trace: kernel cannot launch with %zu bytes of shared memory", smem);
@@ -1123,7 +1124,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
         if constexpr (sizeof(T) == 4)
             e = launch_trace_f32(a, block, (int)grid, smem, s, trace_profile(g, src != nullptr));
         else
-            e = launch_trace_f64(a, block, (int)grid, smem, s);
+            e = launch_trace_f64(a, block, (int)grid, smem, s, trace_profile(g, src != nullptr));
         if (e == cudaSuccess && guard) e = launch_retrace_of(g, gm, a, qhdr, qcap, eps, src != nullptr, s);
     }
     if (ord_scratch) cudaFreeAsync(ord_scratch, s);

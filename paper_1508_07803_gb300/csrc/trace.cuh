@@ -1163,10 +1163,14 @@ struct Photon {
 #ifndef ROBAST_TRACE_MIN_BLOCKS_SRC
 #define ROBAST_TRACE_MIN_BLOCKS_SRC 1  // source mode: uncapped (swept 1, 3, 4; the 128-register cap spills and runs 25% slower)
 #endif
+#ifndef ROBAST_TRACE_MIN_BLOCKS_F64
+#define ROBAST_TRACE_MIN_BLOCKS_F64 1  // FP64: uncapped
+#endif
 template <typename T, int BLOCK, bool SRC = false>
 struct TraceBounds {
-    static constexpr int mb = SRC ? ROBAST_TRACE_MIN_BLOCKS_SRC : ROBAST_TRACE_MIN_BLOCKS;
-    static constexpr int min_blocks = sizeof(T) == 4 && (mb * 128) / BLOCK > 0 ? (mb * 128) / BLOCK : 1;
+    static constexpr int mb =
+        sizeof(T) == 8 ? ROBAST_TRACE_MIN_BLOCKS_F64 : SRC ? ROBAST_TRACE_MIN_BLOCKS_SRC : ROBAST_TRACE_MIN_BLOCKS;
+    static constexpr int min_blocks = (mb * 128) / BLOCK > 0 ? (mb * 128) / BLOCK : 1;
 };
 
 // Rounding units of the FP32 error estimate, per interaction, in ulps of the hit's coordinate
