@@ -259,7 +259,9 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
     scene, groups = W.cone_batch(n_variants=64, angles_deg=W.CONE_ANGLES_DEG,
                                  n_per_group=args.batch_photons_per_group, seed=0)
     geom = robast.build_geometry(scene)
-    if args.no_autotune:
+    if args.batch_shape:
+        (block, bps, rfm), table = _shape(args.batch_shape), {}
+    elif args.no_autotune:
         (block, bps, rfm), table = (0, 0, 0), {}
     else:
         (block, bps, rfm), table = autotune.tune_sources(geom, groups, precision=32, max_bounces=30, stream=stream)
@@ -595,7 +597,12 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
                        "timing": "host wall clock around the synchronous call (value returned to the host)"}}
 
 
-TRAFFIC_SOURCES = ("trace.cuh", "order.cu")  # the kernel and the processing order that shapes its DRAM traffic
+def _shape(text):
+    b, k, r = (int(v) for v in text.split(","))
+    return b, k, r
+
+
+TRAFFIC_SOURCES = ("trace.cuh", "trace_f32.cu", "order.cu")  # the kernel and the processing order that shapes its DRAM traffic
 
 
 def traffic_source_hash():
@@ -642,6 +649,10 @@ def main():
     ap.add_argument("--no-tolerance", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="library launch defaults instead of the tuners (keeps profiler launch counts small)")
+    ap.add_argument("--trace-shape", default=None,
+                    help="block,blocks_per_sm,refill_min for the plain traces instead of the tuner (profiler runs)")
+    ap.add_argument("--batch-shape", default=None,
+                    help="block,blocks_per_sm,refill_min for the batched trace instead of the tuner (profiler runs)")
     ap.add_argument("--grad-photons-per-dish", type=int, default=1_000_000)
     ap.add_argument("--grad-steps", type=int, default=3)
     ap.add_argument("--grad-cone-photons", type=int, default=1_000_000)
@@ -701,7 +712,9 @@ def main():
         wins = [(k * npa, npa) for k in range(n_angles)]
         # launch shape and refill threshold from the autotuner (on the first 2e6 photons, untimed)
         from paper_1508_07803_gb300 import autotune
-        if args.no_autotune:
+        if args.trace_shape:
+            (blk, bps, rfm), table = _shape(args.trace_shape), {}
+        elif args.no_autotune:
             (blk, bps, rfm), table = (0, 0, 0), {}
         else:
             (blk, bps, rfm), table = autotune.tune_trace(geom, o, d, w, precision=precision, stream=stream)

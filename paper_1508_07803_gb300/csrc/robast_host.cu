@@ -919,11 +919,11 @@ static const double kGuardFrac = 0.8;
 static const long long kSrcChunk = 1LL << 27;
 
 // The feature profile of the kernel that traces g (FP32 or FP64, and the FP32 trace's FP64
-// re-trace): the reduced ones where they cover the geometry's features (telescopes in plain
-// traces, concentrators in source mode), else all.
+// re-trace): a reduced one where it covers the geometry's features (telescopes in plain
+// traces, concentrators in either mode), else all.
 static unsigned trace_profile(const robast_geom* g, bool src) {
     if (!src && (g->feat & ~(unsigned)FT_TELESCOPE) == 0) return FT_TELESCOPE;
-    if (src && (g->feat & ~(unsigned)FT_CONCENTRATOR) == 0) return FT_CONCENTRATOR;
+    if ((g->feat & ~(unsigned)FT_CONCENTRATOR) == 0) return FT_CONCENTRATOR;
     return FT_ALL;
 }
 

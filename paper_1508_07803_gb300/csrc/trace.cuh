@@ -627,6 +627,9 @@ __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tma
     // skipped; the in-wedge test at the hit point below is unchanged, so the result is too.
     // margin: 1e-5 of the scale of any point p + t d, t <= best, far above the in-wedge test's rounding
     const T mg = T(1e-5) * (t_abs(p.x) + t_abs(p.y) + t_abs(d.x) + t_abs(d.y) + T(1e-30));
+    // the wall and root loops stay rolled: one copy of the wall code keeps the kernel's
+    // instruction footprint small (warps of a concentrator trace sit in different code paths)
+#pragma unroll 1
     for (int j = 0; j < 6; ++j) {
         T cjj, sjj;
         dir(j, cjj, sjj);
@@ -665,6 +668,7 @@ __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tma
                 }
             }
         }
+#pragma unroll 1
         for (int i = 0; i < nu; ++i) {
             T u = us[i];
             const T gp = T(2) * A * u + B;
@@ -1394,6 +1398,11 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                 ph.eh = est_hyp(e_l, e_a);
                 e_n = est_hyp(e_kap * (e_l + e_a * e_sn), EST_KN);
             }
+            // one call site for the draw (a front-side mirror hit or a refracting face)
+            if ((role == ROLE_MIRROR && front) || ((FEAT & FT_REFR) != 0 && role == ROLE_REFRACT)) {
+                w = philox4x32_10(ctr, key);
+                CNT(U_PHILOX);
+            }
             if (role == ROLE_OBSC) {
                 status = ST_OBSCURED;
             } else if (role == ROLE_FOCAL) {
@@ -1407,8 +1416,6 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                 if (!front) {
                     status = ST_OBSCURED;
                 } else {
-                    w = philox4x32_10(ctr, key);
-                    CNT(U_PHILOX);
                     const double* M = tb.mats + (size_t)si.y * MAT_REC;
                     bool survive;
                     if constexpr (sizeof(T) == 4) {
@@ -1461,8 +1468,6 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     }
                 }
             } else if constexpr ((FEAT & FT_REFR) != 0) {  // ROLE_REFRACT: bulk absorption of the segment, then Snell + unpolarised Fresnel
-                w = philox4x32_10(ctr, key);
-                CNT(U_PHILOX);
                 const int med = front ? si.z : si.w;
                 const T len = sizeof(T) == 4 ? abs_length<T>(meds32(tb) + (size_t)med * MED_REC, ph.lam)
                                              : abs_length<T>(tb.meds + (size_t)med * MED_REC, ph.lam);

@@ -1,6 +1,7 @@
-// float instantiations of the plain persistent trace kernel (see trace.cuh): the full profile
-// for every launch shape and the telescope profile (mirrors, masts and camera boxes); the
-// source-mode instantiations are in trace_f32_src.cu (a separate unit, compiled in parallel).
+// float instantiations of the plain persistent trace kernel (see trace.cuh): the full profile,
+// the telescope profile (mirrors, masts and camera boxes) and the concentrator profile (cones
+// and refracting faces) for every launch shape; the source-mode instantiations are in
+// trace_f32_src.cu (a separate unit, compiled in parallel).
 #include "launch.h"
 
 namespace robast {
@@ -30,8 +31,8 @@ static int occupancy_one(size_t smem) {
 
 template <int BLOCK, bool SRC>
 static int occupancy_prof(size_t smem, unsigned prof) {
-    if (prof == FT_TELESCOPE && !SRC) return occupancy_one<BLOCK, SRC, FT_TELESCOPE>(smem);
-    if (prof == FT_CONCENTRATOR && SRC) return occupancy_one<BLOCK, SRC, FT_CONCENTRATOR>(smem);
+    if (prof == FT_TELESCOPE) return occupancy_one<BLOCK, SRC, FT_TELESCOPE>(smem);
+    if (prof == FT_CONCENTRATOR) return occupancy_one<BLOCK, SRC, FT_CONCENTRATOR>(smem);
     return occupancy_one<BLOCK, SRC, FT_ALL>(smem);
 }
 
@@ -49,10 +50,10 @@ int trace_blocks_per_sm_f32(int block, size_t smem, bool src, unsigned prof) {
 template <int BLOCK, bool SRC>
 static cudaError_t launch_prof(const TraceArgs<float>& a, int grid, size_t smem, cudaStream_t s, unsigned prof) {
     const bool st = a.stage != 0;
-    if (prof == FT_TELESCOPE && !SRC)
+    if (prof == FT_TELESCOPE)
         return st ? launch_one<BLOCK, false, true, SRC, FT_TELESCOPE>(a, grid, smem, s)
                   : launch_one<BLOCK, false, false, SRC, FT_TELESCOPE>(a, grid, smem, s);
-    if (prof == FT_CONCENTRATOR && SRC)
+    if (prof == FT_CONCENTRATOR)
         return st ? launch_one<BLOCK, false, true, SRC, FT_CONCENTRATOR>(a, grid, smem, s)
                   : launch_one<BLOCK, false, false, SRC, FT_CONCENTRATOR>(a, grid, smem, s);
     return st ? launch_one<BLOCK, false, true, SRC, FT_ALL>(a, grid, smem, s)

@@ -1,6 +1,6 @@
-// double instantiations of the plain persistent trace kernel (see trace.cuh): the full profile
-// and the telescope profile (mirrors, masts and camera boxes) for every launch shape, and the
-// counting build; the source-mode and re-trace instantiations are in trace_f64_src.cu.
+// double instantiations of the plain persistent trace kernel (see trace.cuh): the full,
+// telescope and concentrator profiles for every launch shape, and the counting build; the
+// source-mode and re-trace instantiations are in trace_f64_src.cu.
 #include "launch.h"
 
 namespace robast {
@@ -30,7 +30,9 @@ static int occupancy_one(size_t smem) {
 
 template <int BLOCK>
 static int occupancy_prof(size_t smem, unsigned prof) {
-    return prof == FT_TELESCOPE ? occupancy_one<BLOCK, FT_TELESCOPE>(smem) : occupancy_one<BLOCK, FT_ALL>(smem);
+    if (prof == FT_TELESCOPE) return occupancy_one<BLOCK, FT_TELESCOPE>(smem);
+    if (prof == FT_CONCENTRATOR) return occupancy_one<BLOCK, FT_CONCENTRATOR>(smem);
+    return occupancy_one<BLOCK, FT_ALL>(smem);
 }
 
 int trace_blocks_per_sm_f64(int block, size_t smem, bool src, unsigned prof) {
@@ -49,6 +51,9 @@ static cudaError_t launch_prof(const TraceArgs<double>& a, int grid, size_t smem
     if (prof == FT_TELESCOPE)
         return st ? launch_one<BLOCK, false, true, FT_TELESCOPE>(a, grid, smem, s)
                   : launch_one<BLOCK, false, false, FT_TELESCOPE>(a, grid, smem, s);
+    if (prof == FT_CONCENTRATOR)
+        return st ? launch_one<BLOCK, false, true, FT_CONCENTRATOR>(a, grid, smem, s)
+                  : launch_one<BLOCK, false, false, FT_CONCENTRATOR>(a, grid, smem, s);
     return st ? launch_one<BLOCK, false, true, FT_ALL>(a, grid, smem, s)
               : launch_one<BLOCK, false, false, FT_ALL>(a, grid, smem, s);
 }

@@ -80,7 +80,9 @@ int retrace_blocks_per_sm(size_t smem, bool src, unsigned prof) {
     if (src)
         return prof == FT_CONCENTRATOR ? retrace_occupancy<true, FT_CONCENTRATOR>(smem)
                                        : retrace_occupancy<true, FT_ALL>(smem);
-    return prof == FT_TELESCOPE ? retrace_occupancy<false, FT_TELESCOPE>(smem) : retrace_occupancy<false, FT_ALL>(smem);
+    if (prof == FT_TELESCOPE) return retrace_occupancy<false, FT_TELESCOPE>(smem);
+    if (prof == FT_CONCENTRATOR) return retrace_occupancy<false, FT_CONCENTRATOR>(smem);
+    return retrace_occupancy<false, FT_ALL>(smem);
 }
 
 template <bool SRC, unsigned FEAT>
@@ -98,8 +100,9 @@ cudaError_t launch_retrace(const TraceArgs<double, float>& a, int grid, size_t s
     if (a.groups)
         return prof == FT_CONCENTRATOR ? launch_re<true, FT_CONCENTRATOR>(a, grid, smem, s)
                                        : launch_re<true, FT_ALL>(a, grid, smem, s);
-    return prof == FT_TELESCOPE ? launch_re<false, FT_TELESCOPE>(a, grid, smem, s)
-                                : launch_re<false, FT_ALL>(a, grid, smem, s);
+    if (prof == FT_TELESCOPE) return launch_re<false, FT_TELESCOPE>(a, grid, smem, s);
+    if (prof == FT_CONCENTRATOR) return launch_re<false, FT_CONCENTRATOR>(a, grid, smem, s);
+    return launch_re<false, FT_ALL>(a, grid, smem, s);
 }
 
 }  // namespace robast
