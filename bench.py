@@ -317,6 +317,18 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
                          block_size=128, work_units=units_t, accuracy=False)
     torch.cuda.synchronize()
     units = {k: v * frac for k, v in zip(robast.UNIT_NAMES, units_t.cpu().tolist())}
+    # the accuracy guard's share, timed on the same sample: the FP32 launch alone, then with the guard
+    gms = []
+    for acc in (False, None):
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        robast.trace_sources(geom, ssrc, scounts, seed=0, precision=32, max_bounces=30, stream=stream,
+                             block_size=block, blocks_per_sm=bps, refill_min=rfm, accuracy=acc)
+        g1.record(stream)
+        g1.synchronize()
+        gms.append(g0.elapsed_time(g1))
+    guard = {"sample": "1/20 of every group", "fp32_trace_ms": gms[0], "with_guard_ms": gms[1],
+             "guard_ms": gms[1] - gms[0]}
     ssrc.close()
     kern_ms = ms / args.batch_steps
     roof = roofline_of(units, kern_ms, peak32, "robast::trace_kernel<float,SRC> (+ FP64 re-trace)",
@@ -329,6 +341,7 @@ def measure_batched(args, geom_dev, stream, ws, rank, max_over_ranks, sum_over_r
             "steps": args.batch_steps, "photons_per_step": src.n_photons,
             "bounces_per_step": bounces / args.batch_steps / ws,
             "fp64_retraced_per_step": rt[0] // args.batch_steps, "over_bound_not_retraced": rt[1],
+            "guard": dict(guard, retraced_fraction=(rt[0] // args.batch_steps) / src.n_photons),
             "roofline": roof,
             "config": {"workload": "hex_bezier_cone_64_variants_x_41_angles", "variants": 64,
                        "angles_deg": [0, 40, 1], "photons_per_group": args.batch_photons_per_group,
@@ -491,22 +504,38 @@ GRAD_INTERACTION_FLOPS = 158
 GRAD_DUAL_FACTOR = 17
 
 
-def grad_roofline(units, ms_per_eval, peak64):
+def grad_roofline(units, ms_per_eval, peak64, peak32=None, r64=True):
+    """ALU roofline of the gradient launch: the forward pass's interactions run in FP64, the
+    replays and the dual-number interactions in the derivative precision (FP32 for an FP32 dish
+    batch, FP64 through cone walls).  achieved = FLOPs / time; peak = the FLOP-weighted harmonic
+    mean of the two measured peaks (the time the same FLOPs take at peak on each pipe)."""
     fwd, rep, dual = units
-    flops = (fwd + rep) * GRAD_INTERACTION_FLOPS + dual * GRAD_INTERACTION_FLOPS * GRAD_DUAL_FACTOR
+    f64 = fwd * GRAD_INTERACTION_FLOPS
+    fr = rep * GRAD_INTERACTION_FLOPS + dual * GRAD_INTERACTION_FLOPS * GRAD_DUAL_FACTOR
+    if r64 or peak32 is None:
+        f64, fr, pr = f64 + fr, 0.0, peak64
+    else:
+        pr = peak32
+    flops = f64 + fr
+    t_peak = f64 / peak64 + (fr / pr if fr else 0.0)
+    peak = flops / t_peak if t_peak > 0 else peak64
     achieved = flops / (ms_per_eval * 1e-3)
-    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak64, "kernel": "robast::grad_kernel<float> (adjoint, FP64 duals)",
-            "flops_per_eval": flops, "work_units_per_eval": {"fwd_interactions": fwd, "replayed_interactions": rep,
-                                                             "dual_interactions": dual},
-            "peak_source": "DFMA throughput probe robast_measure_alu_peak on this GPU (measured); FLOPs per "
-                           "interaction estimated from the operation counts"}
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "kernel": "robast::grad_kernel<float, " + ("double" if r64 else "float") + "> (adjoint)",
+            "flops_per_eval": flops, "fp64_flops_per_eval": f64,
+            "work_units_per_eval": {"fwd_interactions": fwd, "replayed_interactions": rep,
+                                    "dual_interactions": dual},
+            "peak_source": "DFMA and FFMA throughput probes robast_measure_alu_peak on this GPU (measured), "
+                           "weighted by the FP64 and FP32 FLOPs; FLOPs per interaction estimated from the "
+                           "operation counts"}
 
 
 def measure_grad_cone(args, dev, stream, ws, rank, max_over_ranks, barrier):
     """Soft collection efficiency of a Bezier hexagonal cone behind its window and its gradient
     with respect to the 6 control-point coordinates of the wall profile: 1e6 photons over
-    incidence angles 0-30 deg (FP32 trace, FP64 adjoint).  Metric: gradient evaluations/s."""
+    incidence angles 0-30 deg (FP32 trace; derivative passes in FP64 through the cone walls, whose
+    grazing roots need it).  Metric: gradient evaluations/s."""
     import math
     import torch
     import paper_1508_07803_gb300 as robast
@@ -552,7 +581,7 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
     photons each over field angles 0-2 deg, one evaluation = the summed
     mean-squared spot radius of the 32 dishes AND its gradient with respect to
     every facet's two tilts and eight aspheric coefficients, in one launch
-    (FP32 trace, FP64 dual re-intersection and sums).  Dish v is lit at the
+    (FP32 trace and derivative passes, FP64 forward values, fixed-point sums).  Dish v is lit at the
     field angle 2 v / 31 deg.  Metric: gradient evaluations/s."""
     import torch
     import paper_1508_07803_gb300 as robast
@@ -586,7 +615,7 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
                       work_units=units, grad=False)
     geom.close()
     return {"value": ws * args.grad_steps / dt, "unit": "grad evals/s", "ms_per_eval": 1e3 * dt / args.grad_steps,
-            "roofline": grad_roofline(units.cpu().tolist(), 1e3 * dt / args.grad_steps, args.peak64),
+            "roofline": grad_roofline(units.cpu().tolist(), 1e3 * dt / args.grad_steps, args.peak64, args.peak32, r64=False),
             "photons_per_eval": int(b.n), "photons_per_s": ws * args.grad_steps * b.n / dt,
             "objective": "sum over 32 dishes of the mean-squared spot radius (frozen path, expected weights)",
             "objective_value_m2": value, "gradient_norm": gn, "n_params": int(geom.n_surfaces * robast.N_PARAM),
@@ -760,10 +789,23 @@ def main():
         clk = clocks.stop() if clocks else None
         c = counters.cpu().tolist()
         rt = out["retraced"].cpu().tolist() if "retraced" in out else [0, 0]
+        guard = None
+        if precision == 32:
+            # the accuracy guard's share of the trace: one FP32 launch without it (after the timed region)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            robast.trace(geom, o, d, w, seed=0, precision=precision, first_photon_id=first_id, out=out,
+                         stream=stream, block_size=blk, blocks_per_sm=bps, refill_min=rfm, accuracy=False)
+            g1.record(stream)
+            g1.synchronize()
+            f32_ms = g0.elapsed_time(g1)
+            guard = {"fp32_trace_ms": f32_ms, "with_guard_ms": statistics.mean(kern_ms),
+                     "guard_ms": statistics.mean(kern_ms) - f32_ms,
+                     "retraced_fraction": (rt[0] // steps) / N}
         geom.close()
         return {"ms": ms, "kernel_ms": kern_ms, "bounces": c[0], "counters": c, "units": units, "psf": last,
                 "clocks": clk, "launches": steps * (order_launches + trace_launches + psf_launches),
-                "retraced_per_step": rt[0] // steps, "over_bound_not_retraced": rt[1],
+                "retraced_per_step": rt[0] // steps, "over_bound_not_retraced": rt[1], "guard": guard,
                 "autotune": {"block": blk, "blocks_per_sm": bps, "refill_min": rfm,
                              "candidates_ms": {f"{b}x{p}/r{r}": round(t, 3) for (b, p, r), t in table.items()}}}
 
@@ -778,12 +820,14 @@ def main():
         if precision == 32:
             f["fp64_retraced_per_step"] = m["retraced_per_step"]
             f["over_bound_not_retraced"] = m["over_bound_not_retraced"]
+            f["guard"] = m["guard"]
         f["autotune"] = m["autotune"]
         return f
 
     peak32 = robast.measure_alu_peak(32)
     peak64 = robast.measure_alu_peak(64)
     args.peak64 = peak64
+    args.peak32 = peak32
     npa = args.photons_per_angle
     scene, bundle = W.lst_workload(npa, seed=rank)
     N = bundle.n

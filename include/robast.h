@@ -420,14 +420,18 @@ int robast_param_layout(const robast_geom* g, robast_param_info* out);
  * of its objective terms with respect to the ray state is carried backwards
  * through its interactions; the state before each interaction is
  * recomputed from the photon's inputs (nothing per bounce is stored) and the
- * interaction is evaluated in FP64 dual numbers seeded on that state and on
- * the surface's parameters.  Sums over photons are 128-bit fixed point with
- * integer atomics: repeated calls give identical bits.  info (HOST, 8
- * doubles, may be NULL; totals over variants): W, sum w q_x, sum w q_y,
- * sum w |q|^2, sum w sigmoid, N_detected, photons whose path had more than
- * 64 interactions (untracked: no gradient), N (photons with an invalid
- * variant index are skipped).  Synchronises the stream; uses device scratch
- * owned by g.
+ * interaction is evaluated in dual numbers seeded on that state and on the
+ * surface's parameters.  The recomputations and dual numbers run in the
+ * trace precision, except that an FP32 trace of a geometry with HEXCONE
+ * surfaces runs them in FP64 (grazing Bezier roots); each dual evaluation
+ * starts just short of its hit, in axes shifted to the surface's origin.
+ * Sums over photons are 128-bit fixed point with integer atomics: repeated
+ * calls give identical bits.  info (HOST, 8 doubles, may be NULL; totals
+ * over variants): W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid,
+ * N_detected, untracked photons (no gradient: a path of more than 64
+ * interactions, or a recomputation that no longer met its surface), N
+ * (photons with an invalid variant index are skipped).  Synchronises the
+ * stream; uses device scratch owned by g.
  */
 int robast_trace_grad(robast_geom* g, const void* origins, const void* dirs, const void* wavelengths, int64_t n,
                       uint64_t seed, int32_t objective, double tau, double d_obj, double* value, double* d_params,

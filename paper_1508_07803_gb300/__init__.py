@@ -577,7 +577,8 @@ def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed
     Returns (value, grad [n_surfaces, 16] float64 CUDA tensor or None, info dict).
     `out`, if given, is a float64 CUDA tensor [n_surfaces, 16] the gradient is added to.
     work_units: optional CUDA int64 tensor [>= 3], added to: FP64 interactions of the
-    forward passes, interactions replayed by the reverse sweeps, dual-number interactions.
+    forward passes, interactions replayed by the reverse sweeps, dual-number interactions
+    (the last two in the derivative precision: the trace's, or FP64 for geometries with cones).
     """
     import torch
     lib = load()
@@ -609,8 +610,9 @@ def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed
     res = dict(zip(keys, list(info)))
     if res["n_untracked"] > 0:
         import warnings
-        warnings.warn(f"trace_grad: {int(res['n_untracked'])} photons had paths longer than the adjoint's "
-                      f"64-interaction record and contribute no gradient", RuntimeWarning)
+        warnings.warn(f"trace_grad: {int(res['n_untracked'])} photons contribute no gradient (a path longer than "
+                      f"the adjoint's 64-interaction record, or a recomputed interaction that no longer met "
+                      f"its surface)", RuntimeWarning)
     return val.value, g, res
 
 

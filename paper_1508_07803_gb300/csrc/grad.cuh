@@ -38,7 +38,9 @@ namespace robast {
 
 constexpr int GW = 16;        // dual slots: 6 ray-state components, then 10 surface parameters
 constexpr int GMAXB = 64;     // interactions a path may have and still be differentiated
-using DX = Dn<double, GW>;
+// dual numbers of the derivative passes, in the trace precision R
+template <typename R>
+using DR = Dn<R, GW>;
 
 // ------------------------------------------------------------ fixed point
 // a[0] = low word (fraction, 2^-64 units), a[1] = high word (integer part, two's complement).
@@ -71,31 +73,35 @@ __device__ __forceinline__ double refl_value(const double* M, double lam) {
     return R[i] + (R[i + 1] - R[i]) * ((lam - L[i]) / (L[i + 1] - L[i]));
 }
 
-// Record accessor of the gradient pass: FP64 record values, with derivative slots 6.. for the
-// parameters of a differentiable surface (mode 1, SAG mirror: tilt x, y -> slots 6, 7 through the
-// frame rows, A1..A8 -> slots 8..15; mode 2, HEXCONE mirror: control points P0r, P0z, P1r, P1z,
-// P2r, P2z -> slots 6..11 through the power-basis coefficients of the profile).
+// Record accessor of the derivative passes: FP64 record values rounded to R, with derivative
+// slots 6.. for the parameters of a differentiable surface (mode 1, SAG mirror: tilt x, y ->
+// slots 6, 7 through the frame rows, A1..A8 -> slots 8..15; mode 2, HEXCONE mirror: control
+// points P0r, P0z, P1r, P1z, P2r, P2z -> slots 6..11 through the power-basis coefficients of the
+// profile).  The surface origin reads as 0: a derivative pass works in world axes shifted to the
+// surface's origin (the shift is formed in FP64), so its coordinates are small.
+template <typename R>
 struct GRec {
     const double* S;
     const double* G;  // d rows / d tilt_x (9), d rows / d tilt_y (9)
     int mode;
-    __device__ __forceinline__ DX operator[](int k) const {
-        DX r(S[k]);
+    __device__ __forceinline__ DR<R> operator[](int k) const {
+        if (k >= F_O && k < F_O + 3) return DR<R>(0.0);
+        DR<R> r(S[k]);
         if (mode == 1) {
             if (k >= F_R && k < F_R + 9) {
-                r.d[6] = G[k - F_R];
-                r.d[7] = G[9 + k - F_R];
+                r.d[6] = (R)G[k - F_R];
+                r.d[7] = (R)G[9 + k - F_R];
             } else if (k >= F_A && k < F_A + 8) {
-                r.d[8 + (k - F_A)] = 1.0;
+                r.d[8 + (k - F_A)] = R(1);
             }
         } else if (mode == 2) {
             switch (k) {  // r(u) = ra0 + ra1 u + ra2 u^2 with ra0 = P0r, ra1 = 2 (P1r - P0r), ra2 = P0r - 2 P1r + P2r
-                case F_C + 0: r.d[6] = 1.0; break;
-                case F_C + 1: r.d[6] = -2.0; r.d[8] = 2.0; break;
-                case F_C + 2: r.d[6] = 1.0; r.d[8] = -2.0; r.d[10] = 1.0; break;
-                case F_C + 3: r.d[7] = 1.0; break;
-                case F_C + 4: r.d[7] = -2.0; r.d[9] = 2.0; break;
-                case F_C + 5: r.d[7] = 1.0; r.d[9] = -2.0; r.d[11] = 1.0; break;
+                case F_C + 0: r.d[6] = R(1); break;
+                case F_C + 1: r.d[6] = R(-2); r.d[8] = R(2); break;
+                case F_C + 2: r.d[6] = R(1); r.d[8] = R(-2); r.d[10] = R(1); break;
+                case F_C + 3: r.d[7] = R(1); break;
+                case F_C + 4: r.d[7] = R(-2); r.d[9] = R(2); break;
+                case F_C + 5: r.d[7] = R(1); r.d[9] = R(-2); r.d[11] = R(1); break;
                 default: break;
             }
         }
@@ -103,17 +109,26 @@ struct GRec {
     }
 };
 
+__device__ __forceinline__ double val_of(double x) { return x; }
+__device__ __forceinline__ double val_of(float x) { return (double)x; }
+template <typename R, int NT>
+__device__ __forceinline__ double val_of(const Dn<R, NT>& x) {
+    return (double)x.v;
+}
+// the real type under a dual (or the type itself)
 template <typename N>
-__device__ __forceinline__ double val_of(const N& x);
-template <>
-__device__ __forceinline__ double val_of<double>(const double& x) { return x; }
-template <>
-__device__ __forceinline__ double val_of<DX>(const DX& x) { return x.v; }
+struct RealOf {
+    using type = N;
+};
+template <typename R, int NT>
+struct RealOf<Dn<R, NT>> {
+    using type = R;
+};
 
 enum { GI_LOST = 0, GI_ON = 1, GI_DETECTED = 2, GI_OBSCURED = 3 };
 
-// One interaction of the frozen path on the known surface S (FP64 values; N = double, or DX to
-// carry derivatives): re-intersect, move the point, apply the surface's role.  At a refracting
+// One interaction of the frozen path on the known surface S (N = double or float values, or
+// DR<R> to carry derivatives): re-intersect, move the point, apply the surface's role.  At a refracting
 // face refl_in = 0 refracts, 1 reflects, 2 decides with the trace's Fresnel draw (the forward
 // pass), and *refl_out reports the choice.  Returns GI_LOST if the surface is not met any more,
 // GI_DETECTED (q = local x, y) or GI_OBSCURED at the end of the path, GI_ON otherwise; *seg is
@@ -127,7 +142,7 @@ __device__ __forceinline__ int g_interact(const Tables& tb, SR S, int4 si, doubl
     const V3<N> pl = to_local_pt<N>(S, p), dl = to_local_vec<N>(S, d);
     LHit<N> h;
     bool ok = false, err = false;
-    const N big = N(1.0e300);
+    const N big = N(sizeof(typename RealOf<N>::type) == 4 ? 1.0e30 : 1.0e300);
     if (shape == SHAPE_SAG) {
         ok = hit_sag<false, true, N>(S, (si.x >> 8) & 15, (si.x >> 12) & 1, pl, dl, N(eps), big, N(ntol), h, err, nullptr);
         if (ok) {
@@ -148,10 +163,10 @@ __device__ __forceinline__ int g_interact(const Tables& tb, SR S, int4 si, doubl
         ok = hit_hexcone<N>(S, pl, dl, N(eps), big, h);
     }
     if (!ok || err) return GI_LOST;
-    *seg = val_of<N>(h.t);
+    *seg = val_of(h.t);
     p = p + h.t * d;
     const V3<N> nw = unit(to_world_vec<N>(S, h.nl));
-    const bool front = val_of<N>(dot(d, nw)) < 0.0;
+    const bool front = val_of(dot(d, nw)) < 0.0;
     *front_out = front;
     *refl_out = false;
     if (role == ROLE_FOCAL) {
@@ -171,7 +186,7 @@ __device__ __forceinline__ int g_interact(const Tables& tb, SR S, int4 si, doubl
             T sn, cs;
             t_sincospi(T(2) * u2, &sn, &cs);
             const N g1 = N((double)(sigma * rad * cs)), g2 = N((double)(sigma * rad * sn));
-            const N sgn = N(val_of<N>(nw.z) >= 0.0 ? 1.0 : -1.0);
+            const N sgn = N(val_of(nw.z) >= 0.0 ? 1.0 : -1.0);
             const N aa = N(-1) / (sgn + nw.z);
             const N bb = nw.x * nw.y * aa;
             const V3<N> tt = mk(N(1) + sgn * nw.x * nw.x * aa, sgn * bb, N(0) - sgn * nw.x);
@@ -188,7 +203,7 @@ __device__ __forceinline__ int g_interact(const Tables& tb, SR S, int4 si, doubl
     const V3<N> nf = front ? nw : N(-1) * nw;
     const N ci = N(0) - dot(d, nf);
     bool rv = refl_in == 1;
-    if (refl_in == 2) rv = unit_open<T>(wd.x) < fresnel(n1, n2, (T)val_of<N>(ci));
+    if (refl_in == 2) rv = unit_open<T>(wd.x) < fresnel(n1, n2, (T)val_of(ci));
     *refl_out = rv;
     if (rv) {
         d = unit(d - (N(2) * dot(d, nf)) * nf);
@@ -202,17 +217,17 @@ __device__ __forceinline__ int g_interact(const Tables& tb, SR S, int4 si, doubl
 
 // Signed margin of the exit hexagon (apothem - max_k |x . u_k|) where the ray crosses the plane
 // of the variant's exit surface; false if the ray does not head into it.
-template <typename N>
-__device__ __forceinline__ bool g_exit_margin(const double* S, V3<N> p, V3<N> d, N* m) {
+template <typename N, typename SR>
+__device__ __forceinline__ bool g_exit_margin(SR S, V3<N> p, V3<N> d, N* m) {
     const V3<N> pl = to_local_pt<N>(S, p), dl = to_local_vec<N>(S, d);
-    if (!(val_of<N>(dl.z) < 0.0)) return false;
+    if (!(val_of(dl.z) < 0.0)) return false;
     const N t = N(0) - pl.z / dl.z;
     const V3<N> x = pl + t * dl;
     const N s60 = N(0.86602540378443864676);
     const N c0 = x.x, c1 = N(0.5) * x.x + s60 * x.y, c2 = N(-0.5) * x.x + s60 * x.y;
     N mx = t_abs(c0);
-    if (val_of<N>(t_abs(c1)) > val_of<N>(mx)) mx = t_abs(c1);
-    if (val_of<N>(t_abs(c2)) > val_of<N>(mx)) mx = t_abs(c2);
+    if (val_of(t_abs(c1)) > val_of(mx)) mx = t_abs(c1);
+    if (val_of(t_abs(c2)) > val_of(mx)) mx = t_abs(c2);
     *m = N(S[F_AP]) - mx;
     return true;
 }
@@ -227,12 +242,19 @@ __device__ __forceinline__ T sigmoid_t(T x) {
     return T(1) / (T(1) + (sizeof(T) == 4 ? (T)expf(-(float)x) : (T)exp(-(double)x)));
 }
 
-// Resident blocks of 128 threads per SM the register allocation must allow.
-#ifndef ROBAST_GRAD_MIN_BLOCKS
-#define ROBAST_GRAD_MIN_BLOCKS 4
+// Resident blocks of 128 threads per SM the register allocation must allow (FP32, FP64
+// derivative passes).  FP32: 2 (255 registers; the 32-dish batch ran 162 ms per evaluation
+// against 196 ms at 3 and 182 ms at 4, where the 16-slot duals spill more).
+#ifndef ROBAST_GRAD_MIN_BLOCKS_F32
+#define ROBAST_GRAD_MIN_BLOCKS_F32 2
 #endif
-template <typename T, int BLOCK, bool STAGED>
-__global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(GradArgs<T> A) {
+#ifndef ROBAST_GRAD_MIN_BLOCKS_F64
+#define ROBAST_GRAD_MIN_BLOCKS_F64 4
+#endif
+// T: the trace precision (nearest-hit search); R: the precision of the derivative passes.
+template <typename T, typename R, int BLOCK, bool STAGED>
+__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? ROBAST_GRAD_MIN_BLOCKS_F32 : ROBAST_GRAD_MIN_BLOCKS_F64)
+    grad_kernel(GradArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     Tables tb = A.tab;
     if constexpr (STAGED) {
@@ -260,6 +282,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
     const long long n = A.n;
     const int nq = A.objective == 1 ? 1 : 2;  // objective terms per photon: (qx, qy) or the margin m
     int ids[GMAXB];
+    float segs[GMAXB];  // segment length to each interaction (forward pass): where its derivative pass starts
     unsigned int u_fwd = 0, u_rep = 0, u_dual = 0;  // work units (when A.units is set)
     for (long long i = blockIdx.x * (long long)BLOCK + threadIdx.x; i < n; i += (long long)gridDim.x * BLOCK) {
         const V3<double> p0 = mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]);
@@ -318,6 +341,7 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
                 if (len > T(0)) w *= exp(-seg / (double)len);
             }
             ids[K] = sid;
+            segs[K] = (float)seg;
             if (rev) refl |= 1ull << K;
             if (first_diff < 0 && g_differentiable(si)) first_diff = K;
             ++K;
@@ -359,126 +383,171 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
         }
         (void)m_val;
         if (!contributes || first_diff < 0) continue;
-        // ---- 2. reverse sweep
-        double a[2][6];
+        // ---- 2. reverse sweep in precision R (the trace precision, or FP64 for paths through Bezier
+        // cone walls): the replays and the dual-number interactions (the per-photon derivatives);
+        // the sums over photons are fixed point
+        using DN = DR<R>;
+        R a[2][6];
         int k;  // the adjoint is with respect to the state before interaction k + 1 (after k)
-        auto replay = [&](int upto, V3<double>& pr, V3<double>& dr) {
+        bool lost = false;
+        const double ntol_r = sizeof(R) == 4 ? (double)A.newton_tol : A.newton_tol64;
+        auto replay = [&](int upto, V3<R>& pr, V3<R>& dr) {
             // the state before interaction `upto`, from the photon's inputs
-            pr = p0;
-            dr = d0;
+            pr = mk((R)A.o[i], (R)A.o[n + i], (R)A.o[2 * n + i]);
+            dr = mk((R)A.d[i], (R)A.d[n + i], (R)A.d[2 * n + i]);
             u_rep += (unsigned)upto;
             for (int j = 0; j < upto; ++j) {
                 const uint4 wd = philox4x32_10(
                     make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)j, 0u), key);
-                double qa, qb, sg;
+                R qa, qb;
+                double sg;
                 bool rv, fr;
-                g_interact<T, double>(tb, A.surf64 + (size_t)ids[j] * REC, tb.surf_i[ids[j]], (double)lam, wd,
-                                      (int)((refl >> j) & 1ull), &rv, (double)A.eps, A.newton_tol64, pr, dr, qa, qb, &sg,
-                                      &fr);
+                // the trace's own table when R is its precision, else the FP64 records
+                const R* Sj;
+                if constexpr (sizeof(R) == sizeof(T))
+                    Sj = reinterpret_cast<const R*>(tb.surf) + (size_t)ids[j] * REC;
+                else
+                    Sj = reinterpret_cast<const R*>(A.surf64) + (size_t)ids[j] * REC;
+                if (g_interact<T, R>(tb, Sj, tb.surf_i[ids[j]], (double)lam, wd, (int)((refl >> j) & 1ull), &rv,
+                                     (double)A.eps, ntol_r, pr, dr, qa, qb, &sg, &fr) == GI_LOST)
+                    lost = true;
             }
         };
-        auto seed_state = [](V3<double> pv, V3<double> dv, V3<DX>& ps, V3<DX>& ds) {
-            ps = mk(DX(pv.x), DX(pv.y), DX(pv.z));
-            ds = mk(DX(dv.x), DX(dv.y), DX(dv.z));
-            ps.x.d[0] = 1.0;
-            ps.y.d[1] = 1.0;
-            ps.z.d[2] = 1.0;
-            ds.x.d[3] = 1.0;
-            ds.y.d[4] = 1.0;
-            ds.z.d[5] = 1.0;
+        // Dual state seeded on (position, direction).  The position is first moved along the ray
+        // by t0, to just short of the hit, and expressed in world axes shifted to the origin of the
+        // surface the pass evaluates (both in FP64), so the pass solves its hit from nearby in small
+        // coordinates.  t0 is a constant: the derivative with respect to the direction before the
+        // move is the one after it plus t0 times the position's (applied to the adjoint below).
+        auto seed_state = [](V3<R> pv, V3<R> dv, const double* S, double t0, V3<DN>& ps, V3<DN>& ds) {
+            ps = mk(DN((double)pv.x + t0 * (double)dv.x - S[F_O]), DN((double)pv.y + t0 * (double)dv.y - S[F_O + 1]),
+                    DN((double)pv.z + t0 * (double)dv.z - S[F_O + 2]));
+            ds = mk(DN(dv.x), DN(dv.y), DN(dv.z));
+            ps.x.d[0] = R(1);
+            ps.y.d[1] = R(1);
+            ps.z.d[2] = R(1);
+            ds.x.d[3] = R(1);
+            ds.y.d[4] = R(1);
+            ds.z.d[5] = R(1);
+        };
+        const double ntol_d = sizeof(R) == 4 ? (double)A.newton_tol : A.newton_tol64;
+        // Where a derivative pass starts: short of the hit by more than the self-intersection
+        // epsilon, the segment's FP32 record (6e-8 relative), the replay's rounding, and (an
+        // asphere's Newton starts from its base quadric's first root ahead) 20 times the surface's
+        // distance from that quadric (incidence cosines down to 0.05); never behind the state.
+        auto start_of = [&](int j) {
+            const double sg = (double)segs[j];
+            const double dev = A.surf64[(size_t)ids[j] * REC + F_ADEV];
+            return fmax(0.0, sg - (4.0 * (double)A.eps + (sizeof(R) == 4 ? 1e-5 : 1e-6) * sg + 20.0 * dev));
         };
         if (A.objective != 1) {
             // terminal adjoint: d(qx, qy) / d(state before the detecting interaction K - 1)
-            V3<double> pr, dr;
+            V3<R> pr, dr;
             replay(K - 1, pr, dr);
-            V3<DX> ps, ds;
-            seed_state(pr, dr, ps, ds);
+            const double* S64 = A.surf64 + (size_t)ids[K - 1] * REC;
+            const double t0 = start_of(K - 1);
+            V3<DN> ps, ds;
+            seed_state(pr, dr, S64, t0, ps, ds);
             const uint4 wd = philox4x32_10(
                 make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)(K - 1), 0u), key);
-            DX qa(0.0), qb(0.0);
+            DN qa(0.0), qb(0.0);
             double sg;
             bool rv, fr;
-            const GRec R{A.surf64 + (size_t)ids[K - 1] * REC, A.grec + (size_t)ids[K - 1] * 18, 0};
-            g_interact<T, DX>(tb, R, tb.surf_i[ids[K - 1]], (double)lam, wd, 0, &rv, (double)A.eps, A.newton_tol64, ps,
-                              ds, qa, qb, &sg, &fr);
+            const GRec<R> rec{S64, A.grec + (size_t)ids[K - 1] * 18, 0};
+            if (g_interact<T, DN>(tb, rec, tb.surf_i[ids[K - 1]], (double)lam, wd, 0, &rv, (double)A.eps, ntol_d, ps,
+                                  ds, qa, qb, &sg, &fr) == GI_LOST)
+                lost = true;
             ++u_dual;
-            for (int j = 0; j < 6; ++j) {
+            for (int j = 0; j < 3; ++j) {
                 a[0][j] = qa.d[j];
                 a[1][j] = qb.d[j];
+                a[0][3 + j] = qa.d[3 + j] + R(t0) * qa.d[j];
+                a[1][3 + j] = qb.d[3 + j] + R(t0) * qb.d[j];
             }
             k = K - 2;
         } else {
             // terminal adjoint: d m / d(state after the last interaction)
-            V3<DX> ps, ds;
-            seed_state(p, d, ps, ds);
-            DX m(0.0);
-            g_exit_margin<DX>(A.surf64 + (size_t)ex * REC, ps, ds, &m);
-            for (int j = 0; j < 6; ++j) a[0][j] = m.d[j];
+            const double* Sx = A.surf64 + (size_t)ex * REC;
+            V3<DN> ps, ds;
+            seed_state(mk((R)p.x, (R)p.y, (R)p.z), mk((R)d.x, (R)d.y, (R)d.z), Sx, 0.0, ps, ds);
+            DN m(0.0);
+            g_exit_margin<DN>(GRec<R>{Sx, nullptr, 0}, ps, ds, &m);
+            for (int j = 0; j < 6; ++j) {
+                a[0][j] = m.d[j];
+                a[1][j] = R(0);
+            }
             k = K - 1;
         }
         // per-surface gradient of this photon's terms, flushed when the surface changes
         int cur = -1;
-        double gs[2][10];
+        R gs[2][10];
         auto flush = [&]() {
-            if (cur < 0) return;
+            if (cur < 0 || lost) return;
             const bool sag = (tb.surf_i[cur].x & 15) == SHAPE_SAG;
             const int base = sag ? 0 : 10, np = sag ? 10 : 6;
             unsigned long long* acc = A.acc + (size_t)cur * GRAD_SLOTS;
             for (int m = 0; m < np; ++m) {
                 unsigned long long* c = acc + (size_t)(base + m) * 6;
                 if (A.objective != 1) {
-                    fx_add(c + 0, w * (qx * gs[0][m] + qy * gs[1][m]));
-                    fx_add(c + 2, w * gs[0][m]);
-                    fx_add(c + 4, w * gs[1][m]);
+                    fx_add(c + 0, w * (qx * (double)gs[0][m] + qy * (double)gs[1][m]));
+                    fx_add(c + 2, w * (double)gs[0][m]);
+                    fx_add(c + 4, w * (double)gs[1][m]);
                 } else {
-                    fx_add(c + 0, coef * gs[0][m]);
+                    fx_add(c + 0, coef * (double)gs[0][m]);
                 }
             }
         };
-        for (; k >= first_diff; --k) {
-            V3<double> pr, dr;
+        for (; k >= first_diff && !lost; --k) {
+            V3<R> pr, dr;
             replay(k, pr, dr);
-            V3<DX> ps, ds;
-            seed_state(pr, dr, ps, ds);
             const int sid = ids[k];
             const int4 si = tb.surf_i[sid];
+            const double* S64 = A.surf64 + (size_t)sid * REC;
+            const double t0 = start_of(k);
+            V3<DN> ps, ds;
+            seed_state(pr, dr, S64, t0, ps, ds);
             const int mode = g_differentiable(si) ? ((si.x & 15) == SHAPE_SAG ? 1 : 2) : 0;
-            const GRec R{A.surf64 + (size_t)sid * REC, A.grec + (size_t)sid * 18, mode};
+            const GRec<R> rec{S64, A.grec + (size_t)sid * 18, mode};
             const uint4 wd = philox4x32_10(
                 make_uint4((uint32_t)pid, (uint32_t)((unsigned long long)pid >> 32), (uint32_t)k, 0u), key);
-            DX qa(0.0), qb(0.0);
+            DN qa(0.0), qb(0.0);
             double sg;
             bool rv, fr;
-            g_interact<T, DX>(tb, R, si, (double)lam, wd, (int)((refl >> k) & 1ull), &rv, (double)A.eps,
-                              A.newton_tol64, ps, ds, qa, qb, &sg, &fr);
+            if (g_interact<T, DN>(tb, rec, si, (double)lam, wd, (int)((refl >> k) & 1ull), &rv, (double)A.eps, ntol_d,
+                                  ps, ds, qa, qb, &sg, &fr) == GI_LOST)
+                lost = true;
             ++u_dual;
-            const DX* out[6] = {&ps.x, &ps.y, &ps.z, &ds.x, &ds.y, &ds.z};
+            const DN* out[6] = {&ps.x, &ps.y, &ps.z, &ds.x, &ds.y, &ds.z};
             if (mode) {
                 if (sid != cur) {
                     flush();
                     cur = sid;
                     for (int c = 0; c < 2; ++c)
-                        for (int m = 0; m < 10; ++m) gs[c][m] = 0.0;
+                        for (int m = 0; m < 10; ++m) gs[c][m] = R(0);
                 }
                 const int np = mode == 1 ? 10 : 6;
                 for (int c = 0; c < nq; ++c)
                     for (int m = 0; m < np; ++m) {
-                        double acc = 0.0;
+                        R acc = R(0);
                         for (int j = 0; j < 6; ++j) acc += a[c][j] * out[j]->d[6 + m];
                         gs[c][m] += acc;
                     }
             }
-            double na[2][6];
+            R na[2][6];
             for (int c = 0; c < nq; ++c)
                 for (int j = 0; j < 6; ++j) {
-                    double acc = 0.0;
+                    R acc = R(0);
                     for (int i2 = 0; i2 < 6; ++i2) acc += a[c][i2] * out[i2]->d[j];
                     na[c][j] = acc;
                 }
+            for (int c = 0; c < nq; ++c)  // the move by t0: d/d(direction) += t0 d/d(position)
+                for (int j = 0; j < 3; ++j) na[c][3 + j] += R(t0) * na[c][j];
             for (int c = 0; c < nq; ++c)
                 for (int j = 0; j < 6; ++j) a[c][j] = na[c][j];
         }
         flush();
+        // a derivative pass that no longer met its surface (a grazing hit the trace precision
+        // resolves differently): the photon's remaining gradient is dropped and counted
+        if (lost) fx_add(V + 2 * 6, 1.0);
     }
     if (A.units) {  // one atomic per warp and unit
         const unsigned fw = __reduce_add_sync(0xffffffffu, u_fwd), rp = __reduce_add_sync(0xffffffffu, u_rep),
@@ -491,9 +560,21 @@ __global__ void __launch_bounds__(BLOCK, ROBAST_GRAD_MIN_BLOCKS) grad_kernel(Gra
     }
 }
 
-template <typename T, int BLOCK, bool STAGED>
+// resident blocks of the gradient kernel per SM (0 if it cannot launch)
+template <typename T, typename R>
+static int grad_occupancy(size_t smem) {
+    auto k = smem ? grad_kernel<T, R, 128, true> : grad_kernel<T, R, 128, false>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 128, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+template <typename T, typename R, int BLOCK, bool STAGED>
 static cudaError_t launch_grad_one(const GradArgs<T>& a, int grid, size_t smem, cudaStream_t s) {
-    auto k = grad_kernel<T, BLOCK, STAGED>;
+    auto k = grad_kernel<T, R, BLOCK, STAGED>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

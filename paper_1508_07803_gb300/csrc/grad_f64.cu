@@ -28,9 +28,11 @@ __global__ void grad_finish(const unsigned long long* acc, const unsigned long l
 
 double grad_fx_value(const unsigned long long* a) { return fx_value(a); }
 
+int grad_blocks_per_sm_f64(size_t smem) { return grad_occupancy<double, double>(smem); }
+
 cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cudaStream_t s) {
-    return a.stage ? launch_grad_one<double, 128, true>(a, grid, smem, s)
-                   : launch_grad_one<double, 128, false>(a, grid, 0, s);
+    return a.stage ? launch_grad_one<double, double, 128, true>(a, grid, smem, s)
+                   : launch_grad_one<double, double, 128, false>(a, grid, 0, s);
 }
 cudaError_t launch_grad_finish(const unsigned long long* acc, const unsigned long long* vals, const int* surf_var,
                                int n_params, int objective, double d_obj, double* out, cudaStream_t s) {

@@ -43,7 +43,12 @@ struct GradArgs {
     unsigned long long* units; // optional [3]: FP64 interactions of the forward passes, interactions
                                // replayed by the reverse sweeps, dual-number interactions
 };
+// resident blocks of 128 threads per SM; _r64: FP32 search with FP64 derivative passes (cones)
+int grad_blocks_per_sm_f32(size_t smem);
+int grad_blocks_per_sm_f32_r64(size_t smem);
+int grad_blocks_per_sm_f64(size_t smem);
 cudaError_t launch_grad_f32(const GradArgs<float>& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_grad_f32_r64(const GradArgs<float>& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_grad_f64(const GradArgs<double>& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_grad_finish(const unsigned long long* acc, const unsigned long long* vals, const int* surf_var,
                                int n_params, int objective, double d_obj, double* out, cudaStream_t s);

@@ -608,6 +608,12 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
                 for (int k = 0; k < 8; ++k) R[F_A + k] = s.asph[k];
                 const double rb = 1.1 * aperture_bound(s);
                 R[F_RB2] = rb * rb;
+                double dev = 0.0, r2k = 1.0;
+                for (int k = 0; k < 8; ++k) {
+                    r2k *= rb * rb;
+                    if (s.asph[k] != 0.0) dev += std::fabs(s.asph[k]) * r2k;  // no 0 x inf for unbounded
+                }
+                R[F_ADEV] = dev;
                 double* A = R + F_AP;
                 switch (s.aperture) {
                     case ROBAST_AP_CIRCLE: A[0] = s.ap[0] * s.ap[0]; break;
@@ -1445,10 +1451,17 @@ static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl,
     const size_t smem_tab = sizeof(T) == 4 ? g->smem32 : g->smem64;
     a.stage = smem_tab <= kSmemCap ? 1 : 0;
     const size_t smem = a.stage ? smem_tab : 0;
-    const long long grid = std::max(1LL, std::min<long long>((long long)g->num_sms * 4, (n + 127) / 128));
+    // derivative passes in FP32 for an FP32 trace, except through Bezier cone walls (their grazing
+    // roots need FP64); one resident wave: the kernel strides over the photons
+    const bool r64 = sizeof(T) == 8 || (g->feat & FT_CONE) != 0;
+    const int bps = sizeof(T) == 8 ? grad_blocks_per_sm_f64(smem)
+                    : r64          ? grad_blocks_per_sm_f32_r64(smem)
+                                   : grad_blocks_per_sm_f32(smem);
+    if (bps <= 0) return fail(ROBAST_E_CUDA, "robast_trace_grad: the gradient kernel cannot launch with %zu bytes of shared memory", smem);
+    const long long grid = std::max(1LL, std::min<long long>((long long)g->num_sms * bps, (n + 127) / 128));
     cudaError_t e;
     if constexpr (sizeof(T) == 4)
-        e = launch_grad_f32(a, (int)grid, smem, s);
+        e = r64 ? launch_grad_f32_r64(a, (int)grid, smem, s) : launch_grad_f32(a, (int)grid, smem, s);
     else
         e = launch_grad_f64(a, (int)grid, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "robast_trace_grad: launch");

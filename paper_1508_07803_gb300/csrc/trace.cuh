@@ -59,7 +59,10 @@ enum : unsigned {
 //   [29] bound on the surface's principal curvatures over its aperture (the FP32 error estimate)
 //   [30..32] FP32 record: the origin's rounding error (origin - float(origin)), so that the
 //        origin is the pair [0..2] + [30..32]; FP64 record: 0
-enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_OL = 30, REC = 36 };
+//   [33] SAG: bound on the asphere terms' sag over the Newton seed domain, sum |A_i| r_bound^2i
+//        (how far the surface can lie from its base quadric)
+enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_OL = 30, F_ADEV = 33,
+       REC = 36 };
 // Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12, y = material,
 // z = medium front, w = medium back.
 // Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
