@@ -57,6 +57,43 @@ __device__ __forceinline__ void fx_add(unsigned long long* a, double c) {
     const unsigned long long old = atomicAdd(a, lo);
     atomicAdd(a + 1, hi + (old + lo < old ? 1ull : 0ull));
 }
+// the same for an FP32 contribution, converted with integer operations only (no FP64
+// instruction): |c| = m 2^(E - 150) with the 24-bit significand m, so c 2^64 = m 2^(E - 86),
+// truncated toward zero like the FP64 form
+__device__ __forceinline__ void fx_add(unsigned long long* a, float c) {
+    const unsigned b = __float_as_uint(c);
+    const int E = (int)((b >> 23) & 0xffu);
+    if (E == 0 || E >= 190) return;  // zero or subnormal (far below 2^-64), or |c| >= 2^63 (inf, NaN too)
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = E - 86;
+    unsigned long long lo, hi;
+    if (sh >= 64) {
+        lo = 0ull;
+        hi = m << (sh - 64);
+    } else if (sh > 0) {
+        lo = m << sh;
+        hi = m >> (64 - sh);
+    } else if (sh == 0) {
+        lo = m;
+        hi = 0ull;
+    } else if (sh > -64) {
+        lo = m >> (-sh);
+        hi = 0ull;
+    } else {
+        return;
+    }
+    if (b >> 31) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    if ((lo | hi) == 0ull) return;
+    const unsigned long long old = atomicAdd(a, lo);
+    atomicAdd(a + 1, hi + (old + lo < old ? 1ull : 0ull));
+}
+// an integer count n into the sum: n units of 2^64 in the high word
+__device__ __forceinline__ void fx_add_count(unsigned long long* a, unsigned long long n) {
+    if (n) atomicAdd(a + 1, n);
+}
 __host__ __device__ __forceinline__ double fx_value(const unsigned long long* a) {
     return (double)(long long)a[1] + (double)a[0] * 5.421010862427522e-20;  // 2^-64
 }
@@ -284,6 +321,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? ROBAST_GRAD_MIN_BLOCKS
     int ids[GMAXB];
     float segs[GMAXB];  // segment length to each interaction (forward pass): where its derivative pass starts
     unsigned int u_fwd = 0, u_rep = 0, u_dual = 0;  // work units (when A.units is set)
+    // photons of the current variant counted in a register, added when the variant changes
+    int cnt_var = -1;
+    unsigned long long cnt_n = 0ull;
     for (long long i = blockIdx.x * (long long)BLOCK + threadIdx.x; i < n; i += (long long)gridDim.x * BLOCK) {
         const V3<double> p0 = mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]);
         const V3<double> d0 = mk((double)A.d[i], (double)A.d[n + i], (double)A.d[2 * n + i]);
@@ -356,7 +396,12 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? ROBAST_GRAD_MIN_BLOCKS
             if (role == ROLE_MIRROR) w *= refl_value(tb.mats + (size_t)si.y * MAT_REC, (double)lam);
             if (b + 1 >= A.max_bounces) status = ST_MAXB;
         }
-        fx_add(V + 2 * 7, 1.0);
+        if (var != cnt_var) {
+            if (cnt_var >= 0) fx_add_count(A.vals + (size_t)cnt_var * 16 + 2 * 7, cnt_n);
+            cnt_var = var;
+            cnt_n = 0ull;
+        }
+        ++cnt_n;
         if (untracked) fx_add(V + 2 * 6, 1.0);
         // ---- objective terms of this photon
         bool contributes = false;
@@ -487,12 +532,15 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? ROBAST_GRAD_MIN_BLOCKS
             unsigned long long* acc = A.acc + (size_t)cur * GRAD_SLOTS;
             for (int m = 0; m < np; ++m) {
                 unsigned long long* c = acc + (size_t)(base + m) * 6;
+                // contributions in the derivative precision (an FP32 one is converted with integer
+                // operations); the weights and spot coordinates rounded to it
                 if (A.objective != 1) {
-                    fx_add(c + 0, w * (qx * (double)gs[0][m] + qy * (double)gs[1][m]));
-                    fx_add(c + 2, w * (double)gs[0][m]);
-                    fx_add(c + 4, w * (double)gs[1][m]);
+                    const R wr = (R)w;
+                    fx_add(c + 0, wr * ((R)qx * gs[0][m] + (R)qy * gs[1][m]));
+                    fx_add(c + 2, wr * gs[0][m]);
+                    fx_add(c + 4, wr * gs[1][m]);
                 } else {
-                    fx_add(c + 0, coef * (double)gs[0][m]);
+                    fx_add(c + 0, (R)coef * gs[0][m]);
                 }
             }
         };
@@ -549,6 +597,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? ROBAST_GRAD_MIN_BLOCKS
         // resolves differently): the photon's remaining gradient is dropped and counted
         if (lost) fx_add(V + 2 * 6, 1.0);
     }
+    if (cnt_var >= 0) fx_add_count(A.vals + (size_t)cnt_var * 16 + 2 * 7, cnt_n);
     if (A.units) {  // one atomic per warp and unit
         const unsigned fw = __reduce_add_sync(0xffffffffu, u_fwd), rp = __reduce_add_sync(0xffffffffu, u_rep),
                        du = __reduce_add_sync(0xffffffffu, u_dual);
