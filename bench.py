@@ -631,6 +631,15 @@ def _shape(text):
     return b, k, r
 
 
+def _hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0  # fallback: an earlier measurement on a GB300
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
 TRAFFIC_SOURCES = ("trace.cuh", "trace_f32.cu", "order.cu")  # the kernel and the processing order that shapes its DRAM traffic
 
 
@@ -652,6 +661,23 @@ def traffic_from_profile(n_photons):
         if meta.get("sources_sha256") != traffic_source_hash():
             return None
         return meta["dram_bytes_per_photon"] * n_photons
+    except Exception:
+        return None
+
+
+def issue_from_profile():
+    """Issue and pipe utilisation of the trace kernel from the committed ncu capture
+    (profiles/trace_kernel_issue.json, a small case of the same kernel), if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "trace_kernel_issue.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        meta = json.load(open(path))
+        if meta.get("sources_sha256") != traffic_source_hash():
+            return None
+        return {k: meta[k] for k in ("issue_active", "ipc_per_sm", "fma_pipe", "alu_pipe", "fp64_pipe",
+                                     "warps_active", "lanes_active_per_inst")}
     except Exception:
         return None
 
@@ -837,6 +863,14 @@ def main():
     value = forms["fp32"]["value"]
     roof = dict(forms["fp32"]["roofline"])
     roof["traffic"] = traffic_from_profile(N)
+    # the same launch against the copy bandwidth (DRAM bytes of the committed capture over this
+    # run's kernel time), and its issue utilisation (ncu, committed small-case capture): the
+    # FLOP fraction above counts only algorithmic arithmetic, the issue fraction every instruction
+    if roof["traffic"]:
+        gbs = roof["traffic"] / (roof["kernel_ms"] * 1e-3) / 1e9
+        roof["hbm"] = {"achieved_gbs": gbs, "peak_gbs": HBM_PEAK_GBS, "frac": gbs / HBM_PEAK_GBS,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
+    roof["issue"] = issue_from_profile()
     if not args.no_fp64:
         fp64 = measure(scene, bundle, npa, len(ANGLES), 64, args.fp64_steps, 3, want_clocks=False)
         forms["fp64"] = form_of(fp64, args.fp64_steps, 64, peak64, "robast::trace_kernel<double,128> (+ sort)")
