@@ -615,6 +615,10 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
                 }
                 R[F_ADEV] = dev;
                 double* A = R + F_AP;
+                R[F_APR] = (s.aperture == ROBAST_AP_ANNULUS || s.aperture == ROBAST_AP_SECTOR) ? s.ap[0] : 0.0;
+                R[F_APR + 1] = s.aperture == ROBAST_AP_CIRCLE ? s.ap[0]
+                               : (s.aperture == ROBAST_AP_ANNULUS || s.aperture == ROBAST_AP_SECTOR) ? s.ap[1]
+                                                                                                      : 0.0;
                 switch (s.aperture) {
                     case ROBAST_AP_CIRCLE: A[0] = s.ap[0] * s.ap[0]; break;
                     case ROBAST_AP_ANNULUS:

@@ -61,8 +61,9 @@ enum : unsigned {
 //        origin is the pair [0..2] + [30..32]; FP64 record: 0
 //   [33] SAG: bound on the asphere terms' sag over the Newton seed domain, sum |A_i| r_bound^2i
 //        (how far the surface can lie from its base quadric)
+//   [34..35] SAG: the aperture's inner and outer radius (ANNULUS, SECTOR; CIRCLE: outer)
 enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_OL = 30, F_ADEV = 33,
-       REC = 36 };
+       F_APR = 34, REC = 36 };
 // Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12, y = material,
 // z = medium front, w = medium back.
 // Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
@@ -346,6 +347,31 @@ __device__ __forceinline__ bool aperture_inside(SR S, int ap, T x, T y) {
     return false;
 }
 
+// The aperture grown by m on every side (a point within m of it passes): the asphere's pre-check.
+template <typename T, typename SR>
+__device__ __forceinline__ bool aperture_near(SR S, int ap, T x, T y, T m) {
+    switch (ap) {
+        case AP_NONE: return true;
+        case AP_CIRCLE: return t_sqrt(x * x + y * y) <= T(S[F_APR + 1]) + m;
+        case AP_ANNULUS: {
+            const T r = t_sqrt(x * x + y * y);
+            return r >= T(S[F_APR]) - m && r <= T(S[F_APR + 1]) + m;
+        }
+        case AP_SECTOR: {
+            const T r = t_sqrt(x * x + y * y);
+            return r >= T(S[F_APR]) - m && r <= T(S[F_APR + 1]) + m &&
+                   (T(S[F_AP + 2]) * y - T(S[F_AP + 3]) * x) >= -m && (x * T(S[F_AP + 5]) - y * T(S[F_AP + 4])) >= -m;
+        }
+        case AP_HEX: {
+            const T s60 = T(0.86602540378443864676);
+            const T h = t_max(t_abs(x), t_max(t_abs(T(0.5) * x + s60 * y), t_abs(-T(0.5) * x + s60 * y)));
+            return h <= T(S[F_AP]) + m;
+        }
+        case AP_RECT: return t_abs(x) <= T(S[F_AP]) + m && t_abs(y) <= T(S[F_AP + 1]) + m;
+    }
+    return true;
+}
+
 template <typename T>
 struct LHit {
     T t;
@@ -435,6 +461,20 @@ __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> 
         if (asph) {
             if (t <= eps) continue;
             if (q.x * q.x + q.y * q.y > T(S[F_RB2])) return false;
+            if constexpr (sizeof(T) <= 8) {
+                // Pre-check before Newton: the asphere's hit lies within dev / cos of the quadric's
+                // (dev = the asphere terms' largest sag, cos = the incidence cosine at the quadric
+                // root), so a quadric root further than twice that (plus a rounding slack) outside
+                // the aperture cannot give a hit inside it; skipped at grazing incidence.
+                const T mx = -c * q.x, my = -c * q.y, mz = T(1) - c * k1 * q.z;
+                const T nn = mx * mx + my * my + mz * mz;
+                const T dn = t_abs(d.x * mx + d.y * my + d.z * mz);
+                if (dn * dn > T(0.0025) * nn) {
+                    const T m = T(2) * T(S[F_ADEV]) * t_sqrt(nn) / dn +
+                                T(1e-4) * (t_abs(q.x) + t_abs(q.y) + t_abs(t));
+                    if (!aperture_near(S, ap, q.x, q.y, m)) return false;
+                }
+            }
             bool conv = false;
             T slope = T(0);
             for (int it = 0; it < 32; ++it) {

@@ -1,8 +1,8 @@
 """Full-size launches (the sizes and launch configuration bench.py times)
 checked on sampled photons the oracle traces one by one.
 
-The dish workload (5 x 1e7 photons) and the two-mirror workload (8 x 1e7) are
-traced whole on the GPU with the default launch (persistent grid, coherent
+The dish workload (5 x 1e7 photons), the two-mirror workload (8 x 1e7, FP32 and FP64) and
+the GCT-like workload (5 x 1e7) are traced whole on the GPU with the default launch (persistent grid, coherent
 order, FP32 accuracy guard); windows of contiguous photon ids at random
 offsets, 1e6 photons per workload in all, are traced by the oracle with
 first_photon_id set to the window start and compared photon by photon with
@@ -77,18 +77,33 @@ def test_dish_full_size_sampled(precision):
     geom.close()
 
 
-def test_two_mirror_full_size_sampled():
-    scene, b = W.sct_workload(10_000_000, seed=0)
+def _full_size(scene, b, precision, seed, win_seed):
     geom = robast.build_geometry(scene)
-    o = torch.from_numpy(b.origins).to("cuda", torch.float32)
-    d = torch.from_numpy(b.dirs).to("cuda", torch.float32)
-    w = torch.from_numpy(b.wavelengths).to("cuda", torch.float32)
-    out = robast.trace(geom, o, d, w, seed=1, precision=32)
+    dt = torch.float32 if precision == 32 else torch.float64
+    o = torch.from_numpy(b.origins).to("cuda", dt)
+    d = torch.from_numpy(b.dirs).to("cuda", dt)
+    w = torch.from_numpy(b.wavelengths).to("cuda", dt)
+    out = robast.trace(geom, o, d, w, seed=seed, precision=precision)
     torch.cuda.synchronize()
-    assert int(out["counters"][7]) == b.n
-    assert int(out["retraced"][1]) == 0
-    _check_windows(scene, b, out, 32, 1, _windows(b.n, 10, 100_000, seed=7))
+    c = out["counters"].cpu().numpy()
+    assert c[7] == b.n and c[1:7].sum() == b.n
+    if precision == 32:
+        assert int(out["retraced"][1]) == 0
+    _check_windows(scene, b, out, precision, seed, _windows(b.n, 10, 100_000, seed=win_seed))
     geom.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_two_mirror_full_size_sampled(precision):
+    """The SCT-like workload the bench times (8 field angles x 1e7 photons)."""
+    scene, b = W.sct_workload(10_000_000, seed=0)
+    _full_size(scene, b, precision, 1, 7 + precision)
+
+
+def test_gct_full_size_sampled():
+    """The GCT-like workload the bench times (5 field angles x 1e7 photons), FP32 with the guard."""
+    scene, b = W.gct_workload(10_000_000, seed=0)
+    _full_size(scene, b, 32, 2, 11)
 
 
 def test_batched_full_size_counters_and_sampled_ids():
