@@ -634,6 +634,15 @@ __device__ __forceinline__ FF ff_mul2(FF a, FF b) {
     return p;
 }
 
+// the value of a real (or of a dual number's value part) rounded to FP32 (no FP64 instruction
+// for an FP32 value)
+__device__ __forceinline__ float val_f(float x) { return x; }
+__device__ __forceinline__ float val_f(double x) { return (float)x; }
+template <typename N>
+__device__ __forceinline__ float val_f(const N& x) {
+    return (float)x.v;
+}
+
 // cos and sin of j x 60 degrees, j = 0..5 (a hexagon's face directions)
 static __constant__ float k_hex_c32[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
 static __constant__ float k_hex_s32[6] = {0.0f, 0.86602540378443864676f, 0.86602540378443864676f, 0.0f,
@@ -669,7 +678,11 @@ __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tma
     // whose wedge the ray cannot reach on [0, tmax] (with a margin far above rounding) is
     // skipped; the in-wedge test at the hit point below is unchanged, so the result is too.
     // margin: 1e-5 of the scale of any point p + t d, t <= best, far above the in-wedge test's rounding
-    const T mg = T(1e-5) * (t_abs(p.x) + t_abs(p.y) + t_abs(d.x) + t_abs(d.y) + T(1e-30));
+    // The reach test runs in FP32 in every precision (on duals, on their values): its margin,
+    // 1e-5 of the coordinates' scale, is far above FP32 rounding, so no wall is skipped that the
+    // exact test would reach.
+    const float pxf = val_f(p.x), pyf = val_f(p.y), dxf = val_f(d.x), dyf = val_f(d.y);
+    const float mg = 1e-5f * (fabsf(pxf) + fabsf(pyf) + fabsf(dxf) + fabsf(dyf) + 1e-30f);
     // the wall and root loops stay rolled: one copy of the wall code keeps the kernel's
     // instruction footprint small (warps of a concentrator trace sit in different code paths)
 #pragma unroll 1
@@ -677,15 +690,15 @@ __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tma
         T cjj, sjj;
         dir(j, cjj, sjj);
         bool reach = true;
+        const float bestf = fminf(val_f(best), 1e30f);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            T cm, sm;
-            dir(side ? (j + 1) % 6 : (j + 5) % 6, cm, sm);
-            const T ex = cjj - cm, ey = sjj - sm;
-            const T a = p.x * ex + p.y * ey, b = d.x * ex + d.y * ey;
+            const int m2 = side ? (j + 1) % 6 : (j + 5) % 6;
+            const float ex = k_hex_c32[j] - k_hex_c32[m2], ey = k_hex_s32[j] - k_hex_s32[m2];
+            const float a = pxf * ex + pyf * ey, b = dxf * ex + dyf * ey;
             // largest a + b t over t in [0, best]: at t = best if b > 0 (best may be +inf)
-            const T top = b > T(0) ? a + b * best : a;
-            if (top < -mg * (T(1) + t_min(best, T(1e30)))) reach = false;
+            const float top = b > 0.0f ? a + b * bestf : a;
+            if (top < -mg * (1.0f + bestf)) reach = false;
         }
         if (!reach) continue;
         const T q0 = p.x * cjj + p.y * sjj, dq = d.x * cjj + d.y * sjj;
