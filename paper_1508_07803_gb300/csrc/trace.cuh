@@ -755,13 +755,33 @@ __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tma
             if (t <= eps || t > best) continue;
             if (found && !(t < best)) continue;
             const V3<T> x = p + t * d;
-            const T qj = x.x * cjj + x.y * sjj;
             bool inwedge = true;
+            bool exact = true;
+            if constexpr (sizeof(T) == 8) {
+                // FP64: an FP32 screen decides unless a neighbour's measure lies within its margin
+                // (1e-5 of the coordinates) of wall j's; then the FP64 test below decides
+                const float xf = (float)x.x, yf = (float)x.y;
+                const float qjf = xf * k_hex_c32[j] + yf * k_hex_s32[j];
+                const float mw = 1e-5f * (fabsf(xf) + fabsf(yf)) + 1e-30f;
+                exact = false;
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                T cm, sm;
-                hex_dir(m, cm, sm);
-                if (m != j && x.x * cm + x.y * sm > qj) inwedge = false;
+                for (int m = 0; m < 6; ++m) {
+                    if (m == j) continue;
+                    const float v = xf * k_hex_c32[m] + yf * k_hex_s32[m];
+                    if (v > qjf + mw) inwedge = false;
+                    else if (v > qjf - mw) exact = true;
+                }
+                if (!inwedge) exact = false;
+            }
+            if (exact) {
+                const T qj = x.x * cjj + x.y * sjj;
+                inwedge = true;
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    T cm, sm;
+                    hex_dir(m, cm, sm);
+                    if (m != j && x.x * cm + x.y * sm > qj) inwedge = false;
+                }
             }
             if (!inwedge) continue;
             found = true;
