@@ -425,12 +425,66 @@ __device__ __forceinline__ bool newton_step_fp64(const T* S, V3<T> p, V3<T> d, T
 
 // Ray vs SAG surface (local frame).  Quadric F = c (x^2 + y^2 + (1+k) z^2) - 2z,
 // sag branch (1+k) c z <= 1; both roots in ascending order, first valid one.
+// FP32 screen of an FP64 sag test (no asphere): false if the surface certainly gives no hit.
+// It decides only where the FP32 solve is well conditioned: a, b, g and the discriminant each
+// lose at most a factor 100 to cancellation, so the roots carry a relative error below 1e-4;
+// a root counts as excluded only when it lies more than 1e-3 of the coordinates outside
+// [eps, tmax], off the conic's branch, or outside the aperture.
+template <typename SR>
+__device__ __forceinline__ bool screen_sag_miss(SR S, int ap, V3<double> p, V3<double> d, double eps, double tmax) {
+    const float c = (float)S[F_C], k1 = (float)S[F_K1];
+    const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
+    const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
+    const float ac = fabsf(c), ak = fabsf(k1);
+    const float mp = fabsf(px) + fabsf(py) + fabsf(pz);
+    const float tm = fminf((float)tmax, 3.0e38f);
+    if (c == 0.0f) {  // a plane: t = -pz / dz
+        if (!(fabsf(dz) > 1e-2f * (fabsf(dx) + fabsf(dy)))) return true;
+        const float t = -pz / dz;
+        const float mt = 1e-3f * (fabsf(t) + mp);
+        if (!(t > (float)eps - mt) || !(t < tm + mt)) return false;
+        const float qx = px + t * dx, qy = py + t * dy;
+        return aperture_near(S, ap, qx, qy, mt + 1e-3f * (fabsf(qx) + fabsf(qy)));
+    }
+    const float a = c * (dx * dx + dy * dy + k1 * dz * dz);
+    const float b = c * (px * dx + py * dy + k1 * pz * dz) - dz;
+    const float g = c * (px * px + py * py + k1 * pz * pz) - 2.0f * pz;
+    const float aa = ac * (dx * dx + dy * dy + ak * dz * dz);
+    const float bb = ac * (fabsf(px * dx) + fabsf(py * dy) + ak * fabsf(pz * dz)) + fabsf(dz);
+    const float gg = ac * (px * px + py * py + ak * pz * pz) + 2.0f * fabsf(pz);
+    if (!(fabsf(a) > 1e-2f * aa) || !(fabsf(b) > 1e-2f * bb) || !(fabsf(g) > 1e-2f * gg)) return true;
+    const float disc = b * b - a * g;
+    if (!(fabsf(disc) > 1e-2f * (b * b + fabsf(a * g)))) return true;  // FP64 decides
+    if (disc < 0.0f) return false;                                      // no root
+    const float sq = sqrtf(disc);
+    const float qq = -(b + copysignf(sq, b));
+    const float r[2] = {qq / a, g / qq};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float t = r[i];
+        const float mt = 1e-3f * (fabsf(t) + mp);
+        if (!(t > (float)eps - mt) || !(t < tm + mt)) continue;
+        const float qx = px + t * dx, qy = py + t * dy, qz = pz + t * dz;
+        if (k1 * c * qz - 1.0f > 1e-2f + ac * ak * mt) continue;  // off the branch (with the point's error)
+        if (!aperture_near(S, ap, qx, qy, mt + 1e-3f * (fabsf(qx) + fabsf(qy)))) continue;
+        return true;  // a root may hit: FP64 decides
+    }
+    return false;
+}
+
 // Aspheres: Newton from the first on-branch root beyond eps.
 template <bool C, bool ASPH = true, typename T, typename SR>
 __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> d, T eps, T tmax, T tol, LHit<T>& h,
                                         bool& err, unsigned* cnt) {
     if constexpr (!ASPH) asph = false;  // a profile without aspheres carries no Newton code
     CNT(U_SAG);
+    if constexpr (sizeof(T) == 8) {
+        // FP64, no asphere: an FP32 solve rejects the surface when it is well conditioned and
+        // every root lies clearly off the branch, outside [eps, tmax] or outside the aperture
+        // (margins 1e-4 of the coordinates, far above the FP32 solve's error there); any other
+        // case goes to the FP64 solve below, so the result is the FP64 one.
+        if (!asph && !screen_sag_miss(S, ap, p, d, eps, tmax)) return false;
+    }
     const T c = S[F_C], k1 = S[F_K1];
     const T a = c * (d.x * d.x + d.y * d.y + k1 * d.z * d.z);
     const T b = c * (p.x * d.x + p.y * d.y + k1 * p.z * d.z) - d.z;
