@@ -14,9 +14,11 @@
 // Adjoint method, per photon:
 //  1. forward pass: the path's surfaces come from the trace's nearest-hit
 //     search (in the trace precision); each interaction is re-solved in FP64,
-//     which gives the state, the weight and the objective terms.  Only the
-//     surface ids and the refracting faces' reflect/refract decisions are
-//     kept, not the states;
+//     which gives the state, the weight and the objective terms (the MSR
+//     gradient contracts the spot coordinates with their centroid, which
+//     cancels, so they need FP64).  Only the surface ids, the segment lengths
+//     and the refracting faces' reflect/refract decisions are kept, not the
+//     states;
 //  2. reverse sweep: the derivative of the photon's objective terms with
 //     respect to the ray state (point, direction) is carried backwards
 //     through the interactions.  For interaction k the state before it is
@@ -27,6 +29,10 @@
 //     adjoint one interaction back, the parameter Jacobian contracted with the
 //     adjoint is the photon's gradient for that surface.  Every
 //     differentiable surface the path meets gets its share, however many.
+//     The replays and dual numbers run in precision R: the trace's (FP32
+//     for an FP32 trace) or FP64 where Bezier cone walls need it; each dual
+//     evaluation starts just short of its hit, in axes shifted to the
+//     surface's origin.
 // Sums over photons are 128-bit fixed point (two's complement, 64 fraction
 // bits) accumulated with integer atomics, so they do not depend on the order
 // in which photons finish: repeated runs give identical bits.

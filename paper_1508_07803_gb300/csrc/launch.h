@@ -16,7 +16,7 @@ int trace_blocks_per_sm_f64(int block, size_t smem, bool src, unsigned prof);
 int trace_blocks_per_sm_f32_src(int block, size_t smem, unsigned prof);
 int trace_blocks_per_sm_f64_src(int block, size_t smem, unsigned prof);
 
-// Gradient pass (grad.cu): frozen-path objective sums and per-parameter sums, 128-bit fixed
+// Gradient pass (grad.cuh): frozen-path objective sums and per-parameter sums, 128-bit fixed
 // point (two u64 words each: fraction, integer part).
 constexpr int GRAD_SLOTS = 16 * 3 * 2;  // u64 words per surface: 16 parameters x 3 sums x 2
 template <typename T>
@@ -35,7 +35,7 @@ struct GradArgs {
     int stage;
     T eps;
     T newton_tol;
-    double newton_tol64;  // Newton tolerance of the FP64 dual re-intersection
+    double newton_tol64;  // Newton tolerance of the FP64 re-intersections (forward values, FP64 passes)
     int objective;
     double tau;
     unsigned long long* acc;   // [n_surf * GRAD_SLOTS]
