@@ -478,13 +478,6 @@ __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> 
                                         bool& err, unsigned* cnt) {
     if constexpr (!ASPH) asph = false;  // a profile without aspheres carries no Newton code
     CNT(U_SAG);
-    if constexpr (sizeof(T) == 8) {
-        // FP64, no asphere: an FP32 solve rejects the surface when it is well conditioned and
-        // every root lies clearly off the branch, outside [eps, tmax] or outside the aperture
-        // (margins 1e-4 of the coordinates, far above the FP32 solve's error there); any other
-        // case goes to the FP64 solve below, so the result is the FP64 one.
-        if (!asph && !screen_sag_miss(S, ap, p, d, eps, tmax)) return false;
-    }
     const T c = S[F_C], k1 = S[F_K1];
     const T a = c * (d.x * d.x + d.y * d.y + k1 * d.z * d.z);
     const T b = c * (p.x * d.x + p.y * d.y + k1 * p.z * d.z) - d.z;
@@ -1057,6 +1050,14 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
     bool ok = false, err = false;
     switch (shape) {
         case SHAPE_SAG:
+            if constexpr (sizeof(T) == 8) {
+                // FP64 nearest-hit search, no asphere: an FP32 solve rejects the candidate when it is
+                // well conditioned and every root lies clearly off the branch, outside [eps, t_best]
+                // or outside the aperture; any other case goes to the FP64 solve, so the result is
+                // the FP64 one
+                if (((flags >> 12) & 1) == 0 && !screen_sag_miss(S, (flags >> 8) & 15, pl, dl, (double)eps, (double)bst.t))
+                    break;
+            }
             ok = hit_sag<C, (FEAT & FT_ASPH) != 0>(S, (flags >> 8) & 15, (flags >> 12) & 1, pl, dl, eps, bst.t, tol, h,
                                                    err, cnt);
             break;
