@@ -267,7 +267,7 @@ typedef struct robast_trace_opts {
                                  the new direction by twice the normal's error (reflection) or by
                                  Snell's derivative (refraction); errors carried along add
                                  linearly, fresh roundings in quadrature.  A photon whose estimate
-                                 exceeds 0.8 of a bound, or that ends in ERROR, is re-traced from its
+                                 exceeds 0.9 of a bound, or that ends in ERROR, is re-traced from its
                                  inputs in FP64 (same random streams, same epsilon) by a second
                                  launch on the same stream, whose result replaces the FP32 one.  The
                                  queue has an entry (8 bytes) per photon, from g's memory pool like
