@@ -705,7 +705,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="library launch defaults instead of the tuners (keeps profiler launch counts small)")
     ap.add_argument("--trace-shape", default=None,
-                    help="block,blocks_per_sm,refill_min for the plain traces instead of the tuner (profiler runs)")
+                    help="block,blocks_per_sm,refill_min for the plain FP32 traces instead of the tuner (profiler runs)")
     ap.add_argument("--batch-shape", default=None,
                     help="block,blocks_per_sm,refill_min for the batched trace instead of the tuner (profiler runs)")
     ap.add_argument("--grad-photons-per-dish", type=int, default=1_000_000)
@@ -767,7 +767,7 @@ def main():
         wins = [(k * npa, npa) for k in range(n_angles)]
         # launch shape and refill threshold from the autotuner (on the first 2e6 photons, untimed)
         from paper_1508_07803_gb300 import autotune
-        if args.trace_shape:
+        if args.trace_shape and precision == 32:
             (blk, bps, rfm), table = _shape(args.trace_shape), {}
         elif args.no_autotune:
             (blk, bps, rfm), table = (0, 0, 0), {}
@@ -812,6 +812,9 @@ def main():
         barrier()
         ms = t0.elapsed_time(t1)
         kern_ms = [a.elapsed_time(b) for a, b in evs]
+        # whole steps (trace start to the next trace start, the last to the end): a step much
+        # longer than its kernels means the device waited on the host
+        step_ms = [evs[k][0].elapsed_time(evs[k + 1][0]) for k in range(steps - 1)] + [evs[-1][0].elapsed_time(t1)]
         clk = clocks.stop() if clocks else None
         c = counters.cpu().tolist()
         rt = out["retraced"].cpu().tolist() if "retraced" in out else [0, 0]
@@ -832,6 +835,7 @@ def main():
         return {"ms": ms, "kernel_ms": kern_ms, "bounces": c[0], "counters": c, "units": units, "psf": last,
                 "clocks": clk, "launches": steps * (order_launches + trace_launches + psf_launches),
                 "retraced_per_step": rt[0] // steps, "over_bound_not_retraced": rt[1], "guard": guard,
+                "step_ms": step_ms,
                 "autotune": {"block": blk, "blocks_per_sm": bps, "refill_min": rfm,
                              "candidates_ms": {f"{b}x{p}/r{r}": round(t, 3) for (b, p, r), t in table.items()}}}
 
@@ -840,6 +844,7 @@ def main():
         v = sum_over_ranks(m["bounces"]) / (msx * 1e-3)
         k = statistics.mean(m["kernel_ms"])
         f = {"value": v, "ms_per_step": msx / steps, "kernel_ms": k, "bounces_per_step": m["bounces"] / steps,
+             "step_ms_min_median_max": [min(m["step_ms"]), statistics.median(m["step_ms"]), max(m["step_ms"])],
              "roofline": roofline_of(m["units"], k, peak, label,
                                      ("FFMA" if precision == 32 else "DFMA") +
                                      " throughput probe robast_measure_alu_peak on this GPU (measured)")}
