@@ -709,6 +709,63 @@ __device__ __forceinline__ void hex_dir(int j, T& c, T& s) {
     }
 }
 
+// FP32 screen of wall j of an FP64 cone test: false if the wall certainly gives no hit.  It
+// decides only where the FP32 solve is well conditioned (A, B, C and the discriminant each lose at
+// most a factor 100 to cancellation, the ray is not near the wall's profile plane's normal), and
+// then excludes a root only when it lies more than 1e-3 outside [0, 1] in u, or more than 1e-2
+// of the coordinates outside [eps, best] or outside the wall's wedge; any other case goes to the
+// FP64 solve, so the result is the FP64 one.
+template <typename SR>
+__device__ __forceinline__ bool screen_wall_miss(SR S, int j, float px, float py, float pz, float dx, float dy,
+                                                 float dz, float eps, float best) {
+    const float ra0 = (float)S[F_C], ra1 = (float)S[F_C + 1], ra2 = (float)S[F_C + 2];
+    const float za0 = (float)S[F_C + 3], za1 = (float)S[F_C + 4], za2 = (float)S[F_C + 5];
+    const float cj = k_hex_c32[j], sj = k_hex_s32[j];
+    const float q0 = px * cj + py * sj, dq = dx * cj + dy * sj;
+    const float den = dq * dq + dz * dz;
+    if (!(den > 1e-2f * (dx * dx + dy * dy + dz * dz))) return true;
+    const float A = dz * ra2 - dq * za2, Am = fabsf(dz * ra2) + fabsf(dq * za2);
+    const float B = dz * ra1 - dq * za1, Bm = fabsf(dz * ra1) + fabsf(dq * za1);
+    const float C = dz * (ra0 - q0) - dq * (za0 - pz);
+    const float Cm = fabsf(dz) * (fabsf(ra0) + fabsf(q0)) + fabsf(dq) * (fabsf(za0) + fabsf(pz));
+    if (!(fabsf(B) > 1e-2f * Bm) || !(fabsf(C) > 1e-2f * Cm)) return true;
+    float us[2];
+    int nu = 0;
+    if (Am == 0.0f) {  // a straight profile: one root (the FP64 test takes -C / B too)
+        us[nu++] = -C / B;
+    } else {
+        if (!(fabsf(A) > 1e-2f * Am)) return true;
+        const float disc = B * B - 4.0f * A * C;
+        if (!(fabsf(disc) > 1e-2f * (B * B + 4.0f * fabsf(A * C)))) return true;
+        if (disc < 0.0f) return false;
+        const float sq = sqrtf(disc);
+        const float q = -0.5f * (B + copysignf(sq, B));
+        us[nu++] = q / A;
+        us[nu++] = C / q;
+    }
+    const float ls = fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(ra0) + fabsf(ra1) + fabsf(ra2) + fabsf(za0) +
+                     fabsf(za1) + fabsf(za2);
+#pragma unroll 1
+    for (int i = 0; i < nu; ++i) {
+        const float u = us[i];
+        const float mu = 1e-3f * (1.0f + fabsf(u));
+        if (u < -mu || u > 1.0f + mu) continue;
+        const float R = ra0 + u * (ra1 + u * ra2), Z = za0 + u * (za1 + u * za2);
+        const float t = ((R - q0) * dq + (Z - pz) * dz) / den;
+        const float mt = 1e-2f * (fabsf(t) + ls);
+        if (!(t > eps - mt) || !(t < best + mt)) continue;
+        const float xx = px + t * dx, xy = py + t * dy;
+        const float qj = xx * cj + xy * sj;
+        const float mw = mt + 1e-3f * (fabsf(xx) + fabsf(xy));
+        bool out = false;
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+            if (m != j && xx * k_hex_c32[m] + xy * k_hex_s32[m] > qj + mw) out = true;
+        if (!out) return true;  // a root may hit: FP64 decides
+    }
+    return false;
+}
+
 template <typename T, typename SR>
 __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
     const T ra0 = S[F_C], ra1 = S[F_C + 1], ra2 = S[F_C + 2];
@@ -748,6 +805,9 @@ __device__ __forceinline__ bool hit_hexcone(SR S, V3<T> p, V3<T> d, T eps, T tma
             if (top < -mg * (1.0f + bestf)) reach = false;
         }
         if (!reach) continue;
+        if constexpr (sizeof(T) == 8) {
+            if (!screen_wall_miss(S, j, pxf, pyf, (float)p.z, dxf, dyf, (float)d.z, (float)eps, bestf)) continue;
+        }
         const T q0 = p.x * cjj + p.y * sjj, dq = d.x * cjj + d.y * sjj;
         const T den = dq * dq + d.z * d.z;
         if (den == T(0)) continue;
