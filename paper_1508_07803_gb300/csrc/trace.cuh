@@ -579,6 +579,31 @@ __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> 
 // t0 = -(p.d)_xy / |d_xy|^2: there the linear term vanishes and |p_xy|^2 - r^2
 // is formed from a point near the cylinder, which keeps FP32 accurate for
 // rays that start tens of metres away.
+// FP32 screen of an FP64 cylinder test: false if the cylinder certainly gives no hit.  With the
+// ray at least ~6 degrees off the axis (|d_xy|^2 >= 1e-2), the FP32 closest approach to the axis
+// carries an error below 2e-5 of (|p| + |t0|); the cylinder is rejected only when the ray passes
+// more than 1e-3 of that scale outside the radius, or when the whole chord lies more than that
+// outside [eps, tmax] or outside 0 <= z <= length.  Anything else goes to the FP64 test.
+__device__ __forceinline__ bool screen_cyl_miss(const double* S, V3<double> p, V3<double> d, double eps, double tmax) {
+    const float rad = (float)S[F_C], len = (float)S[F_K1];
+    const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
+    const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
+    const float a = dx * dx + dy * dy;
+    if (!(a >= 1e-2f * (a + dz * dz))) return true;
+    const float t0 = -(px * dx + py * dy) / a;
+    const float cx = px + t0 * dx, cy = py + t0 * dy;
+    const float m = 1e-3f * (fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(t0));
+    const float dist = sqrtf(cx * cx + cy * cy);
+    if (dist > rad + m) return false;  // the ray passes outside the tube
+    const float H = (rad + m) * rsqrtf(a);  // bound on the half chord
+    const float tlo = t0 - H, thi = t0 + H;
+    const float mt = m + 1e-3f * H;
+    if (thi < (float)eps - mt || tlo > fminf((float)tmax, 3.0e38f) + mt) return false;
+    const float z0 = pz + tlo * dz, z1 = pz + thi * dz;
+    if (fmaxf(z0, z1) < -mt || fminf(z0, z1) > len + mt) return false;
+    return true;
+}
+
 template <typename T>
 __device__ __forceinline__ bool hit_cyl(const T* S, V3<T> p, V3<T> d, T eps, T tmax, LHit<T>& h) {
     const T rad = S[F_C], len = S[F_K1];
@@ -1124,6 +1149,9 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
         case SHAPE_CYL:
             if constexpr ((FEAT & FT_CYL) != 0) {
                 CNT(U_CYL);
+                if constexpr (sizeof(T) == 8) {
+                    if (!screen_cyl_miss(S, pl, dl, (double)eps, (double)bst.t)) break;
+                }
                 ok = hit_cyl(S, pl, dl, eps, bst.t, h);
             }
             break;
