@@ -677,8 +677,13 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
             mat3_mul(dryT, t1, t2);  // d/db
             for (int k = 0; k < 9; ++k) grec64[(size_t)i * 18 + 9 + k] = t2[k];
         }
-        reci[i] = make_int4(s.shape | (s.role << 4) | (s.aperture << 8) | ((asph ? 1 : 0) << 12), s.material,
-                            s.medium_front, s.medium_back);
+        // a plane whose tilted frame has only 0 and +-1 entries: its world normal comes out exact in
+        // FP32 (the FP32 error estimate then adds no rounding of the normal)
+        bool exact_n = s.shape == ROBAST_SHAPE_SAG && s.curv == 0.0 && !asph;
+        for (int k = 0; k < 9 && exact_n; ++k) exact_n = rows[k] == 0.0 || rows[k] == 1.0 || rows[k] == -1.0;
+        reci[i] = make_int4(s.shape | (s.role << 4) | (s.aperture << 8) | ((asph ? 1 : 0) << 12) |
+                                ((exact_n ? 1 : 0) << 13),
+                            s.material, s.medium_front, s.medium_back);
         feat |= (asph ? (unsigned)FT_ASPH : 0u) | (s.shape == ROBAST_SHAPE_CYLINDER ? (unsigned)FT_CYL : 0u) |
                 (s.shape == ROBAST_SHAPE_BOX ? (unsigned)FT_BOX : 0u) |
                 (s.shape == ROBAST_SHAPE_HEXCONE ? (unsigned)FT_CONE : 0u) |

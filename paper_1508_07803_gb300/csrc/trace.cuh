@@ -64,7 +64,8 @@ enum : unsigned {
 //   [34..35] SAG: the aperture's inner and outer radius (ANNULUS, SECTOR; CIRCLE: outer)
 enum { F_O = 0, F_R = 3, F_C = 12, F_K1 = 13, F_A = 14, F_AP = 22, F_RB2 = 28, F_KAP = 29, F_OL = 30, F_ADEV = 33,
        F_APR = 34, REC = 36 };
-// Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12, y = material,
+// Integer record: x = shape | role << 4 | aperture << 8 | has_asph << 12 | exact_normal << 13
+// (a plane in a frame of 0 / +-1 entries), y = material,
 // z = medium front, w = medium back.
 // Material record (doubles): [0] n, [1..16] lambda, [17..32] R, [33] sigma.
 enum { MAT_REC = 34 };
@@ -950,15 +951,38 @@ __device__ __forceinline__ void pair_advance(float& hi, float& lo, float t, floa
     lo = __fsub_rn(l, __fsub_rn(hi, s));
 }
 
+// Signed normal curvatures of the quadric c (x^2 + y^2 + k1 z^2) - 2 z = 0 at its point x, against
+// the front normal (-c x, -c y, 1 - c k1 z) / |g|: the normal curvature along a unit tangent v is
+// c (1 + (k1 - 1) v_z^2) / |g|, and v_z^2 runs over [0, 1 - n_z^2] = [0, c^2 (x^2 + y^2) / |g|^2].
+// dk widens the range on both sides (the asphere terms); a 1e-3 relative margin covers the
+// rounding of the point.  Returns the range's mid-point km and width kw.
+__device__ __forceinline__ void quadric_curvatures(float c, float k1, V3<float> x, float dk, float& km, float& kw) {
+    const float cr2 = c * c * (x.x * x.x + x.y * x.y);
+    const float gz = fmaf(-c * k1, x.z, 1.0f);
+    const float g2 = fmaf(gz, gz, cr2);
+    if (!(g2 > 0.0f)) return;  // keeps the default (sign unknown)
+    const float ig = rsqrtf(g2);
+    const float ka = c * ig, kb = c * fmaf(k1 - 1.0f, __fdividef(cr2, g2), 1.0f) * ig;
+    km = 0.5f * (ka + kb);
+    kw = fabsf(ka - kb) + 2.0f * dk + 2e-3f * fmaxf(fabsf(ka), fabsf(kb));
+}
+
 // Hit of the ray (P + t d), P = the pair (ph, pl) at (or very near) surface S, re-solved in
 // S's local frame for the small parameter dt.  Returns false where no root is found near the
 // point (a grazing ray the FP32 search only just met); the caller then keeps the search's hit.
 // kap: the curvature bound to use at this hit (the profile's local curvature for a cone wall,
-// else the surface's bound).
+// else the surface's bound); km, kw: the mid-point and width of the signed normal curvatures
+// at the hit (the default, sign unknown: 0 and 2 kap).
 template <unsigned FEAT>
 __device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph, V3<float> ph, V3<float> plo,
-                                           V3<float> d, float& dt, V3<float>& xl, V3<float>& nl, float& kap) {
+                                           V3<float> d, float& dt, V3<float>& xl, V3<float>& nl, float& kap,
+                                           float& km, float& kw) {
     kap = S[F_KAP];
+    // signed normal curvatures at the hit (positive: the surface bends towards its front side),
+    // as the mid-point km and width kw of their range over tangent directions; the default
+    // (an unknown sign) spans [-kap, kap]
+    km = 0.0f;
+    kw = 2.0f * kap;
     if constexpr ((FEAT & FT_ASPH) == 0) asph = false;
     if (((FEAT & FT_CYL) == 0 && shape == SHAPE_CYL) || ((FEAT & FT_BOX) == 0 && shape == SHAPE_BOX) ||
         ((FEAT & FT_CONE) == 0 && shape == SHAPE_HEXCONE))
@@ -985,6 +1009,7 @@ __device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph,
                 const V3<float> x = p + t * dl;
                 xl = x;
                 nl = unit(mk(-c * x.x, -c * x.y, 1.0f - c * k1 * x.z));
+                quadric_curvatures(c, k1, x, 0.0f, km, kw);
             } else {
                 float slope = 0.0f;
                 for (int it = 0; it < 2; ++it) {  // Newton from the point: quadratic convergence
@@ -996,10 +1021,17 @@ __device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph,
                     t -= (x.z - z) / fp;
                 }
                 const V3<float> x = p + t * dl;
+                const float rho = x.x * x.x + x.y * x.y;
                 float z;
-                if (!sag_slope(S, x.x * x.x + x.y * x.y, &z, &slope)) return false;
+                if (!sag_slope(S, rho, &z, &slope)) return false;
                 xl = x;
                 nl = unit(mk(-2.0f * x.x * slope, -2.0f * x.y * slope, 1.0f));
+                // the asphere terms P(r) = sum A_i r^2i add at most max(|P''|, |P'/r|) <= sum 2i(2i-1)|A_i| r^(2i-2)
+                // to a normal curvature of the base quadric (the slope factor is at most 1)
+                float dk = 0.0f;
+#pragma unroll
+                for (int i = 8; i >= 1; --i) dk = fmaf(dk, rho, (float)(2 * i * (2 * i - 1)) * fabsf(S[F_A + i - 1]));
+                quadric_curvatures(S[F_C], S[F_K1], x, dk, km, kw);
             }
             break;
         }
@@ -1092,9 +1124,14 @@ __device__ __forceinline__ bool refine_hit(const float* S, int shape, bool asph,
                 const float Rp = ra1 + 2.0f * ra2 * bu, Zp = za1 + 2.0f * za2 * bu;
                 nl = unit(mk(-Zp * cj, -Zp * sj, Rp));
                 // the wall is straight across the profile plane: its one curvature is the profile's,
-                // |r' z'' - z' r''| / (r'^2 + z'^2)^(3/2) at the hit, with a margin for the hit's error
+                // (r' z'' - z' r'') / (r'^2 + z'^2)^(3/2) at the hit (signed against the normal
+                // (-z', r') of the profile plane), with a margin for the hit's error; the other
+                // principal curvature is 0
                 const float q2 = Rp * Rp + Zp * Zp;
-                kap = 1.2f * fabsf(Rp * 2.0f * za2 - Zp * 2.0f * ra2) / (q2 * sqrtf(q2));
+                const float ks = 1.2f * (Rp * 2.0f * za2 - Zp * 2.0f * ra2) / (q2 * sqrtf(q2));
+                kap = fabsf(ks);
+                km = 0.5f * ks;
+                kw = kap;
                 break;
             }
             break;
@@ -1370,6 +1407,7 @@ struct Photon {
     float ep;  // lateral offset of the current ray (m)
     float ed;  // direction (rad)
     float eh;  // last interaction point (m)
+    float gp, gd;  // the signed carried pair: lateral (m) and direction (rad) parts
 };
 
 // STAGED: the tables fit in shared memory and every table pointer is derived
@@ -1533,6 +1571,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     ph.ep = 0.0f;
                     ph.ed = 0.0f;
                     ph.eh = 0.0f;
+                    ph.gp = 0.0f;
+                    ph.gd = 0.0f;
                 } else {
                     done = true;
                 }
@@ -1558,22 +1598,26 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             const int4 si = tb.surf_i[bst.sid];
             float e_s = 0.0f;     // FP32: coordinate scale of this hit's rounding
             float e_kap = 0.0f;   // FP32: curvature bound at this hit
+            float e_km = 0.0f, e_kw = 0.0f;  // FP32: signed normal curvatures at this hit (mid-point, width)
             bool refined = false;  // FP32: hit re-solved from the compensated position
             if constexpr (sizeof(T) == 4) {
                 e_s = fmaxf(fabsf(ph.p.x), fmaxf(fabsf(ph.p.y), fabsf(ph.p.z))) +
                       fmaxf(fabsf(S[F_O]), fmaxf(fabsf(S[F_O + 1]), fabsf(S[F_O + 2]))) + bst.t;
                 e_kap = S[F_KAP];
+                e_kw = 2.0f * e_kap;
                 pair_advance(ph.p.x, ph.plo.x, bst.t, ph.d.x);
                 pair_advance(ph.p.y, ph.plo.y, bst.t, ph.d.y);
                 pair_advance(ph.p.z, ph.plo.z, bst.t, ph.d.z);
-                float dt, kap;
+                float dt, kap, km, kw;
                 V3<float> xl, nl;
                 CNT(U_REFINE);
                 // accepted only as a correction of the search's own rounding (a grazing ray
                 // whose re-solve lands on the other root keeps the search's hit)
-                if (refine_hit<FEAT>(S, si.x & 15, (si.x >> 12) & 1, ph.p, ph.plo, ph.d, dt, xl, nl, kap) &&
+                if (refine_hit<FEAT>(S, si.x & 15, (si.x >> 12) & 1, ph.p, ph.plo, ph.d, dt, xl, nl, kap, km, kw) &&
                     fabsf(dt) <= 1e-4f * e_s) {
                     e_kap = kap;
+                    e_km = km;
+                    e_kw = kw;
                     pair_advance(ph.p.x, ph.plo.x, dt, ph.d.x);
                     pair_advance(ph.p.y, ph.plo.y, dt, ph.d.y);
                     pair_advance(ph.p.z, ph.plo.z, dt, ph.d.z);
@@ -1601,21 +1645,27 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
             // segment t) at a point off by el = (ep + t ed) / c along the surface, plus the frame
             // transform's rounding KT s / c (s: the coordinate scale of the hit's rounding); the
             // root adds ea = KA s / c along the ray.  The normal there is off by (curvature
-            // bound) x (el + ea sin(incidence)), plus rounding.  The outgoing ray's lateral offset
-            // is el times its own cosine plus ea times the sine of the turn (the part of an
+            // bound) x (el + ea sin(incidence)), plus its own rounding (none for a plane in an
+            // axis-aligned frame, whose normal comes out exact).  The outgoing ray's lateral
+            // offset is el times its own cosine plus ea times the sine of the turn (the part of an
             // along-ray shift that is across the new direction) plus the rounding of its origin.
             // Errors carried along the path add linearly (they may be correlated); the fresh
             // roundings of one interaction are independent of them and of each other and add in
-            // quadrature.
-            float e_n = 0.0f, e_l = 0.0f, e_a = 0.0f, e_c = 1.0f, e_sn = 0.0f;
+            // quadrature.  One carried error is kept signed, as a (lateral, direction) pair
+            // (gp, gd) that travels and turns exactly: the lateral offset a curved mirror turns
+            // into a direction error (so that a focusing mirror's next segment takes back part
+            // of the offset instead of adding to it, see the mirror branch).
+            float e_l = 0.0f, e_a = 0.0f, e_c = 1.0f, e_sn = 0.0f, e_ic = 1.0f, e_lat = 0.0f, e_kn = 0.0f;
             if constexpr (EST) {
                 e_c = fmaxf(fabsf((float)d_n), 1e-20f);
                 e_sn = est_sqrt(1.0f - e_c * e_c);
-                const float ic = __fdividef(1.0f, e_c);
-                e_l = est_hyp((ph.ep + (float)bst.t * ph.ed) * ic, EST_KT * e_s * ic);
-                e_a = (refined ? EST_KA : EST_KW) * e_s * ic;
+                e_ic = __fdividef(1.0f, e_c);
+                ph.gp = fmaf((float)bst.t, ph.gd, ph.gp);
+                e_lat = fmaf((float)bst.t, ph.ed, ph.ep) + fabsf(ph.gp);
+                e_l = est_hyp(e_lat * e_ic, EST_KT * e_s * e_ic);
+                e_a = (refined ? EST_KA : EST_KW) * e_s * e_ic;
                 ph.eh = est_hyp(e_l, e_a);
-                e_n = est_hyp(e_kap * (e_l + e_a * e_sn), EST_KN);
+                e_kn = ((si.x >> 13) & 1) ? 0.0f : EST_KN;
             }
             // one call site for the draw (a front-side mirror hit or a refracting face)
             if ((role == ROLE_MIRROR && front) || ((FEAT & FT_REFR) != 0 && role == ROLE_REFRACT)) {
@@ -1677,12 +1727,37 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         }
                         ph.d = unit(ph.d - (T(2) * dot(ph.d, nn)) * nn);
                         CNT(U_REFLECT);
-                        // reflection: the direction error grows by twice the normal's; the
-                        // outgoing ray leaves at the incidence cosine and turns by twice the
-                        // incidence angle (sine 2 s c)
                         if constexpr (EST) {
-                            ph.ed = est_hyp(ph.ed + 2.0f * (e_n - EST_KN), EST_KR2);
-                            ph.ep = est_hyp(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
+                            // A lateral offset L of the incoming ray moves the hit along the
+                            // surface and so turns the reflected ray by P L, with P between
+                            // 2 kmin c (sagittal) and 2 kmax / c (tangential) for signed normal
+                            // curvatures in [kmin, kmax] = km -+ kw / 2.  Their mean over
+                            // transverse directions, pm = km (c + 1/c), is applied signed; the
+                            // rest, at most pr = |km| (1/c - c) + kw / c, goes to the box.  Of
+                            // the two carried laterals (the box's, ep + t ed, and the signed
+                            // pair's) the larger becomes the signed pair, turned by -pm; the
+                            // other joins the box with its turn.  Fresh: the normal's error from
+                            // this hit's own rounding, the normal's and the new direction's
+                            // rounding, the outgoing origin's rounding and the part of the
+                            // along-ray error across the new direction (sine of the turn 2 s c).
+                            const float pm = e_km * (e_c + e_ic);
+                            const float pr = fmaf(fabsf(e_km), e_ic - e_c, e_kw * e_ic);
+                            const float lb = fmaf((float)bst.t, ph.ed, ph.ep);
+                            const float gd1 = fmaf(-pm, ph.gp, ph.gd);
+                            float dcar, lcar;
+                            if (lb > fabsf(ph.gp)) {
+                                dcar = fabsf(gd1);
+                                lcar = fabsf(ph.gp);
+                                ph.gp = lb;
+                                ph.gd = -pm * lb;
+                            } else {
+                                dcar = fabsf(pm) * lb;
+                                lcar = lb;
+                                ph.gd = gd1;
+                            }
+                            const float e_nf = e_kap * fmaf(EST_KT * e_s, e_ic, e_a * e_sn);
+                            ph.ed = est_hyp(ph.ed + dcar + pr * e_lat + 2.0f * e_nf, est_hyp(2.0f * e_kn, EST_KD));
+                            ph.ep = lcar + est_hyp(fmaf(EST_KT, e_s, e_a * (2.0f * e_sn * e_c)), EST_KP * e_s);
                         }
                     }
                 }
@@ -1704,6 +1779,15 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     na = refr_index<T>(tb.meds + (size_t)si.z * MED_REC, ph.lam);
                     nb = refr_index<T>(tb.meds + (size_t)si.w * MED_REC, ph.lam);
                 }
+                // the estimate's signed pair joins the box at a refracting face: the face's
+                // turn depends on the plane of incidence (no mean to keep signed)
+                float e_in = 0.0f, e_nc = 0.0f;
+                if constexpr (EST) {
+                    e_in = ph.ed + fabsf(ph.gd);
+                    ph.gp = 0.0f;
+                    ph.gd = 0.0f;
+                    e_nc = e_kap * fmaf(e_a, e_sn, e_l);
+                }
                 const T n1 = front ? na : nb, n2 = front ? nb : na;
                 const V3<T> nf = front ? n : T(-1) * n;
                 const T ci = -dot(ph.d, nf);
@@ -1713,7 +1797,9 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                     ph.d = unit(ph.d - (T(2) * dot(ph.d, nf)) * nf);
                     CNT(U_REFLECT);
                     if constexpr (EST) {
-                        ph.ed = est_hyp(ph.ed + 2.0f * (e_n - EST_KN), EST_KR2);
+                        // the direction error grows by twice the normal's; the outgoing ray
+                        // leaves at the incidence cosine and turns by twice the incidence angle
+                        ph.ed = est_hyp(e_in + 2.0f * e_nc, est_hyp(2.0f * e_kn, EST_KD));
                         ph.ep = est_hyp(e_l * e_c + e_a * (2.0f * e_sn * e_c), EST_KP * e_s);
                     }
                 } else {
@@ -1727,7 +1813,8 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                         // leaves at cosine ct and turns by theta_i - theta_t
                         const float ctf = fmaxf((float)ct, 1e-20f);
                         const float g = __fdividef((float)(eta * ci), ctf);
-                        ph.ed = est_hyp((ph.ed + e_n) * g + e_n, EST_KD);
+                        const float e_n = est_hyp(e_nc, e_kn);
+                        ph.ed = est_hyp((e_in + e_n) * g + e_n, EST_KD);
                         const float st = est_sqrt(1.0f - ctf * ctf);
                         ph.ep = est_hyp(e_l * ctf + e_a * fabsf(e_sn * ctf - e_c * st), EST_KP * e_s);
                     }
@@ -1756,13 +1843,14 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
         if constexpr (EST) {
             // the stored position adds its own rounding
             const float e_pos = est_hyp(ph.eh, 0.5f * EST_U * fmaxf(fabsf(ph.p.x), fmaxf(fabsf(ph.p.y), fabsf(ph.p.z))));
+            const float e_dir = ph.ed + fabsf(ph.gd);
             if (A.err) {
                 A.err[i] = e_pos;
-                A.err[n + i] = ph.ed;
+                A.err[n + i] = e_dir;
             }
             // over a bound (or an ERROR, which FP64 may not reproduce): re-traced in FP64 by the
             // next launch, which writes every output and counts the photon
-            if (A.queue_out && (e_pos > A.acc_pos || ph.ed > A.acc_dir || status == ST_ERROR)) {
+            if (A.queue_out && (e_pos > A.acc_pos || e_dir > A.acc_dir || status == ST_ERROR)) {
                 const unsigned long long k = atomicAdd(A.queue_n, 1ull);
                 if ((long long)k < A.queue_cap) {
                     A.queue_out[k] = i;
