@@ -343,8 +343,10 @@ typedef struct robast_source_group {
 typedef struct robast_sources robast_sources; /* opaque device-resident group table */
 
 /* Upload n_groups groups (host array, deep-copied) for geometry g.  Synchronous.  Also
- * allocates the FP32 accuracy guard's re-trace queue for one chunk of these photons (8 bytes per
- * photon, at most 2^27 photons), so that robast_trace_sources allocates nothing. */
+ * allocates, for one chunk of these photons (at most 2^27 photons), the FP32 accuracy guard's
+ * re-trace queue (8 bytes per photon) and the chunk's coherent-order scratch (generated origins
+ * and the sort's counts, about 13 bytes per photon), so that robast_trace_sources allocates
+ * nothing. */
 int robast_sources_create(const robast_geom* g, const robast_source_group* groups, int32_t n_groups,
                           robast_sources** out);
 void robast_sources_free(robast_sources* s);
@@ -358,9 +360,12 @@ int robast_sources_info(const robast_sources* s, int32_t* n_groups, int64_t* n_p
  * total photon count, any field NULL) may be NULL.  opts as for
  * robast_trace_ex (variant_of_photon must be NULL).  Asynchronous; issues
  * only memsets and kernel launches on the stream (with the FP32 accuracy guard
- * on: per chunk of 2^27 photons, the trace launch and the FP64 re-trace
- * launch of the chunk's queued photons), so it can be captured in a CUDA
- * graph.
+ * on: per chunk of 2^27 photons, the coherent-order sort of the chunk's
+ * generated origins unless opts->coherent_order is -1, the trace launch and
+ * the FP64 re-trace launch of the chunk's queued photons), so it can be
+ * captured in a CUDA graph once a first call on the device has run outside
+ * the capture (the sort's kernels take their shared-memory size then).
+ * Results do not depend on the order.
  */
 int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64_t seed,
                          unsigned long long* group_counts, const robast_trace_out* out,

@@ -515,7 +515,7 @@ def sources_create(geom: Geometry, groups) -> Sources:
 def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, precision: int = 32,
                   max_bounces: int = 100, stream=None, out: Optional[dict] = None, first_photon_id: int = 0,
                   eps: Optional[float] = None, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0,
-                  accuracy=None, work_units=None):
+                  accuracy=None, work_units=None, coherent_order: int = 0):
     """robast_trace_sources: trace every photon of the source groups in one launch.
 
     group_counts: CUDA int64 tensor [n_groups, 8], added to.  out: optional
@@ -523,6 +523,9 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
     accuracy as for trace() (FP32: the FP64 re-trace is a second launch).
     work_units: optional CUDA int64 tensor [N_UNITS] (FP32 only): run the
     counting build (block 128) and add its work units to it.
+    coherent_order: -1 traces the photons in id order instead of sorting each
+    chunk by the cell of its generated origins (FP32 with the guard); the
+    results are the same.
     """
     import torch
     lib = load()
@@ -537,7 +540,8 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
     if out is not None:
         tout = _trace_out(out)
     o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), None, first_photon_id, eps, block_size,
-              blocks_per_sm, units=work_units, refill_min=refill_min, accuracy=_accuracy(geom, precision, accuracy))
+              blocks_per_sm, units=work_units, coherent_order=coherent_order, refill_min=refill_min,
+              accuracy=_accuracy(geom, precision, accuracy))
     _check(lib.robast_trace_sources(geom.handle, src.handle, ctypes.c_uint64(seed & (2**64 - 1)),
                                     ctypes.c_void_p(group_counts.data_ptr()),
                                     ctypes.byref(tout) if tout is not None else None, ctypes.byref(o)))

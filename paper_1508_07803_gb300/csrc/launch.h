@@ -61,6 +61,11 @@ long long order_scratch_bytes(long long n);
 cudaError_t build_order_f32(const float* o, long long n, void* scratch, int** order, int sms, cudaStream_t s);
 cudaError_t build_order_f64(const double* o, long long n, void* scratch, int** order, int sms, cudaStream_t s);
 
+// Source mode: the FP32-rounded origins (x then y, [2 nw]) of photons base .. base + nw - 1 of
+// the groups, generated as the trace kernel generates them (the coherent-order sort's input).
+cudaError_t launch_src_origins(const SrcGroup* groups, int n_groups, long long base, long long nw,
+                               long long first_id, unsigned long long seed, float* xy, int sms, cudaStream_t s);
+
 // Launch the persistent trace kernel; returns the cudaError_t of the launch.
 cudaError_t launch_trace_f32(const TraceArgs<float>& a, int block, int grid, size_t smem, cudaStream_t s,
                              unsigned prof);

@@ -922,6 +922,10 @@ struct robast_sources {
     // qcap photon indices
     unsigned long long* d_queue = nullptr;
     long long qcap = 0;
+    // the coherent order of a chunk of qcap photons: their generated origins (x, y in FP32) and
+    // the counting sort's scratch (order_scratch_bytes(qcap))
+    float* d_xy = nullptr;
+    void* d_ord = nullptr;
 };
 
 // The accuracy guard re-traces a photon whose error estimate exceeds this fraction of a bound.
@@ -1129,6 +1133,10 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     // one launch over all work, or (source mode with the guard) chunks of the queue's size, each
     // followed by its FP64 re-trace
     const long long chunk = guard && src ? qcap : n;
+    // source mode with the guard: each chunk's photons in coherent order too, sorted by the cell
+    // of their generated origins (the photons of one group and cell share their path, so a warp's
+    // lanes and, through the queue's fill order, the re-trace's stay together)
+    const bool src_order = guard && src && src->d_xy && src->d_ord && o.coherent_order >= 0 && !a.units;
     cudaError_t e = cudaSuccess;
     for (long long base = 0; base < n && e == cudaSuccess; base += chunk) {
         a.work_base = base;
@@ -1138,6 +1146,14 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
             e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
             if (e == cudaSuccess && guard) e = cudaMemsetAsync(qhdr, 0, sizeof(unsigned long long), s);
             if (e != cudaSuccess) break;
+        }
+        if (src_order) {
+            int* order = nullptr;
+            e = launch_src_origins(src->d_groups, src->n_groups, base, a.n_work, a.first_id, seed, src->d_xy,
+                                   g->num_sms, s);
+            if (e == cudaSuccess) e = build_order_f32(src->d_xy, a.n_work, src->d_ord, &order, g->num_sms, s);
+            if (e != cudaSuccess) break;
+            a.order = order;
         }
         if constexpr (sizeof(T) == 4)
             e = launch_trace_f32(a, block, (int)grid, smem, s, trace_profile(g, src != nullptr));
@@ -1228,9 +1244,13 @@ extern "C" int robast_sources_create(const robast_geom* g, const robast_source_g
     if (e == cudaSuccess) e = cudaMalloc(&s->d_groups, h.size() * sizeof(SrcGroup));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_groups, h.data(), h.size() * sizeof(SrcGroup), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_queue, (size_t)(4 + s->qcap) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_xy, (size_t)s->qcap * 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ord, (size_t)order_scratch_bytes(s->qcap));
     if (e != cudaSuccess) {
         if (s->d_groups) cudaFree(s->d_groups);
         if (s->d_queue) cudaFree(s->d_queue);
+        if (s->d_xy) cudaFree(s->d_xy);
+        if (s->d_ord) cudaFree(s->d_ord);
         delete s;
         return cuda_fail(e, "robast_sources_create");
     }
@@ -1243,6 +1263,8 @@ extern "C" void robast_sources_free(robast_sources* s) {
     cudaDeviceSynchronize();
     cudaFree(s->d_groups);
     cudaFree(s->d_queue);
+    cudaFree(s->d_xy);
+    cudaFree(s->d_ord);
     delete s;
 }
 

@@ -1533,7 +1533,7 @@ __global__ void __launch_bounds__(BLOCK, (TraceBounds<T, BLOCK, SRC>::min_blocks
                 const long long widx = (long long)base + __popc(m & lt_mask);
                 if (widx < n_work) {
                     const long long idx = A.queue_in ? A.queue_in[widx]
-                                          : A.order  ? (long long)A.order[widx]
+                                          : A.order  ? A.work_base + (long long)A.order[widx]
                                                      : A.work_base + widx;
                     ph.i = idx;
                     if constexpr (SRC) {
