@@ -359,13 +359,13 @@ int robast_sources_info(const robast_sources* s, int32_t* n_groups, int64_t* n_p
  * collection efficiency = counts[1] / counts[7].  `out` (device arrays of the
  * total photon count, any field NULL) may be NULL.  opts as for
  * robast_trace_ex (variant_of_photon must be NULL).  Asynchronous; issues
- * only memsets and kernel launches on the stream (with the FP32 accuracy guard
- * on: per chunk of 2^27 photons, the coherent-order sort of the chunk's
- * generated origins unless opts->coherent_order is -1, the trace launch and
- * the FP64 re-trace launch of the chunk's queued photons), so it can be
- * captured in a CUDA graph once a first call on the device has run outside
- * the capture (the sort's kernels take their shared-memory size then).
- * Results do not depend on the order.
+ * only memsets and kernel launches on the stream: per chunk of 2^27 photons,
+ * the coherent-order sort of the chunk's generated origins (unless
+ * opts->coherent_order is -1), the trace launch and, with the FP32 accuracy
+ * guard on, the FP64 re-trace launch of the chunk's queued photons.  It can
+ * be captured in a CUDA graph once a first call on the device has run
+ * outside the capture (the sort's kernels take their shared-memory size
+ * then).  Results do not depend on the order.
  */
 int robast_trace_sources(const robast_geom* g, const robast_sources* src, uint64_t seed,
                          unsigned long long* group_counts, const robast_trace_out* out,

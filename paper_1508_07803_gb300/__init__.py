@@ -88,7 +88,7 @@ class TraceOpts(ctypes.Structure):
 
 # Default FP32 accuracy: final positions within 1e-6 of the system focal length, final
 # directions within 1e-5 rad of an exact trace of the same inputs (the accuracy guard re-traces
-# in FP64 every photon whose running error estimate exceeds half of either bound).
+# in FP64 every photon whose running error estimate exceeds 0.9 of either bound).
 ACCURACY_REL_POS = 1e-6
 ACCURACY_DIR = 1e-5
 
@@ -301,8 +301,8 @@ def trace(geom: Geometry, origins, dirs, wavelengths, seed: int = 0, precision: 
     photons) shape the launch only: the results do not depend on them.
     accuracy (FP32): None = final positions within 1e-6 of the geometry's focal
     length and directions within 1e-5 rad of an exact trace, enforced by
-    re-tracing in FP64 the photons whose running error estimate exceeds half a
-    bound; a (pos_m, dir_rad) pair sets the bounds; False turns the guard off.
+    re-tracing in FP64 the photons whose running error estimate exceeds 0.9 of
+    a bound; a (pos_m, dir_rad) pair sets the bounds; False turns the guard off.
     out["retraced"] counts (re-traced, over a bound but not re-traced).
     error_estimate: also return out["err"] [2, n] float32, the per-photon
     position / direction error estimate (-1 where the photon was re-traced).
@@ -524,8 +524,7 @@ def trace_sources(geom: Geometry, src: Sources, group_counts, seed: int = 0, pre
     work_units: optional CUDA int64 tensor [N_UNITS] (FP32 only): run the
     counting build (block 128) and add its work units to it.
     coherent_order: -1 traces the photons in id order instead of sorting each
-    chunk by the cell of its generated origins (FP32 with the guard); the
-    results are the same.
+    chunk by the cell of its generated origins; the results are the same.
     """
     import torch
     lib = load()

@@ -929,11 +929,11 @@ struct robast_sources {
 };
 
 // The accuracy guard re-traces a photon whose error estimate exceeds this fraction of a bound.
-// Measured on 1e6 photons of each test system: among photons whose error exceeds a tenth of the
-// bound, the error stays below 0.9 of the estimate, so an unflagged photon stays below 0.81 of
-// the bound; the largest error of an unflagged photon was 0.24 of the bound.  (At 0.8 the
-// two-mirror systems re-traced 17% of their photons, whose estimates cluster just under the
-// bound while their errors stay below a quarter of it.)
+// Measured with the guard off on 2.5e5-3.2e5 photons of the dish, two-mirror, GCT-like and cone
+// systems: among photons whose error exceeds 0.3 of the bound, the error stays below 0.87 of the
+// estimate, so an unflagged photon stays below 0.78 of the bound (between 0.1 and 0.3 of the
+// bound the estimate can fall up to 5% short, far inside it); the largest error of an unflagged
+// photon was 0.55 of the bound.
 static const double kGuardFrac = 0.9;
 
 // Photons per launch of a source-mode trace with the accuracy guard on: each chunk is followed by
@@ -1041,7 +1041,7 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
     if (sizeof(T) == 4) a.err = out->err;
     if (!(o.accuracy_pos >= 0.0) || !(o.accuracy_dir >= 0.0))
         return fail(ROBAST_E_INVALID, "robast_trace: accuracy bounds must be >= 0");
-    // FP32 accuracy guard: photons over half a bound are queued and re-traced in FP64
+    // FP32 accuracy guard: photons over 0.9 of a bound (kGuardFrac) are queued and re-traced in FP64
     const bool guard = sizeof(T) == 4 && (o.accuracy_pos > 0.0 || o.accuracy_dir > 0.0) && !o.track && !o.work_units;
     if (o.track) {
         const robast_track_opts& t = *o.track;
@@ -1130,13 +1130,13 @@ static int do_trace(const robast_geom* g, const void* origins, const void* dirs,
         a.acc_dir = o.accuracy_dir > 0.0 ? (float)(kGuardFrac * o.accuracy_dir) : INFINITY;
         a.retraced = out->retraced ? out->retraced : qhdr + 1;
     }
-    // one launch over all work, or (source mode with the guard) chunks of the queue's size, each
-    // followed by its FP64 re-trace
-    const long long chunk = guard && src ? qcap : n;
-    // source mode with the guard: each chunk's photons in coherent order too, sorted by the cell
-    // of their generated origins (the photons of one group and cell share their path, so a warp's
-    // lanes and, through the queue's fill order, the re-trace's stay together)
-    const bool src_order = guard && src && src->d_xy && src->d_ord && o.coherent_order >= 0 && !a.units;
+    // source mode: each chunk's photons in coherent order, sorted by the cell of their generated
+    // origins (the photons of one group and cell share their path, so a warp's lanes and, through
+    // the queue's fill order, the FP64 re-trace's stay together)
+    const bool src_order = src && src->d_xy && src->d_ord && o.coherent_order >= 0 && !a.units;
+    // one launch over all work, or (source mode with the guard or the order) chunks of the source
+    // handle's chunk size, each followed by its FP64 re-trace
+    const long long chunk = src && (guard || src_order) ? src->qcap : n;
     cudaError_t e = cudaSuccess;
     for (long long base = 0; base < n && e == cudaSuccess; base += chunk) {
         a.work_base = base;
