@@ -852,6 +852,7 @@ extern "C" int robast_build_geometry(const robast_geom_desc* d, robast_geom** ou
     t.n_med = std::max(1, d->n_media);
     g->tab64 = t;
     g->tab64.surf = base + o64;
+    g->tab64.surf32 = reinterpret_cast<const float*>(base + o32);  // the FP64 search's FP32 screens
     g->tab32 = t;
     g->tab32.surf = base + o32;
     g->work = reinterpret_cast<unsigned long long*>(base + ow);

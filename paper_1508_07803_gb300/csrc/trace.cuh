@@ -119,6 +119,8 @@ struct Tables {
     const double* meds;
     const float* mats32;  // the material records rounded to FP32 (the FP32 kernel's reads), followed
                           // (16-byte aligned) by the medium records rounded to FP32: meds32(tb)
+    const float* surf32;  // FP64 tables: the FP32 surface records (global memory), for the FP32
+                          // screens of the FP64 search; NULL elsewhere
     int n_surf, n_nodes, n_prims, n_var, n_glob, n_mat, n_med, pad;
 };
 
@@ -432,7 +434,7 @@ __device__ __forceinline__ bool newton_step_fp64(const T* S, V3<T> p, V3<T> d, T
 // a root counts as excluded only when it lies more than 1e-3 of the coordinates outside
 // [eps, tmax], off the conic's branch, or outside the aperture.
 template <typename SR>
-__device__ __forceinline__ bool screen_sag_miss(SR S, int ap, V3<double> p, V3<double> d, double eps, double tmax) {
+__device__ __forceinline__ bool screen_sag_miss(SR S, int ap, V3<float> p, V3<float> d, double eps, double tmax) {
     const float c = (float)S[F_C], k1 = (float)S[F_K1];
     const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
     const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
@@ -585,7 +587,8 @@ __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> 
 // carries an error below 2e-5 of (|p| + |t0|); the cylinder is rejected only when the ray passes
 // more than 1e-3 of that scale outside the radius, or when the whole chord lies more than that
 // outside [eps, tmax] or outside 0 <= z <= length.  Anything else goes to the FP64 test.
-__device__ __forceinline__ bool screen_cyl_miss(const double* S, V3<double> p, V3<double> d, double eps, double tmax) {
+template <typename SR>
+__device__ __forceinline__ bool screen_cyl_miss(SR S, V3<float> p, V3<float> d, double eps, double tmax) {
     const float rad = (float)S[F_C], len = (float)S[F_K1];
     const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
     const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
@@ -1160,24 +1163,51 @@ __device__ __noinline__ bool hit_hexcone_call(const T* S, V3<T> p, V3<T> d, T ep
     return hit_hexcone(S, p, d, eps, tmax, *h);
 }
 
+// The FP64 search's photon in FP32 for the FP32 screens: the position as a float pair (hi + lo)
+// and the direction.
+struct Ray32 {
+    V3<float> ph, pl, d;
+};
+
 template <bool C, unsigned FEAT = FT_ALL, typename T>
 __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p, V3<T> d, T eps, T tol, Best<T>& bst,
-                                             unsigned* cnt) {
+                                             unsigned* cnt, const Ray32& r32, bool use32) {
     CNT(U_REBASE);
     const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)sid * REC;
     const int flags = tb.surf_i[sid].x;
     const int shape = flags & 15;
+    // FP64 nearest-hit search, sag surfaces without asphere terms and cylinders: an FP32 solve
+    // rejects the candidate when it is well conditioned and every root lies clearly outside the
+    // surface's reach (off the conic's branch, outside [eps, t_best], outside the aperture or the
+    // tube's length); any other case goes to the FP64 solve, so the result is the FP64 one.
+    // With the FP32 records at hand the screen also rebases in FP32 (the position pair minus the
+    // origin pair, a few ulps of the local scale; the margins are 1e-3 of the coordinates), so a
+    // rejected candidate costs no FP64 instruction.
+    bool screened = false;
+    if constexpr (sizeof(T) == 8) {
+        const bool sag_plain = shape == SHAPE_SAG && ((flags >> 12) & 1) == 0;
+        const bool cyl = (FEAT & FT_CYL) != 0 && shape == SHAPE_CYL;
+        if (use32 && (sag_plain || cyl)) {
+            const float* S32 = tb.surf32 + (size_t)sid * REC;
+            const float qx = __fadd_rn(__fsub_rn(r32.ph.x, S32[F_O]), __fsub_rn(r32.pl.x, S32[F_OL]));
+            const float qy = __fadd_rn(__fsub_rn(r32.ph.y, S32[F_O + 1]), __fsub_rn(r32.pl.y, S32[F_OL + 1]));
+            const float qz = __fadd_rn(__fsub_rn(r32.ph.z, S32[F_O + 2]), __fsub_rn(r32.pl.z, S32[F_OL + 2]));
+            const V3<float> q32 = to_local_vec(S32, mk(qx, qy, qz)), d32 = to_local_vec(S32, r32.d);
+            const bool may = sag_plain ? screen_sag_miss(S32, (flags >> 8) & 15, q32, d32, (double)eps, (double)bst.t)
+                                       : screen_cyl_miss(S32, q32, d32, (double)eps, (double)bst.t);
+            if (!may) return;
+            screened = true;
+        }
+    }
     const V3<T> pl = to_local_pt(S, p), dl = to_local_vec(S, d);
     LHit<T> h;
     bool ok = false, err = false;
     switch (shape) {
         case SHAPE_SAG:
             if constexpr (sizeof(T) == 8) {
-                // FP64 nearest-hit search, no asphere: an FP32 solve rejects the candidate when it is
-                // well conditioned and every root lies clearly off the branch, outside [eps, t_best]
-                // or outside the aperture; any other case goes to the FP64 solve, so the result is
-                // the FP64 one
-                if (((flags >> 12) & 1) == 0 && !screen_sag_miss(S, (flags >> 8) & 15, pl, dl, (double)eps, (double)bst.t))
+                if (!screened && ((flags >> 12) & 1) == 0 &&
+                    !screen_sag_miss(S, (flags >> 8) & 15, mk((float)pl.x, (float)pl.y, (float)pl.z),
+                                     mk((float)dl.x, (float)dl.y, (float)dl.z), (double)eps, (double)bst.t))
                     break;
             }
             ok = hit_sag<C, (FEAT & FT_ASPH) != 0>(S, (flags >> 8) & 15, (flags >> 12) & 1, pl, dl, eps, bst.t, tol, h,
@@ -1187,7 +1217,10 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
             if constexpr ((FEAT & FT_CYL) != 0) {
                 CNT(U_CYL);
                 if constexpr (sizeof(T) == 8) {
-                    if (!screen_cyl_miss(S, pl, dl, (double)eps, (double)bst.t)) break;
+                    if (!screened && !screen_cyl_miss(S, mk((float)pl.x, (float)pl.y, (float)pl.z),
+                                                      mk((float)dl.x, (float)dl.y, (float)dl.z), (double)eps,
+                                                      (double)bst.t))
+                        break;
                 }
                 ok = hit_cyl(S, pl, dl, eps, bst.t, h);
             }
@@ -1242,7 +1275,17 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
     bst.sid = 0x7fffffff;
     bst.err = false;
     const int4 vr = tb.variants[var];
-    for (int k = 0; k < vr.z; ++k) test_surface<C, FEAT>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt);
+    Ray32 r32{};
+    bool use32 = false;
+    if constexpr (sizeof(T) == 8) {
+        if (tb.surf32) {
+            use32 = true;
+            r32.ph = mk((float)p.x, (float)p.y, (float)p.z);
+            r32.pl = mk((float)(p.x - (double)r32.ph.x), (float)(p.y - (double)r32.ph.y), (float)(p.z - (double)r32.ph.z));
+            r32.d = mk((float)d.x, (float)d.y, (float)d.z);
+        }
+    }
+    for (int k = 0; k < vr.z; ++k) test_surface<C, FEAT>(tb, tb.glob[vr.y + k], p, d, eps, tol, bst, cnt, r32, use32);
     if (vr.x < 0) return;
     // Inverse direction with zero components replaced by +-1e-30, so that the
     // FMA slab form never meets inf - inf (the boxes are padded, so a ray grazing
@@ -1299,7 +1342,8 @@ __device__ __forceinline__ void nearest_hit(const Tables& tb, int var, V3<T> p, 
             }
         }
         if (ref < 0) break;
-        for (int k = 0; k < n; ++k) test_surface<C, FEAT>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt);
+        for (int k = 0; k < n; ++k)
+            test_surface<C, FEAT>(tb, tb.prims[ref + k], p, d, eps, tol, bst, cnt, r32, use32);
         update_tc();
         pop(ref, n);
     }
