@@ -475,6 +475,62 @@ __device__ __forceinline__ bool screen_sag_miss(SR S, int ap, V3<float> p, V3<fl
     return false;
 }
 
+// FP32 screen of an FP64 aspheric sag test: false only where the FP64 test certainly gives up on
+// the surface before its Newton iteration.  The FP64 test takes the first conic root (ascending)
+// that lies on the branch and beyond eps; it gives up when that root's point lies outside the
+// Newton seed domain or, away from grazing incidence, further outside the aperture than the
+// asphere terms can move the hit; and it finds nothing when no root qualifies.  The screen takes
+// the same steps on the FP32 solve (well conditioned as in screen_sag_miss: roots to 1e-4
+// relative, points to 1e-3 of the coordinates) and decides each comparison only outside that
+// margin; anything closer, and any root the FP64 test would hand to Newton, goes to FP64.
+template <typename SR>
+__device__ __forceinline__ bool screen_asph_miss(SR S, int ap, V3<float> p, V3<float> d, double eps) {
+    const float c = (float)S[F_C], k1 = (float)S[F_K1];
+    if (c == 0.0f) return true;  // a plane base: FP64 decides
+    const float px = p.x, py = p.y, pz = p.z, dx = d.x, dy = d.y, dz = d.z;
+    const float ac = fabsf(c), ak = fabsf(k1);
+    const float mp = fabsf(px) + fabsf(py) + fabsf(pz);
+    const float a = c * (dx * dx + dy * dy + k1 * dz * dz);
+    const float b = c * (px * dx + py * dy + k1 * pz * dz) - dz;
+    const float g = c * (px * px + py * py + k1 * pz * pz) - 2.0f * pz;
+    const float aa = ac * (dx * dx + dy * dy + ak * dz * dz);
+    const float bb = ac * (fabsf(px * dx) + fabsf(py * dy) + ak * fabsf(pz * dz)) + fabsf(dz);
+    const float gg = ac * (px * px + py * py + ak * pz * pz) + 2.0f * fabsf(pz);
+    if (!(fabsf(a) > 1e-2f * aa) || !(fabsf(b) > 1e-2f * bb) || !(fabsf(g) > 1e-2f * gg)) return true;
+    const float disc = b * b - a * g;
+    if (!(fabsf(disc) > 1e-2f * (b * b + fabsf(a * g)))) return true;
+    if (disc < 0.0f) return false;  // no conic root: FP64 finds none either
+    const float sq = sqrtf(disc);
+    const float qq = -(b + copysignf(sq, b));
+    const float t1 = qq / a, t2 = g / qq;
+    const float tl = fminf(t1, t2), th = fmaxf(t1, t2);
+    if (!(th - tl > 2e-3f * (fabsf(tl) + fabsf(th) + mp))) return true;  // their order is uncertain
+    const float ep = (float)eps;
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
+        const float t = i ? th : tl;
+        const float mt = 1e-3f * (fabsf(t) + mp);
+        const float qx = px + t * dx, qy = py + t * dy, qz = pz + t * dz;
+        const float v = k1 * c * qz - 1.0f, mv = 1e-2f + ac * ak * mt;
+        if (v > mv) continue;             // off the branch in FP64 too
+        if (!(v < -mv)) return true;      // on the edge of the branch
+        if (t < ep - mt) continue;        // at or before eps in FP64 too
+        if (!(t > ep + mt)) return true;  // near eps
+        // the first qualifying root: the seed domain, then the pre-check
+        const float eq = mt + 1e-3f * (fabsf(qx) + fabsf(qy));
+        const float r = sqrtf(qx * qx + qy * qy), rb = sqrtf((float)S[F_RB2]);
+        if (r > rb * 1.001f + eq) return false;
+        if (!(r < rb * 0.999f - eq)) return true;
+        const float mx = -c * qx, my = -c * qy, mz = 1.0f - c * k1 * qz;
+        const float nn = mx * mx + my * my + mz * mz;
+        const float dn = fabsf(dx * mx + dy * my + dz * mz);
+        if (!(dn * dn > 0.0025f * 1.01f * nn)) return true;  // grazing, or near the threshold: Newton in FP64
+        const float m = 2.0f * (float)S[F_ADEV] * sqrtf(nn) / dn + 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(t));
+        return aperture_near(S, ap, qx, qy, 1.001f * m + eq);
+    }
+    return false;  // no root qualifies: FP64 finds no hit
+}
+
 // Aspheres: Newton from the first on-branch root beyond eps.
 template <bool C, bool ASPH = true, typename T, typename SR>
 __device__ __forceinline__ bool hit_sag(SR S, int ap, bool asph, V3<T> p, V3<T> d, T eps, T tmax, T tol, LHit<T>& h,
@@ -1176,25 +1232,28 @@ __device__ __forceinline__ void test_surface(const Tables& tb, int sid, V3<T> p,
     const T* S = reinterpret_cast<const T*>(tb.surf) + (size_t)sid * REC;
     const int flags = tb.surf_i[sid].x;
     const int shape = flags & 15;
-    // FP64 nearest-hit search, sag surfaces without asphere terms and cylinders: an FP32 solve
-    // rejects the candidate when it is well conditioned and every root lies clearly outside the
-    // surface's reach (off the conic's branch, outside [eps, t_best], outside the aperture or the
-    // tube's length); any other case goes to the FP64 solve, so the result is the FP64 one.
+    // FP64 nearest-hit search, sag surfaces and cylinders: an FP32 solve rejects the candidate when
+    // it is well conditioned and every root lies clearly outside the surface's reach (off the
+    // conic's branch, outside [eps, t_best], outside the aperture or the tube's length; for an
+    // asphere, where the FP64 test would give up before Newton); any other case goes to the FP64
+    // solve, so the result is the FP64 one.
     // With the FP32 records at hand the screen also rebases in FP32 (the position pair minus the
     // origin pair, a few ulps of the local scale; the margins are 1e-3 of the coordinates), so a
     // rejected candidate costs no FP64 instruction.
     bool screened = false;
     if constexpr (sizeof(T) == 8) {
         const bool sag_plain = shape == SHAPE_SAG && ((flags >> 12) & 1) == 0;
+        const bool sag_asph = (FEAT & FT_ASPH) != 0 && shape == SHAPE_SAG && ((flags >> 12) & 1) != 0;
         const bool cyl = (FEAT & FT_CYL) != 0 && shape == SHAPE_CYL;
-        if (use32 && (sag_plain || cyl)) {
+        if (use32 && (sag_plain || sag_asph || cyl)) {
             const float* S32 = tb.surf32 + (size_t)sid * REC;
             const float qx = __fadd_rn(__fsub_rn(r32.ph.x, S32[F_O]), __fsub_rn(r32.pl.x, S32[F_OL]));
             const float qy = __fadd_rn(__fsub_rn(r32.ph.y, S32[F_O + 1]), __fsub_rn(r32.pl.y, S32[F_OL + 1]));
             const float qz = __fadd_rn(__fsub_rn(r32.ph.z, S32[F_O + 2]), __fsub_rn(r32.pl.z, S32[F_OL + 2]));
             const V3<float> q32 = to_local_vec(S32, mk(qx, qy, qz)), d32 = to_local_vec(S32, r32.d);
-            const bool may = sag_plain ? screen_sag_miss(S32, (flags >> 8) & 15, q32, d32, (double)eps, (double)bst.t)
-                                       : screen_cyl_miss(S32, q32, d32, (double)eps, (double)bst.t);
+            const bool may = sag_plain  ? screen_sag_miss(S32, (flags >> 8) & 15, q32, d32, (double)eps, (double)bst.t)
+                             : sag_asph ? screen_asph_miss(S32, (flags >> 8) & 15, q32, d32, (double)eps)
+                                        : screen_cyl_miss(S32, q32, d32, (double)eps, (double)bst.t);
             if (!may) return;
             screened = true;
         }
