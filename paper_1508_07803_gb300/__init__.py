@@ -574,7 +574,7 @@ def param_layout(geom: Geometry):
 def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed: int = 0, precision: int = 32,
                tau: float = 0.5e-3, d_obj: float = 1.0, grad=True, max_bounces: int = 100, stream=None,
                variant_of_photon=None, first_photon_id: int = 0, eps: Optional[float] = None, out=None,
-               work_units=None):
+               work_units=None, coherent_order: int = 0):
     """robast_trace_grad: frozen-path objective value and d_obj * gradient.
 
     Returns (value, grad [n_surfaces, 16] float64 CUDA tensor or None, info dict).
@@ -582,6 +582,7 @@ def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed
     work_units: optional CUDA int64 tensor [>= 3], added to: FP64 interactions of the
     forward passes, interactions replayed by the reverse sweeps, dual-number interactions
     (the last two in the derivative precision: the trace's, or FP64 for geometries with cones).
+    coherent_order: as for trace() (launch shape only; the sums are the same bits).
     """
     import torch
     lib = load()
@@ -602,7 +603,7 @@ def trace_grad(geom: Geometry, origins, dirs, wavelengths, objective="msr", seed
         stream = torch.cuda.current_stream(origins.device)
     vop = ctypes.c_void_p(variant_of_photon.data_ptr()) if variant_of_photon is not None else None
     o = _opts(precision, max_bounces, ctypes.c_void_p(stream.cuda_stream), vop, first_photon_id, eps, 0, 0,
-              units=work_units)
+              units=work_units, coherent_order=coherent_order)
     val = ctypes.c_double()
     info = (ctypes.c_double * 8)()
     _check(lib.robast_trace_grad(geom.handle, _ptr(origins), _ptr(dirs), _ptr(wavelengths), n,

@@ -330,7 +330,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? ROBAST_GRAD_MIN_BLOCKS
     // photons of the current variant counted in a register, added when the variant changes
     int cnt_var = -1;
     unsigned long long cnt_n = 0ull;
-    for (long long i = blockIdx.x * (long long)BLOCK + threadIdx.x; i < n; i += (long long)gridDim.x * BLOCK) {
+    for (long long j = blockIdx.x * (long long)BLOCK + threadIdx.x; j < n; j += (long long)gridDim.x * BLOCK) {
+        // in coherent order a warp's photons start close together and share their facets; every
+        // photon keeps its index, random stream and contributions (integer sums: any order)
+        const long long i = A.order ? (long long)A.order[j] : j;
         const V3<double> p0 = mk((double)A.o[i], (double)A.o[n + i], (double)A.o[2 * n + i]);
         const V3<double> d0 = mk((double)A.d[i], (double)A.d[n + i], (double)A.d[2 * n + i]);
         const T lam = A.lam[i];

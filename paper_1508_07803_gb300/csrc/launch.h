@@ -42,6 +42,7 @@ struct GradArgs {
     unsigned long long* vals;  // [n_variants * 8 * 2]
     unsigned long long* units; // optional [3]: FP64 interactions of the forward passes, interactions
                                // replayed by the reverse sweeps, dual-number interactions
+    const int* order;          // optional processing order (work index -> photon index)
 };
 // resident blocks of 128 threads per SM; _r64: FP32 search with FP64 derivative passes (cones)
 int grad_blocks_per_sm_f32(size_t smem);

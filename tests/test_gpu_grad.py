@@ -88,6 +88,19 @@ def test_cone_soft_ce_gradient_matches_oracle_duals(precision, tol):
     assert np.max(_rel(g[1, 10:16], rg[1, 10:16])) < tol, (g[1, 10:16], rg[1, 10:16])
 
 
+def test_cone_soft_ce_gradient_does_not_depend_on_the_order():
+    """Coherent (origin-cell) order and id order give the same bits: contributions are summed
+    in 128-bit fixed point."""
+    scene = W.cone_scene(n_variants=1, seed=0)
+    H = W.cone_heights(1)[0]
+    b = W.concat([W.hexagon_bundle(20_011, W.CONE_A_IN, H + W.CONE_WINDOW + 1e-4, math.radians(a), seed=5,
+                                   stream=80 + i) for i, a in enumerate((5.0, 20.0, 28.0, 33.0))])
+    runs = [_gpu(scene, b, "soft_ce", 32, seed=4, max_bounces=30, coherent_order=c) for c in (1, -1, 0)]
+    for v, g, _ in runs[1:]:
+        assert v == runs[0][0]
+        assert np.array_equal(g, runs[0][1])
+
+
 def test_autograd_function_returns_the_launch_gradient():
     scene, b = W.lst_workload(2_000, seed=9, angles_deg=(0.5,))
     F = robast.objective_function()
@@ -180,14 +193,17 @@ def test_two_mirror_gradient_covers_primary_and_secondary(precision, tol):
 
 
 def test_gradient_is_bit_identical_from_run_to_run():
-    """The sums over photons are fixed point with integer atomics: the order in which photons
-    finish does not change a bit of the value or the gradient."""
+    """The sums over photons are fixed point with integer atomics: neither the order in which
+    photons finish nor the processing order changes a bit of the value or the gradient."""
     scene, b, vop, _ = W.dish_batch(n_dishes=4, n_min=60, n_max=198, photons_per_dish=50_000)
     geom = robast.build_geometry(scene)
     o, d, w = _dev(b, 32)
     v = torch.from_numpy(vop).cuda()
     runs = [robast.trace_grad(geom, o, d, w, objective="msr", precision=32, seed=1, variant_of_photon=v)
             for _ in range(3)]
+    # photons in the coherent (origin-cell) order instead of id order: the same bits too
+    runs.append(robast.trace_grad(geom, o, d, w, objective="msr", precision=32, seed=1, variant_of_photon=v,
+                                  coherent_order=1))
     geom.close()
     for val, g, _ in runs[1:]:
         assert val == runs[0][0]
