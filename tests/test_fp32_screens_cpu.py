@@ -1,4 +1,4 @@
-"""The two FP32 shortcuts of the CUDA path, checked numerically on the CPU.
+"""Three FP32 shortcuts of the CUDA path, checked numerically on the CPU.
 
 1. The spot-diagram reduction bins r^2 in FP32 (dx = x - fl(cx), r2 =
    fma(dx, dx, fl(dy * dy)), f = fl(r2 * fl(scale))) and trusts the bin only
@@ -8,6 +8,9 @@
 2. The device photon source screens each hexagon candidate in FP32 and
    decides in FP64 only within 1e-5 a of the boundary; the FP32 hexagon
    measure must stay within 2e-6 a of the FP64 one.
+3. The FP64 nearest-hit search screens each aspheric candidate in FP32
+   before its FP64 test; a ray the screen excludes must have no hit in the
+   oracle's FP64 intersection of that surface.
 
 numpy float32 arithmetic rounds once per operation, as the device does; the
 fused multiply-add is emulated exactly (the product of two floats is exact in
@@ -87,3 +90,129 @@ def test_fp32_hexagon_screen_stays_within_its_band():
         sure_in = mf < a32 * float(F(1.0) - F(1e-5))
         sure_out = mf > a32 * float(F(1.0) + F(1e-5))
         assert np.all(m64[sure_in] <= a) and np.all(m64[sure_out] > a)
+
+
+def _aperture_near_sector(ap32, x, y, m):
+    """The FP64 search's aperture test with margin m for an annular sector (FP32 record values)."""
+    rmin, rmax, c0, s0, c1, s1 = ap32
+    r = np.sqrt((x * x + y * y).astype(F)).astype(F)
+    return (r >= rmin - m) & (r <= rmax + m) & ((c0 * y - s0 * x).astype(F) >= -m) & ((x * s1 - y * c1).astype(F) >= -m)
+
+
+def _screen_asph_may_hit(c, k1, rb2, adev, ap32, p, d, eps):
+    """The FP32 screen of an aspheric candidate (device `screen_asph_miss`), restated with one
+    FP32 rounding per operation: True where the candidate must go to the FP64 test."""
+    c, k1 = F(c), F(k1)
+    px, py, pz = (p[k].astype(F) for k in range(3))
+    dx, dy, dz = (d[k].astype(F) for k in range(3))
+    ac, ak = F(abs(c)), F(abs(k1))
+    mp = (np.abs(px) + np.abs(py) + np.abs(pz)).astype(F)
+    a = (c * (dx * dx + dy * dy + k1 * dz * dz)).astype(F)
+    b = (c * (px * dx + py * dy + k1 * pz * dz) - dz).astype(F)
+    g = (c * (px * px + py * py + k1 * pz * pz) - F(2) * pz).astype(F)
+    aa = (ac * (dx * dx + dy * dy + ak * dz * dz)).astype(F)
+    bb = (ac * (np.abs(px * dx) + np.abs(py * dy) + ak * np.abs(pz * dz)) + np.abs(dz)).astype(F)
+    gg = (ac * (px * px + py * py + ak * pz * pz) + F(2) * np.abs(pz)).astype(F)
+    may = np.zeros(px.shape, bool)
+    open_ = np.ones(px.shape, bool)  # not decided yet
+
+    def decide(mask, value):
+        nonlocal may, open_
+        mask = mask & open_
+        may[mask] = value[mask] if isinstance(value, np.ndarray) else value
+        open_ &= ~mask
+
+    decide(~(np.abs(a) > F(1e-2) * aa) | ~(np.abs(b) > F(1e-2) * bb) | ~(np.abs(g) > F(1e-2) * gg), True)
+    disc = (b * b - a * g).astype(F)
+    decide(~(np.abs(disc) > F(1e-2) * (b * b + np.abs(a * g))), True)
+    decide(disc < 0, False)
+    with np.errstate(all="ignore"):
+        sq = np.sqrt(np.maximum(disc, F(0))).astype(F)
+        qq = (-(b + np.copysign(sq, b))).astype(F)
+        t1, t2 = (qq / a).astype(F), (g / qq).astype(F)
+    tl, th = np.minimum(t1, t2), np.maximum(t1, t2)
+    decide(~((th - tl) > F(2e-3) * (np.abs(tl) + np.abs(th) + mp)), True)
+    ep = F(eps)
+    for t in (tl, th):
+        mt = (F(1e-3) * (np.abs(t) + mp)).astype(F)
+        qx, qy, qz = (px + t * dx).astype(F), (py + t * dy).astype(F), (pz + t * dz).astype(F)
+        v = (k1 * c * qz - F(1)).astype(F)
+        mv = (F(1e-2) + ac * ak * mt).astype(F)
+        skip = open_ & (v > mv)
+        decide(~skip & ~(v < -mv), True)
+        skip |= open_ & (t < ep - mt)
+        decide(~skip & ~(t > ep + mt), True)
+        here = open_ & ~skip  # the first qualifying root
+        eq = (mt + F(1e-3) * (np.abs(qx) + np.abs(qy))).astype(F)
+        r = np.sqrt(qx * qx + qy * qy).astype(F)
+        rb = F(math.sqrt(float(F(rb2))))
+        decide(here & (r > rb * F(1.001) + eq), False)
+        decide(here & ~(r < rb * F(0.999) - eq), True)
+        mx, my, mz = (-c * qx).astype(F), (-c * qy).astype(F), (F(1) - c * k1 * qz).astype(F)
+        nn = (mx * mx + my * my + mz * mz).astype(F)
+        dn = np.abs(dx * mx + dy * my + dz * mz).astype(F)
+        decide(here & ~(dn * dn > F(0.0025) * F(1.01) * nn), True)
+        with np.errstate(all="ignore"):
+            m = (F(2) * F(adev) * np.sqrt(nn) / dn + F(1e-4) * (np.abs(qx) + np.abs(qy) + np.abs(t))).astype(F)
+        decide(here, _aperture_near_sector(ap32, qx, qy, (F(1.001) * m + eq).astype(F)))
+    decide(np.ones(px.shape, bool), False)  # no qualifying root
+    return may
+
+
+def test_fp32_asphere_screen_never_rejects_a_hit():
+    """The FP64 search screens each aspheric candidate in FP32 first and skips the FP64 test
+    where the screen excludes a hit.  On rays aimed at and around an aspheric SC primary panel
+    (from above, obliquely, grazing, from below), every ray the screen excludes must have no hit
+    in the oracle's FP64 intersection of that panel (nor a Newton failure, which the FP64 test
+    reports), and the screen must exclude most rays that miss (it is not vacuous)."""
+    import oracle
+    import workloads as W
+    scene = W.sct_scene(seed=0)
+    L = scene.length_scale
+    eps = 1e-9 * L
+    rng = np.random.default_rng(17)
+    for idx in (2, 20):  # an inner-ring and an outer-ring primary panel (identity frame at the origin)
+        s = scene.surfaces[idx]
+        assert s.shape == "sag" and any(a != 0 for a in s.asph)
+        rmin, rmax, phi0, phi1 = s.ap[:4]
+        rb = 1.1 * rmax
+        rb2 = rb * rb
+        adev = sum(abs(s.asph[k]) * rb2 ** (k + 1) for k in range(8))
+        ap32 = tuple(F(v) for v in (rmin, rmax, math.cos(phi0), math.sin(phi0), math.cos(phi1), math.sin(phi1)))
+        n = 6000
+        rows = []
+        # from above towards points around the panel, some nearly parallel to the mirror
+        for zt_lo, zt_hi, z0_lo, z0_hi in ((0.0, 0.6, 4.0, 14.0), (0.0, 0.6, 0.3, 1.2), (-1.0, 1.0, -3.0, -0.5)):
+            tx = rng.uniform(-6.0, 6.0, n)
+            ty = rng.uniform(-6.0, 6.0, n)
+            tz = rng.uniform(zt_lo, zt_hi, n)
+            ox = rng.uniform(-8.0, 8.0, n)
+            oy = rng.uniform(-8.0, 8.0, n)
+            oz = rng.uniform(z0_lo, z0_hi, n)
+            dd = np.stack([tx - ox, ty - oy, tz - oz])
+            dd /= np.linalg.norm(dd, axis=0)
+            rows.append((np.stack([ox, oy, oz]), dd))
+        # aimed at the panel's sector and just beyond its edges, from above and obliquely
+        rr = rng.uniform(rmin - 0.2, rmax + 0.2, 2 * n)
+        ph = rng.uniform(phi0 - 0.1, phi1 + 0.1, 2 * n)
+        tgt = np.stack([rr * np.cos(ph), rr * np.sin(ph), rng.uniform(0.0, 0.6, 2 * n)])
+        org = tgt + np.stack([rng.uniform(-6.0, 6.0, 2 * n), rng.uniform(-6.0, 6.0, 2 * n),
+                              rng.uniform(0.5, 12.0, 2 * n)])
+        dd = tgt - org
+        dd /= np.linalg.norm(dd, axis=0)
+        rows.append((org, dd))
+        p = np.concatenate([r[0] for r in rows], axis=1)
+        d = np.concatenate([r[1] for r in rows], axis=1)
+        p32 = p.astype(F).astype(np.float64)
+        d32 = d.astype(F).astype(np.float64)
+        may = _screen_asph_may_hit(s.curv, 1.0 + s.conic, rb2, adev, ap32, p32, d32, eps)
+        def fp64_needed(i):  # a hit, or a Newton failure (which the FP64 test reports as ERROR)
+            try:
+                return oracle.intersect(s, p32[:, i], d32[:, i], eps) is not None
+            except ArithmeticError:
+                return True
+
+        hits = np.array([fp64_needed(i) for i in range(p.shape[1])])
+        assert not np.any(hits & ~may), f"panel {idx}: the screen excluded {int((hits & ~may).sum())} hits"
+        assert hits.sum() > 2000
+        assert (~may).sum() > 0.5 * (~hits).sum(), f"panel {idx}: the screen excluded only {int((~may).sum())} rays"
