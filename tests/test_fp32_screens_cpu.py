@@ -8,9 +8,10 @@
 2. The device photon source screens each hexagon candidate in FP32 and
    decides in FP64 only within 1e-5 a of the boundary; the FP32 hexagon
    measure must stay within 2e-6 a of the FP64 one.
-3. The FP64 nearest-hit search screens each aspheric candidate in FP32
-   before its FP64 test; a ray the screen excludes must have no hit in the
-   oracle's FP64 intersection of that surface.
+3. The FP64 nearest-hit search screens each sag candidate in FP32 (rebased
+   in FP32 from float pairs) before its FP64 test; a ray the screen excludes
+   must have no hit in the oracle's FP64 intersection of that surface, for
+   aspheric SC panels and for tilted dish facets far from the origin.
 
 numpy float32 arithmetic rounds once per operation, as the device does; the
 fused multiply-add is emulated exactly (the product of two floats is exact in
@@ -216,3 +217,98 @@ def test_fp32_asphere_screen_never_rejects_a_hit():
         assert not np.any(hits & ~may), f"panel {idx}: the screen excluded {int((hits & ~may).sum())} hits"
         assert hits.sum() > 2000
         assert (~may).sum() > 0.5 * (~hits).sum(), f"panel {idx}: the screen excluded only {int((~may).sum())} rays"
+
+
+def _rows_tilted(s):
+    """The facet's tilted frame rows, Ry(b)^T Rx(a)^T R (rows = local axes in world coordinates)."""
+    ca, sa = math.cos(s.tilt[0]), math.sin(s.tilt[0])
+    cb, sb = math.cos(s.tilt[1]), math.sin(s.tilt[1])
+    rxT = np.array([[1, 0, 0], [0, ca, sa], [0, -sa, ca]])
+    ryT = np.array([[cb, 0, -sb], [0, 1, 0], [sb, 0, cb]])
+    return ryT @ (rxT @ np.asarray(s.rot, np.float64).reshape(3, 3))
+
+
+def _rebase32(rows, origin, p, d):
+    """The FP64 search's FP32 rebase: the photon as a float pair minus the origin as a float pair,
+    then the FP32 rows; one FP32 rounding per operation."""
+    o = np.asarray(origin, np.float64)
+    ohi = o.astype(F)
+    olo = (o - ohi.astype(np.float64)).astype(F)
+    phi = p.astype(F)
+    plo = (p - phi.astype(np.float64)).astype(F)
+    q = ((phi - ohi[:, None]).astype(F) + (plo - olo[:, None]).astype(F)).astype(F)
+    R = rows.astype(F)
+    d32 = d.astype(F)
+
+    def rot(v):
+        return np.stack([((R[k, 0] * v[0]).astype(F) + (R[k, 1] * v[1]).astype(F) + (R[k, 2] * v[2]).astype(F))
+                         .astype(F) for k in range(3)])
+
+    return rot(q), rot(d32)
+
+
+def _screen_sag_may_hit(c, k1, apothem, p, d, eps):
+    """The FP32 screen of a sag candidate without asphere terms (device `screen_sag_miss`, no best
+    hit yet, hexagonal aperture), restated with one FP32 rounding per operation."""
+    c, k1 = F(c), F(k1)
+    px, py, pz = p
+    dx, dy, dz = d
+    ac, ak = F(abs(c)), F(abs(k1))
+    mp = (np.abs(px) + np.abs(py) + np.abs(pz)).astype(F)
+    a = (c * (dx * dx + dy * dy + k1 * dz * dz)).astype(F)
+    b = (c * (px * dx + py * dy + k1 * pz * dz) - dz).astype(F)
+    g = (c * (px * px + py * py + k1 * pz * pz) - F(2) * pz).astype(F)
+    aa = (ac * (dx * dx + dy * dy + ak * dz * dz)).astype(F)
+    bb = (ac * (np.abs(px * dx) + np.abs(py * dy) + ak * np.abs(pz * dz)) + np.abs(dz)).astype(F)
+    gg = (ac * (px * px + py * py + ak * pz * pz) + F(2) * np.abs(pz)).astype(F)
+    ill = ~(np.abs(a) > F(1e-2) * aa) | ~(np.abs(b) > F(1e-2) * bb) | ~(np.abs(g) > F(1e-2) * gg)
+    disc = (b * b - a * g).astype(F)
+    ill |= ~(np.abs(disc) > F(1e-2) * (b * b + np.abs(a * g)))
+    with np.errstate(all="ignore"):
+        sq = np.sqrt(np.maximum(disc, F(0))).astype(F)
+        qq = (-(b + np.copysign(sq, b))).astype(F)
+        roots = ((qq / a).astype(F), (g / qq).astype(F))
+    may = np.zeros(px.shape, bool)
+    s60 = F(0.86602540378443864676)
+    for t in roots:
+        mt = (F(1e-3) * (np.abs(t) + mp)).astype(F)
+        ok = (t > F(eps) - mt) & (t < F(3.0e38) + mt)
+        qx, qy, qz = (px + t * dx).astype(F), (py + t * dy).astype(F), (pz + t * dz).astype(F)
+        ok &= ~((k1 * c * qz - F(1)).astype(F) > F(1e-2) + ac * ak * mt)
+        h = np.maximum(np.abs(qx), np.maximum(np.abs(F(0.5) * qx + s60 * qy), np.abs(F(-0.5) * qx + s60 * qy)))
+        ok &= h <= F(apothem) + (mt + F(1e-3) * (np.abs(qx) + np.abs(qy))).astype(F)
+        may |= ok
+    return ill | (~(disc < 0) & may)
+
+
+def test_fp32_rebase_and_sag_screen_never_reject_a_hit():
+    """The FP64 search rebases each sag candidate in FP32 (photon and origin as float pairs, FP32
+    frame rows) and screens it before any FP64 instruction.  On dish facets far from the origin,
+    with tilted frames, rays coming down from the source plane and going up from the dish must
+    never be excluded where the oracle's FP64 intersection hits, and most misses must be."""
+    import oracle
+    import workloads as W
+    scene = W.lst_scene(seed=0)
+    eps = 1e-9 * scene.length_scale
+    rng = np.random.default_rng(23)
+    facets = [s for s in scene.surfaces if s.shape == "sag" and s.role == "mirror"]
+    for s in (facets[0], facets[97], facets[-1]):
+        c = np.asarray(s.origin)
+        n = 8000
+        # down from the source plane towards points within 3 m of the facet centre
+        tgt = c[:, None] + np.stack([rng.uniform(-3, 3, n), rng.uniform(-3, 3, n), rng.uniform(-0.3, 0.3, n)])
+        org = np.stack([tgt[0] + rng.uniform(-1, 1, n), tgt[1] + rng.uniform(-1, 1, n), np.full(n, 32.0)])
+        # up from points near the facet towards the focal plane
+        org2 = c[:, None] + np.stack([rng.uniform(-2, 2, n), rng.uniform(-2, 2, n), rng.uniform(-0.2, 0.5, n)])
+        tgt2 = np.stack([rng.uniform(-1.5, 1.5, n), rng.uniform(-1.5, 1.5, n), np.full(n, 28.0)])
+        p = np.concatenate([org, org2], axis=1)
+        d = np.concatenate([tgt - org, tgt2 - org2], axis=1)
+        d /= np.linalg.norm(d, axis=0)
+        p32 = p.astype(F).astype(np.float64)
+        d32 = d.astype(F).astype(np.float64)
+        pl, dl = _rebase32(_rows_tilted(s), s.origin, p32, d32)
+        may = _screen_sag_may_hit(s.curv, 1.0 + s.conic, s.ap[0], pl, dl, eps)
+        hits = np.array([oracle.intersect(s, p32[:, i], d32[:, i], eps) is not None for i in range(p.shape[1])])
+        assert not np.any(hits & ~may), f"the screen excluded {int((hits & ~may).sum())} hits"
+        assert hits.sum() > 500
+        assert (~may).sum() > 0.5 * (~hits).sum()
