@@ -597,7 +597,7 @@ def measure_grad(args, dev, stream, ws, rank, max_over_ranks, barrier):
     def evaluate():
         g.zero_()
         return robast.trace_grad(geom, o, d, w, objective="msr", precision=32, seed=0, variant_of_photon=v,
-                                 stream=stream, out=g)
+                                 stream=stream, out=g, coherent_order=args.grad_order)
 
     for _ in range(2):
         evaluate()
@@ -710,6 +710,9 @@ def main():
                     help="block,blocks_per_sm,refill_min for the batched trace instead of the tuner (profiler runs)")
     ap.add_argument("--grad-photons-per-dish", type=int, default=1_000_000)
     ap.add_argument("--grad-steps", type=int, default=3)
+    ap.add_argument("--grad-order", type=int, default=0, choices=[-1, 0, 1],
+                    help="processing order of the dish-batch gradient (profiler runs): 0 the library default, "
+                         "1 coherent (origin cell), -1 photon id")
     ap.add_argument("--grad-cone-photons", type=int, default=1_000_000)
     ap.add_argument("--batch-photons-per-group", type=int, default=2_000_000)
     ap.add_argument("--batch-steps", type=int, default=1)
