@@ -434,9 +434,8 @@ int robast_param_layout(const robast_geom* g, robast_param_info* out);
  * calls give identical bits, in any processing order (opts->coherent_order:
  * 1 sorts the photons by origin cell first, scratch from g's pool; the
  * default 0 does so only for geometries with HEXCONE surfaces and n >= 65536,
- * since on mirror batches neighbouring photons share a facet and contend for
- * its sums; -1 never).  info (HOST, 8 doubles, may be NULL; totals
- * over variants): W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid,
+ * where it was measured faster; -1 never).  info (HOST, 8 doubles, may be
+ * NULL; totals over variants): W, sum w q_x, sum w q_y, sum w |q|^2, sum w sigmoid,
  * N_detected, untracked photons (no gradient: a path of more than 64
  * interactions, or a recomputation that no longer met its surface), N
  * (photons with an invalid variant index are skipped).  Synchronises the

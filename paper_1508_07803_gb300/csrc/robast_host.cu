@@ -1495,11 +1495,10 @@ static int do_grad(robast_geom* g, const void* o, const void* d, const void* wl,
     if (bps <= 0) return fail(ROBAST_E_CUDA, "robast_trace_grad: the gradient kernel cannot launch with %zu bytes of shared memory", smem);
     const long long grid = std::max(1LL, std::min<long long>((long long)g->num_sms * bps, (n + 127) / 128));
     // coherent processing order (stream-ordered scratch from g's pool).  By default only for
-    // geometries with cones: there a path's wall reflections diverge most, and every photon adds
-    // to the one cone's six slots in either order (soft-CE gradient 248 -> 142 ms per 1e6
-    // photons); on a dish batch, neighbouring photons share a facet, so a warp's 128-bit atomics
-    // land on the same words (MSR gradient 144 -> 213 ms per 3.2e7 photons), and id order, which
-    // spreads them over the facets, stays the default
+    // geometries with cones, where a path's wall reflections diverge most (soft-CE gradient
+    // 248 -> 142 ms per 1e6 photons).  On a dish batch the coherent order raises the active lanes
+    // but the kernel then waits far longer on instruction fetch (its code and spilled frames;
+    // MSR gradient 144 -> 213 ms per 3.2e7 photons), so id order stays the default there
     void* ord_scratch = nullptr;
     const bool want_order = op.coherent_order > 0 || (op.coherent_order == 0 && n >= 65536 && (g->feat & FT_CONE) != 0);
     if (n > 0 && n < (1LL << 31) && want_order) {
