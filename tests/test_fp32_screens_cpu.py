@@ -11,7 +11,8 @@
 3. The FP64 nearest-hit search screens each sag candidate in FP32 (rebased
    in FP32 from float pairs) before its FP64 test; a ray the screen excludes
    must have no hit in the oracle's FP64 intersection of that surface, for
-   aspheric SC panels and for tilted dish facets far from the origin.
+   aspheric SC panels and for tilted dish facets far from the origin; the
+   same for the cylinder screen on the dish's slanted masts.
 
 numpy float32 arithmetic rounds once per operation, as the device does; the
 fused multiply-add is emulated exactly (the product of two floats is exact in
@@ -311,4 +312,60 @@ def test_fp32_rebase_and_sag_screen_never_reject_a_hit():
         hits = np.array([oracle.intersect(s, p32[:, i], d32[:, i], eps) is not None for i in range(p.shape[1])])
         assert not np.any(hits & ~may), f"the screen excluded {int((hits & ~may).sum())} hits"
         assert hits.sum() > 500
+        assert (~may).sum() > 0.5 * (~hits).sum()
+
+
+def _screen_cyl_may_hit(rad, length, p, d, eps):
+    """The FP32 screen of a cylinder candidate (device `screen_cyl_miss`, no best hit yet),
+    restated with one FP32 rounding per operation."""
+    rad, length = F(rad), F(length)
+    px, py, pz = p
+    dx, dy, dz = d
+    a = (dx * dx + dy * dy).astype(F)
+    near_axis = ~(a >= F(1e-2) * (a + dz * dz))
+    with np.errstate(all="ignore"):
+        t0 = (-(px * dx + py * dy) / a).astype(F)
+        cx, cy = (px + t0 * dx).astype(F), (py + t0 * dy).astype(F)
+        m = (F(1e-3) * (np.abs(px) + np.abs(py) + np.abs(pz) + np.abs(t0))).astype(F)
+        dist = np.sqrt(cx * cx + cy * cy).astype(F)
+        H = ((rad + m) / np.sqrt(a)).astype(F)
+    tlo, thi = (t0 - H).astype(F), (t0 + H).astype(F)
+    mt = (m + F(1e-3) * H).astype(F)
+    z0, z1 = (pz + tlo * dz).astype(F), (pz + thi * dz).astype(F)
+    miss = (dist > rad + m) | (thi < F(eps) - mt) | (tlo > F(3.0e38) + mt) | \
+           (np.maximum(z0, z1) < -mt) | (np.minimum(z0, z1) > length + mt)
+    return near_axis | ~miss
+
+
+def test_fp32_rebase_and_cylinder_screen_never_reject_a_hit():
+    """The same for the dish's slanted masts (cylinders in tilted frames from the rim to the
+    camera box): rays from the source plane and from the dish must never be excluded where the
+    oracle's FP64 intersection hits, and most misses must be."""
+    import oracle
+    import workloads as W
+    scene = W.lst_scene(seed=0)
+    eps = 1e-9 * scene.length_scale
+    rng = np.random.default_rng(29)
+    masts = [s for s in scene.surfaces if s.shape == "cylinder"]
+    assert len(masts) == 4
+    for s in masts[:2]:
+        o = np.asarray(s.origin)
+        axis = _rows_tilted(s)[2]
+        n = 8000
+        # targets along the mast and up to 0.5 m off it
+        tt = rng.uniform(-1.0, s.prm[1] + 1.0, n)
+        tgt = o[:, None] + axis[:, None] * tt + rng.uniform(-0.5, 0.5, (3, n))
+        org = np.concatenate([np.stack([tgt[0, :n // 2] + rng.uniform(-2, 2, n // 2),
+                                        tgt[1, :n // 2] + rng.uniform(-2, 2, n // 2), np.full(n // 2, 32.0)]),
+                              np.stack([rng.uniform(-11, 11, n - n // 2), rng.uniform(-11, 11, n - n // 2),
+                                        rng.uniform(0.0, 1.2, n - n // 2)])], axis=1)
+        d = tgt - org
+        d /= np.linalg.norm(d, axis=0)
+        p32 = org.astype(F).astype(np.float64)
+        d32 = d.astype(F).astype(np.float64)
+        pl, dl = _rebase32(_rows_tilted(s), s.origin, p32, d32)
+        may = _screen_cyl_may_hit(s.prm[0], s.prm[1], pl, dl, eps)
+        hits = np.array([oracle.intersect(s, p32[:, i], d32[:, i], eps) is not None for i in range(n)])
+        assert not np.any(hits & ~may), f"the screen excluded {int((hits & ~may).sum())} hits"
+        assert hits.sum() > 300
         assert (~may).sum() > 0.5 * (~hits).sum()
